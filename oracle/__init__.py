@@ -1,0 +1,221 @@
+"""FP64 CPU oracle of APR-native convolution (arXiv 2112.03592) -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may import this
+package. The product (paper_2112_03592_gb300 and its CUDA library) never imports it, and this
+package never imports the product: the two share no code. The only shared module is `aprsynth`,
+which makes seeded inputs and holds none of the method's arithmetic.
+
+Contents
+  apr_oracle.c     the plain FP64 definition: APR tree (Sec. 3.4), isotropic patch values
+                   (Sec. 3.5), APR convolution (Sec. 4.1), its transpose, and the coarse-fill
+                   property the convolution relies on (Sec. 5.1 footnote).
+  restrict_stencil the restricted stencils w_l of Eq. (restrict_stenc), K_{w_l} = R_l K_w P_l,
+                   formed from explicit 1-D restriction / prolongation / shift matrices.
+
+Every function is pinned by tests/test_oracle_*.py against brute force, closed forms, library
+routines (scipy.ndimage) and hand-derived values under tests/golden/.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import pathlib
+import subprocess
+
+import numpy as np
+
+_HERE = pathlib.Path(__file__).resolve().parent
+_SO = _HERE / "_build" / "liboracle.so"
+_lib = None
+
+
+def build(force: bool = False) -> pathlib.Path:
+    """Compile apr_oracle.c with the host C compiler (portable flags only)."""
+    src = _HERE / "apr_oracle.c"
+    if force or not _SO.exists() or _SO.stat().st_mtime < src.stat().st_mtime:
+        _SO.parent.mkdir(parents=True, exist_ok=True)
+        tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", str(tmp), str(src), "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(str(_SO))
+        P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        lib.ora_create.restype = P
+        lib.ora_create.argtypes = [I32, I32, P, P, P, I64, P, I32]
+        lib.ora_destroy.argtypes = [P]
+        lib.ora_num_tree.restype = I64
+        lib.ora_num_tree.argtypes = [P]
+        lib.ora_error.restype = I32
+        lib.ora_error.argtypes = [P]
+        lib.ora_tree_coords.argtypes = [P, P]
+        lib.ora_tree_layout.argtypes = [P, P, P]
+        lib.ora_tree_fill.restype = I32
+        lib.ora_tree_fill.argtypes = [P]
+        lib.ora_get_tree.argtypes = [P, D]
+        lib.ora_set_values.argtypes = [P, D]
+        lib.ora_conv.restype = I32
+        lib.ora_conv.argtypes = [P, D, I32, I32, I32, P, I64, D]
+        lib.ora_conv_backward.restype = I32
+        lib.ora_conv_backward.argtypes = [P, D, I32, I32, I32, D, D, D]
+        lib.ora_check_coarse_fill.restype = I64
+        lib.ora_check_coarse_fill.argtypes = [P, I32]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+BC_REFLECT, BC_ZERO = 0, 1
+
+
+class Oracle:
+    """The oracle's view of one APR: its own index, its own tree, FP64 values [N][C]."""
+
+    def __init__(self, apr, values=None):
+        lib = _load()
+        self.apr = apr
+        vals = apr.values if values is None else values
+        vals = np.ascontiguousarray(np.asarray(vals, dtype=np.float64))
+        if vals.ndim == 1:
+            vals = vals[:, None]
+        self.C = vals.shape[1]
+        self._keep = [np.ascontiguousarray(np.asarray(apr.dims, np.int64)),
+                      np.ascontiguousarray(apr.row_ptr.astype(np.int64)),
+                      np.ascontiguousarray(apr.y_idx.astype(np.int32))]
+        self.h = lib.ora_create(apr.l_min, apr.l_max, _ptr(self._keep[0]), _ptr(self._keep[1]),
+                                _ptr(self._keep[2]), apr.n_particles, _ptr(vals), self.C)
+        if not self.h:
+            raise ValueError("oracle: bad arguments")
+        self.n_tree = int(lib.ora_num_tree(self.h))
+        self._filled = False
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ora_destroy(self.h)
+            self.h = None
+
+    @property
+    def error(self) -> int:
+        return int(_load().ora_error(self.h))
+
+    # ---- structure
+    def tree_coords(self) -> np.ndarray:
+        out = np.zeros((self.n_tree, 4), np.int32)
+        _load().ora_tree_coords(self.h, _ptr(out))
+        return out
+
+    def tree_layout(self):
+        """(row_ptr int64 [R_t+1], y_idx int32 [N_t]) of the tree, rows of levels l_min..l_max-1."""
+        a = self.apr
+        rows = sum(a.level_dims(l)[0] * a.level_dims(l)[1] for l in range(a.l_min, a.l_max))
+        rp = np.zeros(rows + 1, np.int64)
+        yi = np.zeros(max(self.n_tree, 1), np.int32)
+        _load().ora_tree_layout(self.h, _ptr(rp), _ptr(yi))
+        return rp, yi[:self.n_tree]
+
+    # ---- values
+    def set_values(self, values):
+        v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(self.apr.n_particles, self.C))
+        _load().ora_set_values(self.h, _ptr(v))
+        self._filled = False
+
+    def tree(self) -> np.ndarray:
+        """Tree values [N_t][C] (Sec. 3.4: average of children, finest level first)."""
+        lib = _load()
+        if not self._filled:
+            rc = lib.ora_tree_fill(self.h)
+            if rc:
+                raise ValueError(f"oracle: invalid APR (tree fill error {rc})")
+            self._filled = True
+        out = np.zeros((max(self.n_tree, 1), self.C), np.float64)
+        lib.ora_get_tree(self.h, _ptr(out))
+        return out[:self.n_tree]
+
+    def _stencils(self, stencils, k, C_out):
+        L = self.apr.n_levels
+        W = np.ascontiguousarray(np.asarray(stencils, np.float64).reshape(L, C_out, self.C, k ** 3))
+        return W
+
+    def conv(self, stencils, k, bc=BC_REFLECT, sample=None, C_out=1) -> np.ndarray:
+        """APR convolution outputs [ns][C_out] (Sec. 4.1) for `sample` particle ids (all if None)."""
+        self.tree()
+        W = self._stencils(stencils, k, C_out)
+        if sample is None:
+            ns, sp = self.apr.n_particles, None
+        else:
+            s = np.ascontiguousarray(np.asarray(sample, np.int64))
+            ns, sp = s.size, s
+        out = np.zeros((max(ns, 1), C_out), np.float64)
+        rc = _load().ora_conv(self.h, _ptr(W), k, C_out, bc, _ptr(sp) if sp is not None else None, ns, _ptr(out))
+        if rc:
+            raise ValueError(f"oracle: stencil tap without a source (code {rc})")
+        return out[:ns]
+
+    def conv_backward(self, stencils, k, grad_out, bc=BC_REFLECT, C_out=1):
+        """(dL/d particles [N][C], dL/d stencils [L][C_out][C][k^3]) for dL/d out = grad_out."""
+        self.tree()
+        W = self._stencils(stencils, k, C_out)
+        G = np.ascontiguousarray(np.asarray(grad_out, np.float64).reshape(self.apr.n_particles, C_out))
+        gp = np.zeros((max(self.apr.n_particles, 1), self.C), np.float64)
+        gw = np.zeros(W.shape, np.float64)
+        rc = _load().ora_conv_backward(self.h, _ptr(W), k, C_out, bc, _ptr(G), _ptr(gp), _ptr(gw))
+        if rc:
+            raise ValueError(f"oracle: invalid APR in backward (code {rc})")
+        return gp[:self.apr.n_particles], gw
+
+    def check_coarse_fill(self, r: int) -> int:
+        return int(_load().ora_check_coarse_fill(self.h, r))
+
+
+# --------------------------------------------------------------------------------------------
+# restricted stencils, Eq. (restrict_stenc): K_{w_l} u_l = R_l K_w P_l u_l
+# --------------------------------------------------------------------------------------------
+def _shift_restrict_1d(s: int, d: int, n_c: int) -> np.ndarray:
+    """(R S_d P) for a 1-D grid of n_c coarse cells of s fine cells each.
+
+    P (n_f x n_c): piecewise-constant prolongation, P[i, j] = [i // s == j].
+    S_d (n_f x n_f): shift, (S_d u)[i] = u[i + d] (zero outside).
+    R (n_c x n_f): block average, R = P^T / s.
+    """
+    n_f = n_c * s
+    P = np.zeros((n_f, n_c))
+    P[np.arange(n_f), np.arange(n_f) // s] = 1.0
+    SP = np.zeros_like(P)
+    src = np.arange(n_f) + d
+    ok = (src >= 0) & (src < n_f)
+    SP[ok] = P[src[ok]]
+    R = P.T / s
+    return R @ SP
+
+
+def restrict_stencil(w: np.ndarray, l_max: int, l_min: int) -> np.ndarray:
+    """Per-level stencils [L][k][k][k] (level l_min first) with w_l = R_l K_w P_l (FP64).
+
+    K_w = sum_d w[d] S_dz (x) S_dx (x) S_dy, and R, P act per axis, so
+    R K_w P = sum_d w[d] (R S_dz P) (x) (R S_dx P) (x) (R S_dy P); the coarse stencil is the row of
+    this Toeplitz operator at an interior coarse cell. Each 1-D factor is formed as an explicit
+    matrix product on a small grid (no closed form is used).
+    """
+    w = np.asarray(w, np.float64)
+    k = w.shape[0]
+    r = k // 2
+    out = np.zeros((l_max - l_min + 1, k, k, k))
+    n_c = 2 * r + 3
+    i0 = n_c // 2
+    for l in range(l_min, l_max + 1):
+        s = 1 << (l_max - l)
+        row = np.zeros((k, k))  # row[d + r, e + r] = (R S_d P)[i0, i0 + e]
+        for d in range(-r, r + 1):
+            M = _shift_restrict_1d(s, d, n_c)
+            for e in range(-r, r + 1):
+                row[d + r, e + r] = M[i0, i0 + e]
+        out[l - l_min] = np.einsum("abc,ai,bj,ck->ijk", w, row, row, row)
+    return out
