@@ -29,7 +29,7 @@ def test_generator_is_deterministic():
 
 def test_uniform_and_hand_built():
     a = S.uniform_level_apr((8, 8, 8), 2)
-    assert a.n_particles == 8 and a.l_max == 3
+    assert a.n_particles == 64 and a.l_max == 3
     S.validate_apr(a)
     b = S.apr_from_particles((2, 2, 2), 1, [(1, z, x, y, 1.0) for z in range(2) for x in range(2) for y in range(2)])
     assert b.n_particles == 8
