@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: APR-native convolution hot path on the 1024x1024x512-pixel blob APR (~8M particles).
+
+One step = APR tree restriction (Sec. 3.4) + APR convolution with the per-level restricted 5^3
+Gaussian stencils (Sec. 4.1-4.2) + its backward (gradients w.r.t. particle values, through the tree,
+and w.r.t. the stencils). The index and the work lists are built once (apr_build_device) and reused,
+as the paper allows for repeated convolutions (Sec. 6.1.2). Inputs are synthetic (seeded blob
+image, Poisson noise). The data set (~0.1 GB) is smaller than L2, so L2 is flushed (a 512 MB write)
+before every timed step, outside the step's own timing events.
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle on a bounded sample instead.
+Multi-GPU: the path has no exchange step here, so N ranks run N independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "blob1024"
+K = 5
+SIGMA = 1.5
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(apr, lay, k):
+    """Bytes the method must move (no index overhead, no re-reads), per SURVEY-style accounting:
+    conv forward  = N_p (4 in + 2 y + 4 out) + N_t (4 + 2) + (R_p + R_t) 4 + stencils
+    tree restrict = N_p (4 + 2) + N_t (4 write + 2) + (R_p + R_t) 4   (tree read-back of finer levels ~ N_t 4)
+    """
+    Np, Nt = apr.n_particles, lay.n_tree
+    Rp = int(apr.row_ptr.size - 1)
+    Rt = sum(apr.level_dims(l)[0] * apr.level_dims(l)[1] for l in range(apr.l_min, apr.l_max))
+    st = apr.n_levels * k ** 3 * 4
+    conv = Np * 10 + Nt * 6 + (Rp + Rt) * 4 + st
+    restrict = Np * 6 + Nt * 10 + (Rp + Rt) * 4
+    return conv, restrict
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    apr = S.make_config(WORKLOAD)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
+    st_h = G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
+    Np = apr.n_particles
+    st = torch.as_tensor(st_h, device=dev)
+    vals = torch.as_tensor(apr.values, device=dev)
+    gout = torch.as_tensor(np.random.default_rng(0).normal(size=Np).astype(np.float32), device=dev)
+    tree = torch.empty(lay.n_tree, device=dev)
+    out = torch.empty(Np, device=dev)
+    gp = torch.empty(Np, device=dev)
+    gw = torch.empty((apr.n_levels, K ** 3), device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        G.apr_tree_restrict(lay, vals, tree)
+        G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
+        G.apr_convolve_backward(lay, vals, tree, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            e = ev[i]
+            e[0].record(stream)
+            G.apr_tree_restrict(lay, vals, tree)
+            e[1].record(stream)
+            G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
+            e[2].record(stream)
+            G.apr_convolve_backward(lay, vals, tree, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
+            e[3].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    lay.sync_status()
+    t_restrict = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_conv = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    t_bwd = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
+    step_ms = sum(t_restrict[i] + t_conv[i] + t_bwd[i] for i in range(args.steps)) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # end to end through the public API with host buffers: H2D of the step's inputs (values,
+    # upstream gradient), the step, D2H of its results (outputs, both gradients)
+    h_vals = torch.as_tensor(apr.values).pin_memory()
+    h_gout = gout.cpu().pin_memory()
+    h_out = torch.empty(Np).pin_memory()
+    h_gp = torch.empty(Np).pin_memory()
+    h_gw = torch.empty_like(gw, device="cpu").pin_memory()
+    d_vals = torch.empty_like(vals)
+    d_gout = torch.empty_like(gout)
+
+    def e2e_step():
+        d_vals.copy_(h_vals, non_blocking=True)
+        d_gout.copy_(h_gout, non_blocking=True)
+        G.apr_tree_restrict(lay, d_vals, tree)
+        G.apr_convolve(lay, d_vals, tree, st, K, G.APR_BC_REFLECT, out)
+        G.apr_convolve_backward(lay, d_vals, tree, st, K, d_gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
+        h_out.copy_(out, non_blocking=True)
+        h_gp.copy_(gp, non_blocking=True)
+        h_gw.copy_(gw, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # forward-only pipeline (tree restriction + convolution), the paper's timed pipeline
+    fwd_ms = (sum(t_restrict) + sum(t_conv)) / args.steps
+    conv_ms = sum(t_conv) / args.steps
+    conv_bytes, restrict_bytes = algorithmic_bytes(apr, lay, K)
+    peaks, src = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    pix_bytes = float(np.prod(apr.dims)) * 4.0
+    # our kernels per step: restriction (one per level holding tree nodes), convolution, backward
+    # data part, push-down (one per level holding tree nodes), stencil-gradient partials, reduction
+    n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
+    launches_per_step = n_tree_levels + 1 + (1 + n_tree_levels + 2)
+    clocks = clk.summary()
+    rec = {
+        "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
+        "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4),
+        "unit": "Gparticles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded 2000-blob image with Poisson noise -> APR)",
+        "config": {"workload": "blob APR 1024x1024x512 pixels (z=512), 5^3 Gaussian sigma=1.5, restricted per-level stencils",
+                   "model": None, "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
+                   "computational_ratio": round(float(np.prod(apr.dims)) / Np, 2),
+                   "step": "tree restrict + convolve + convolve_backward (data + stencil grads)",
+                   "l2": "flushed before every step (512 MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "pixel_equiv_GBps": round(world * pix_bytes / (step_ms * 1e-3) / 1e9, 2),
+        "forward_pipeline": {"ms": round(fwd_ms, 5),
+                             "Gparticles_per_s": round(Np / (fwd_ms * 1e-3) / 1e9, 3),
+                             "pixel_equiv_GBps": round(pix_bytes / (fwd_ms * 1e-3) / 1e9, 2),
+                             "restrict_ms": round(sum(t_restrict) / args.steps, 5),
+                             "conv_ms": round(conv_ms, 5),
+                             "backward_ms": round(sum(t_bwd) / args.steps, 5),
+                             "paper_context": "up to 1 TB/s pixel-equivalent on one RTX 2080 Max-Q (P:51)"},
+        "roofline": {"kernel": "conv_fwd_kernel<2>", "bound": "hbm",
+                     "achieved": round(conv_bytes / (conv_ms * 1e-3) / 1e9, 2), "peak": hbm,
+                     "unit": "GB/s", "frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4),
+                     "traffic": None, "peak_source": src,
+                     "algorithmic_bytes_per_launch": conv_bytes},
+        "e2e": {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
+                "h2d_bytes_per_step": int(h_vals.numel() * 4 + h_gout.numel() * 4),
+                "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),
+                "ms_per_step": round(e2e, 4)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": round(wall, 4),
+        "layout_bytes": lay.layout_bytes(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(apr, st_h, gout.cpu().numpy(), budget_s=args.cpu_budget)
+    return rec
+
+
+def cpu_baseline(apr, st, gout, budget_s=20.0, sample_n=None):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample of the same step: the full
+    tree fill, then forward and backward for a random sample of output particles. The tree fill
+    time is scaled by sample/N (it is linear in N) so the rate is per particle of the whole step."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(apr)
+    t0 = time.perf_counter()
+    o.tree()
+    t_fill = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    n = sample_n or 2000
+    W = st.astype(np.float64)
+    t0 = time.perf_counter()
+    s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+    o.conv(W, K, sample=s)
+    o.conv_backward(W, K, gout.astype(np.float64), sample=s)
+    t_probe = time.perf_counter() - t0
+    # size the real sample to the time budget
+    n2 = int(min(apr.n_particles, max(n, n * (budget_s - t_fill) / max(t_probe, 1e-6) * 0.8)))
+    s = np.sort(rng.choice(apr.n_particles, n2, replace=False))
+    t0 = time.perf_counter()
+    o.conv(W, K, sample=s)
+    o.conv_backward(W, K, gout.astype(np.float64), sample=s)
+    t_s = time.perf_counter() - t0
+    t_per = t_fill / apr.n_particles + t_s / n2
+    return {"value": round(1.0 / t_per / 1e9, 9), "unit": "Gparticles/s", "cores": 1, "kind": "oracle",
+            "sample": f"full tree fill ({t_fill:.2f} s, scaled by sample/N) + forward and backward of "
+                      f"{n2} random output particles of the same APR ({t_s:.2f} s), FP64, 1 thread"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is a bounded sample of the workload."""
+    import numpy as np
+
+    import aprsynth as S
+    import oracle
+    apr = S.make_config(WORKLOAD)
+    w = S.gaussian_stencil(K, SIGMA)
+    st = oracle.restrict_stencil(w.astype(np.float32).astype(np.float64), apr.l_max, apr.l_min).reshape(apr.n_levels, -1)
+    gout = np.random.default_rng(0).normal(size=apr.n_particles)
+    o = oracle.Oracle(apr)
+    rng = np.random.default_rng(1)
+    n = args.ref_sample
+    t_fill, t_samp = [], []
+    for i in range(args.warmup + args.steps):
+        s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+        t0 = time.perf_counter()
+        o.set_values(apr.values)
+        o.tree()
+        t1 = time.perf_counter()
+        o.conv(st, K, sample=s)
+        o.conv_backward(st, K, gout, sample=s)
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            t_fill.append(t1 - t0)
+            t_samp.append(t2 - t1)
+    # per particle of the whole step: the tree fill is linear in N, the rest is per output particle
+    per = statistics.mean(t_fill) / apr.n_particles + statistics.mean(t_samp) / n
+    ms = 1e3 * (statistics.mean(t_fill) + statistics.mean(t_samp))
+    val = 1.0 / per / 1e9
+    return {"metric": "APR conv Gparticles/s & pixel-equiv GB/s", "value": round(val, 9), "unit": "Gparticles/s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded 2000-blob image with Poisson noise -> APR)",
+            "config": {"workload": "blob APR 1024x1024x512 pixels (z=512), 5^3 Gaussian sigma=1.5, restricted per-level stencils",
+                       "step": f"oracle: full tree fill + forward and backward of {n} random output particles; "
+                               "rate per particle = 1 / (fill time / N_p + sample time / sample size)"},
+            "cpu_baseline": {"value": round(val, 9), "unit": "Gparticles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} random output particles per step (plus the full tree fill)"},
+            "e2e": {"value": round(val, 9), "unit": "Gparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-sample", type=int, default=3000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    rec = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(rec))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * apr.h -- C ABI of the GB300 (sm_103a) library for discrete convolution evaluated natively on an
+ * Adaptive Particle Representation (APR) of a 3-D image.
+ *
+ * Method: Jonsson, Cheeseman, Maddu, Gonciarz, Sbalzarini, "Parallel Discrete Convolutions on
+ * Adaptive Particle Representations of Images" (arXiv 2112.03592). Section numbers below refer to it.
+ *
+ * Conventions shared by every call
+ *   - Every call returns apr_status_t; nothing aborts or exits. apr_status_string() names a code.
+ *   - Image axes are (z, x, y); y is the contiguous, sparsely stored axis (Sec. 3.1 footnote).
+ *     l_max = ceil(log2(max(D_z, D_x, D_y))); level l has a grid of ceil(D / 2^(l_max-l)) cells
+ *     per axis (Eq. 2, cells of edge 2^(l_max-l) pixels).
+ *   - Particles are ordered l -> z -> x -> y (Alg. 2). Tree nodes (the APR tree, Sec. 3.4: every
+ *     strict ancestor of a particle cell) use the same order over levels l_min .. l_max-1.
+ *   - Value, output, gradient and stencil buffers are CALLER-OWNED DEVICE pointers (float32 unless
+ *     stated), never freed or retained by the library. The opaque handle owns only the index
+ *     structure it allocated in apr_build_device.
+ *   - Work is enqueued asynchronously on the given stream (NULL = the legacy default stream); the
+ *     caller synchronises. Launch failures return APR_ERR_CUDA. Device-side checks record into an
+ *     error word read by apr_sync_status().
+ *   - Not thread-safe per handle: calls on one handle must not run concurrently on different
+ *     streams when they share output buffers or the handle's scratch.
+ */
+#ifndef APR_H
+#define APR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    APR_OK = 0,
+    APR_ERR_INVALID_ARG = 1,    /* NULL pointer, bad size, unknown flag or enum */
+    APR_ERR_INVALID_LAYOUT = 2, /* the index arrays do not describe a (balanced) APR */
+    APR_ERR_UNSUPPORTED = 3,    /* e.g. stencil size not 3 or 5, channel count not supported */
+    APR_ERR_OOM = 4,            /* device or host allocation failed */
+    APR_ERR_CUDA = 5,           /* a CUDA runtime call or kernel launch failed */
+    APR_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    APR_ERR_DEVICE = 7          /* a device-side check recorded an error (see apr_sync_status) */
+} apr_status_t;
+
+/* Same underlying type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *apr_stream_t;
+
+typedef struct apr_handle_s *apr_handle_t;
+
+/* Host description of an APR in the linear-access layout of Alg. 1 (LinearAccess).
+ *   row_ptr: [R+1] int64, host memory. Rows are (l, z, x) for l = l_min..l_max, z, x in level grid
+ *            order; row r holds particles row_ptr[r] .. row_ptr[r+1]-1 (CSR form of xz_end).
+ *   y_idx:   [n_particles] int32, host memory, strictly increasing inside each row, < grid y size.
+ * The library copies what it needs; the caller keeps ownership of both arrays. */
+typedef struct {
+    int32_t l_min;
+    int32_t l_max;
+    int64_t dims[3];          /* D_z, D_x, D_y in pixels, each >= 1 and <= 65536 */
+    const int64_t *row_ptr;
+    const int32_t *y_idx;
+    int64_t n_particles;      /* < 2^31 */
+} apr_host_layout;
+
+/* apr_build_device flags */
+#define APR_VALIDATE 1u          /* check that the particle cells partition the image exactly */
+#define APR_REQUIRE_BALANCE 2u   /* check the 2:1 balance the 5^3 convolution relies on */
+#define APR_HOST_ONLY 4u         /* build the index on the host only (no device memory): for
+                                    inspecting the structure on machines without a GPU */
+
+/* Boundary modes of the convolution (the paper pads without naming a rule, Sec. 5.1) */
+#define APR_BC_REFLECT 0         /* half-sample symmetric reflection at each level's grid */
+#define APR_BC_ZERO 1            /* taps outside the level grid contribute zero */
+
+/* apr_export_structure selectors (copy to host memory) */
+#define APR_STRUCT_ROW_PTR 0       /* uint32 [R+1]    particle rows (CSR) */
+#define APR_STRUCT_Y_IDX 1         /* uint16 [N_p]    particle y */
+#define APR_STRUCT_TREE_ROW_PTR 2  /* uint32 [R_t+1]  tree rows, levels l_min..l_max-1 */
+#define APR_STRUCT_TREE_Y_IDX 3    /* uint16 [N_t]    tree node y */
+#define APR_STRUCT_FWD_ITEMS 4     /* int32 [n][4]    convolution work items (l, tz, tx, yb) */
+#define APR_STRUCT_TREE_ITEMS 5    /* int32 [n][4]    tree work items (l, z, x, yb) */
+
+/* Build the device-resident index of an APR (Sec. 3.1 LinearAccess for the particles, Sec. 3.4
+ * APR tree structure, and the list of non-empty tiles the kernels are launched on, Sec. 5.2 last
+ * paragraph). The tree structure (which nodes exist) is derived from the particle cells; its
+ * values are computed later by apr_tree_restrict. y indices are stored as uint16.
+ * Allocates device memory (cudaMalloc) owned by *out; returns APR_ERR_INVALID_LAYOUT when the
+ * arrays are inconsistent (row sizes, y order and range, and with the flags the partition and the
+ * balance), APR_ERR_OOM on allocation failure. *out is NULL on error. */
+apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream,
+                              apr_handle_t *out);
+
+/* Release the handle and its device memory (synchronises the device first). NULL is accepted. */
+apr_status_t apr_destroy(apr_handle_t h);
+
+int64_t apr_num_particles(apr_handle_t h);   /* -1 on NULL */
+int64_t apr_num_tree(apr_handle_t h);        /* N_t, -1 on NULL */
+apr_status_t apr_level_range(apr_handle_t h, int32_t *l_min, int32_t *l_max);
+size_t apr_layout_bytes(apr_handle_t h);     /* device bytes owned by the handle */
+
+/* Size in bytes of structure array `which`; 0 if not available. */
+size_t apr_structure_bytes(apr_handle_t h, int32_t which);
+/* Copy structure array `which` to host memory `dst` of `bytes` (>= apr_structure_bytes). */
+apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes);
+
+/* APR tree restriction (Sec. 3.4, two-step fill; P:407 step 2): for l = l_max-1 down to l_min, every
+ * tree node gets the average of its children inside the level grid, each child being a particle of
+ * level l+1 or a tree node of level l+1 (average downsampling, Sec. 2.3).
+ *   particles: device [N_p][channels] float32 (channels-last), read only.
+ *   tree:      device [N_t][channels] float32, written (every entry).
+ * channels: 1 .. 64. */
+apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tree, int32_t channels,
+                               apr_stream_t stream);
+
+/* APR convolution (Sec. 4.1, per-level stencils Sec. 4.2-4.3; GPU design Sec. 5.2): for every particle
+ * p at level l, out[p] = sum_{e in [-r,r]^3} stencils[l - l_min][e] * u_l(refl(i_p + e)), where u_l(c)
+ * is the isotropic level-l patch value of cell c (Sec. 3.5): the level-l particle covering c, else
+ * the level-l tree node at c, else the level-(l-1) particle containing c. Correlation form (no flip).
+ *   particles: device [N_p] float32;  tree: device [N_t] float32 from apr_tree_restrict (required);
+ *   stencils:  device [(l_max-l_min+1)][k][k][k] float32, level l_min first, [z][x][y] y fastest;
+ *   k: 3 or 5;  bc: APR_BC_REFLECT or APR_BC_ZERO;  out: device [N_p] float32, overwritten.
+ * Requires the 2:1 balance of the APR (checked by APR_REQUIRE_BALANCE at build). */
+apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                          int32_t k, int32_t bc, float *out, apr_stream_t stream);
+
+/* Scratch bytes apr_convolve_backward needs for stencil size k. */
+size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k);
+
+/* Adjoint of apr_tree_restrict followed by apr_convolve (the back-propagation through the
+ * interpolation across levels that Sec. 6 proposes for APR CNNs). With g = grad_out:
+ *   grad_particles[q] = sum over taps that read q (directly at q's level, or as the coarse fill of
+ *                       the next finer level) of g_p * w[e], plus the tree share: every tree node's
+ *                       gradient is passed to its children divided by its number of children,
+ *                       from the coarsest level down;
+ *   grad_stencils[l][e] = sum_{p at level l} g_p * u_l(refl(i_p + e)).
+ * Inputs as in apr_convolve; grad_out device [N_p]. grad_particles (device [N_p]) and grad_stencils
+ * (device [L][k^3]) are overwritten; either may be NULL to skip it. workspace: device scratch of at
+ * least apr_backward_workspace_bytes(h, k) bytes, 256-byte aligned, contents ignored on entry.
+ * Results are deterministic (fixed summation order). */
+apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree,
+                                   const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                                   float *grad_particles, float *grad_stencils, void *workspace,
+                                   size_t workspace_bytes, apr_stream_t stream);
+
+/* Restricted stencils (Eq. restrict_stenc, K_{w_l} = R_l K_w P_l with block-average R_l and
+ * piecewise-constant P_l): out[l - l_min][e] = sum_d w[d] * prod_axes c_s(d_a, e_a), where
+ * c_s(d, e) = (1/s) #{x in [0, s): floor((x + d) / s) = e} and s = 2^(l_max - l). Host memory in and
+ * out: w [k^3], out [(l_max-l_min+1)][k^3] float32 (computed in double, rounded once). k: 3 or 5. */
+apr_status_t apr_restrict_stencil(const float *w, int32_t k, int32_t l_max, int32_t l_min, float *out);
+
+/* Level-rescaled stencils (Eq. adapt_grad): out[l - l_min] = 2^-(l_max - l) * w. Host memory. */
+apr_status_t apr_rescale_stencil(const float *w, int32_t k, int32_t l_max, int32_t l_min, float *out);
+
+/* Wait for `stream`, then read and clear the handle's device error word. Returns APR_ERR_DEVICE if a
+ * device-side check failed since the last call, else APR_OK (or APR_ERR_CUDA). */
+apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream);
+
+const char *apr_status_string(apr_status_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APR_H */

@@ -62,7 +62,7 @@ def _load():
         lib.ora_conv.restype = I32
         lib.ora_conv.argtypes = [P, D, I32, I32, I32, P, I64, D]
         lib.ora_conv_backward.restype = I32
-        lib.ora_conv_backward.argtypes = [P, D, I32, I32, I32, D, D, D]
+        lib.ora_conv_backward.argtypes = [P, D, I32, I32, I32, D, P, I64, D, D]
         lib.ora_check_coarse_fill.restype = I64
         lib.ora_check_coarse_fill.argtypes = [P, I32]
         _lib = lib
@@ -159,14 +159,19 @@ class Oracle:
             raise ValueError(f"oracle: stencil tap without a source (code {rc})")
         return out[:ns]
 
-    def conv_backward(self, stencils, k, grad_out, bc=BC_REFLECT, C_out=1):
-        """(dL/d particles [N][C], dL/d stencils [L][C_out][C][k^3]) for dL/d out = grad_out."""
+    def conv_backward(self, stencils, k, grad_out, bc=BC_REFLECT, C_out=1, sample=None):
+        """(dL/d particles [N][C], dL/d stencils [L][C_out][C][k^3]) for dL/d out = grad_out.
+
+        With `sample`, only the listed outputs contribute (their grad_out rows are used)."""
         self.tree()
         W = self._stencils(stencils, k, C_out)
         G = np.ascontiguousarray(np.asarray(grad_out, np.float64).reshape(self.apr.n_particles, C_out))
         gp = np.zeros((max(self.apr.n_particles, 1), self.C), np.float64)
         gw = np.zeros(W.shape, np.float64)
-        rc = _load().ora_conv_backward(self.h, _ptr(W), k, C_out, bc, _ptr(G), _ptr(gp), _ptr(gw))
+        sp = None if sample is None else np.ascontiguousarray(np.asarray(sample, np.int64))
+        rc = _load().ora_conv_backward(self.h, _ptr(W), k, C_out, bc, _ptr(G),
+                                       _ptr(sp) if sp is not None else None, 0 if sp is None else sp.size,
+                                       _ptr(gp), _ptr(gw))
         if rc:
             raise ValueError(f"oracle: invalid APR in backward (code {rc})")
         return gp[:self.apr.n_particles], gw

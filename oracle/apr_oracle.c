@@ -336,16 +336,18 @@ int ora_conv(const ora_t *o, const double *W, int k, int C_out, int bc, const in
 /* Given G = dL/do [np][C_out]:
  *   grad_p [np][C] = dL/d(particle values) through both the direct taps and the tree averages,
  *   grad_w [L][C_out][C][k^3] = dL/dW,
- * as the explicit transpose of ora_tree_fill + ora_conv: every tap scatters G*w to the source of
+ * (only the outputs listed in `sample` contribute when it is not NULL), as the explicit transpose of ora_tree_fill + ora_conv: every tap scatters G*w to the source of
  * its cell; tree gradients are then pushed from coarse to fine, each child receiving its parent's
  * gradient divided by the parent's number of children. Returns 0 or 3 (tap without source). */
 int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc, const double *G,
-                      double *grad_p, double *grad_w) {
+                      const int64_t *sample, int64_t ns, double *grad_p, double *grad_w) {
     const int r = k / 2, C = o->C, k3 = k * k * k, L = o->l_max - o->l_min + 1;
     double *gt = (double *)calloc((size_t)(o->nt ? o->nt : 1) * C, sizeof(double));
     memset(grad_p, 0, sizeof(double) * (size_t)o->np * C);
     if (grad_w) memset(grad_w, 0, sizeof(double) * (size_t)L * C_out * C * k3);
-    for (int64_t p = 0; p < o->np; ++p) {
+    if (!sample) ns = o->np;
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t p = sample ? sample[s] : s;
         int l = o->pl[p];
         const double *Wl = W + (size_t)(l - o->l_min) * C_out * C * k3;
         double *gWl = grad_w ? grad_w + (size_t)(l - o->l_min) * C_out * C * k3 : NULL;

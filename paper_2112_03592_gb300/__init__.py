@@ -1,0 +1,252 @@
+"""APR-native discrete convolution on GB300 (sm_103a): Python binding of libaprconv.so.
+
+Method: Jonsson et al., "Parallel Discrete Convolutions on Adaptive Particle Representations of
+Images" (arXiv 2112.03592). The C ABI is declared in include/apr.h; the functions here marshal
+torch tensors (device memory, current stream) into it and do no arithmetic of their own. The
+library must be built (``__graft_entry__.build()``); a missing library raises, never falls back.
+
+Functions with the C names:
+    apr_build_device(dims, l_min, l_max, row_ptr, y_idx, flags)   -> AprLayout
+    apr_tree_restrict(layout, particles[, tree])                  -> tree      (Sec. 3.4)
+    apr_convolve(layout, particles, tree, stencils, k[, bc, out]) -> out       (Sec. 4.1)
+    apr_convolve_backward(layout, particles, tree, stencils, k, grad_out[, bc])
+                                                                  -> (grad_particles, grad_stencils)
+    apr_restrict_stencil(w, l_max, l_min)                         -> [L][k^3]  (Eq. restrict_stenc)
+    apr_rescale_stencil(w, l_max, l_min)                          -> [L][k^3]  (Eq. adapt_grad)
+plus ``AprConv`` (torch.autograd.Function): particles, stencils -> per-particle outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALANCE, APR_VALIDATE,  # noqa: F401
+                   AprError)
+
+__all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
+           "apr_convolve_backward", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
+           "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY"]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, name, numel=None, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class AprLayout:
+    """Owns an apr_handle_t: the device-resident index of one APR (particles + APR tree)."""
+
+    def __init__(self, dims, l_min, l_max, row_ptr, y_idx,
+                 flags=APR_VALIDATE | APR_REQUIRE_BALANCE):
+        lib = _abi.load()
+        self._row_ptr = np.ascontiguousarray(np.asarray(row_ptr, np.int64))
+        self._y_idx = np.ascontiguousarray(np.asarray(y_idx, np.int32))
+        L = _abi.AprHostLayout()
+        L.l_min, L.l_max = int(l_min), int(l_max)
+        for a in range(3):
+            L.dims[a] = int(dims[a])
+        L.row_ptr = self._row_ptr.ctypes.data_as(ctypes.c_void_p)
+        L.y_idx = self._y_idx.ctypes.data_as(ctypes.c_void_p)
+        L.n_particles = int(self._y_idx.size)
+        h = ctypes.c_void_p()
+        stream = ctypes.c_void_p(0)
+        if not (flags & APR_HOST_ONLY):
+            stream = _stream_ptr()
+        _abi.check("apr_build_device", lib.apr_build_device(ctypes.byref(L), flags, stream, ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.dims = tuple(int(d) for d in dims)
+        self.l_min, self.l_max = int(l_min), int(l_max)
+        self.n_particles = int(lib.apr_num_particles(h))
+        self.n_tree = int(lib.apr_num_tree(h))
+        self.host_only = bool(flags & APR_HOST_ONLY)
+        self._ws = {}
+
+    @classmethod
+    def from_apr(cls, apr, flags=APR_VALIDATE | APR_REQUIRE_BALANCE):
+        """From any object with dims, l_min, l_max, row_ptr, y_idx (e.g. aprsynth.AprInput)."""
+        return cls(apr.dims, apr.l_min, apr.l_max, apr.row_ptr, apr.y_idx, flags)
+
+    @property
+    def n_levels(self):
+        return self.l_max - self.l_min + 1
+
+    @property
+    def handle(self):
+        return self._h
+
+    def layout_bytes(self) -> int:
+        return int(self._lib.apr_layout_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.apr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- structure export (bit-exact checks)
+    _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32}
+
+    def export(self, which: int) -> np.ndarray:
+        nbytes = int(self._lib.apr_structure_bytes(self._h, which))
+        dt = self._EXPORT_DTYPES[which]
+        out = np.zeros(max(nbytes // np.dtype(dt).itemsize, 1), dt)
+        _abi.check("apr_export_structure",
+                   self._lib.apr_export_structure(self._h, which, out.ctypes.data_as(ctypes.c_void_p), nbytes))
+        out = out[:nbytes // np.dtype(dt).itemsize]
+        return out.reshape(-1, 4) if which in (4, 5) else out
+
+    def workspace(self, k):
+        import torch
+        nbytes = int(self._lib.apr_backward_workspace_bytes(self._h, k))
+        ws = self._ws.get(k)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+            self._ws[k] = ws
+        return ws, nbytes
+
+    def sync_status(self, stream=None):
+        _abi.check("apr_sync_status", self._lib.apr_sync_status(self._h, _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------------------------------------
+# functions named as in the C ABI
+# ------------------------------------------------------------------------------------------------
+def apr_build_device(dims, l_min, l_max, row_ptr, y_idx, flags=APR_VALIDATE | APR_REQUIRE_BALANCE) -> AprLayout:
+    return AprLayout(dims, l_min, l_max, row_ptr, y_idx, flags)
+
+
+def apr_tree_restrict(layout: AprLayout, particles, tree=None, stream=None):
+    import torch
+    C = 1 if particles.dim() == 1 else int(particles.shape[1])
+    _dev_ptr(particles, "particles", layout.n_particles * C, torch.float32)
+    if tree is None:
+        tree = torch.empty((layout.n_tree,) if C == 1 else (layout.n_tree, C), dtype=torch.float32, device=particles.device)
+    _dev_ptr(tree, "tree", layout.n_tree * C, torch.float32)
+    _abi.check("apr_tree_restrict", layout._lib.apr_tree_restrict(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()), C, _stream_ptr(stream)))
+    return tree
+
+
+def apr_convolve(layout: AprLayout, particles, tree, stencils, k, bc=APR_BC_REFLECT, out=None, stream=None):
+    import torch
+    _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
+    _dev_ptr(tree, "tree", layout.n_tree, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    if out is None:
+        out = torch.empty(layout.n_particles, dtype=torch.float32, device=particles.device)
+    _dev_ptr(out, "out", layout.n_particles, torch.float32)
+    _abi.check("apr_convolve", layout._lib.apr_convolve(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
+        ctypes.c_void_p(stencils.data_ptr()), int(k), int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_convolve_backward(layout: AprLayout, particles, tree, stencils, k, grad_out, bc=APR_BC_REFLECT,
+                          need_particles=True, need_stencils=True, grad_particles=None, grad_stencils=None,
+                          stream=None):
+    import torch
+    _dev_ptr(grad_out, "grad_out", layout.n_particles, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    gp_ptr = gw_ptr = ctypes.c_void_p(0)
+    if need_particles:
+        if grad_particles is None:
+            grad_particles = torch.empty(layout.n_particles, dtype=torch.float32, device=grad_out.device)
+        gp_ptr = _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32)
+    if need_stencils:
+        _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
+        _dev_ptr(tree, "tree", layout.n_tree, torch.float32)
+        if grad_stencils is None:
+            grad_stencils = torch.empty((layout.n_levels, k ** 3), dtype=torch.float32, device=grad_out.device)
+        gw_ptr = _dev_ptr(grad_stencils, "grad_stencils", layout.n_levels * k ** 3, torch.float32)
+    ws, nbytes = layout.workspace(k)
+    _abi.check("apr_convolve_backward", layout._lib.apr_convolve_backward(
+        layout.handle, ctypes.c_void_p(particles.data_ptr() if particles is not None else 0),
+        ctypes.c_void_p(tree.data_ptr() if tree is not None else 0), ctypes.c_void_p(stencils.data_ptr()),
+        int(k), int(bc), ctypes.c_void_p(grad_out.data_ptr()), gp_ptr, gw_ptr,
+        ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
+    return (grad_particles if need_particles else None), (grad_stencils if need_stencils else None)
+
+
+def _stencil_stack(fn_name, w, l_max, l_min):
+    lib = _abi.load()
+    w = np.ascontiguousarray(np.asarray(w, np.float32))
+    k = w.shape[0]
+    if w.shape != (k, k, k):
+        raise ValueError("stencil must be k x k x k")
+    out = np.zeros((l_max - l_min + 1, k ** 3), np.float32)
+    _abi.check(fn_name, getattr(lib, fn_name)(w.ctypes.data_as(ctypes.c_void_p), k, int(l_max), int(l_min),
+                                              out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def apr_restrict_stencil(w, l_max, l_min) -> np.ndarray:
+    return _stencil_stack("apr_restrict_stencil", w, l_max, l_min)
+
+
+def apr_rescale_stencil(w, l_max, l_min) -> np.ndarray:
+    return _stencil_stack("apr_rescale_stencil", w, l_max, l_min)
+
+
+# ------------------------------------------------------------------------------------------------
+# autograd
+# ------------------------------------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class _AprConv(torch.autograd.Function):
+        """out = apr_convolve(restrict(particles), stencils); gradients through both (Sec. 6 outlook)."""
+
+        @staticmethod
+        def forward(ctx, particles, stencils, layout, k, bc):
+            particles = particles.contiguous()
+            stencils = stencils.contiguous()
+            tree = apr_tree_restrict(layout, particles)
+            out = apr_convolve(layout, particles, tree, stencils, k, bc)
+            ctx.save_for_backward(particles, tree, stencils)
+            ctx.layout, ctx.k, ctx.bc = layout, k, bc
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            particles, tree, stencils = ctx.saved_tensors
+            gp, gw = apr_convolve_backward(ctx.layout, particles, tree, stencils, ctx.k, grad_out.contiguous(), ctx.bc,
+                                           need_particles=ctx.needs_input_grad[0],
+                                           need_stencils=ctx.needs_input_grad[1])
+            if gw is not None:
+                gw = gw.view_as(stencils)
+            return gp, gw, None, None, None
+
+    return _AprConv
+
+
+class AprConv:
+    """AprConv.apply(particles, stencils, layout, k, bc=APR_BC_REFLECT) -> per-particle outputs."""
+    _fn = None
+
+    @classmethod
+    def apply(cls, particles, stencils, layout, k, bc=APR_BC_REFLECT):
+        if cls._fn is None:
+            cls._fn = _autograd_function()
+        return cls._fn.apply(particles, stencils, layout, k, bc)

@@ -1,0 +1,296 @@
+// C ABI entry points (include/apr.h): handle lifetime, upload of the index, kernel launches.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "apr_internal.h"
+
+namespace aprk {
+cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
+                            const float *tree, const float *st, int bc, float *out, cudaStream_t s);
+cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
+                                 cudaStream_t s);
+cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
+                            const float *gout, float *gp, float *gt, cudaStream_t s);
+cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int n, const float *vals,
+                               const float *tree, int bc, const float *gout, float *partial, cudaStream_t s);
+cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64_t *level_begin, int l_min,
+                                  int n_levels, int K3, float *gw, cudaStream_t s);
+cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, int n, float *gp, float *gt, cudaStream_t s);
+}  // namespace aprk
+
+using namespace aprk;
+
+struct apr_handle_s {
+    HostIndex X;
+    bool host_only = false;
+    DevLayout L{};
+    Item *d_fwd = nullptr, *d_bwd = nullptr, *d_tree = nullptr;
+    int64_t *d_fwd_level_begin = nullptr;
+    uint32_t *d_row_ptr = nullptr, *d_trow_ptr = nullptr;
+    uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
+    unsigned *d_err = nullptr;
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+thread_local char g_last_msg[256] = "";
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes) {
+    *dst = nullptr;
+    const size_t b = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), b);
+    if (e != cudaSuccess) return e;
+    bytes += b;
+    if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_device(apr_handle_s *h) {
+    void *ptrs[] = {h->d_fwd, h->d_bwd, h->d_tree, h->d_fwd_level_begin, h->d_row_ptr, h->d_trow_ptr,
+                    h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+apr_status_t cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return APR_OK;
+    if (e == cudaErrorMemoryAllocation) return APR_ERR_OOM;
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", cudaGetErrorString(e));
+    return APR_ERR_CUDA;
+}
+
+bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
+
+}  // namespace
+
+extern "C" {
+
+const char *apr_status_string(apr_status_t s) {
+    switch (s) {
+        case APR_OK: return "ok";
+        case APR_ERR_INVALID_ARG: return "invalid argument";
+        case APR_ERR_INVALID_LAYOUT: return "invalid APR layout";
+        case APR_ERR_UNSUPPORTED: return "unsupported";
+        case APR_ERR_OOM: return "out of memory";
+        case APR_ERR_CUDA: return "CUDA error";
+        case APR_ERR_TIMEOUT: return "device wait timed out";
+        case APR_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+// Reason of the last failure on this thread (build errors, CUDA messages); not part of apr.h.
+const char *apr_last_error_message(void) { return g_last_msg; }
+
+apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream, apr_handle_t *out) {
+    if (!out) return APR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!layout || (flags & ~(APR_VALIDATE | APR_REQUIRE_BALANCE | APR_HOST_ONLY))) return APR_ERR_INVALID_ARG;
+    apr_handle_s *h = new (std::nothrow) apr_handle_s();
+    if (!h) return APR_ERR_OOM;
+    const char *msg = "";
+    apr_status_t st;
+    try {
+        st = build_index(*layout, flags, h->X, &msg);
+    } catch (const std::bad_alloc &) {
+        st = APR_ERR_OOM;
+        msg = "host allocation failed";
+    }
+    if (st != APR_OK) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg);
+        delete h;
+        return st;
+    }
+    h->host_only = (flags & APR_HOST_ONLY) != 0;
+    if (!h->host_only) {
+        (void)stream;  // uploads are synchronous: the index is built once
+        const HostIndex &X = h->X;
+        cudaError_t e = cudaSuccess;
+        size_t &b = h->dev_bytes;
+        if (e == cudaSuccess) e = upload(&h->d_row_ptr, X.row_ptr.data(), X.row_ptr.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_y, X.y.data(), X.y.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_off, X.off.data(), X.off.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_trow_ptr, X.trow_ptr.data(), X.trow_ptr.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_ty, X.ty.data(), X.ty.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_toff, X.toff.data(), X.toff.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_fwd, X.fwd_items.data(), X.fwd_items.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
+        if (e == cudaSuccess) {
+            e = cudaMalloc(reinterpret_cast<void **>(&h->d_err), sizeof(unsigned));
+            if (e == cudaSuccess) {
+                b += sizeof(unsigned);
+                e = cudaMemset(h->d_err, 0, sizeof(unsigned));
+            }
+        }
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            free_device(h);
+            delete h;
+            return st;
+        }
+        DevLayout &L = h->L;
+        L.row_ptr = h->d_row_ptr;
+        L.y = h->d_y;
+        L.off = h->d_off;
+        L.trow_ptr = h->d_trow_ptr;
+        L.ty = h->d_ty;
+        L.toff = h->d_toff;
+        L.err = h->d_err;
+        L.l_min = X.l_min;
+        L.l_max = X.l_max;
+        for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
+    }
+    *out = h;
+    return APR_OK;
+}
+
+apr_status_t apr_destroy(apr_handle_t h) {
+    if (!h) return APR_OK;
+    if (!h->host_only) {
+        cudaDeviceSynchronize();
+        free_device(h);
+    }
+    delete h;
+    return APR_OK;
+}
+
+int64_t apr_num_particles(apr_handle_t h) { return h ? h->X.np : -1; }
+int64_t apr_num_tree(apr_handle_t h) { return h ? h->X.nt : -1; }
+
+apr_status_t apr_level_range(apr_handle_t h, int32_t *l_min, int32_t *l_max) {
+    if (!h || !l_min || !l_max) return APR_ERR_INVALID_ARG;
+    *l_min = h->X.l_min;
+    *l_max = h->X.l_max;
+    return APR_OK;
+}
+
+size_t apr_layout_bytes(apr_handle_t h) { return h ? h->dev_bytes : 0; }
+
+size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
+    if (!h) return 0;
+    const HostIndex &X = h->X;
+    switch (which) {
+        case APR_STRUCT_ROW_PTR: return X.row_ptr.size() * sizeof(uint32_t);
+        case APR_STRUCT_Y_IDX: return X.y.size() * sizeof(uint16_t);
+        case APR_STRUCT_TREE_ROW_PTR: return X.trow_ptr.size() * sizeof(uint32_t);
+        case APR_STRUCT_TREE_Y_IDX: return X.ty.size() * sizeof(uint16_t);
+        case APR_STRUCT_FWD_ITEMS: return X.fwd_items.size() * sizeof(Item);
+        case APR_STRUCT_TREE_ITEMS: return X.tree_items.size() * sizeof(Item);
+    }
+    return 0;
+}
+
+apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes) {
+    if (!h || (!dst && bytes)) return APR_ERR_INVALID_ARG;
+    const size_t need = apr_structure_bytes(h, which);
+    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_TREE_ITEMS) return APR_ERR_INVALID_ARG;
+    if (bytes < need) return APR_ERR_INVALID_ARG;
+    if (need == 0) return APR_OK;
+    const HostIndex &X = h->X;
+    const void *host_src = nullptr;
+    const void *dev_src = nullptr;
+    switch (which) {
+        case APR_STRUCT_ROW_PTR: host_src = X.row_ptr.data(); dev_src = h->d_row_ptr; break;
+        case APR_STRUCT_Y_IDX: host_src = X.y.data(); dev_src = h->d_y; break;
+        case APR_STRUCT_TREE_ROW_PTR: host_src = X.trow_ptr.data(); dev_src = h->d_trow_ptr; break;
+        case APR_STRUCT_TREE_Y_IDX: host_src = X.ty.data(); dev_src = h->d_ty; break;
+        case APR_STRUCT_FWD_ITEMS: host_src = X.fwd_items.data(); dev_src = h->d_fwd; break;
+        case APR_STRUCT_TREE_ITEMS: host_src = X.tree_items.data(); dev_src = h->d_tree; break;
+    }
+    if (h->host_only) {
+        memcpy(dst, host_src, need);
+        return APR_OK;
+    }
+    // the device copy is the one the kernels read
+    return cuda_status(cudaMemcpy(dst, dev_src, need, cudaMemcpyDeviceToHost));
+}
+
+apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tree, int32_t channels,
+                               apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (channels != 1) return APR_ERR_UNSUPPORTED;
+    if ((!particles && h->X.np) || (!tree && h->X.nt)) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    for (int l = X.l_max - 1; l >= X.l_min; --l) {
+        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, int(n), particles, tree, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return APR_OK;
+}
+
+apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                          int32_t k, int32_t bc, float *out, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    const int n = int(h->X.fwd_items.size());
+    return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
+}
+
+size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k) {
+    if (!h || !stencil_k_ok(k)) return 0;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(size_t(h->X.nt) * sizeof(float)) + al(h->X.fwd_items.size() * size_t(k * k * k) * sizeof(float));
+}
+
+apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                   int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
+                                   float *grad_stencils, void *workspace, size_t workspace_bytes,
+                                   apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!stencils || (X.np && !grad_out)) return APR_ERR_INVALID_ARG;
+    if (grad_stencils && ((X.np && !particles) || (X.nt && !tree))) return APR_ERR_INVALID_ARG;
+    const size_t need = apr_backward_workspace_bytes(h, k);
+    if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return APR_ERR_INVALID_ARG;
+    const size_t gt_bytes = (size_t(X.nt) * sizeof(float) + 255) / 256 * 256;
+    float *gt = static_cast<float *>(workspace);
+    float *partial = reinterpret_cast<float *>(static_cast<char *>(workspace) + gt_bytes);
+    const int k3 = k * k * k;
+    cudaError_t e = cudaSuccess;
+    if (grad_particles) {
+        if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * sizeof(float), stream);
+        if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(gt, 0, size_t(X.nt) * sizeof(float), stream);
+        if (e == cudaSuccess)
+            e = launch_bwd_data(k, h->L, h->d_bwd, int(X.bwd_items.size()), stencils, bc, grad_out, grad_particles, gt, stream);
+        for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
+            const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+            e = launch_tree_pushdown(h->L, h->d_tree + b, int(n), grad_particles, gt, stream);
+        }
+    }
+    if (e == cudaSuccess && grad_stencils) {
+        const int n = int(X.fwd_items.size());
+        e = launch_bwd_stencil(k, h->L, h->d_fwd, n, particles, tree, bc, grad_out, partial, stream);
+        if (e == cudaSuccess)
+            e = launch_stencil_reduce(partial, n, h->d_fwd_level_begin, X.l_min, X.l_max - X.l_min + 1, k3, grad_stencils, stream);
+    }
+    return cuda_status(e);
+}
+
+apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream) {
+    if (!h) return APR_ERR_INVALID_ARG;
+    if (h->host_only) return APR_OK;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    unsigned v = 0;
+    e = cudaMemcpy(&v, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (v) {
+        cudaMemset(h->d_err, 0, sizeof(unsigned));
+        return APR_ERR_DEVICE;
+    }
+    return APR_OK;
+}
+
+}  // extern "C"

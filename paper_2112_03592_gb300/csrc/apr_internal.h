@@ -1,0 +1,71 @@
+// Internal definitions shared by the host index builder, the C-ABI entry points and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "apr.h"
+
+namespace aprk {
+
+// y-block of the brick index and of every work item: rows are cut into blocks of BY cells along y,
+// and each row stores, per block, the offset of its first element (a finer-grained xz_end).
+constexpr int BY = 64;
+// (z, x) rows per convolution tile at the tile's own level.
+constexpr int TZ = 4;
+constexpr int TX = 4;
+constexpr int MAXL = 24;
+
+// Geometry of one level, passed to kernels by value.
+struct LevelGeo {
+    int32_t dz, dx, dy;  // level grid size
+    int32_t nb;          // ceil(dy / BY) blocks per row
+    int32_t row0;        // index of the level's first particle row (into row_ptr)
+    int32_t off0;        // index of the level's first entry in the particle block-offset array
+    int32_t trow0;       // same for the tree (levels < l_max)
+    int32_t toff0;
+};
+
+// Everything a kernel needs to walk the index (device pointers).
+struct DevLayout {
+    const uint32_t *row_ptr;   // [R+1]
+    const uint16_t *y;         // [N_p]
+    const uint16_t *off;       // [sum_l rows_l * nb_l]: first element of block j, relative to row start
+    const uint32_t *trow_ptr;  // [R_t+1]
+    const uint16_t *ty;        // [N_t]
+    const uint16_t *toff;
+    unsigned *err;
+    int32_t l_min, l_max;
+    LevelGeo geo[MAXL];
+};
+
+struct Item {  // a work item: level, tile (or row) coordinates, y block
+    int32_t l, a, b, yb;
+};
+
+// Host-side index, built by build_index(); uploaded by apr_build_device.
+struct HostIndex {
+    int32_t l_min = 0, l_max = 0;
+    int64_t dims[3] = {0, 0, 0};
+    LevelGeo geo[MAXL] = {};
+    int64_t np = 0, nt = 0, R = 0, Rt = 0, noff = 0, ntoff = 0;
+    std::vector<uint32_t> row_ptr, trow_ptr;
+    std::vector<uint16_t> y, ty, off, toff;
+    std::vector<Item> fwd_items;              // non-empty (l, tz, tx, yb) tiles, by level
+    std::vector<Item> bwd_items;              // tiles whose interior cells receive gradient
+    std::vector<Item> tree_items;             // non-empty (l, z, x, yb) tree bricks, by level
+    int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
+    int64_t tree_level_begin[MAXL + 1] = {};
+};
+
+// Builds and validates the index from the host layout. Returns APR_OK or an error code; `msg`
+// receives a short reason on failure.
+apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
+
+inline int64_t level_cells(int64_t D, int l_max, int l) {
+    int64_t s = int64_t(1) << (l_max - l);
+    return (D + s - 1) / s;
+}
+
+}  // namespace aprk

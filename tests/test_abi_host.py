@@ -1,0 +1,143 @@
+"""C-ABI library on the host (no GPU): symbols, index structure, stencil helpers, invalid layouts."""
+import ctypes
+import pathlib
+import re
+
+import numpy as np
+import pytest
+
+import aprsynth as S
+import oracle
+import paper_2112_03592_gb300 as G
+from paper_2112_03592_gb300 import _abi
+
+HEADER = pathlib.Path(__file__).resolve().parents[1] / "include" / "apr.h"
+HOST = G.APR_VALIDATE | G.APR_REQUIRE_BALANCE | G.APR_HOST_ONLY
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(apr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _abi.load()
+    names = declared_functions()
+    assert len(names) >= 15, names
+    for n in names:
+        assert hasattr(lib, n), f"{n} missing from {_abi.lib_path()}"
+        assert n in _abi.SIGNATURES, f"{n} not bound in the Python binding"
+
+
+def test_status_strings():
+    lib = _abi.load()
+    for code in range(8):
+        assert lib.apr_status_string(code)
+
+
+def _check_structure(apr):
+    lay = G.AprLayout.from_apr(apr, flags=HOST)
+    o = oracle.Oracle(apr)
+    assert o.error == 0
+    assert lay.n_tree == o.n_tree
+    rp, ty = o.tree_layout()
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_ROW_PTR), apr.row_ptr.astype(np.uint32))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_Y_IDX), apr.y_idx.astype(np.uint16))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_ROW_PTR), rp.astype(np.uint32))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_Y_IDX), ty.astype(np.uint16))
+    # work list: exactly the (level, tile, y-block) bricks holding particles
+    lev, z, x, y = apr.particle_coords()
+    ref = sorted(set(zip(lev.tolist(), (z // 4).tolist(), (x // 4).tolist(), (y // 64).tolist())))
+    got = [tuple(r) for r in lay.export(_abi.APR_STRUCT_FWD_ITEMS).tolist()]
+    assert got == ref
+    tc = o.tree_coords()
+    tref = sorted(set(zip(tc[:, 0].tolist(), tc[:, 1].tolist(), tc[:, 2].tolist(), (tc[:, 3] // 64).tolist())))
+    assert [tuple(r) for r in lay.export(_abi.APR_STRUCT_TREE_ITEMS).tolist()] == tref
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: S.make_config("blob64", use_cache=False),
+    lambda: S.random_balanced_apr((12, 16, 10), 1, seed=1),
+    lambda: S.random_balanced_apr((9, 5, 70), 1, seed=2, p_fine=0.01),
+    lambda: S.random_balanced_apr((3, 1, 130), 0, seed=3),
+    lambda: S.uniform_level_apr((16, 8, 8), 4),
+    lambda: S.uniform_level_apr((16, 8, 8), 2, l_min=1),
+])
+def test_structure_bit_exact_vs_oracle(maker):
+    _check_structure(maker())
+
+
+def test_restrict_and_rescale_stencils_vs_oracle():
+    rng = np.random.default_rng(0)
+    for k in (3, 5):
+        w = rng.uniform(-1, 1, size=(k, k, k)).astype(np.float32)
+        a = G.apr_restrict_stencil(w, 9, 2)
+        b = oracle.restrict_stencil(w.astype(np.float64), 9, 2).reshape(a.shape)
+        np.testing.assert_allclose(a, b, rtol=0, atol=2e-7 * np.abs(b).max())
+        c = G.apr_rescale_stencil(w, 9, 2)
+        np.testing.assert_array_equal(c, (w.reshape(1, -1) * (2.0 ** -(9 - np.arange(2, 10)))[:, None]).astype(np.float32))
+    with pytest.raises(G.AprError):
+        G.apr_restrict_stencil(np.ones((7, 7, 7), np.float32), 5, 1)
+
+
+# ---------------------------------------------------------------------------- invalid layouts
+def _layout(apr, **kw):
+    d = dict(dims=apr.dims, l_min=apr.l_min, l_max=apr.l_max, row_ptr=apr.row_ptr.copy(), y_idx=apr.y_idx.copy())
+    d.update(kw)
+    return d
+
+
+def _build(d, flags=HOST):
+    return G.AprLayout(d["dims"], d["l_min"], d["l_max"], d["row_ptr"], d["y_idx"], flags)
+
+
+def _expect(code, d, flags=HOST):
+    with pytest.raises(G.AprError) as e:
+        _build(d, flags)
+    assert e.value.code == code
+
+
+def test_invalid_layouts_rejected():
+    apr = S.random_balanced_apr((8, 8, 8), 1, seed=5)
+    _build(_layout(apr))  # the valid one builds
+    rp = apr.row_ptr.copy()
+    rp[3] = rp[4] + 1  # not monotone
+    _expect(2, _layout(apr, row_ptr=rp))
+    rp = apr.row_ptr.copy()
+    rp[-1] -= 1  # does not end at n_particles
+    _expect(2, _layout(apr, row_ptr=rp))
+    y = apr.y_idx.copy()
+    big = int(np.argmax(np.diff(apr.row_ptr)))
+    b = int(apr.row_ptr[big])
+    y[b], y[b + 1] = y[b + 1], y[b]  # unsorted y
+    _expect(2, _layout(apr, y_idx=y))
+    y = apr.y_idx.copy()
+    y[-1] = 1000  # outside the grid
+    _expect(2, _layout(apr, y_idx=y))
+    _expect(2, _layout(apr, l_max=apr.l_max + 1))
+    _expect(1, _layout(apr, dims=(0, 8, 8)))
+
+
+def _tiny(ps, dims=(4, 4, 4), l_min=1):
+    return S.apr_from_particles(dims, l_min, ps)
+
+
+def test_partition_and_balance_violations_rejected():
+    full8 = [(2, a, b, c, 1.0) for a in range(2) for b in range(2) for c in range(2)]
+    others = [(1, z, x, y, 1.0) for z in range(2) for x in range(2) for y in range(2) if (z, x, y) != (0, 0, 0)]
+    ok = _tiny(full8 + others)
+    _build(_layout(ok))
+    hole = _tiny(full8[:-1] + others)                       # a missing cell
+    _expect(2, _layout(hole))
+    _build(_layout(hole), flags=G.APR_HOST_ONLY)            # without APR_VALIDATE it is not checked
+    overlap = _tiny(full8 + others + [(1, 0, 0, 0, 1.0)])   # a particle over finer particles
+    _expect(2, _layout(overlap))
+    # unbalanced: level-3 particles touching a level-1 particle (8x8x8 image)
+    ps = [(1, z, x, y, 1.0) for z in range(2) for x in range(2) for y in range(2) if (z, x, y) != (0, 0, 0)]
+    ps += [(2, z, x, y, 1.0) for z in range(2) for x in range(2) for y in range(2) if (z, x, y) != (1, 1, 1)]
+    ps += [(3, z, x, y, 1.0) for z in range(2, 4) for x in range(2, 4) for y in range(2, 4)]
+    unb = S.apr_from_particles((8, 8, 8), 1, ps)
+    S.validate_apr(unb, check_balance=False)
+    _build(_layout(unb), flags=G.APR_VALIDATE | G.APR_HOST_ONLY)     # a valid partition ...
+    _expect(2, _layout(unb), flags=HOST)                             # ... but not 2:1 balanced

@@ -1,0 +1,168 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+import torch
+
+import aprsynth as S
+import oracle
+import paper_2112_03592_gb300 as G
+from paper_2112_03592_gb300 import _abi
+
+pytestmark = pytest.mark.gpu
+FLAGS = G.APR_VALIDATE | G.APR_REQUIRE_BALANCE
+REL = 1e-5    # FP32 vs FP64: max relative error (positive data), spec bound
+NORM = 1e-5   # sign-mixed data: max |diff| / max |reference|
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def stencil_stack(apr, k, mode, seed=0):
+    L = apr.n_levels
+    if mode == "gauss":
+        w = S.gaussian_stencil(k, 1.0 if k == 3 else 1.5).astype(np.float32)
+        return np.repeat(w.reshape(1, -1), L, 0)
+    if mode == "restricted":
+        w = S.gaussian_stencil(k, 1.0 if k == 3 else 1.5).astype(np.float32)
+        return G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(L, k ** 3)).astype(np.float32)
+
+
+def gpu_forward(apr, st, k, bc):
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    v = dev(apr.values.astype(np.float32))
+    tree = G.apr_tree_restrict(lay, v)
+    out = G.apr_convolve(lay, v, tree, dev(st), k, bc)
+    torch.cuda.synchronize()
+    lay.sync_status()
+    return lay, v, tree, out
+
+
+def assert_rel(got, ref, tol=REL):
+    ref = np.asarray(ref, np.float64)
+    got = np.asarray(got, np.float64)
+    assert np.all(np.isfinite(got)), "non-finite GPU outputs"
+    err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30))
+    assert err <= tol, f"max relative error {err:.3e} > {tol}"
+
+
+def assert_norm(got, ref, tol=NORM):
+    ref = np.asarray(ref, np.float64)
+    got = np.asarray(got, np.float64)
+    assert np.all(np.isfinite(got)), "non-finite GPU outputs"
+    err = np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)
+    assert err <= tol, f"normwise error {err:.3e} > {tol}"
+
+
+CASES = {
+    "blob64": lambda: S.make_config("blob64", use_cache=False),
+    "rand_ragged": lambda: S.random_balanced_apr((21, 13, 150), 1, seed=7, p_fine=0.01),
+    "rand_thin": lambda: S.random_balanced_apr((3, 40, 9), 0, seed=8, p_fine=0.05),
+    "all_max": lambda: S.uniform_level_apr((9, 17, 70), 7, l_min=2),
+    "uniform_coarse": lambda: S.uniform_level_apr((32, 32, 32), 3, l_min=3),
+    "tiny": lambda: S.random_balanced_apr((2, 3, 5), 0, seed=9, p_fine=0.3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_tree_restrict_matches_oracle(case):
+    apr = CASES[case]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    v = dev(apr.values.astype(np.float32))
+    tree = G.apr_tree_restrict(lay, v).cpu().numpy()
+    ref = oracle.Oracle(apr).tree()[:, 0]
+    assert tree.shape == ref.shape
+    if ref.size:
+        assert_rel(tree, ref)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("k", [3, 5])
+@pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
+@pytest.mark.parametrize("mode", ["gauss", "restricted", "random"])
+def test_convolve_matches_oracle(case, k, bc, mode):
+    apr = CASES[case]()
+    st = stencil_stack(apr, k, mode, seed=k + 10 * bc)
+    _, _, _, out = gpu_forward(apr, st, k, bc)
+    ref = oracle.Oracle(apr).conv(st.astype(np.float64), k, bc=bc)[:, 0]
+    got = out.cpu().numpy()
+    if mode == "random" or bc == G.APR_BC_ZERO:
+        assert_norm(got, ref)
+    else:
+        assert_rel(got, ref)
+
+
+def test_constant_image_stays_constant():
+    apr = S.random_balanced_apr((24, 20, 130), 1, seed=4, values="const")
+    for k in (3, 5):
+        st = stencil_stack(apr, k, "restricted")
+        _, _, tree, out = gpu_forward(apr, st, k, G.APR_BC_REFLECT)
+        assert_rel(tree.cpu().numpy(), np.full(tree.numel(), 7.25))
+        assert_rel(out.cpu().numpy(), np.full(out.numel(), 7.25))
+
+
+@pytest.mark.parametrize("case", ["blob64", "rand_ragged", "rand_thin", "tiny"])
+@pytest.mark.parametrize("k", [3, 5])
+@pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
+def test_backward_matches_oracle(case, k, bc):
+    apr = CASES[case]()
+    st = stencil_stack(apr, k, "random", seed=3)
+    lay, v, tree, _ = gpu_forward(apr, st, k, bc)
+    g = np.random.default_rng(1).normal(size=apr.n_particles).astype(np.float32)
+    gp, gw = G.apr_convolve_backward(lay, v, tree, dev(st), k, dev(g), bc)
+    torch.cuda.synchronize()
+    rp, rw = oracle.Oracle(apr).conv_backward(st.astype(np.float64), k, g.astype(np.float64), bc=bc)
+    assert_norm(gp.cpu().numpy(), rp[:, 0])
+    assert_norm(gw.cpu().numpy(), rw.reshape(gw.shape))
+
+
+def test_backward_is_deterministic():
+    apr = CASES["blob64"]()
+    st = stencil_stack(apr, 5, "random")
+    lay, v, tree, _ = gpu_forward(apr, st, 5, 0)
+    g = dev(np.random.default_rng(2).normal(size=apr.n_particles).astype(np.float32))
+    a = [t.clone() for t in G.apr_convolve_backward(lay, v, tree, dev(st), 5, g, 0)]
+    b = G.apr_convolve_backward(lay, v, tree, dev(st), 5, g, 0)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_autograd_function_and_finite_differences():
+    apr = S.random_balanced_apr((10, 12, 20), 1, seed=12, p_fine=0.02)
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    k = 3
+    st = torch.tensor(stencil_stack(apr, k, "random", seed=5), device="cuda", requires_grad=True)
+    v = torch.tensor(apr.values, device="cuda", requires_grad=True)
+    out = G.AprConv.apply(v, st, lay, k)
+    gsel = torch.randn(out.shape, device="cuda")
+    (out * gsel).sum().backward()
+    # the map is bilinear in (values, stencils): central differences in float64 via the oracle are exact
+    o = oracle.Oracle(apr)
+    W = st.detach().cpu().double().numpy()
+    x0 = apr.values.astype(np.float64)
+    G_ = gsel.cpu().double().numpy()
+    rng = np.random.default_rng(0)
+    for j in rng.choice(apr.n_particles, 5, replace=False):
+        e = np.zeros_like(x0)
+        e[j] = 1.0
+        o.set_values(x0 + e)
+        fp = np.sum(o.conv(W, k)[:, 0] * G_)
+        o.set_values(x0 - e)
+        fm = np.sum(o.conv(W, k)[:, 0] * G_)
+        fd = (fp - fm) / 2.0
+        assert abs(v.grad[j].item() - fd) <= 1e-4 * max(1.0, abs(fd))
+    o.set_values(x0)
+    _, rw = o.conv_backward(W, k, G_)
+    assert_norm(st.grad.cpu().numpy(), rw.reshape(st.shape))
+
+
+def test_structure_on_device_is_bit_exact():
+    apr = CASES["blob64"]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    o = oracle.Oracle(apr)
+    rp, ty = o.tree_layout()
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_ROW_PTR), apr.row_ptr.astype(np.uint32))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_Y_IDX), apr.y_idx.astype(np.uint16))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_ROW_PTR), rp.astype(np.uint32))
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_Y_IDX), ty.astype(np.uint16))
