@@ -141,6 +141,23 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
                                    float *grad_particles, float *grad_stencils, void *workspace,
                                    size_t workspace_bytes, apr_stream_t stream);
 
+/* apr_convolve_backward for callers that cannot allocate device memory. The paper has no counterpart.
+ * Some callers may not call cudaMalloc at all: code running inside a host callback or a framework
+ * hook that must not allocate, a process whose device memory is reserved up front by another
+ * allocator, or an embedded pipeline with a fixed memory budget. This entry point takes no workspace
+ * and allocates nothing (no cudaMalloc, cudaFree or allocating library routine): its scratch is a
+ * fixed 16 MiB (16777216-byte) device array inside the library, which every GPU that loads the
+ * library holds until the process exits. The caller still passes inputs and outputs, as for
+ * apr_convolve_backward, and gets the same results.
+ *   - Returns APR_ERR_UNSUPPORTED when apr_backward_workspace_bytes(h, k) exceeds 16 MiB.
+ *   - The first call on each device looks up the array's device address with that device current
+ *     (cudaGetSymbolAddress); make that first call before any stream capture on that device.
+ *   - Every call shares the one array, which keeps the previous call's contents (the call clears what
+ *     must start at zero itself). Calls that overlap on the GPU, from any handle or stream, race on it. */
+apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particles, const float *tree,
+                                           const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                                           float *grad_particles, float *grad_stencils, apr_stream_t stream);
+
 /* Restricted stencils (Eq. restrict_stenc, K_{w_l} = R_l K_w P_l with block-average R_l and
  * piecewise-constant P_l): out[l - l_min][e] = sum_d w[d] * prod_axes c_s(d_a, e_a), where
  * c_s(d, e) = (1/s) #{x in [0, s): floor((x + d) / s) = e} and s = 2^(l_max - l). Host memory in and

@@ -68,6 +68,10 @@ bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
 
 }  // namespace
 
+namespace aprk {
+void set_last_message(const char *msg) { snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg); }
+}  // namespace aprk
+
 extern "C" {
 
 const char *apr_status_string(apr_status_t s) {

@@ -63,6 +63,9 @@ struct HostIndex {
 // receives a short reason on failure.
 apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
 
+// Record a short reason for the last failure on this thread (read by apr_last_error_message).
+void set_last_message(const char *msg);
+
 inline int64_t level_cells(int64_t D, int l_max, int l) {
     int64_t s = int64_t(1) << (l_max - l);
     return (D + s - 1) / s;
