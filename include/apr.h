@@ -71,6 +71,11 @@ typedef struct {
 #define APR_BC_REFLECT 0         /* half-sample symmetric reflection at each level's grid */
 #define APR_BC_ZERO 1            /* taps outside the level grid contribute zero */
 
+/* Work-item geometry: a convolution work item is a tile of APR_TILE_ZX x APR_TILE_ZX rows (z, x)
+ * of one level and one y-block of APR_BLOCK_Y cells; every row's particles are indexed per y-block. */
+#define APR_TILE_ZX 8
+#define APR_BLOCK_Y 64
+
 /* apr_export_structure selectors (copy to host memory) */
 #define APR_STRUCT_ROW_PTR 0       /* uint32 [R+1]    particle rows (CSR) */
 #define APR_STRUCT_Y_IDX 1         /* uint16 [N_p]    particle y */

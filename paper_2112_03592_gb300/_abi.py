@@ -14,6 +14,7 @@ APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY = 1, 2, 4
 APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
 APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS = 4, 5
+APR_TILE_ZX, APR_BLOCK_Y = 8, 64  # work-item geometry, as in include/apr.h
 
 # every function include/apr.h declares, with (restype, argtypes)
 _P, _I32, _I64, _U32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t

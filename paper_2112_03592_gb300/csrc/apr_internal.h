@@ -12,9 +12,10 @@ namespace aprk {
 // y-block of the brick index and of every work item: rows are cut into blocks of BY cells along y,
 // and each row stores, per block, the offset of its first element (a finer-grained xz_end).
 constexpr int BY = 64;
-// (z, x) rows per convolution tile at the tile's own level.
-constexpr int TZ = 4;
-constexpr int TX = 4;
+// (z, x) rows per convolution tile at the tile's own level (APR_TILE_ZX in apr.h).
+constexpr int TZ = APR_TILE_ZX;
+constexpr int TX = APR_TILE_ZX;
+static_assert(BY == APR_BLOCK_Y, "y-block must match apr.h");
 constexpr int MAXL = 24;
 
 // Geometry of one level, passed to kernels by value.

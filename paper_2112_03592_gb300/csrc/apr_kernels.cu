@@ -5,13 +5,16 @@
 //   y-block j of BY cells, the offset of the row's first particle with y >= j*BY. The tree has the
 //   same three arrays. A work item names a tile of TZ x TX rows and one y-block of one level.
 //
-// Every kernel finds the particles of a tile's neighbourhood from block offsets (no searches), reads
-// y indices and values with consecutive lanes on consecutive particles (coalesced), and stages an
-// isotropic level-l patch in shared memory (Sec. 3.5): same-level particles directly, the
-// coarser (level l-1) particle of each remaining cell piecewise-constant, and finer content through
-// the level-l tree node (Sec. 4.1, Fig. treeconv).
+// Convolution-type kernels stage an isotropic level-l patch (Sec. 3.5) of the tile plus an R-cell
+// halo in shared memory: same-level particles directly, the level-(l-1) particle of each remaining
+// cell piecewise-constant, and finer content through the level-l tree node (Sec. 4.1, Fig.
+// treeconv). The source elements of all patch rows are loaded in one flattened, unrolled loop
+// (consecutive lanes on consecutive particles, several loads in flight per thread), then the
+// stencil is applied to 8-cell windows along y that hold target particles, four threads per window,
+// with 16-byte shared-memory loads.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "apr_internal.h"
@@ -20,7 +23,23 @@ namespace aprk {
 
 namespace {
 
-constexpr int NT = 256;  // threads per block of every kernel below
+constexpr int NT = 256;                // threads per block of every kernel below
+constexpr int NWARP = NT / 32;
+constexpr int WIN = 8;                 // y cells per compute window
+constexpr int NWIN = BY / WIN;         // windows per interior row
+constexpr int NIR = TZ * TX;           // interior rows of a tile
+constexpr int NIW = NIR * NWIN;        // window slots of a tile
+constexpr int UNROLL = 8;              // element loads in flight per thread and staging step
+static_assert(NIW == 2 * NT, "window slots are scanned two per thread");
+static_assert(TZ % 2 == 0 && TX % 2 == 0, "tiles must be even-aligned (coarse cells)");
+
+// Block barrier. The warp is reconverged first: threads of one warp may reach this point at
+// different times after data-dependent loops, and the block barrier must be executed by converged
+// warps.
+__device__ __forceinline__ void block_sync() {
+    __syncwarp();
+    __syncthreads();
+}
 
 __device__ __forceinline__ int reflect_idx(int i, int d) {
     // half-sample symmetric reflection into [0, d), repeated for grids smaller than the stencil
@@ -30,483 +49,429 @@ __device__ __forceinline__ int reflect_idx(int i, int d) {
     return m >= d ? p - 1 - m : m;
 }
 
-// First particle of y-block j of row rr (level geometry g); j == nb gives the row end.
+// First element of y-block j of a row (particles or tree); j >= nb gives the row end.
+__device__ __forceinline__ uint32_t blk_start(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb,
+                                              int rr, int j) {
+    if (j >= nb) return rp[row0 + rr + 1];
+    return rp[row0 + rr] + off[off0 + rr * nb + j];
+}
+
 __device__ __forceinline__ uint32_t pblock(const DevLayout &L, const LevelGeo &g, int rr, int j) {
-    if (j >= g.nb) return L.row_ptr[g.row0 + rr + 1];
-    return L.row_ptr[g.row0 + rr] + L.off[g.off0 + rr * g.nb + j];
+    return blk_start(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, j);
 }
 
 __device__ __forceinline__ uint32_t tblock(const DevLayout &L, const LevelGeo &g, int rr, int j) {
-    if (j >= g.nb) return L.trow_ptr[g.trow0 + rr + 1];
-    return L.trow_ptr[g.trow0 + rr] + L.toff[g.toff0 + rr * g.nb + j];
+    return blk_start(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, j);
 }
 
-// Positions v in [-R, d + R) with reflect(v) == c: c itself and the out-of-grid positions that
-// mirror onto it (at most 2R of them). Returns the count.
-template <int R>
-__device__ __forceinline__ int preimages(int c, int d, int *out) {
-    int n = 0;
-    out[n++] = c;
-    for (int v = -R; v < 0; ++v)
-        if (reflect_idx(v, d) == c) out[n++] = v;
-    for (int v = d; v < d + R; ++v)
-        if (reflect_idx(v, d) == c) out[n++] = v;
-    return n;
+// Index range [lo, hi) of a row containing every element with y in [ya, yb) (ya < yb), plus at
+// most BY/2 extra elements on each side (callers filter by y). Uses the per-block offsets only:
+// at most BY - ra elements of block ja lie at or after ya, at most rb elements of block jb before yb.
+__device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb, int rr,
+                                          int ya, int yb, int &lo, int &hi) {
+    const int rs = int(rp[row0 + rr]), re = int(rp[row0 + rr + 1]);
+    const int ja = ya / BY, ra = ya - ja * BY;
+    const int jb = yb / BY, rb = yb - jb * BY;
+    int a = ra <= BY / 2 ? int(blk_start(rp, off, row0, off0, nb, rr, ja))
+                         : int(blk_start(rp, off, row0, off0, nb, rr, ja + 1)) - (BY - ra);
+    int b = rb <= BY / 2 ? int(blk_start(rp, off, row0, off0, nb, rr, jb)) + rb
+                         : int(blk_start(rp, off, row0, off0, nb, rr, jb + 1));
+    a = max(a, rs);
+    b = min(b, re);
+    lo = a;
+    hi = max(a, b);
 }
 
 template <int R>
 struct Geo {
     static constexpr int K = 2 * R + 1;
     static constexpr int K3 = K * K * K;
-    // forward patch: tile rows plus R halo rows; y-block plus R halo cells
-    static constexpr int PZ = TZ + 2 * R, PX = TX + 2 * R, PY = BY + 2 * R, PYS = PY + 1;
+    static constexpr int NPAIR = K * K;                    // (dz, dx) pairs
+    static constexpr int PZ = TZ + 2 * R, PX = TX + 2 * R, PY = BY + 2 * R;
+    static constexpr int PYS = (PY + 3) / 4 * 4;           // row stride, 16-byte multiple
     static constexpr int NROW = PZ * PX;
-    static constexpr int NSEG = 3 * NROW;  // particle, tree and parent-level segment per patch row
-    // backward gradient patch: halo 2R (taps of halo cells reach 2R)
-    static constexpr int GZ = TZ + 4 * R, GX = TX + 4 * R, GY = BY + 4 * R, GYS = GY + 1;
-    static constexpr int NGROW = GZ * GX;
+    static constexpr int NSEG = 3 * NROW;                  // particle, tree, coarser-particle source per row
+    static constexpr int NRSEG = 2 * NIR + NIR / 4;        // backward routing: particles, tree, coarser particles
+    static_assert(WIN + 2 * R <= 12, "a window's taps must fit three 16-byte loads");
+    static_assert((NWIN - 1) * WIN + 12 <= PYS, "window loads stay inside the row");
+    static_assert(NSEG <= 2 * NT && NROW + NRSEG <= 2 * NT, "segments are scanned two per thread");
 };
 
+// Block-wide exclusive scan of values held two per thread (entries 2t, 2t+1): writes pre[0..n]
+// (pre[n] = total). n <= 2*NT. Starts and ends with a barrier.
+__device__ void block_scan2(int c0, int c1, int n, int *pre, int *warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = c0 + c1;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    block_sync();
+    if (lane == 31) warp_tot[warp] = incl;
+    block_sync();
+    if (tid == 0) {
+        int acc = 0;
+        for (int w = 0; w < NWARP; ++w) {
+            const int v = warp_tot[w];
+            warp_tot[w] = acc;
+            acc += v;
+        }
+        warp_tot[NWARP] = acc;
+    }
+    block_sync();
+    const int excl = warp_tot[warp] + incl - s;
+    if (2 * tid < n) pre[2 * tid] = excl;
+    if (2 * tid + 1 < n) pre[2 * tid + 1] = excl + c0;
+    if (tid == 0) pre[n] = warp_tot[NWARP];
+    block_sync();
+}
+
+struct SlotYV {
+    int y;
+    float v;
+};
+
+// Loads y and value of element i of segment seg; segments [t0, t1) are tree segments.
+struct YVLoader {
+    using Slot = SlotYV;
+    const uint16_t *py, *ty;
+    const float *pv, *tv;
+    int t0, t1;
+    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
+        const bool t = seg >= t0 && seg < t1;
+        s.y = t ? int(ty[i]) : int(py[i]);
+        s.v = t ? tv[i] : pv[i];
+    }
+};
+
+// Flattened loop over the elements of nseg segments (segment s: global indices seg_lo[s] ..
+// seg_lo[s] + pre[s+1] - pre[s]). Each warp takes a contiguous share, lanes are strided, and the
+// loads of UNROLL elements per thread are issued before any of them is used.
+template <typename Load, typename Use>
+__device__ __forceinline__ void for_each_element(const int *seg_lo, const int *pre, int nseg, const Load &load, Use use) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int E0 = pre[0], E1 = pre[nseg];
+    const int share = (E1 - E0 + NWARP - 1) / NWARP;
+    const int ea = E0 + warp * share, eb = min(E1, ea + share);
+    // the trip count depends on the warp only, so the lanes stay converged
+    int lo = 0, hi = nseg;  // largest s with pre[s] <= ea + lane
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= ea + lane) lo = mid;
+        else hi = mid;
+    }
+    int seg = lo;
+    for (int base = ea; base < eb; base += 32 * UNROLL) {
+        int sg[UNROLL], ix[UNROLL];
+        typename Load::Slot slot[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int eu = base + lane + 32 * u;
+            sg[u] = -1;
+            ix[u] = 0;
+            if (eu < eb) {
+                while (pre[seg + 1] <= eu) ++seg;
+                sg[u] = seg;
+                ix[u] = seg_lo[seg] + (eu - pre[seg]);
+                load(seg, ix[u], slot[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (sg[u] >= 0) use(sg[u], ix[u], slot[u]);
+    }
+}
+
+// Deterministic compaction of the windows w (0 <= w < NIW) with flag(w) into act[0..*nact).
+template <typename Flag>
+__device__ __forceinline__ void compact_windows(Flag flag, unsigned short *act, int *pre, int *warp_tot, int *nact) {
+    const int tid = threadIdx.x;
+    const int f0 = flag(2 * tid) ? 1 : 0, f1 = flag(2 * tid + 1) ? 1 : 0;
+    block_scan2(f0, f1, NIW, pre, warp_tot);
+    if (f0) act[pre[2 * tid]] = (unsigned short)(2 * tid);
+    if (f1) act[pre[2 * tid + 1]] = (unsigned short)(2 * tid + 1);
+    if (tid == 0) *nact = pre[NIW];
+    block_sync();
+}
+
 // ------------------------------------------------------------------------------------------------
-// Forward patch staging shared by the convolution and the stencil-gradient kernels.
-// Fills patch[NROW][PYS] with the isotropic level-l values of cells
-//   z in [tz*TZ - R, tz*TZ + TZ + R), x likewise, y in [yb*BY - R, yb*BY + BY + R)
-// (rows outside the grid: reflected rows or zeros; cells outside in y: reflected cells or zeros).
-// Also lists the tile's target particles (level-l particles of the TZ x TX interior rows inside
-// y-block yb): tgt_lo[r], tgt_pre[r] (prefix counts, tgt_pre[TZ*TX] = total).
+// Shared-memory image of a staged forward tile.
 // ------------------------------------------------------------------------------------------------
 template <int R>
-__device__ void stage_forward_patch(const DevLayout &L, const Item &it, const float *__restrict__ vals,
-                                    const float *__restrict__ tree, int bc, float *patch, int *seg_lo,
-                                    int *seg_hi, int *row_valid, int *tgt_lo, int *tgt_pre) {
+struct PatchSmem {
+    using G = Geo<R>;
+    float patch[G::NROW * G::PYS];       // first member: 16-byte aligned
+    __align__(16) float w8[G::NPAIR * 8];  // taps of every (dz, dx) pair, padded to 8
+    int seg_lo[G::NSEG];
+    int seg_meta[G::NSEG];               // patch row | kind << 8 | (interior row + 1) << 10
+    int pre[(G::NSEG > NIW ? G::NSEG : NIW) + 1];
+    int warp_tot[NWARP + 1];
+    float red[NWARP][32][WIN];           // partial window sums of the second half of the stencil rows
+    unsigned wmask[NIW];                 // target bits of every window
+    int wfirst[NIW];                     // first target (particle index) of every window
+    unsigned short act[NIW];             // active windows, in window order
+    int nact;
+    int boundary;                        // the tile with its halo reaches outside the grid
+};
+
+// Stage the forward patch of item `it` (Sec. 3.5): patch rows z in [z0-R, z0+TZ+R), x likewise, y in
+// [y0-R, y0+BY+R); rows outside the grid are reflected rows (or zeros), cells outside the grid in y
+// are reflected cells (or zeros). Marks the target windows (level-l particles of the interior rows in
+// y-block yb) and lists the active ones. If gwin is given, also stores dL/dout of every target at
+// gwin[row * BY + (y - y0)] (zero elsewhere).
+template <int R>
+__device__ void stage_patch(const DevLayout &L, const Item &it, const float *__restrict__ vals,
+                            const float *__restrict__ tree, int bc, PatchSmem<R> &S,
+                            const float *__restrict__ gout = nullptr, float *gwin = nullptr) {
     using G = Geo<R>;
     const int tid = threadIdx.x;
     const int l = it.l;
     const LevelGeo g = L.geo[l];
-    const int yw = it.yb * BY - R;  // level y of patch column 0
+    const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY;
+    const int yw = y0 - R;  // level y of patch column 0
 
-    for (int i = tid; i < G::NROW * G::PYS; i += NT) patch[i] = __int_as_float(0x7fc00000);  // NaN: unfilled
-    if (tid < G::NSEG) {
-        const int s = tid, kind = s / G::NROW, pr = s % G::NROW;
-        const int a = pr / G::PX, b = pr % G::PX;
-        int z = it.a * TZ - R + a, x = it.b * TX - R + b;
+    for (int i = tid; i < NIW; i += NT) {
+        S.wmask[i] = 0u;
+        S.wfirst[i] = INT_MAX;
+    }
+    if (gwin)
+        for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(gwin)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0)
+        S.boundary = (z0 - R < 0 || x0 - R < 0 || yw < 0 || z0 + TZ + R > g.dz || x0 + TX + R > g.dx || yw + G::PY > g.dy);
+
+    // segment bounds, two per thread (entries 2t, 2t+1) for the scan
+    int cnt[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = 2 * tid + h;
+        if (s >= G::NSEG) break;
+        const int kind = s / G::NROW, pr = s % G::NROW;
+        int z = z0 - R + pr / G::PX, x = x0 - R + pr % G::PX;
         const bool inside = z >= 0 && z < g.dz && x >= 0 && x < g.dx;
-        const bool use = inside || bc == APR_BC_REFLECT;
-        uint32_t lo = 0, hi = 0;
-        if (use) {
+        int lo = 0, hi = 0;
+        if (inside || bc == APR_BC_REFLECT) {
             z = reflect_idx(z, g.dz);
             x = reflect_idx(x, g.dx);
-            const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);  // in-grid y range of the patch
+            const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
             const int rr = z * g.dx + x;
             if (kind == 0) {
-                lo = pblock(L, g, rr, ylo / BY);
-                hi = pblock(L, g, rr, (yhi - 1) / BY + 1);
+                row_range(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, ylo, yhi, lo, hi);
             } else if (kind == 1) {
-                if (l < L.l_max) {
-                    lo = tblock(L, g, rr, ylo / BY);
-                    hi = tblock(L, g, rr, (yhi - 1) / BY + 1);
-                }
+                if (l < L.l_max) row_range(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, ylo, yhi, lo, hi);
             } else if (l > L.l_min) {
                 const LevelGeo gp = L.geo[l - 1];
                 const int prr = (z >> 1) * gp.dx + (x >> 1);
-                lo = pblock(L, gp, prr, (ylo >> 1) / BY);
-                hi = pblock(L, gp, prr, ((yhi - 1) >> 1) / BY + 1);
+                row_range(L.row_ptr, L.off, gp.row0, gp.off0, gp.nb, prr, ylo >> 1, ((yhi - 1) >> 1) + 1, lo, hi);
             }
         }
-        seg_lo[s] = int(lo);
-        seg_hi[s] = int(hi);
-        if (kind == 0) row_valid[pr] = use ? 1 : 0;
+        S.seg_lo[s] = lo;
+        cnt[h] = hi - lo;
+        // interior row of a particle segment whose particles are targets (+1; 0: none)
+        const int a = pr / G::PX - R, b = pr % G::PX - R;
+        const int trow = (kind == 0 && a >= 0 && a < TZ && b >= 0 && b < TX && z0 + a < g.dz && x0 + b < g.dx)
+                             ? a * TX + b + 1 : 0;
+        S.seg_meta[s] = pr | (kind << 8) | (trow << 10);
     }
-    if (tid < TZ * TX) {
-        const int z = it.a * TZ + tid / TX, x = it.b * TX + tid % TX;
-        uint32_t lo = 0, hi = 0;
-        if (z < g.dz && x < g.dx) {
-            const int rr = z * g.dx + x;
-            lo = pblock(L, g, rr, it.yb);
-            hi = pblock(L, g, rr, it.yb + 1);
-        }
-        tgt_lo[tid] = int(lo);
-        tgt_pre[tid + 1] = int(hi - lo);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        tgt_pre[0] = 0;
-        for (int r = 0; r < TZ * TX; ++r) tgt_pre[r + 1] += tgt_pre[r];
-    }
-    // fill: one warp per segment, consecutive lanes on consecutive particles
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int s = warp; s < G::NSEG; s += NT / 32) {
-        const int lo = seg_lo[s], hi = seg_hi[s];
-        const int kind = s / G::NROW;
-        float *prow = patch + (s % G::NROW) * G::PYS;
+    block_scan2(cnt[0], cnt[1], G::NSEG, S.pre, S.warp_tot);
+
+    const YVLoader ld{L.y, L.ty, vals, tree, G::NROW, 2 * G::NROW};
+    for_each_element(S.seg_lo, S.pre, G::NSEG, ld, [&](int seg, int i, SlotYV &s) {
+        const int meta = S.seg_meta[seg];
+        const int kind = (meta >> 8) & 3;
+        float *prow = S.patch + (meta & 255) * G::PYS;
         if (kind < 2) {
-            const uint16_t *ys = kind == 0 ? L.y : L.ty;
-            const float *src = kind == 0 ? vals : tree;
-            for (int i = lo + lane; i < hi; i += 32) {
-                const int pos = int(ys[i]) - yw;
-                const float v = src[i];
-                if (pos >= 0 && pos < G::PY) prow[pos] = v;
+            const int pos = s.y - yw;
+            if (pos >= 0 && pos < G::PY) prow[pos] = s.v;
+            const int trow = (meta >> 10) - 1;
+            const int yr = s.y - y0;
+            if (trow >= 0 && yr >= 0 && yr < BY) {
+                // a target: level-l particle of an interior row inside y-block yb
+                const int w = trow * NWIN + yr / WIN;
+                atomicOr(&S.wmask[w], 1u << (yr % WIN));
+                atomicMin(&S.wfirst[w], i);
+                if (gwin) gwin[trow * BY + yr] = gout[i];
             }
         } else {
-            for (int i = lo + lane; i < hi; i += 32) {
-                const int yy = 2 * int(L.y[i]);  // first level-l cell of the coarser particle
-                const float v = vals[i];
-                const int pos = yy - yw;
-                if (pos >= 0 && pos < G::PY && yy < g.dy) prow[pos] = v;
-                if (pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy) prow[pos + 1] = v;
+            const int yy = 2 * s.y;  // first level-l cell of the coarser particle
+            const int pos = yy - yw;
+            if (pos >= 0 && pos < G::PY && yy < g.dy) prow[pos] = s.v;
+            if (pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy) prow[pos + 1] = s.v;
+        }
+    });
+    block_sync();
+    if (S.boundary) {
+        // rows outside the grid with zero boundary: zero; cells outside the grid in y (the first
+        // max(0, -yw) and the last max(0, yw + PY - dy) of a row): mirror (reflect) or zero
+        const int nlo = max(0, -yw), hi0 = min(G::PY, g.dy - yw);
+        for (int pr = tid; pr < G::NROW; pr += NT) {
+            const int z = z0 - R + pr / G::PX, x = x0 - R + pr % G::PX;
+            float *prow = S.patch + pr * G::PYS;
+            if (bc != APR_BC_REFLECT && (z < 0 || z >= g.dz || x < 0 || x >= g.dx)) {
+                for (int pos = 0; pos < G::PY; ++pos) prow[pos] = 0.f;
+                continue;
             }
+            for (int pos = 0; pos < nlo; ++pos)
+                prow[pos] = bc == APR_BC_REFLECT ? prow[reflect_idx(yw + pos, g.dy) - yw] : 0.f;
+            for (int pos = hi0; pos < G::PY; ++pos)
+                prow[pos] = bc == APR_BC_REFLECT ? prow[reflect_idx(yw + pos, g.dy) - yw] : 0.f;
         }
     }
-    __syncthreads();
-    // cells outside the grid in y: mirror (reflect) or zero; rows outside with zero boundary: zero
-    for (int i = tid; i < G::NROW * G::PY; i += NT) {
-        const int pr = i / G::PY, pos = i % G::PY;
-        float *prow = patch + pr * G::PYS;
-        if (!row_valid[pr]) {
-            prow[pos] = 0.f;
-            continue;
+    block_sync();
+    compact_windows([&](int w) { return S.wmask[w] != 0u; }, S.act, S.pre, S.warp_tot, &S.nact);
+}
+
+// Stencil taps of level l into w8[pair][0..K), optionally flipped (the transpose uses w[-e]).
+template <int R>
+__device__ void load_taps(const float *__restrict__ stencils, int l_idx, bool flip, float *w8) {
+    using G = Geo<R>;
+    for (int i = threadIdx.x; i < G::NPAIR * 8; i += NT) {
+        const int pair = i / 8, t = i % 8;
+        float v = 0.f;
+        if (t < G::K) {
+            const int e = pair * G::K + t;
+            v = stencils[l_idx * G::K3 + (flip ? G::K3 - 1 - e : e)];
         }
-        const int yy = yw + pos;
-        if (yy < 0 || yy >= g.dy) prow[pos] = bc == APR_BC_REFLECT ? prow[reflect_idx(yy, g.dy) - yw] : 0.f;
+        w8[i] = v;
     }
-    __syncthreads();
+}
+
+// acc[j] += sum over stencil rows (dz, dx) = pairs [P0, P1) of sum_dy w8[(dz,dx)][dy] *
+// P[row (ia+dz, ib+dx)][col + j + dy], j < WIN. base points at P[row (ia, ib)][col]; the loop is
+// unrolled so every row offset is a constant.
+template <int R, int P0, int P1>
+__device__ __forceinline__ void window_rows(const float *base, const float *w8, float acc[WIN]) {
+    using G = Geo<R>;
+#pragma unroll
+    for (int pair = P0; pair < P1; ++pair) {
+        const int dz = pair / G::K, dx = pair % G::K;
+        const float4 *src = reinterpret_cast<const float4 *>(base + (dz * G::PX + dx) * G::PYS);
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+        const float4 wa = *reinterpret_cast<const float4 *>(w8 + pair * 8);
+        const float wt[5] = {wa.x, wa.y, wa.z, wa.w, w8[pair * 8 + 4]};
+#pragma unroll
+        for (int j = 0; j < WIN; ++j)
+#pragma unroll
+            for (int t = 0; t < G::K; ++t) acc[j] = fmaf(wt[t], v[j + t], acc[j]);
+    }
+}
+
+// Stencil sums of the active windows act[0..nact) of a patch: warps 2v and 2v+1 take the same 32
+// windows, the first half of the stencil rows and the second half; the second writes its partial
+// sums to red[], the first adds them (fixed order) and calls emit(window, acc).
+template <int R, typename Emit>
+__device__ __forceinline__ void windows_apply(const float *patch, const float *w8, const unsigned short *act, int nact,
+                                              float (*red)[32][WIN], Emit emit) {
+    using G = Geo<R>;
+    constexpr int HALF = (G::NPAIR + 1) / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = warp & 1, grp = warp >> 1;
+    for (int base = 0; base < nact; base += 32 * (NWARP / 2)) {
+        const int a = base + grp * 32 + lane;
+        float acc[WIN];
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
+        int w = 0;
+        if (a < nact) {
+            w = act[a];
+            const int r = w / NWIN;
+            const float *b = patch + ((r / TX) * G::PX + (r % TX)) * G::PYS + (w % NWIN) * WIN;
+            if (half == 0) window_rows<R, 0, HALF>(b, w8, acc);
+            else window_rows<R, HALF, G::NPAIR>(b, w8, acc);
+        }
+        if (half == 1)
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) red[warp][lane][j] = acc[j];
+        block_sync();
+        if (half == 0 && a < nact) {
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) acc[j] += red[warp + 1][lane][j];
+            emit(w, acc);
+        }
+        block_sync();
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
-// APR convolution, one block per work item (Sec. 4.1; Sec. 5.2 with a tile of TZ x TX rows and a
-// y-block instead of the paper's 4x4 / 8x8 warp grid and sliding buffer).
+// APR convolution (Sec. 4.1; Sec. 5.2 with 8x8-row tiles and 64-cell y-blocks instead of the
+// paper's 4x4 / 8x8 warp grid with a sliding buffer).
 // ------------------------------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                      const float *__restrict__ vals,
-                                                      const float *__restrict__ tree,
-                                                      const float *__restrict__ stencils, int bc,
-                                                      float *__restrict__ out) {
-    using G = Geo<R>;
-    __shared__ float patch[G::NROW * G::PYS];
-    __shared__ float w[G::K3];
-    __shared__ int seg_lo[G::NSEG], seg_hi[G::NSEG], row_valid[G::NROW];
-    __shared__ int tgt_lo[TZ * TX], tgt_pre[TZ * TX + 1];
-    const Item it = items[blockIdx.x];
-    for (int i = threadIdx.x; i < G::K3; i += NT) w[i] = stencils[(it.l - L.l_min) * G::K3 + i];
-    stage_forward_patch<R>(L, it, vals, tree, bc, patch, seg_lo, seg_hi, row_valid, tgt_lo, tgt_pre);
-
-    const int yw = it.yb * BY - R;
-    const int total = tgt_pre[TZ * TX];
-    for (int t = threadIdx.x; t < total; t += NT) {
-        int r = 0;
-        while (tgt_pre[r + 1] <= t) ++r;
-        const int i = tgt_lo[r] + (t - tgt_pre[r]);
-        const int pos = int(L.y[i]) - yw - R;  // patch column of tap dy = -R
-        const int ia = r / TX, ib = r % TX;
-        float acc = 0.f;
-#pragma unroll
-        for (int dz = 0; dz < G::K; ++dz)
-#pragma unroll
-            for (int dx = 0; dx < G::K; ++dx) {
-                const float *prow = patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + pos;
-#pragma unroll
-                for (int dy = 0; dy < G::K; ++dy) acc = fmaf(w[(dz * G::K + dx) * G::K + dy], prow[dy], acc);
-            }
-        out[i] = acc;
-    }
-}
-
-// ------------------------------------------------------------------------------------------------
-// APR tree restriction for one level l (Sec. 3.4): block per tree brick (l, z, x, yb). The children
-// of the brick's nodes live in the 2x2 child rows of level l+1, y-blocks 2yb and 2yb+1; each child
-// value goes to a slot (a, b, y&1) of its parent, then every node averages its in-grid slots in a
-// fixed order.
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           const float *__restrict__ vals,
-                                                           float *__restrict__ tree) {
-    __shared__ float slot[8][BY];
-    __shared__ int seg_lo[8], seg_hi[8];
-    const Item it = items[blockIdx.x];
-    const int l = it.l, tid = threadIdx.x;
-    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
-    const int y0 = it.yb * BY;
-    if (tid < 8) {
-        const int kind = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
-        const int cz = 2 * it.a + a, cx = 2 * it.b + b;
-        uint32_t lo = 0, hi = 0;
-        if (cz < gc.dz && cx < gc.dx) {
-            const int crr = cz * gc.dx + cx;
-            const int j0 = 2 * it.yb, j1 = min(2 * it.yb + 2, gc.nb);
-            if (kind == 0) {
-                lo = pblock(L, gc, crr, j0);
-                hi = pblock(L, gc, crr, j1);
-            } else if (l + 1 < L.l_max) {
-                lo = tblock(L, gc, crr, j0);
-                hi = tblock(L, gc, crr, j1);
-            }
-        }
-        seg_lo[tid] = int(lo);
-        seg_hi[tid] = int(hi);
-    }
-    __syncthreads();
-    {
-        const int s = tid >> 5, lane = tid & 31;  // 8 warps, one per child segment
-        const int kind = s >> 2, ab = s & 3;
-        const uint16_t *ys = kind == 0 ? L.y : L.ty;
-        const float *src = kind == 0 ? vals : tree;
-        for (int i = seg_lo[s] + lane; i < seg_hi[s]; i += 32) {
-            const int yv = ys[i];
-            slot[ab * 2 + (yv & 1)][(yv >> 1) - y0] = src[i];
-        }
-    }
-    __syncthreads();
-    const int rr = it.a * g.dx + it.b;
-    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
-    for (int t = tlo + tid; t < thi; t += NT) {
-        const int yv = L.ty[t];
-        float s = 0.f;
-        int n = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int a = c >> 2, b = (c >> 1) & 1, e = c & 1;
-            if (2 * it.a + a < gc.dz && 2 * it.b + b < gc.dx && 2 * yv + e < gc.dy) {
-                s += slot[(a * 2 + b) * 2 + e][yv - y0];
-                ++n;
-            }
-        }
-        tree[t] = s / float(n);
-    }
-}
-
-// ------------------------------------------------------------------------------------------------
-// Backward, data part: for every cell c of the tile interior that a target can reach,
-//   H(c) = sum over preimages c' of c under the boundary reflection of sum_e w[e] g(c' - e),
-// g being dL/dout at the level-l particles (zero elsewhere). H is then routed to the source that
-// supplied cell c in the forward patch: the level-l particle (atomic add: it receives exactly one
-// more term, from the next finer level), the level-l tree node (store), or the level-(l-1) particle
-// containing c (sum over its cells in this tile, one atomic add).
-// ------------------------------------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(NT) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           const float *__restrict__ stencils, int bc,
-                                                           const float *__restrict__ gout,
-                                                           float *__restrict__ gp, float *__restrict__ gt) {
-    using G = Geo<R>;
+__global__ void __launch_bounds__(NT, 3) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                         const float *__restrict__ vals,
+                                                         const float *__restrict__ tree,
+                                                         const float *__restrict__ stencils, int bc,
+                                                         float *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *gpatch = reinterpret_cast<float *>(smem_raw);                   // [NGROW][GYS]
-    float *H = gpatch + G::NGROW * G::GYS;                                 // [TZ*TX][BY]
-    unsigned long long *tmask = reinterpret_cast<unsigned long long *>(H + TZ * TX * BY);  // [NGROW][2]
-    unsigned long long *need = tmask + 2 * G::NGROW;                       // [TZ*TX]
-    __shared__ float w[G::K3];
-    __shared__ int seg_lo[3 * TZ * TX], seg_hi[3 * TZ * TX];
-    __shared__ int gseg_lo[G::NGROW], gseg_hi[G::NGROW];
-
+    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    const int l = it.l, tid = threadIdx.x;
-    const LevelGeo g = L.geo[l];
-    const int y0 = it.yb * BY;
-    const int gw0 = y0 - 2 * R;  // level y of gradient-patch column 0
-    const int z0 = it.a * TZ, x0 = it.b * TX;
-
-    for (int i = tid; i < G::K3; i += NT) w[i] = stencils[(l - L.l_min) * G::K3 + i];
-    for (int i = tid; i < G::NGROW * G::GYS; i += NT) gpatch[i] = 0.f;
-    for (int i = tid; i < 2 * G::NGROW; i += NT) tmask[i] = 0ull;
-    for (int i = tid; i < G::NGROW; i += NT) {
-        const int z = z0 - 2 * R + i / G::GX, x = x0 - 2 * R + i % G::GX;
-        uint32_t lo = 0, hi = 0;
-        if (z >= 0 && z < g.dz && x >= 0 && x < g.dx) {  // gradient is zero outside the grid
-            const int rr = z * g.dx + x;
-            const int ylo = max(gw0, 0), yhi = min(gw0 + G::GY, g.dy);
-            if (yhi > ylo) {
-                lo = pblock(L, g, rr, ylo / BY);
-                hi = pblock(L, g, rr, (yhi - 1) / BY + 1);
-            }
-        }
-        gseg_lo[i] = int(lo);
-        gseg_hi[i] = int(hi);
-    }
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int s = warp; s < G::NGROW; s += NT / 32) {
-        for (int i = gseg_lo[s] + lane; i < gseg_hi[s]; i += 32) {
-            const int pos = int(L.y[i]) - gw0;
-            if (pos >= 0 && pos < G::GY) {
-                gpatch[s * G::GYS + pos] = gout[i];
-                atomicOr(&tmask[2 * s + (pos >> 6)], 1ull << (pos & 63));
-            }
-        }
-    }
-    __syncthreads();
-    // cells of the interior that need H: within R (Chebyshev) of a target, or (reflect) close
-    // enough to the grid boundary to receive a mirrored contribution
-    if (tid < TZ * TX) {
-        const int ia = tid / TX, ib = tid % TX;
-        unsigned long long m = 0ull;
-        for (int dz = -R; dz <= R; ++dz)
-            for (int dx = -R; dx <= R; ++dx) {
-                const int s = (ia + 2 * R + dz) * G::GX + (ib + 2 * R + dx);
-                const unsigned long long m0 = tmask[2 * s], m1 = tmask[2 * s + 1];
-                // window bits [2R, 2R + BY) of the 128-bit row mask, dilated by +-R
-                for (int d = -R; d <= R; ++d) {
-                    const int sh = 2 * R + d;  // bit of window cell 0 shifted by d
-                    m |= (m0 >> sh) | (sh > 0 ? (m1 << (64 - sh)) : 0ull);
-                }
-            }
-        const int z = z0 + ia, x = x0 + ib;
-        if (z >= g.dz || x >= g.dx) m = 0ull;
-        else if (bc == APR_BC_REFLECT) {
-            // cells within R of the grid boundary have mirrored preimages; take them all
-            if (z < R || z >= g.dz - R || x < R || x >= g.dx - R) {
-                m = ~0ull;
-            } else {
-                for (int j = 0; j < BY; ++j) {
-                    const int yy = y0 + j;
-                    if (yy < R || yy >= g.dy - R) m |= 1ull << j;
-                }
-            }
-        }
-        // cells outside the grid in y are not interior cells
-        const int nvalid = min(BY, g.dy - y0);
-        if (nvalid < BY) m &= (nvalid <= 0) ? 0ull : ((1ull << nvalid) - 1ull);
-        need[tid] = m;
-    }
-    __syncthreads();
-    // H at needed interior cells
-    for (int c = tid; c < TZ * TX * BY; c += NT) {
-        const int r = c / BY, j = c % BY;
-        float h = 0.f;
-        if ((need[r] >> j) & 1ull) {
-            const int ia = r / TX, ib = r % TX;
-            const int z = z0 + ia, x = x0 + ib, yy = y0 + j;
-            const bool mirror = bc == APR_BC_REFLECT &&
-                                (z < R || z >= g.dz - R || x < R || x >= g.dx - R || yy < R || yy >= g.dy - R);
-            if (!mirror) {
+    load_taps<R>(stencils, it.l - L.l_min, false, S.w8);
+    stage_patch<R>(L, it, vals, tree, bc, S);
+    windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
+        const unsigned m = S.wmask[w];
+        const int first = S.wfirst[w];
 #pragma unroll
-                for (int dz = 0; dz < G::K; ++dz)
-#pragma unroll
-                    for (int dx = 0; dx < G::K; ++dx) {
-                        // cell (c - e): gradient row (ia + 2R - (dz - R)), column (j + 2R - (dy - R))
-                        const float *grow = gpatch + ((ia + 3 * R - dz) * G::GX + (ib + 3 * R - dx)) * G::GYS + j + 3 * R;
-#pragma unroll
-                        for (int dy = 0; dy < G::K; ++dy) h = fmaf(w[(dz * G::K + dx) * G::K + dy], grow[-dy], h);
-                    }
-            } else {
-                // preimages per axis: c itself and every out-of-grid position in [-R, d+R) that
-                // reflects onto it
-                int pz[2 * R + 1], px[2 * R + 1], py[2 * R + 1];
-                const int nz = preimages<R>(z, g.dz, pz), nx = preimages<R>(x, g.dx, px),
-                          ny = preimages<R>(yy, g.dy, py);
-#pragma unroll 1
-                for (int iz = 0; iz < nz; ++iz)
-#pragma unroll 1
-                    for (int ix = 0; ix < nx; ++ix)
-#pragma unroll 1
-                        for (int iy = 0; iy < ny; ++iy)
-#pragma unroll 1
-                            for (int dz = 0; dz < G::K; ++dz)
-#pragma unroll 1
-                                for (int dx = 0; dx < G::K; ++dx)
-#pragma unroll 1
-                                    for (int dy = 0; dy < G::K; ++dy) {
-                                        const int sz = pz[iz] - (dz - R) - (z0 - 2 * R);
-                                        const int sx = px[ix] - (dx - R) - (x0 - 2 * R);
-                                        const int sy = py[iy] - (dy - R) - gw0;
-                                        if (sz < 0 || sz >= G::GZ || sx < 0 || sx >= G::GX || sy < 0 || sy >= G::GY) continue;
-                                        h = fmaf(w[(dz * G::K + dx) * G::K + dy], gpatch[(sz * G::GX + sx) * G::GYS + sy], h);
-                                    }
-            }
-        }
-        H[c] = h;
-    }
-    // segments of the sources of interior cells
-    if (tid < 3 * TZ * TX) {
-        const int kind = tid / (TZ * TX), r = tid % (TZ * TX);
-        uint32_t lo = 0, hi = 0;
-        if (kind < 2) {
-            const int z = z0 + r / TX, x = x0 + r % TX;
-            if (z < g.dz && x < g.dx) {
-                const int rr = z * g.dx + x;
-                if (kind == 0) {
-                    lo = pblock(L, g, rr, it.yb);
-                    hi = pblock(L, g, rr, it.yb + 1);
-                } else if (l < L.l_max) {
-                    lo = tblock(L, g, rr, it.yb);
-                    hi = tblock(L, g, rr, it.yb + 1);
-                }
-            }
-        } else if (l > L.l_min && r < (TZ / 2) * (TX / 2)) {
-            const LevelGeo gq = L.geo[l - 1];
-            const int pz = z0 / 2 + r / (TX / 2), px = x0 / 2 + r % (TX / 2);
-            if (pz < gq.dz && px < gq.dx) {
-                const int prr = pz * gq.dx + px;
-                const int pj = (y0 / 2) / BY;
-                lo = pblock(L, gq, prr, pj);
-                hi = pblock(L, gq, prr, pj + 1);
-            }
-        }
-        seg_lo[tid] = int(lo);
-        seg_hi[tid] = int(hi);
-    }
-    __syncthreads();
-    for (int s = warp; s < 3 * TZ * TX; s += NT / 32) {
-        const int kind = s / (TZ * TX), r = s % (TZ * TX);
-        for (int i = seg_lo[s] + lane; i < seg_hi[s]; i += 32) {
-            if (kind == 0) {
-                atomicAdd(&gp[i], H[r * BY + (int(L.y[i]) - y0)]);
-            } else if (kind == 1) {
-                gt[i] = H[r * BY + (int(L.ty[i]) - y0)];
-            } else {
-                const int py = int(L.y[i]);
-                const int j0 = 2 * py - y0;  // first level-l cell column of the coarser particle
-                if (j0 < 0 || j0 >= BY) continue;
-                const int pa = r / (TX / 2), pb = r % (TX / 2);
-                float s2 = 0.f;
-                for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b)
-                        for (int e = 0; e < 2; ++e) {
-                            const int ia = 2 * pa + a, ib = 2 * pb + b;
-                            if (z0 + ia < g.dz && x0 + ib < g.dx && y0 + j0 + e < g.dy)
-                                s2 += H[(ia * TX + ib) * BY + j0 + e];
-                        }
-                atomicAdd(&gp[i], s2);
-            }
-        }
-    }
+        for (int j = 0; j < WIN; ++j)
+            if ((m >> j) & 1u) out[first + __popc(m & ((1u << j) - 1u))] = acc[j];
+    });
 }
 
 // ------------------------------------------------------------------------------------------------
-// Backward, stencil part: per work item, partial[e][item] = sum over the item's targets p of
-// g_p * u_l(p + e) (fixed order); the per-level sums follow in stencil_grad_reduce_kernel.
+// Backward, stencil part: per work item, partial[e][item] = sum over its targets p of g_p *
+// u_l(p + e) (fixed order); stencil_grad_reduce_kernel then sums the items of every level.
 // ------------------------------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                              int n_items, const float *__restrict__ vals,
-                                                              const float *__restrict__ tree, int bc,
-                                                              const float *__restrict__ gout,
-                                                              float *__restrict__ partial) {
+struct StencilGradSmem {
+    PatchSmem<R> P;
+    __align__(16) float gwin[NIR * BY];
+    float red[(NT / Geo<R>::NPAIR) * Geo<R>::NPAIR * Geo<R>::K];
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT, 2) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                                 int n_items, const float *__restrict__ vals,
+                                                                 const float *__restrict__ tree, int bc,
+                                                                 const float *__restrict__ gout,
+                                                                 float *__restrict__ partial) {
     using G = Geo<R>;
-    __shared__ float patch[G::NROW * G::PYS];
-    __shared__ int seg_lo[G::NSEG], seg_hi[G::NSEG], row_valid[G::NROW];
-    __shared__ int tgt_lo[TZ * TX], tgt_pre[TZ * TX + 1];
-    __shared__ float half_sum[G::K3];
+    constexpr int NGRP = NT / G::NPAIR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StencilGradSmem<R> &S = *reinterpret_cast<StencilGradSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    stage_forward_patch<R>(L, it, vals, tree, bc, patch, seg_lo, seg_hi, row_valid, tgt_lo, tgt_pre);
-    const int yw = it.yb * BY - R;
-    const int total = tgt_pre[TZ * TX];
-    // two threads per stencil entry: targets of even / odd rank
-    const int e = threadIdx.x % 128, half = threadIdx.x / 128;
-    float acc = 0.f;
-    if (e < G::K3) {
-        const int dz = e / (G::K * G::K), dx = (e / G::K) % G::K, dy = e % G::K;
-        int r = 0;
-        for (int t = half; t < total; t += 2) {
-            while (tgt_pre[r + 1] <= t) ++r;
-            const int i = tgt_lo[r] + (t - tgt_pre[r]);
-            const int pos = int(L.y[i]) - yw - R;
+    stage_patch<R>(L, it, vals, tree, bc, S.P, gout, S.gwin);
+    const int tid = threadIdx.x;
+    const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
+    float acc[G::K];
+#pragma unroll
+    for (int t = 0; t < G::K; ++t) acc[t] = 0.f;
+    if (grp < NGRP) {
+        const int dz = pair / G::K, dx = pair % G::K;
+        for (int a = grp; a < S.P.nact; a += NGRP) {
+            const int w = S.P.act[a], r = w / NWIN, col = (w % NWIN) * WIN;
             const int ia = r / TX, ib = r % TX;
-            acc = fmaf(gout[i], patch[((ia + dz) * G::PX + (ib + dx)) * G::PYS + pos + dy], acc);
+            const float4 *src = reinterpret_cast<const float4 *>(S.P.patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + col);
+            const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+            const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+            const float4 *gs = reinterpret_cast<const float4 *>(S.gwin + r * BY + col);
+            const float4 g0 = gs[0], g1 = gs[1];
+            const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int t = 0; t < G::K; ++t)
+#pragma unroll
+                for (int j = 0; j < WIN; ++j) acc[t] = fmaf(gg[j], v[j + t], acc[t]);
         }
+#pragma unroll
+        for (int t = 0; t < G::K; ++t) S.red[(grp * G::NPAIR + pair) * G::K + t] = acc[t];
     }
-    if (half == 1 && e < G::K3) half_sum[e] = acc;
-    __syncthreads();
-    if (half == 0 && e < G::K3) partial[size_t(e) * n_items + blockIdx.x] = acc + half_sum[e];
+    block_sync();
+    if (tid < G::K3) {
+        const int pr = tid / G::K, t = tid % G::K;
+        float s = 0.f;
+        for (int q = 0; q < NGRP; ++q) s += S.red[(q * G::NPAIR + pr) * G::K + t];
+        partial[size_t(tid) * n_items + blockIdx.x] = s;
+    }
 }
 
 // grad_w[l][e] = sum over the level's items of partial[e][item], fixed-order block reduction.
@@ -519,77 +484,429 @@ __global__ void __launch_bounds__(NT) stencil_grad_reduce_kernel(const float *__
     float s = 0.f;
     for (int64_t i = b + threadIdx.x; i < en; i += NT) s += partial[size_t(e) * n_items + i];
     red[threadIdx.x] = s;
-    __syncthreads();
+    block_sync();
     for (int h = NT / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
+        block_sync();
     }
     if (threadIdx.x == 0) gw[size_t(blockIdx.y) * K3 + e] = red[0];
 }
 
 // ------------------------------------------------------------------------------------------------
-// Backward through the tree averages, one level l (coarse to fine): each child (particle or tree
-// node of level l+1) of a tree node t receives gt[t] / n_children(t).
+// Backward, data part: for every interior cell c a target can reach,
+//   H(c) = sum over preimages c' of c under the boundary reflection of sum_e w[e] g(c' - e),
+// g = dL/dout at the level-l particles (zero elsewhere, and outside the grid). H is routed to the
+// source that supplied cell c in the forward patch: the level-l particle (atomic add; it receives
+// exactly one more term, from the next finer level, so the sum does not depend on order), the
+// level-l tree node (store), or the level-(l-1) particle containing c (sum of its cells in this
+// tile, then one atomic add).
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           float *__restrict__ gp, float *__restrict__ gt) {
-    __shared__ float share[BY];
-    __shared__ int seg_lo[8], seg_hi[8];
+template <int R>
+struct BwdSmem {
+    using G = Geo<R>;
+    float gpatch[G::NROW * G::PYS];
+    __align__(16) float H[NIR * BY];
+    __align__(16) float w8[G::NPAIR * 8];     // flipped taps: w8[pair][t] = w[K3 - 1 - (pair*K + t)]
+    unsigned rmask[G::NROW * 3];              // nonzero-gradient columns of every patch row
+    int seg_lo[G::NROW + G::NRSEG];
+    int pre[(G::NROW + G::NRSEG > NIW ? G::NROW + G::NRSEG : NIW) + 1];
+    int warp_tot[NWARP + 1];
+    unsigned long long need[NIR];
+    float red[NWARP][32][WIN];
+    unsigned char wmir[NIW];                  // window has cells with mirrored preimages
+    unsigned short act[NIW];
+    int nact;
+};
+
+struct YLoader {
+    using Slot = SlotYV;
+    const uint16_t *py, *ty;
+    int t0, t1;
+    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
+        s.y = (seg >= t0 && seg < t1) ? int(ty[i]) : int(py[i]);
+        s.v = 0.f;
+    }
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                              const float *__restrict__ stencils, int bc,
+                                                              const float *__restrict__ gout,
+                                                              float *__restrict__ gp, float *__restrict__ gt) {
+    using G = Geo<R>;
+    constexpr int NSG = G::NROW + G::NRSEG;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdSmem<R> &S = *reinterpret_cast<BwdSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
     const int l = it.l, tid = threadIdx.x;
+    const LevelGeo g = L.geo[l];
+    const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY;
+    const int yw = y0 - R;
+    const bool reflect = bc == APR_BC_REFLECT;
+
+    load_taps<R>(stencils, l - L.l_min, true, S.w8);
+    for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.gpatch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(S.H)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < G::NROW * 3; i += NT) S.rmask[i] = 0u;
+
+    // segments: gradient rows (in-grid patch rows, no reflection: g is zero outside the grid), then the
+    // sources of the interior cells: particles and tree nodes of the interior rows in y-block yb, and
+    // the coarser particles of the interior (TZ/2 x TX/2 parent rows, parent y in [y0/2, y0/2+BY/2))
+    int cnt[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = 2 * tid + h;
+        if (s >= NSG) break;
+        int lo = 0, hi = 0;
+        if (s < G::NROW) {
+            const int z = z0 - R + s / G::PX, x = x0 - R + s % G::PX;
+            if (z >= 0 && z < g.dz && x >= 0 && x < g.dx) {
+                const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
+                row_range(L.row_ptr, L.off, g.row0, g.off0, g.nb, z * g.dx + x, ylo, yhi, lo, hi);
+            }
+        } else {
+            const int q = s - G::NROW;
+            if (q < 2 * NIR) {
+                const int r = q % NIR;
+                const int z = z0 + r / TX, x = x0 + r % TX;
+                if (z < g.dz && x < g.dx) {
+                    const int rr = z * g.dx + x;
+                    if (q < NIR) {
+                        lo = int(pblock(L, g, rr, it.yb));
+                        hi = int(pblock(L, g, rr, it.yb + 1));
+                    } else if (l < L.l_max) {
+                        lo = int(tblock(L, g, rr, it.yb));
+                        hi = int(tblock(L, g, rr, it.yb + 1));
+                    }
+                }
+            } else if (l > L.l_min) {
+                const int r = q - 2 * NIR;
+                const LevelGeo gq = L.geo[l - 1];
+                const int pz = z0 / 2 + r / (TX / 2), px = x0 / 2 + r % (TX / 2);
+                if (pz < gq.dz && px < gq.dx)
+                    row_range(L.row_ptr, L.off, gq.row0, gq.off0, gq.nb, pz * gq.dx + px, y0 / 2,
+                              min(y0 / 2 + BY / 2, gq.dy), lo, hi);
+            }
+        }
+        S.seg_lo[s] = lo;
+        cnt[h] = hi - lo;
+    }
+    block_scan2(cnt[0], cnt[1], NSG, S.pre, S.warp_tot);
+
+    // gradient patch and its occupancy masks (the first NROW segments)
+    const YVLoader gl{L.y, L.ty, gout, gout, 0, 0};
+    for_each_element(S.seg_lo, S.pre, G::NROW, gl, [&](int seg, int, SlotYV &s) {
+        const int pos = s.y - yw;
+        if (pos >= 0 && pos < G::PY) {
+            S.gpatch[seg * G::PYS + pos] = s.v;
+            atomicOr(&S.rmask[seg * 3 + (pos >> 5)], 1u << (pos & 31));
+        }
+    });
+    block_sync();
+
+    // cells that need H: within R of a nonzero gradient, or (reflect) close enough to the grid
+    // boundary to have mirrored preimages; windows with any such cell are active
+    if (tid < NIR) {
+        const int ia = tid / TX, ib = tid % TX;
+        const int z = z0 + ia, x = x0 + ib;
+        unsigned long long m = 0ull;
+        bool edge_zx = false;
+        if (z < g.dz && x < g.dx) {
+            for (int dz = 0; dz < 2 * R + 1; ++dz)
+                for (int dx = 0; dx < 2 * R + 1; ++dx) {
+                    const int row = (ia + dz) * G::PX + (ib + dx);
+                    const unsigned long long lo64 =
+                        (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
+                    const unsigned long long hi64 = S.rmask[row * 3 + 2];
+                    // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
+                    m |= lo64;
+#pragma unroll
+                    for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
+                }
+            edge_zx = z < R || z >= g.dz - R || x < R || x >= g.dx - R;
+            if (reflect) {
+                if (edge_zx) m = ~0ull;
+                else
+                    for (int j = 0; j < BY; ++j)
+                        if (y0 + j < R || y0 + j >= g.dy - R) m |= 1ull << j;
+            }
+            const int nvalid = g.dy - y0;
+            if (nvalid < BY) m &= nvalid <= 0 ? 0ull : ((1ull << nvalid) - 1ull);
+        }
+        for (int w = 0; w < NWIN; ++w) {
+            bool mir = false;
+            if (reflect && z < g.dz && x < g.dx) {
+                mir = edge_zx;
+                for (int j = 0; j < WIN; ++j) {
+                    const int yy = y0 + w * WIN + j;
+                    mir = mir || (yy < g.dy && (yy < R || yy >= g.dy - R));
+                }
+            }
+            S.wmir[tid * NWIN + w] = mir ? 1 : 0;
+        }
+        S.need[tid] = m;
+    }
+    block_sync();
+    // (compact_windows reuses pre[] as scratch; the routing prefix is rebuilt from cnt[] below)
+    compact_windows([&](int w) { return ((S.need[w / NWIN] >> ((w % NWIN) * WIN)) & 0xffull) != 0ull; }, S.act,
+                    S.pre, S.warp_tot, &S.nact);
+
+    // H = (flipped stencil) correlated with the gradient patch, at the active windows (c' = c term)
+    windows_apply<R>(S.gpatch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
+        float4 *dst = reinterpret_cast<float4 *>(S.H + (w / NWIN) * BY + (w % NWIN) * WIN);
+        dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    });
+    // mirrored preimages (cells within R of the grid boundary, reflect only): add their terms. The
+    // gradient outside the staged window is outside the grid, hence zero.
+    if (reflect) {
+        for (int c = tid; c < S.nact * WIN; c += NT) {
+            const int w = S.act[c / WIN];
+            if (!S.wmir[w]) continue;
+            const int r = w / NWIN, j = (w % NWIN) * WIN + c % WIN;
+            const int ia = r / TX, ib = r % TX;
+            const int z = z0 + ia, x = x0 + ib, yy = y0 + j;
+            if (yy >= g.dy || z >= g.dz || x >= g.dx) continue;
+            int pz[2 * R + 1], px[2 * R + 1], py[2 * R + 1];
+            int nz = 0, nx = 0, ny = 0;
+            pz[nz++] = z;
+            px[nx++] = x;
+            py[ny++] = yy;
+            for (int v = -R; v < 0; ++v) {
+                if (reflect_idx(v, g.dz) == z) pz[nz++] = v;
+                if (reflect_idx(v, g.dx) == x) px[nx++] = v;
+                if (reflect_idx(v, g.dy) == yy) py[ny++] = v;
+            }
+            for (int v = 0; v < R; ++v) {
+                if (reflect_idx(g.dz + v, g.dz) == z) pz[nz++] = g.dz + v;
+                if (reflect_idx(g.dx + v, g.dx) == x) px[nx++] = g.dx + v;
+                if (reflect_idx(g.dy + v, g.dy) == yy) py[ny++] = g.dy + v;
+            }
+            float h = 0.f;
+#pragma unroll 1
+            for (int iz = 0; iz < nz; ++iz)
+#pragma unroll 1
+                for (int ix = 0; ix < nx; ++ix)
+#pragma unroll 1
+                    for (int iy = 0; iy < ny; ++iy) {
+                        if (iz == 0 && ix == 0 && iy == 0) continue;  // the c' = c term is done
+                        // taps e with c' - e inside the staged window (the rest reads zero gradient)
+                        const int cz = pz[iz] - (z0 - R), cx = px[ix] - (x0 - R), cy = py[iy] - yw;
+                        const int ez0 = max(-R, cz - G::PZ + 1), ez1 = min(R, cz);
+                        const int ex0 = max(-R, cx - G::PX + 1), ex1 = min(R, cx);
+                        const int ey0 = max(-R, cy - G::PY + 1), ey1 = min(R, cy);
+#pragma unroll 1
+                        for (int ez = ez0; ez <= ez1; ++ez)
+#pragma unroll 1
+                            for (int ex = ex0; ex <= ex1; ++ex) {
+                                // unflipped tap w[ez][ex][ey] sits at flipped pair (R-ez, R-ex), slot R-ey
+                                const float *wrow = S.w8 + ((R - ez) * G::K + (R - ex)) * 8 + R;
+                                const float *grow = S.gpatch + ((cz - ez) * G::PX + (cx - ex)) * G::PYS + cy;
+#pragma unroll 1
+                                for (int ey = ey0; ey <= ey1; ++ey) h = fmaf(wrow[-ey], grow[-ey], h);
+                            }
+                    }
+            S.H[r * BY + j] += h;
+        }
+        block_sync();
+    }
+    // prefix of the routing segments (entries rbase .. rbase + NRSEG): every thread still holds the
+    // counts of its entries 2t, 2t+1 in cnt[]
+    const int rbase = G::NROW;
+    {
+        const int e0 = 2 * tid, e1 = 2 * tid + 1;
+        const int c0 = (e0 >= rbase && e0 < NSG) ? cnt[0] : 0;
+        const int c1 = (e1 >= rbase && e1 < NSG) ? cnt[1] : 0;
+        block_scan2(c0, c1, NSG, S.pre, S.warp_tot);
+    }
+    const YLoader rl{L.y, L.ty, NIR, 2 * NIR};
+    for_each_element(S.seg_lo + rbase, S.pre + rbase, G::NRSEG, rl, [&](int seg, int i, SlotYV &s) {
+        if (seg < NIR) {
+            const float h = S.H[seg * BY + (s.y - y0)];
+            if (h != 0.f) atomicAdd(&gp[i], h);
+        } else if (seg < 2 * NIR) {
+            const float h = S.H[(seg - NIR) * BY + (s.y - y0)];
+            if (h != 0.f) gt[i] = h;
+        } else {
+            const int r = seg - 2 * NIR;
+            const int j0 = 2 * s.y - y0;  // first level-l cell column of the coarser particle
+            if (j0 < 0 || j0 >= BY) return;
+            const int pa = r / (TX / 2), pb = r % (TX / 2);
+            float sum = 0.f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int ia = 2 * pa + a, ib = 2 * pb + b;
+                        if (z0 + ia < g.dz && x0 + ib < g.dx && y0 + j0 + e < g.dy) sum += S.H[(ia * TX + ib) * BY + j0 + e];
+                    }
+            if (sum != 0.f) atomicAdd(&gp[i], sum);
+        }
+    });
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tree kernels, one warp per tree brick (l, z, x, yb), eight bricks per block. The children of the
+// brick's nodes live in the 2x2 child rows of level l+1, y-blocks 2yb and 2yb+1 (lanes 0..3:
+// particle rows (a, b), lanes 4..7: tree rows).
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void child_segment(const DevLayout &L, const Item &it, int lane, int &lo, int &n) {
+    const int l = it.l;
+    const LevelGeo gc = L.geo[l + 1];
+    lo = 0;
+    n = 0;
+    if (lane < 8) {
+        const int kind = lane >> 2, a = (lane >> 1) & 1, b = lane & 1;
+        const int cz = 2 * it.a + a, cx = 2 * it.b + b;
+        if (cz < gc.dz && cx < gc.dx && (kind == 0 || l + 1 < L.l_max)) {
+            const int crr = cz * gc.dx + cx;
+            const int j0 = 2 * it.yb, j1 = min(2 * it.yb + 2, gc.nb);
+            const uint32_t a0 = kind == 0 ? pblock(L, gc, crr, j0) : tblock(L, gc, crr, j0);
+            const uint32_t a1 = kind == 0 ? pblock(L, gc, crr, j1) : tblock(L, gc, crr, j1);
+            lo = int(a0);
+            n = int(a1 - a0);
+        }
+    }
+}
+
+// Warp-level flattened loop over the children: f(segment, index, y, value), values read from vp
+// (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use.
+template <typename F>
+__device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f) {
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int ex[8], sl[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        ex[k] = __shfl_sync(0xffffffffu, incl - n, k);
+        sl[k] = __shfl_sync(0xffffffffu, lo, k);
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 7);
+    for (int e0 = 0; e0 < total; e0 += 32 * UNROLL) {
+        int sg[UNROLL], ix[UNROLL], yv[UNROLL];
+        float vv[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int e = e0 + lane + 32 * u;
+            sg[u] = -1;
+            ix[u] = 0;
+            yv[u] = 0;
+            vv[u] = 0.f;
+            if (e < total) {
+                int s = 0;
+#pragma unroll
+                for (int k = 1; k < 8; ++k) s = ex[k] <= e ? k : s;
+                int slo = sl[0], sex = ex[0];
+#pragma unroll
+                for (int k = 1; k < 8; ++k)
+                    if (k == s) {
+                        slo = sl[k];
+                        sex = ex[k];
+                    }
+                sg[u] = s;
+                ix[u] = slo + (e - sex);
+                yv[u] = s >= 4 ? int(L.ty[ix[u]]) : int(L.y[ix[u]]);
+                vv[u] = s >= 4 ? vt[ix[u]] : vp[ix[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (sg[u] >= 0) f(sg[u], ix[u], yv[u], vv[u]);
+    }
+}
+
+// APR tree restriction for one level l (Sec. 3.4): each child value goes to a slot (a, b, y&1) of its
+// parent, then every node averages its in-grid slots in a fixed order.
+__global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+                                                           const float *__restrict__ vals,
+                                                           float *__restrict__ tree) {
+    __shared__ float slot[NWARP][8][BY];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * NWARP + warp;
+    if (bi >= n) return;
+    const Item it = items[bi];
+    const int l = it.l;
+    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+    const int y0 = it.yb * BY;
+    int lo, cn;
+    child_segment(L, it, lane, lo, cn);
+    const int rr = it.a * g.dx + it.b;
+    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
+    float(*sl)[BY] = slot[warp];
+    warp_children(L, lo, cn, vals, tree, [&](int s, int, int yv, float v) {
+        sl[(s & 3) * 2 + (yv & 1)][(yv >> 1) - y0] = v;
+    });
+    __syncwarp();
+    for (int t = tlo + lane; t < thi; t += 32) {
+        const int yv = L.ty[t];
+        float s = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c >> 2, b = (c >> 1) & 1, e = c & 1;
+            if (2 * it.a + a < gc.dz && 2 * it.b + b < gc.dx && 2 * yv + e < gc.dy) {
+                s += sl[(a * 2 + b) * 2 + e][yv - y0];
+                ++cnt;
+            }
+        }
+        tree[t] = s / float(cnt);
+    }
+}
+
+// Backward through the tree averages, one level l (coarse to fine): each child (particle or tree
+// node of level l+1) of a tree node t receives gt[t] / n_children(t).
+__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+                                                           float *__restrict__ gp, float *__restrict__ gt) {
+    __shared__ float share[NWARP][BY];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * NWARP + warp;
+    if (bi >= n) return;
+    const Item it = items[bi];
+    const int l = it.l;
     const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
     const int y0 = it.yb * BY;
     const int rr = it.a * g.dx + it.b;
     const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
-    for (int t = tlo + tid; t < thi; t += NT) {
+    for (int t = tlo + lane; t < thi; t += 32) {
         const int yv = L.ty[t];
-        const int n = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
-        share[yv - y0] = gt[t] / float(n);
+        const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
+        share[warp][yv - y0] = gt[t] / float(cnt);
     }
-    if (tid < 8) {
-        const int kind = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
-        const int cz = 2 * it.a + a, cx = 2 * it.b + b;
-        uint32_t lo = 0, hi = 0;
-        if (cz < gc.dz && cx < gc.dx) {
-            const int crr = cz * gc.dx + cx;
-            const int j0 = 2 * it.yb, j1 = min(2 * it.yb + 2, gc.nb);
-            if (kind == 0) {
-                lo = pblock(L, gc, crr, j0);
-                hi = pblock(L, gc, crr, j1);
-            } else if (l + 1 < L.l_max) {
-                lo = tblock(L, gc, crr, j0);
-                hi = tblock(L, gc, crr, j1);
-            }
-        }
-        seg_lo[tid] = int(lo);
-        seg_hi[tid] = int(hi);
-    }
-    __syncthreads();
-    const int s = tid >> 5, lane = tid & 31;
-    const int kind = s >> 2;
-    const uint16_t *ys = kind == 0 ? L.y : L.ty;
-    float *dst = kind == 0 ? gp : gt;
-    for (int i = seg_lo[s] + lane; i < seg_hi[s]; i += 32) dst[i] += share[(int(ys[i]) >> 1) - y0];
+    int lo, cn;
+    child_segment(L, it, lane, lo, cn);
+    __syncwarp();
+    warp_children(L, lo, cn, gp, gt, [&](int s, int i, int yv, float v) {
+        float *dst = s >= 4 ? gt : gp;
+        dst[i] = v + share[warp][(yv >> 1) - y0];
+    });
 }
 
-template <int R>
-size_t bwd_data_smem() {
-    using G = Geo<R>;
-    return sizeof(float) * (size_t(G::NGROW) * G::GYS + TZ * TX * BY) + sizeof(unsigned long long) * (2 * G::NGROW + TZ * TX);
+cudaError_t set_smem(const void *fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
 template <int R>
 cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                               const float *st, int bc, float *out, cudaStream_t s) {
-    if (n > 0) conv_fwd_kernel<R><<<n, NT, 0, s>>>(L, items, vals, tree, st, bc, out);
+    const size_t sm = sizeof(PatchSmem<R>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_fwd_kernel<R>), sm);
+    if (e != cudaSuccess) return e;
+    if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out);
     return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int n, const float *st, int bc,
                               const float *gout, float *gp, float *gt, cudaStream_t s) {
-    const size_t sm = bwd_data_smem<R>();
-    cudaError_t e = cudaFuncSetAttribute(conv_bwd_data_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    const size_t sm = sizeof(BwdSmem<R>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_data_kernel<R>), sm);
     if (e != cudaSuccess) return e;
     if (n > 0) conv_bwd_data_kernel<R><<<n, NT, sm, s>>>(L, items, st, bc, gout, gp, gt);
     return cudaGetLastError();
@@ -598,7 +915,10 @@ cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int n, cons
 template <int R>
 cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, const float *vals,
                                  const float *tree, int bc, const float *gout, float *partial, cudaStream_t s) {
-    if (n > 0) conv_bwd_stencil_kernel<R><<<n, NT, 0, s>>>(L, items, n, vals, tree, bc, gout, partial);
+    const size_t sm = sizeof(StencilGradSmem<R>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_stencil_kernel<R>), sm);
+    if (e != cudaSuccess) return e;
+    if (n > 0) conv_bwd_stencil_kernel<R><<<n, NT, sm, s>>>(L, items, n, vals, tree, bc, gout, partial);
     return cudaGetLastError();
 }
 
@@ -613,7 +933,7 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
 
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
                                  cudaStream_t s) {
-    if (n > 0) tree_restrict_kernel<<<n, NT, 0, s>>>(L, items, vals, tree);
+    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, vals, tree);
     return cudaGetLastError();
 }
 
@@ -636,7 +956,7 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
 }
 
 cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, int n, float *gp, float *gt, cudaStream_t s) {
-    if (n > 0) tree_pushdown_kernel<<<n, NT, 0, s>>>(L, items, gp, gt);
+    if (n > 0) tree_pushdown_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, gp, gt);
     return cudaGetLastError();
 }
 

@@ -48,11 +48,12 @@ def _check_structure(apr):
     assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_Y_IDX), ty.astype(np.uint16))
     # work list: exactly the (level, tile, y-block) bricks holding particles
     lev, z, x, y = apr.particle_coords()
-    ref = sorted(set(zip(lev.tolist(), (z // 4).tolist(), (x // 4).tolist(), (y // 64).tolist())))
+    T, B = _abi.APR_TILE_ZX, _abi.APR_BLOCK_Y
+    ref = sorted(set(zip(lev.tolist(), (z // T).tolist(), (x // T).tolist(), (y // B).tolist())))
     got = [tuple(r) for r in lay.export(_abi.APR_STRUCT_FWD_ITEMS).tolist()]
     assert got == ref
     tc = o.tree_coords()
-    tref = sorted(set(zip(tc[:, 0].tolist(), tc[:, 1].tolist(), tc[:, 2].tolist(), (tc[:, 3] // 64).tolist())))
+    tref = sorted(set(zip(tc[:, 0].tolist(), tc[:, 1].tolist(), tc[:, 2].tolist(), (tc[:, 3] // B).tolist())))
     assert [tuple(r) for r in lay.export(_abi.APR_STRUCT_TREE_ITEMS).tolist()] == tref
 
 
