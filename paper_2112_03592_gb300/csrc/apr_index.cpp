@@ -211,39 +211,38 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &X,
 
     // ---- work lists
     // forward: (l, tz, tx, yb) tiles holding at least one level-l particle
-    // backward: the same tiles dilated by one tile / block (gradient reaches r <= 2 cells around)
+    // backward: tiles whose interior lies within kMaxRadius cells (Chebyshev) of a level-l particle:
+    // every other tile receives no gradient (its staged window holds no nonzero dL/dout)
+    constexpr int kMaxRadius = 2;
     X.fwd_items.clear();
     X.bwd_items.clear();
-    std::vector<uint8_t> occ, dil;
+    std::vector<uint8_t> occ, near;
     for (int l = L.l_min; l <= L.l_max; ++l) {
         X.fwd_level_begin[l] = int64_t(X.fwd_items.size());
         const LevelGeo &g = X.geo[l];
         const int32_t ntz = (g.dz + TZ - 1) / TZ, ntx = (g.dx + TX - 1) / TX;
         occ.assign(size_t(ntz) * ntx * g.nb, 0);
+        near.assign(occ.size(), 0);
+        auto fdiv = [](int32_t a, int32_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
         for (int32_t z = 0; z < g.dz; ++z)
             for (int32_t x = 0; x < g.dx; ++x) {
                 const int64_t r = g.row0 + int64_t(z) * g.dx + x;
-                for (int64_t i = rp[r]; i < rp[r + 1]; ++i)
-                    occ[(size_t(z / TZ) * ntx + x / TX) * g.nb + L.y_idx[i] / BY] = 1;
+                for (int64_t i = rp[r]; i < rp[r + 1]; ++i) {
+                    const int32_t y = L.y_idx[i];
+                    occ[(size_t(z / TZ) * ntx + x / TX) * g.nb + y / BY] = 1;
+                    for (int32_t a = std::max(0, fdiv(z - kMaxRadius, TZ)); a <= std::min(ntz - 1, (z + kMaxRadius) / TZ); ++a)
+                        for (int32_t b = std::max(0, fdiv(x - kMaxRadius, TX)); b <= std::min(ntx - 1, (x + kMaxRadius) / TX); ++b)
+                            for (int32_t j = std::max(0, fdiv(y - kMaxRadius, BY)); j <= std::min(g.nb - 1, (y + kMaxRadius) / BY); ++j)
+                                near[(size_t(a) * ntx + b) * g.nb + j] = 1;
+                }
             }
-        dil.assign(occ.size(), 0);
         for (int32_t a = 0; a < ntz; ++a)
             for (int32_t b = 0; b < ntx; ++b)
                 for (int32_t j = 0; j < g.nb; ++j) {
-                    if (!occ[(size_t(a) * ntx + b) * g.nb + j]) continue;
-                    X.fwd_items.push_back(Item{l, a, b, j});
-                    for (int da = -1; da <= 1; ++da)
-                        for (int db = -1; db <= 1; ++db)
-                            for (int dj = -1; dj <= 1; ++dj) {
-                                const int32_t aa = a + da, bb = b + db, jj = j + dj;
-                                if (aa < 0 || bb < 0 || jj < 0 || aa >= ntz || bb >= ntx || jj >= g.nb) continue;
-                                dil[(size_t(aa) * ntx + bb) * g.nb + jj] = 1;
-                            }
+                    const size_t k = (size_t(a) * ntx + b) * g.nb + j;
+                    if (occ[k]) X.fwd_items.push_back(Item{l, a, b, j});
+                    if (near[k]) X.bwd_items.push_back(Item{l, a, b, j});
                 }
-        for (int32_t a = 0; a < ntz; ++a)
-            for (int32_t b = 0; b < ntx; ++b)
-                for (int32_t j = 0; j < g.nb; ++j)
-                    if (dil[(size_t(a) * ntx + b) * g.nb + j]) X.bwd_items.push_back(Item{l, a, b, j});
     }
     X.fwd_level_begin[L.l_max + 1] = int64_t(X.fwd_items.size());
     for (int l = L.l_max + 2; l <= MAXL; ++l) X.fwd_level_begin[l] = X.fwd_level_begin[L.l_max + 1];

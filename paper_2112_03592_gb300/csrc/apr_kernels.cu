@@ -147,40 +147,47 @@ struct YVLoader {
 };
 
 // Flattened loop over the elements of nseg segments (segment s: global indices seg_lo[s] ..
-// seg_lo[s] + pre[s+1] - pre[s]). Each warp takes a contiguous share, lanes are strided, and the
-// loads of UNROLL elements per thread are issued before any of them is used.
+// seg_lo[s] + pre[s+1] - pre[s]), in chunks of SEGID_CAP elements. For every chunk, the threads
+// first write the segment id of each element into segid[] (one thread per segment), then every warp
+// takes a contiguous share of the chunk with strided lanes, issuing the loads of UNROLL elements
+// per thread before any of them is used. Trip counts depend on the warp only (lanes stay converged).
+// Ends with a block barrier.
+constexpr int SEGID_CAP = 4096;
+
 template <typename Load, typename Use>
-__device__ __forceinline__ void for_each_element(const int *seg_lo, const int *pre, int nseg, const Load &load, Use use) {
+__device__ __forceinline__ void for_each_element(const int *seg_lo, const int *pre, int nseg, unsigned short *segid,
+                                                 const Load &load, Use use) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int E0 = pre[0], E1 = pre[nseg];
-    const int share = (E1 - E0 + NWARP - 1) / NWARP;
-    const int ea = E0 + warp * share, eb = min(E1, ea + share);
-    // the trip count depends on the warp only, so the lanes stay converged
-    int lo = 0, hi = nseg;  // largest s with pre[s] <= ea + lane
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (pre[mid] <= ea + lane) lo = mid;
-        else hi = mid;
-    }
-    int seg = lo;
-    for (int base = ea; base < eb; base += 32 * UNROLL) {
-        int sg[UNROLL], ix[UNROLL];
-        typename Load::Slot slot[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const int eu = base + lane + 32 * u;
-            sg[u] = -1;
-            ix[u] = 0;
-            if (eu < eb) {
-                while (pre[seg + 1] <= eu) ++seg;
-                sg[u] = seg;
-                ix[u] = seg_lo[seg] + (eu - pre[seg]);
-                load(seg, ix[u], slot[u]);
-            }
+    for (int c0 = E0; c0 < E1; c0 += SEGID_CAP) {
+        const int c1 = min(E1, c0 + SEGID_CAP);
+        for (int sg = threadIdx.x; sg < nseg; sg += NT) {
+            const int a = max(pre[sg], c0), b = min(pre[sg + 1], c1);
+            for (int e = a; e < b; ++e) segid[e - c0] = (unsigned short)sg;
         }
+        block_sync();
+        const int share = (c1 - c0 + NWARP - 1) / NWARP;
+        const int ea = c0 + warp * share, eb = min(c1, ea + share);
+        for (int base = ea; base < eb; base += 32 * UNROLL) {
+            int sg[UNROLL], ix[UNROLL];
+            typename Load::Slot slot[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
-            if (sg[u] >= 0) use(sg[u], ix[u], slot[u]);
+            for (int u = 0; u < UNROLL; ++u) {
+                const int eu = base + lane + 32 * u;
+                sg[u] = -1;
+                ix[u] = 0;
+                if (eu < eb) {
+                    const int sgu = segid[eu - c0];
+                    sg[u] = sgu;
+                    ix[u] = seg_lo[sgu] + (eu - pre[sgu]);
+                    load(sgu, ix[u], slot[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (sg[u] >= 0) use(sg[u], ix[u], slot[u]);
+        }
+        block_sync();
     }
 }
 
@@ -212,6 +219,7 @@ struct PatchSmem {
     unsigned wmask[NIW];                 // target bits of every window
     int wfirst[NIW];                     // first target (particle index) of every window
     unsigned short act[NIW];             // active windows, in window order
+    unsigned short segid[SEGID_CAP];     // segment of every staged element of the current chunk
     int nact;
     int boundary;                        // the tile with its halo reaches outside the grid
 };
@@ -252,8 +260,10 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
         const bool inside = z >= 0 && z < g.dz && x >= 0 && x < g.dx;
         int lo = 0, hi = 0;
         if (inside || bc == APR_BC_REFLECT) {
-            z = reflect_idx(z, g.dz);
-            x = reflect_idx(x, g.dx);
+            if (!inside) {
+                z = reflect_idx(z, g.dz);
+                x = reflect_idx(x, g.dx);
+            }
             const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
             const int rr = z * g.dx + x;
             if (kind == 0) {
@@ -277,7 +287,7 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
     block_scan2(cnt[0], cnt[1], G::NSEG, S.pre, S.warp_tot);
 
     const YVLoader ld{L.y, L.ty, vals, tree, G::NROW, 2 * G::NROW};
-    for_each_element(S.seg_lo, S.pre, G::NSEG, ld, [&](int seg, int i, SlotYV &s) {
+    for_each_element(S.seg_lo, S.pre, G::NSEG, S.segid, ld, [&](int seg, int i, SlotYV &s) {
         const int meta = S.seg_meta[seg];
         const int kind = (meta >> 8) & 3;
         float *prow = S.patch + (meta & 255) * G::PYS;
@@ -515,6 +525,7 @@ struct BwdSmem {
     float red[NWARP][32][WIN];
     unsigned char wmir[NIW];                  // window has cells with mirrored preimages
     unsigned short act[NIW];
+    unsigned short segid[SEGID_CAP];
     int nact;
 };
 
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
 
     // gradient patch and its occupancy masks (the first NROW segments)
     const YVLoader gl{L.y, L.ty, gout, gout, 0, 0};
-    for_each_element(S.seg_lo, S.pre, G::NROW, gl, [&](int seg, int, SlotYV &s) {
+    for_each_element(S.seg_lo, S.pre, G::NROW, S.segid, gl, [&](int seg, int, SlotYV &s) {
         const int pos = s.y - yw;
         if (pos >= 0 && pos < G::PY) {
             S.gpatch[seg * G::PYS + pos] = s.v;
@@ -720,7 +731,7 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         block_scan2(c0, c1, NSG, S.pre, S.warp_tot);
     }
     const YLoader rl{L.y, L.ty, NIR, 2 * NIR};
-    for_each_element(S.seg_lo + rbase, S.pre + rbase, G::NRSEG, rl, [&](int seg, int i, SlotYV &s) {
+    for_each_element(S.seg_lo + rbase, S.pre + rbase, G::NRSEG, S.segid, rl, [&](int seg, int i, SlotYV &s) {
         if (seg < NIR) {
             const float h = S.H[seg * BY + (s.y - y0)];
             if (h != 0.f) atomicAdd(&gp[i], h);
