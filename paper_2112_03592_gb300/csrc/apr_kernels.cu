@@ -368,6 +368,45 @@ __device__ __forceinline__ void window_rows(const float *base, const float *w8, 
     }
 }
 
+// Like window_rows over all stencil rows, for a window whose centre row (ia, ib) may lie outside
+// the tile interior (a mirrored row): stencil rows that fall outside the staged patch read zero.
+template <int R>
+__device__ __forceinline__ void window_rows_checked(const float *patch, const float *w8, int ia, int ib, int col,
+                                                    float acc[WIN]) {
+    using G = Geo<R>;
+#pragma unroll
+    for (int pair = 0; pair < G::NPAIR; ++pair) {
+        const int dz = pair / G::K, dx = pair % G::K;
+        const int rz = ia + dz, rx = ib + dx;
+        if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+        const float4 *src = reinterpret_cast<const float4 *>(patch + (rz * G::PX + rx) * G::PYS + col);
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+        const float4 wa = *reinterpret_cast<const float4 *>(w8 + pair * 8);
+        const float wt[5] = {wa.x, wa.y, wa.z, wa.w, w8[pair * 8 + 4]};
+#pragma unroll
+        for (int j = 0; j < WIN; ++j)
+#pragma unroll
+            for (int t = 0; t < G::K; ++t) acc[j] = fmaf(wt[t], v[j + t], acc[j]);
+    }
+}
+
+// Positions v in [-R, d + R) outside [0, d) that reflect onto c (at most 2R). Returns the count.
+template <int R>
+__device__ __forceinline__ int mirror_preimages(int c, int d, int *out) {
+    int n = 0;
+    if (d >= 2 * R) {  // at most one mirror per side: -c-1 (c < R) and 2d-1-c (c >= d-R)
+        if (c < R) out[n++] = -c - 1;
+        if (c >= d - R) out[n++] = 2 * d - 1 - c;
+        return n;
+    }
+    for (int v = -R; v < 0; ++v)
+        if (reflect_idx(v, d) == c) out[n++] = v;
+    for (int v = d; v < d + R; ++v)
+        if (reflect_idx(v, d) == c) out[n++] = v;
+    return n;
+}
+
 // Stencil sums of the active windows act[0..nact) of a patch: warps 2v and 2v+1 take the same 32
 // windows, the first half of the stencil rows and the second half; the second writes its partial
 // sums to red[], the first adds them (fixed order) and calls emit(window, acc).
@@ -623,37 +662,49 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         unsigned long long m = 0ull;
         bool edge_zx = false;
         if (z < g.dz && x < g.dx) {
-            for (int dz = 0; dz < 2 * R + 1; ++dz)
-                for (int dx = 0; dx < 2 * R + 1; ++dx) {
-                    const int row = (ia + dz) * G::PX + (ib + dx);
-                    const unsigned long long lo64 =
-                        (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
-                    const unsigned long long hi64 = S.rmask[row * 3 + 2];
-                    // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
-                    m |= lo64;
-#pragma unroll
-                    for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
-                }
-            edge_zx = z < R || z >= g.dz - R || x < R || x >= g.dx - R;
+            // preimage rows of this row: itself and (reflect) the out-of-grid rows mirroring onto it
+            int pz[2 * R + 1], px[2 * R + 1];
+            int nz = 1, nx = 1;
+            pz[0] = z;
+            px[0] = x;
             if (reflect) {
-                if (edge_zx) m = ~0ull;
-                else
-                    for (int j = 0; j < BY; ++j)
-                        if (y0 + j < R || y0 + j >= g.dy - R) m |= 1ull << j;
+                nz += mirror_preimages<R>(z, g.dz, pz + 1);
+                nx += mirror_preimages<R>(x, g.dx, px + 1);
             }
+            edge_zx = nz > 1 || nx > 1;
+            for (int iz = 0; iz < nz; ++iz)
+                for (int ix = 0; ix < nx; ++ix)
+                    for (int dz = 0; dz < 2 * R + 1; ++dz)
+                        for (int dx = 0; dx < 2 * R + 1; ++dx) {
+                            const int rz = pz[iz] - z0 + dz, rx = px[ix] - x0 + dx;  // patch row
+                            if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+                            const int row = rz * G::PX + rx;
+                            const unsigned long long lo64 =
+                                (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
+                            const unsigned long long hi64 = S.rmask[row * 3 + 2];
+                            // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
+                            m |= lo64;
+#pragma unroll
+                            for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
+                        }
+            if (reflect)
+                for (int j = 0; j < BY; ++j)
+                    if (y0 + j < R || y0 + j >= g.dy - R) m |= 1ull << j;
             const int nvalid = g.dy - y0;
             if (nvalid < BY) m &= nvalid <= 0 ? 0ull : ((1ull << nvalid) - 1ull);
         }
+        // wmir: bit 0 = the row has mirrored rows (z or x), bit 1 = the window has cells within R of the
+        // y boundary
         for (int w = 0; w < NWIN; ++w) {
-            bool mir = false;
+            int mir = 0;
             if (reflect && z < g.dz && x < g.dx) {
-                mir = edge_zx;
+                mir = edge_zx ? 1 : 0;
                 for (int j = 0; j < WIN; ++j) {
                     const int yy = y0 + w * WIN + j;
-                    mir = mir || (yy < g.dy && (yy < R || yy >= g.dy - R));
+                    if (yy < g.dy && (yy < R || yy >= g.dy - R)) mir |= 2;
                 }
             }
-            S.wmir[tid * NWIN + w] = mir ? 1 : 0;
+            S.wmir[tid * NWIN + w] = (unsigned char)mir;
         }
         S.need[tid] = m;
     }
@@ -668,56 +719,70 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
     });
-    // mirrored preimages (cells within R of the grid boundary, reflect only): add their terms. The
-    // gradient outside the staged window is outside the grid, hence zero.
+    // mirrored preimages (reflect only). Rows with mirrored z / x rows: one thread per active window
+    // sums the windows of all mirrored row combinations (z', x') != (z, x) (same y cells) with the
+    // window machinery; stencil rows outside the staged patch read zero, as the gradient outside the
+    // grid is zero. Cells within R of the y boundary then add the combinations whose y is mirrored.
     if (reflect) {
-        for (int c = tid; c < S.nact * WIN; c += NT) {
-            const int w = S.act[c / WIN];
-            if (!S.wmir[w]) continue;
-            const int r = w / NWIN, j = (w % NWIN) * WIN + c % WIN;
-            const int ia = r / TX, ib = r % TX;
-            const int z = z0 + ia, x = x0 + ib, yy = y0 + j;
-            if (yy >= g.dy || z >= g.dz || x >= g.dx) continue;
-            int pz[2 * R + 1], px[2 * R + 1], py[2 * R + 1];
-            int nz = 0, nx = 0, ny = 0;
-            pz[nz++] = z;
-            px[nx++] = x;
-            py[ny++] = yy;
-            for (int v = -R; v < 0; ++v) {
-                if (reflect_idx(v, g.dz) == z) pz[nz++] = v;
-                if (reflect_idx(v, g.dx) == x) px[nx++] = v;
-                if (reflect_idx(v, g.dy) == yy) py[ny++] = v;
-            }
-            for (int v = 0; v < R; ++v) {
-                if (reflect_idx(g.dz + v, g.dz) == z) pz[nz++] = g.dz + v;
-                if (reflect_idx(g.dx + v, g.dx) == x) px[nx++] = g.dx + v;
-                if (reflect_idx(g.dy + v, g.dy) == yy) py[ny++] = g.dy + v;
-            }
-            float h = 0.f;
-#pragma unroll 1
+        for (int a = tid; a < S.nact; a += NT) {
+            const int w = S.act[a];
+            if (!(S.wmir[w] & 1)) continue;
+            const int r = w / NWIN, col = (w % NWIN) * WIN;
+            const int z = z0 + r / TX, x = x0 + r % TX;
+            int pz[2 * R + 1], px[2 * R + 1];
+            pz[0] = z;
+            px[0] = x;
+            const int nz = 1 + mirror_preimages<R>(z, g.dz, pz + 1), nx = 1 + mirror_preimages<R>(x, g.dx, px + 1);
+            float acc[WIN];
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
             for (int iz = 0; iz < nz; ++iz)
-#pragma unroll 1
                 for (int ix = 0; ix < nx; ++ix)
-#pragma unroll 1
+                    if (iz != 0 || ix != 0) window_rows_checked<R>(S.gpatch, S.w8, pz[iz] - z0, px[ix] - x0, col, acc);
+            float *dst = S.H + r * BY + col;
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) dst[j] += acc[j];
+        }
+        block_sync();
+        // y-mirrored combinations: one thread per (interior row, cell within R of the y boundary)
+        const int nlow = y0 == 0 ? min(R, g.dy) : 0;                       // cells 0 .. nlow-1
+        const int hb = max(g.dy - R, max(y0, nlow));                        // cells hb .. min(dy, y0+BY)-1
+        const int nhigh = max(0, min(g.dy, y0 + BY) - hb);
+        const int per_row = nlow + nhigh;
+        for (int task = tid; task < NIR * per_row; task += NT) {
+            const int r = task / per_row, q = task % per_row;
+            const int j = q < nlow ? q : hb - y0 + (q - nlow);
+            const int z = z0 + r / TX, x = x0 + r % TX, yy = y0 + j;
+            if (z >= g.dz || x >= g.dx) continue;
+            if (!((S.need[r] >> j) & 1ull)) continue;
+            int pz[2 * R + 1], px[2 * R + 1], py[2 * R];
+            pz[0] = z;
+            px[0] = x;
+            const int nz = 1 + mirror_preimages<R>(z, g.dz, pz + 1), nx = 1 + mirror_preimages<R>(x, g.dx, px + 1);
+            const int ny = mirror_preimages<R>(yy, g.dy, py);
+            float h0 = 0.f, h1 = 0.f;
+            for (int iz = 0; iz < nz; ++iz)
+                for (int ix = 0; ix < nx; ++ix)
                     for (int iy = 0; iy < ny; ++iy) {
-                        if (iz == 0 && ix == 0 && iy == 0) continue;  // the c' = c term is done
                         // taps e with c' - e inside the staged window (the rest reads zero gradient)
                         const int cz = pz[iz] - (z0 - R), cx = px[ix] - (x0 - R), cy = py[iy] - yw;
-                        const int ez0 = max(-R, cz - G::PZ + 1), ez1 = min(R, cz);
-                        const int ex0 = max(-R, cx - G::PX + 1), ex1 = min(R, cx);
                         const int ey0 = max(-R, cy - G::PY + 1), ey1 = min(R, cy);
-#pragma unroll 1
-                        for (int ez = ez0; ez <= ez1; ++ez)
-#pragma unroll 1
-                            for (int ex = ex0; ex <= ex1; ++ex) {
+#pragma unroll
+                        for (int ez = -R; ez <= R; ++ez)
+#pragma unroll
+                            for (int ex = -R; ex <= R; ++ex) {
+                                const int sz = cz - ez, sx = cx - ex;
+                                if (sz < 0 || sz >= G::PZ || sx < 0 || sx >= G::PX) continue;
                                 // unflipped tap w[ez][ex][ey] sits at flipped pair (R-ez, R-ex), slot R-ey
                                 const float *wrow = S.w8 + ((R - ez) * G::K + (R - ex)) * 8 + R;
-                                const float *grow = S.gpatch + ((cz - ez) * G::PX + (cx - ex)) * G::PYS + cy;
-#pragma unroll 1
-                                for (int ey = ey0; ey <= ey1; ++ey) h = fmaf(wrow[-ey], grow[-ey], h);
+                                const float *grow = S.gpatch + (sz * G::PX + sx) * G::PYS + cy;
+                                for (int ey = ey0; ey <= ey1; ++ey) {
+                                    if ((ey & 1) == 0) h0 = fmaf(wrow[-ey], grow[-ey], h0);
+                                    else h1 = fmaf(wrow[-ey], grow[-ey], h1);
+                                }
                             }
                     }
-            S.H[r * BY + j] += h;
+            S.H[r * BY + j] += h0 + h1;
         }
         block_sync();
     }
