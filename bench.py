@@ -55,7 +55,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -65,7 +65,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -75,10 +75,16 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons over the samples taken in [t0, t1] (all
+        samples if none fall inside, e.g. a timed region shorter than the sampling period)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if t0 is not None:
+            inside = [x for x in lines if t0 <= x[0] <= t1]
+            lines = inside if inside else lines
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -91,7 +97,25 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "timed region" if t0 is not None and any(t0 <= x[0] <= t1 for x in self.lines)
+                else "warm-up and timed region (timed region shorter than the 50 ms sampling period)"}
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source is
+    unchanged since that capture (sha1 prefix match); else None."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha1(f.read()).hexdigest()[:12]
+    except (OSError, KeyError, ValueError):
+        return None
+    if sha != rec.get("sha1_prefix"):
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
 def algorithmic_bytes(apr, lay, k):
@@ -132,12 +156,30 @@ def run_ours(args, rank, world):
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def step():
-        G.apr_tree_restrict(lay, vals, tree)
-        G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
-        G.apr_convolve_backward(lay, vals, tree, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
+    gtree = torch.empty(lay.n_tree, device=dev)
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    def step(e=None):
+        # tree restriction | convolution | convolution adjoint | tree adjoint | stencil gradient
+        if e is not None:
+            e[0].record(stream)
+        G.apr_tree_restrict(lay, vals, tree)
+        if e is not None:
+            e[1].record(stream)
+        G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
+        if e is not None:
+            e[2].record(stream)
+        G.apr_convolve_adjoint(lay, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_tree=gtree)
+        if e is not None:
+            e[3].record(stream)
+        G.apr_tree_restrict_adjoint(lay, gtree, gp)
+        if e is not None:
+            e[4].record(stream)
+        G.apr_convolve_stencil_grad(lay, vals, tree, K, gout, G.APR_BC_REFLECT, grad_stencils=gw)
+        if e is not None:
+            e[5].record(stream)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    clk = ClockSampler(dev.index).__enter__()
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -145,27 +187,21 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clk:
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            e = ev[i]
-            e[0].record(stream)
-            G.apr_tree_restrict(lay, vals, tree)
-            e[1].record(stream)
-            G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
-            e[2].record(stream)
-            G.apr_convolve_backward(lay, vals, tree, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
-            e[3].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        step(ev[i])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    wall = t1 - t0
+    time.sleep(0.12)
+    clk.__exit__()
     if world > 1:
         torch.distributed.barrier()
     lay.sync_status()
-    t_restrict = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    t_conv = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    t_bwd = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
-    step_ms = sum(t_restrict[i] + t_conv[i] + t_bwd[i] for i in range(args.steps)) / args.steps
+    parts = [[ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)] for j in range(5)]
+    t_restrict, t_conv, t_adj, t_tadj, t_sgrad = parts
+    step_ms = sum(sum(p) for p in parts) / args.steps
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -210,17 +246,24 @@ def run_ours(args, rank, world):
         e2e = float(t.item())
 
     # forward-only pipeline (tree restriction + convolution), the paper's timed pipeline
-    fwd_ms = (sum(t_restrict) + sum(t_conv)) / args.steps
-    conv_ms = sum(t_conv) / args.steps
+    mean = lambda v: sum(v) / len(v)
+    fwd_ms = mean(t_restrict) + mean(t_conv)
+    conv_ms, adj_ms = mean(t_conv), mean(t_adj)
     conv_bytes, restrict_bytes = algorithmic_bytes(apr, lay, K)
     peaks, src = _peaks()
     hbm = float(peaks["hbm_gbs"])
     pix_bytes = float(np.prod(apr.dims)) * 4.0
-    # our kernels per step: restriction (one per level holding tree nodes), convolution, backward
-    # data part, push-down (one per level holding tree nodes), stencil-gradient partials, reduction
+    # our kernels per step: restriction (one per level holding tree nodes), convolution, convolution
+    # adjoint, push-down (one per level holding tree nodes), stencil-gradient partials, reduction
     n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
-    launches_per_step = n_tree_levels + 1 + (1 + n_tree_levels + 2)
-    clocks = clk.summary()
+    launches_per_step = n_tree_levels + 1 + 1 + n_tree_levels + 2
+    # the dominant kernel of the step: the convolution adjoint (one kernel; its call also clears the
+    # two gradient outputs with cudaMemsetAsync). Its algorithmic bytes equal the forward's: dL/dout
+    # in, dL/dparticles and dL/dtree out, y indices and row pointers.
+    dom_ms, dom_kernel = (adj_ms, "conv_bwd_data_kernel<2>") if adj_ms >= conv_ms else (conv_ms, "conv_fwd_kernel<2>")
+    dom_name = dom_kernel + (" (apr_convolve_adjoint)" if dom_kernel.startswith("conv_bwd") else " (apr_convolve)")
+    traffic = recorded_traffic(dom_kernel)
+    clocks = clk.summary(t0, t1)
     rec = {
         "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
         "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4),
@@ -244,15 +287,17 @@ def run_ours(args, rank, world):
         "forward_pipeline": {"ms": round(fwd_ms, 5),
                              "Gparticles_per_s": round(Np / (fwd_ms * 1e-3) / 1e9, 3),
                              "pixel_equiv_GBps": round(pix_bytes / (fwd_ms * 1e-3) / 1e9, 2),
-                             "restrict_ms": round(sum(t_restrict) / args.steps, 5),
-                             "conv_ms": round(conv_ms, 5),
-                             "backward_ms": round(sum(t_bwd) / args.steps, 5),
-                             "paper_context": "up to 1 TB/s pixel-equivalent on one RTX 2080 Max-Q (P:51)"},
-        "roofline": {"kernel": "conv_fwd_kernel<2>", "bound": "hbm",
-                     "achieved": round(conv_bytes / (conv_ms * 1e-3) / 1e9, 2), "peak": hbm,
-                     "unit": "GB/s", "frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4),
-                     "traffic": None, "peak_source": src,
-                     "algorithmic_bytes_per_launch": conv_bytes},
+                             "paper_context": "up to 1 TB/s pixel-equivalent on one RTX 2080 Max-Q (paper abstract)"},
+        "step_ms_parts": {"tree_restrict": round(mean(t_restrict), 5), "convolve": round(conv_ms, 5),
+                          "convolve_adjoint": round(adj_ms, 5), "tree_restrict_adjoint": round(mean(t_tadj), 5),
+                          "stencil_grad": round(mean(t_sgrad), 5)},
+        "roofline": {"kernel": dom_name, "bound": "hbm",
+                     "achieved": round(conv_bytes / (dom_ms * 1e-3) / 1e9, 2), "peak": hbm,
+                     "unit": "GB/s", "frac": round(conv_bytes / (dom_ms * 1e-3) / 1e9 / hbm, 4),
+                     "traffic": traffic, "traffic_source": "profiles/traffic.json (ncu dram bytes, same source)"
+                     if traffic else None, "peak_source": src + " (hbm_gbs, copy bandwidth)",
+                     "algorithmic_bytes_per_launch": conv_bytes,
+                     "convolve_frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4)},
         "e2e": {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
                 "h2d_bytes_per_step": int(h_vals.numel() * 4 + h_gout.numel() * 4),
                 "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),

@@ -146,6 +146,32 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
                                    float *grad_particles, float *grad_stencils, void *workspace,
                                    size_t workspace_bytes, apr_stream_t stream);
 
+/* The three parts of apr_convolve_backward, callable on their own (each is the adjoint of one
+ * forward piece; apr_convolve_backward runs them in this order).
+ *
+ * apr_convolve_adjoint: transpose of apr_convolve w.r.t. its value inputs (Sec. 4.1, 5.2): with
+ * g = grad_out, grad_particles[q] = sum of g_p * w[e] over the taps that read particle q directly
+ * (at q's level) or as the coarse fill of the next finer level; grad_tree[t] = the same for tree
+ * node t. Both outputs are overwritten (device [N_p] and [N_t] float32). */
+apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                                  float *grad_particles, float *grad_tree, apr_stream_t stream);
+
+/* apr_tree_restrict_adjoint: transpose of apr_tree_restrict (Sec. 3.4), from the coarsest level
+ * down: every tree node's gradient is divided by its number of in-grid children and added to each
+ * child (tree node or particle). grad_tree (device [N_t]) is updated in place to the accumulated tree
+ * gradients; the particle shares are ADDED to grad_particles (device [N_p]). */
+apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *grad_particles, apr_stream_t stream);
+
+/* Scratch bytes of apr_convolve_stencil_grad for stencil size k (per-tile partial sums). */
+size_t apr_stencil_grad_workspace_bytes(apr_handle_t h, int32_t k);
+
+/* apr_convolve_stencil_grad: grad_stencils[l][e] = sum over particles p of level l of
+ * grad_out[p] * u_l(refl(i_p + e)) (device [L][k^3], overwritten), summed in a fixed order.
+ * workspace: device scratch of apr_stencil_grad_workspace_bytes(h, k) bytes, 256-byte aligned. */
+apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, const float *tree, int32_t k, int32_t bc,
+                                       const float *grad_out, float *grad_stencils, void *workspace,
+                                       size_t workspace_bytes, apr_stream_t stream);
+
 /* apr_convolve_backward for callers that cannot allocate device memory. The paper has no counterpart.
  * Some callers may not call cudaMalloc at all: code running inside a host callback or a framework
  * hook that must not allocate, a process whose device memory is reserved up front by another

@@ -11,6 +11,7 @@ Functions with the C names:
     apr_convolve(layout, particles, tree, stencils, k[, bc, out]) -> out       (Sec. 4.1)
     apr_convolve_backward(layout, particles, tree, stencils, k, grad_out[, bc])
                                                                   -> (grad_particles, grad_stencils)
+      = apr_convolve_adjoint + apr_tree_restrict_adjoint + apr_convolve_stencil_grad
     apr_restrict_stencil(w, l_max, l_min)                         -> [L][k^3]  (Eq. restrict_stenc)
     apr_rescale_stencil(w, l_max, l_min)                          -> [L][k^3]  (Eq. adapt_grad)
 plus ``AprConv`` (torch.autograd.Function): particles, stencils -> per-particle outputs.
@@ -26,7 +27,8 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
                    AprError)
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
-           "apr_convolve_backward", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
+           "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
+           "apr_convolve_stencil_grad", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY"]
 
 
@@ -187,6 +189,53 @@ def apr_convolve_backward(layout: AprLayout, particles, tree, stencils, k, grad_
         int(k), int(bc), ctypes.c_void_p(grad_out.data_ptr()), gp_ptr, gw_ptr,
         ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
     return (grad_particles if need_particles else None), (grad_stencils if need_stencils else None)
+
+
+def apr_convolve_adjoint(layout: AprLayout, stencils, k, grad_out, bc=APR_BC_REFLECT, grad_particles=None,
+                         grad_tree=None, stream=None):
+    """(grad_particles, grad_tree): transpose of apr_convolve w.r.t. particle and tree values."""
+    import torch
+    _dev_ptr(grad_out, "grad_out", layout.n_particles, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    if grad_particles is None:
+        grad_particles = torch.empty(layout.n_particles, dtype=torch.float32, device=grad_out.device)
+    if grad_tree is None:
+        grad_tree = torch.empty(layout.n_tree, dtype=torch.float32, device=grad_out.device)
+    _abi.check("apr_convolve_adjoint", layout._lib.apr_convolve_adjoint(
+        layout.handle, _dev_ptr(stencils, "stencils"), int(k), int(bc), _dev_ptr(grad_out, "grad_out"),
+        _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32),
+        _dev_ptr(grad_tree, "grad_tree", layout.n_tree, torch.float32), _stream_ptr(stream)))
+    return grad_particles, grad_tree
+
+
+def apr_tree_restrict_adjoint(layout: AprLayout, grad_tree, grad_particles, stream=None):
+    """Push tree gradients down to the particles (adds into grad_particles; grad_tree is updated)."""
+    import torch
+    _abi.check("apr_tree_restrict_adjoint", layout._lib.apr_tree_restrict_adjoint(
+        layout.handle, _dev_ptr(grad_tree, "grad_tree", layout.n_tree, torch.float32),
+        _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32), _stream_ptr(stream)))
+    return grad_particles
+
+
+def apr_convolve_stencil_grad(layout: AprLayout, particles, tree, k, grad_out, bc=APR_BC_REFLECT,
+                              grad_stencils=None, stream=None):
+    """dL/d stencils [L][k^3] for dL/d out = grad_out."""
+    import torch
+    if grad_stencils is None:
+        grad_stencils = torch.empty((layout.n_levels, k ** 3), dtype=torch.float32, device=grad_out.device)
+    nbytes = int(layout._lib.apr_stencil_grad_workspace_bytes(layout.handle, k))
+    key = ("sg", k)
+    ws = layout._ws.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=grad_out.device)
+        layout._ws[key] = ws
+    _abi.check("apr_convolve_stencil_grad", layout._lib.apr_convolve_stencil_grad(
+        layout.handle, _dev_ptr(particles, "particles", layout.n_particles, torch.float32),
+        _dev_ptr(tree, "tree", layout.n_tree, torch.float32), int(k), int(bc),
+        _dev_ptr(grad_out, "grad_out", layout.n_particles, torch.float32),
+        _dev_ptr(grad_stencils, "grad_stencils", layout.n_levels * k ** 3, torch.float32),
+        ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
+    return grad_stencils
 
 
 def _stencil_stack(fn_name, w, l_max, l_min):

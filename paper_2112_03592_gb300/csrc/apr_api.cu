@@ -246,6 +246,56 @@ size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k) {
     return al(size_t(h->X.nt) * sizeof(float)) + al(h->X.fwd_items.size() * size_t(k * k * k) * sizeof(float));
 }
 
+apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                                  float *grad_particles, float *grad_tree, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!stencils || (X.np && (!grad_out || !grad_particles)) || (X.nt && !grad_tree)) return APR_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * sizeof(float), stream);
+    if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(grad_tree, 0, size_t(X.nt) * sizeof(float), stream);
+    if (e == cudaSuccess)
+        e = launch_bwd_data(k, h->L, h->d_bwd, int(X.bwd_items.size()), stencils, bc, grad_out, grad_particles, grad_tree, stream);
+    return cuda_status(e);
+}
+
+apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *grad_particles, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if ((X.nt && !grad_tree) || (X.np && !grad_particles)) return APR_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
+        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        e = launch_tree_pushdown(h->L, h->d_tree + b, int(n), grad_particles, grad_tree, stream);
+    }
+    return cuda_status(e);
+}
+
+size_t apr_stencil_grad_workspace_bytes(apr_handle_t h, int32_t k) {
+    if (!h || !stencil_k_ok(k)) return 0;
+    return (h->X.fwd_items.size() * size_t(k * k * k) * sizeof(float) + 255) / 256 * 256;
+}
+
+apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, const float *tree, int32_t k, int32_t bc,
+                                       const float *grad_out, float *grad_stencils, void *workspace,
+                                       size_t workspace_bytes, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!grad_stencils || (X.np && (!particles || !grad_out)) || (X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    const size_t need = apr_stencil_grad_workspace_bytes(h, k);
+    if (need && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255))) return APR_ERR_INVALID_ARG;
+    const int n = int(X.fwd_items.size());
+    float *partial = static_cast<float *>(workspace);
+    cudaError_t e = launch_bwd_stencil(k, h->L, h->d_fwd, n, particles, tree, bc, grad_out, partial, stream);
+    if (e == cudaSuccess)
+        e = launch_stencil_reduce(partial, n, h->d_fwd_level_begin, X.l_min, X.l_max - X.l_min + 1, k * k * k, grad_stencils, stream);
+    return cuda_status(e);
+}
+
 apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                                    int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
                                    float *grad_stencils, void *workspace, size_t workspace_bytes,
@@ -260,26 +310,16 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
     if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return APR_ERR_INVALID_ARG;
     const size_t gt_bytes = (size_t(X.nt) * sizeof(float) + 255) / 256 * 256;
     float *gt = static_cast<float *>(workspace);
-    float *partial = reinterpret_cast<float *>(static_cast<char *>(workspace) + gt_bytes);
-    const int k3 = k * k * k;
-    cudaError_t e = cudaSuccess;
+    void *partial = static_cast<char *>(workspace) + gt_bytes;
+    apr_status_t st = APR_OK;
     if (grad_particles) {
-        if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * sizeof(float), stream);
-        if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(gt, 0, size_t(X.nt) * sizeof(float), stream);
-        if (e == cudaSuccess)
-            e = launch_bwd_data(k, h->L, h->d_bwd, int(X.bwd_items.size()), stencils, bc, grad_out, grad_particles, gt, stream);
-        for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
-            const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-            e = launch_tree_pushdown(h->L, h->d_tree + b, int(n), grad_particles, gt, stream);
-        }
+        st = apr_convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream);
+        if (st == APR_OK) st = apr_tree_restrict_adjoint(h, gt, grad_particles, stream);
     }
-    if (e == cudaSuccess && grad_stencils) {
-        const int n = int(X.fwd_items.size());
-        e = launch_bwd_stencil(k, h->L, h->d_fwd, n, particles, tree, bc, grad_out, partial, stream);
-        if (e == cudaSuccess)
-            e = launch_stencil_reduce(partial, n, h->d_fwd_level_begin, X.l_min, X.l_max - X.l_min + 1, k3, grad_stencils, stream);
-    }
-    return cuda_status(e);
+    if (st == APR_OK && grad_stencils)
+        st = apr_convolve_stencil_grad(h, particles, tree, k, bc, grad_out, grad_stencils, partial,
+                                       workspace_bytes - gt_bytes, stream);
+    return st;
 }
 
 apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream) {

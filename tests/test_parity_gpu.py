@@ -166,3 +166,33 @@ def test_structure_on_device_is_bit_exact():
     assert np.array_equal(lay.export(_abi.APR_STRUCT_Y_IDX), apr.y_idx.astype(np.uint16))
     assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_ROW_PTR), rp.astype(np.uint32))
     assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_Y_IDX), ty.astype(np.uint16))
+
+
+def test_backward_parts_compose_to_backward():
+    apr = CASES["rand_ragged"]()
+    st = stencil_stack(apr, 5, "random", seed=8)
+    lay, v, tree, _ = gpu_forward(apr, st, 5, G.APR_BC_REFLECT)
+    g = dev(np.random.default_rng(3).normal(size=apr.n_particles).astype(np.float32))
+    ref_p, ref_w = G.apr_convolve_backward(lay, v, tree, dev(st), 5, g)
+    gp, gt = G.apr_convolve_adjoint(lay, dev(st), 5, g)
+    G.apr_tree_restrict_adjoint(lay, gt, gp)
+    gw = G.apr_convolve_stencil_grad(lay, v, tree, 5, g)
+    torch.cuda.synchronize()
+    assert torch.equal(gp, ref_p) and torch.equal(gw, ref_w)
+
+
+def test_convolve_adjoint_dot_product():
+    # <A x, y> == <x, A^T y> for the convolution alone (tree values as an independent input)
+    apr = CASES["blob64"]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    rng = np.random.default_rng(7)
+    st = dev(rng.normal(size=(apr.n_levels, 27)).astype(np.float32))
+    x = rng.normal(size=apr.n_particles)
+    t = rng.normal(size=lay.n_tree)
+    y = rng.normal(size=apr.n_particles)
+    out = G.apr_convolve(lay, dev(x.astype(np.float32)), dev(t.astype(np.float32)), st, 3)
+    gp, gt = G.apr_convolve_adjoint(lay, st, 3, dev(y.astype(np.float32)))
+    torch.cuda.synchronize()
+    lhs = float(np.dot(out.cpu().double().numpy(), y))
+    rhs = float(np.dot(x, gp.cpu().double().numpy()) + np.dot(t, gt.cpu().double().numpy()))
+    assert abs(lhs - rhs) <= 1e-5 * max(1.0, abs(lhs)), (lhs, rhs)
