@@ -65,6 +65,10 @@ def _load():
         lib.ora_conv_backward.argtypes = [P, D, I32, I32, I32, D, P, I64, D, D]
         lib.ora_check_coarse_fill.restype = I64
         lib.ora_check_coarse_fill.argtypes = [P, I32]
+        lib.ora_tree_fill_bf16.restype = I32
+        lib.ora_tree_fill_bf16.argtypes = [P]
+        lib.ora_round_bf16.restype = ctypes.c_double
+        lib.ora_round_bf16.argtypes = [ctypes.c_double]
         _lib = lib
     return _lib
 
@@ -74,6 +78,11 @@ def _ptr(a):
 
 
 BC_REFLECT, BC_ZERO = 0, 1
+
+
+def round_bf16(v: float) -> float:
+    """The oracle's bfloat16 rounding (nearest, ties to even) of one value."""
+    return float(_load().ora_round_bf16(float(v)))
 
 
 class Oracle:
@@ -135,6 +144,18 @@ class Oracle:
             if rc:
                 raise ValueError(f"oracle: invalid APR (tree fill error {rc})")
             self._filled = True
+        out = np.zeros((max(self.n_tree, 1), self.C), np.float64)
+        lib.ora_get_tree(self.h, _ptr(out))
+        return out[:self.n_tree]
+
+    def tree_bf16(self) -> np.ndarray:
+        """Tree values [N_t][C] for bfloat16 features: every node's average rounded to bfloat16
+        (nearest, ties to even) before the next coarser level uses it. Later conv() calls use them."""
+        lib = _load()
+        rc = lib.ora_tree_fill_bf16(self.h)
+        if rc:
+            raise ValueError(f"oracle: invalid APR (tree fill error {rc})")
+        self._filled = True
         out = np.zeros((max(self.n_tree, 1), self.C), np.float64)
         lib.ora_get_tree(self.h, _ptr(out))
         return out[:self.n_tree]

@@ -268,6 +268,58 @@ int ora_tree_fill(ora_t *o) {
     return 0;
 }
 
+/* Round a double to the nearest bfloat16 (ties to even) and return it as a double. The value is
+ * first rounded to float (round-to-nearest), then the low 16 bits of the float are rounded away. */
+static double round_bf16(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;  /* inf / nan unchanged */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+double ora_round_bf16(double v) { return round_bf16(v); }
+
+/* Tree fill for bfloat16 features: the same average of children (Sec. 3.4), each node's value
+ * rounded to bfloat16 before it is used by the next coarser level. */
+int ora_tree_fill_bf16(ora_t *o) {
+    const int C = o->C;
+    int rc = 0;
+    for (int l = o->l_max - 1; l >= o->l_min && !rc; --l) {
+        /* one level at a time: fill (exact FP64 average), then round this level */
+        for (int64_t j = 0; j < o->T[l].n; ++j) {
+            int64_t t = o->t_off[l] + j;
+            int64_t z = o->tz[t], x = o->tx[t], y = o->ty[t];
+            double *acc = &o->tval[t * C];
+            for (int c = 0; c < C; ++c) acc[c] = 0.0;
+            int n = 0;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int e = 0; e < 2; ++e) {
+                        int64_t cz = 2 * z + a, cx = 2 * x + b, cy = 2 * y + e;
+                        if (cz >= o->ld[l + 1][0] || cx >= o->ld[l + 1][1] || cy >= o->ld[l + 1][2]) continue;
+                        uint64_t k = cell_key(o, l + 1, cz, cx, cy);
+                        int64_t i = find(&o->P[l + 1], k);
+                        const double *v;
+                        if (i >= 0) v = &o->pval[i * C];
+                        else {
+                            int64_t ti = find(&o->T[l + 1], k);
+                            if (ti < 0) { o->error = 2; return 2; }
+                            v = &o->tval[ti * C];
+                        }
+                        for (int c = 0; c < C; ++c) acc[c] += v[c];
+                        ++n;
+                    }
+            for (int c = 0; c < C; ++c) acc[c] = round_bf16(acc[c] / (double)n);
+        }
+    }
+    return rc;
+}
+
 void ora_get_tree(const ora_t *o, double *out) { memcpy(out, o->tval, sizeof(double) * (size_t)o->nt * (size_t)o->C); }
 void ora_set_values(ora_t *o, const double *values) { memcpy(o->pval, values, sizeof(double) * (size_t)o->np * (size_t)o->C); }
 

@@ -253,3 +253,28 @@ def test_invalid_layouts_are_detected():
     ps2 += [(1, z, x, y, 1.0) for z in range(2) for x in range(2) for y in range(2)]
     assert Oracle(S.apr_from_particles((4, 4, 4), 1, ps2)).error != 0
     assert Oracle(apr).error == 0
+
+
+# ------------------------------------------------------------------------------------------ bf16
+def test_bf16_rounding_matches_torch():
+    import torch
+    rng = np.random.default_rng(0)
+    v = np.concatenate([rng.normal(size=2000) * 10.0 ** rng.integers(-6, 6, size=2000),
+                        [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, -(1.0 + 2 ** -9), 0.0, 255.5, 256.5]])
+    ref = torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle.round_bf16(x) for x in v])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_bf16_tree_is_rounded_average_level_by_level():
+    apr = S.random_balanced_apr((16, 16, 16), 1, seed=6)
+    rng = np.random.default_rng(1)
+    vals = rng.integers(-64, 65, size=(apr.n_particles, 3)) / 8.0
+    o = Oracle(apr, vals)
+    t = o.tree_bf16()
+    # every value is a bfloat16, and the finest-level nodes are the rounded exact averages
+    assert all(oracle.round_bf16(x) == x for x in t.ravel())
+    tc = o.tree_coords()
+    exact = Oracle(apr, vals).tree()
+    fin = tc[:, 0] == apr.l_max - 1
+    np.testing.assert_array_equal(t[fin], np.vectorize(oracle.round_bf16)(exact[fin]))
