@@ -1,0 +1,163 @@
+// Device helpers shared by the single-channel and multi-channel kernels: block barrier, reflection,
+// per-block row offsets, block scan and the flattened element-staging loop.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "apr_internal.h"
+
+namespace aprk {
+namespace dev {
+
+constexpr int NT = 256;                // threads per block of every kernel below
+constexpr int NWARP = NT / 32;
+constexpr int UNROLL = 8;              // element loads in flight per thread and staging step
+static_assert(TZ % 2 == 0 && TX % 2 == 0, "tiles must be even-aligned (coarse cells)");
+
+// Block barrier. The warp is reconverged first: threads of one warp may reach this point at
+// different times after data-dependent loops, and the block barrier must be executed by converged
+// warps.
+__device__ __forceinline__ void block_sync() {
+    __syncwarp();
+    __syncthreads();
+}
+
+__device__ __forceinline__ int reflect_idx(int i, int d) {
+    // half-sample symmetric reflection into [0, d), repeated for grids smaller than the stencil
+    const int p = 2 * d;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m >= d ? p - 1 - m : m;
+}
+
+// First element of y-block j of a row (particles or tree); j >= nb gives the row end.
+__device__ __forceinline__ uint32_t blk_start(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb,
+                                              int rr, int j) {
+    if (j >= nb) return rp[row0 + rr + 1];
+    return rp[row0 + rr] + off[off0 + rr * nb + j];
+}
+
+__device__ __forceinline__ uint32_t pblock(const DevLayout &L, const LevelGeo &g, int rr, int j) {
+    return blk_start(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, j);
+}
+
+__device__ __forceinline__ uint32_t tblock(const DevLayout &L, const LevelGeo &g, int rr, int j) {
+    return blk_start(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, j);
+}
+
+// Index range [lo, hi) of a row containing every element with y in [ya, yb) (ya < yb), plus at
+// most BY/2 extra elements on each side (callers filter by y). Uses the per-block offsets only:
+// at most BY - ra elements of block ja lie at or after ya, at most rb elements of block jb before yb.
+__device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb, int rr,
+                                          int ya, int yb, int &lo, int &hi) {
+    const int rs = int(rp[row0 + rr]), re = int(rp[row0 + rr + 1]);
+    const int ja = ya / BY, ra = ya - ja * BY;
+    const int jb = yb / BY, rb = yb - jb * BY;
+    int a = ra <= BY / 2 ? int(blk_start(rp, off, row0, off0, nb, rr, ja))
+                         : int(blk_start(rp, off, row0, off0, nb, rr, ja + 1)) - (BY - ra);
+    int b = rb <= BY / 2 ? int(blk_start(rp, off, row0, off0, nb, rr, jb)) + rb
+                         : int(blk_start(rp, off, row0, off0, nb, rr, jb + 1));
+    a = max(a, rs);
+    b = min(b, re);
+    lo = a;
+    hi = max(a, b);
+}
+
+// Block-wide exclusive scan of values held two per thread (entries 2t, 2t+1): writes pre[0..n]
+// (pre[n] = total). n <= 2*NT. Starts and ends with a barrier.
+__device__ void block_scan2(int c0, int c1, int n, int *pre, int *warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = c0 + c1;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    block_sync();
+    if (lane == 31) warp_tot[warp] = incl;
+    block_sync();
+    if (tid == 0) {
+        int acc = 0;
+        for (int w = 0; w < NWARP; ++w) {
+            const int v = warp_tot[w];
+            warp_tot[w] = acc;
+            acc += v;
+        }
+        warp_tot[NWARP] = acc;
+    }
+    block_sync();
+    const int excl = warp_tot[warp] + incl - s;
+    if (2 * tid < n) pre[2 * tid] = excl;
+    if (2 * tid + 1 < n) pre[2 * tid + 1] = excl + c0;
+    if (tid == 0) pre[n] = warp_tot[NWARP];
+    block_sync();
+}
+
+struct SlotYV {
+    int y;
+    float v;
+};
+
+// Loads y and value of element i of segment seg; segments [t0, t1) are tree segments.
+struct YVLoader {
+    using Slot = SlotYV;
+    const uint16_t *py, *ty;
+    const float *pv, *tv;
+    int t0, t1;
+    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
+        const bool t = seg >= t0 && seg < t1;
+        s.y = t ? int(ty[i]) : int(py[i]);
+        s.v = t ? tv[i] : pv[i];
+    }
+};
+
+// Flattened loop over the elements of nseg segments (segment s: global indices seg_lo[s] ..
+// seg_lo[s] + pre[s+1] - pre[s]), in chunks of SEGID_CAP elements. For every chunk, the threads
+// first write the segment id of each element into segid[] (one thread per segment), then every warp
+// takes a contiguous share of the chunk with strided lanes, issuing the loads of UNROLL elements
+// per thread before any of them is used. Trip counts depend on the warp only (lanes stay converged).
+// Ends with a block barrier.
+constexpr int SEGID_CAP = 4096;
+
+template <typename Load, typename Use>
+__device__ __forceinline__ void for_each_element(const int *seg_lo, const int *pre, int nseg, unsigned short *segid,
+                                                 const Load &load, Use use) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int E0 = pre[0], E1 = pre[nseg];
+    for (int c0 = E0; c0 < E1; c0 += SEGID_CAP) {
+        const int c1 = min(E1, c0 + SEGID_CAP);
+        for (int sg = threadIdx.x; sg < nseg; sg += NT) {
+            const int a = max(pre[sg], c0), b = min(pre[sg + 1], c1);
+            for (int e = a; e < b; ++e) segid[e - c0] = (unsigned short)sg;
+        }
+        block_sync();
+        const int share = (c1 - c0 + NWARP - 1) / NWARP;
+        const int ea = c0 + warp * share, eb = min(c1, ea + share);
+        for (int base = ea; base < eb; base += 32 * UNROLL) {
+            int sg[UNROLL], ix[UNROLL];
+            typename Load::Slot slot[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int eu = base + lane + 32 * u;
+                sg[u] = -1;
+                ix[u] = 0;
+                if (eu < eb) {
+                    const int sgu = segid[eu - c0];
+                    sg[u] = sgu;
+                    ix[u] = seg_lo[sgu] + (eu - pre[sgu]);
+                    load(sgu, ix[u], slot[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (sg[u] >= 0) use(sg[u], ix[u], slot[u]);
+        }
+        block_sync();
+    }
+}
+
+}  // namespace dev
+}  // namespace aprk
