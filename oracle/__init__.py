@@ -96,6 +96,7 @@ class Oracle:
         if vals.ndim == 1:
             vals = vals[:, None]
         self.C = vals.shape[1]
+        self._vals = vals
         self._keep = [np.ascontiguousarray(np.asarray(apr.dims, np.int64)),
                       np.ascontiguousarray(apr.row_ptr.astype(np.int64)),
                       np.ascontiguousarray(apr.y_idx.astype(np.int32))]
@@ -134,6 +135,7 @@ class Oracle:
     def set_values(self, values):
         v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(self.apr.n_particles, self.C))
         _load().ora_set_values(self.h, _ptr(v))
+        self._vals = v
         self._filled = False
 
     def tree(self) -> np.ndarray:
@@ -149,9 +151,14 @@ class Oracle:
         return out[:self.n_tree]
 
     def tree_bf16(self) -> np.ndarray:
-        """Tree values [N_t][C] for bfloat16 features: every node's average rounded to bfloat16
-        (nearest, ties to even) before the next coarser level uses it. Later conv() calls use them."""
+        """Tree values [N_t][C] for bfloat16 features with FP32 accumulation: per node and channel,
+        the FP32 sum of the in-grid children in (dz, dx, dy) order divided by their count in FP32,
+        rounded to bfloat16 (nearest, ties to even) before the next coarser level uses it. The
+        particle values must be bfloat16 numbers. Later conv() / conv_backward() calls use them."""
         lib = _load()
+        v32 = self._vals.astype(np.float32)
+        if not (np.all(v32.astype(np.float64) == self._vals) and np.all((v32.view(np.uint32) & 0xFFFF) == 0)):
+            raise ValueError("oracle: tree_bf16 needs particle values that are bfloat16 numbers")
         rc = lib.ora_tree_fill_bf16(self.h)
         if rc:
             raise ValueError(f"oracle: invalid APR (tree fill error {rc})")

@@ -287,15 +287,18 @@ double ora_round_bf16(double v) { return round_bf16(v); }
 /* Tree fill for bfloat16 features: the same average of children (Sec. 3.4), each node's value
  * rounded to bfloat16 before it is used by the next coarser level. */
 int ora_tree_fill_bf16(ora_t *o) {
+    /* BF16 tree of the multi-channel path (BF16 activations, FP32 accumulation): per node and
+     * channel, the in-grid children are summed in FP32 in (dz, dx, dy) order starting from 0, the
+     * sum is divided by their count in FP32, and the quotient is rounded to BF16. Levels are filled
+     * finest first, each from the rounded values of the level below. */
     const int C = o->C;
-    int rc = 0;
-    for (int l = o->l_max - 1; l >= o->l_min && !rc; --l) {
-        /* one level at a time: fill (exact FP64 average), then round this level */
+    float acc[64];
+    if (C > 64) return 1;
+    for (int l = o->l_max - 1; l >= o->l_min; --l)
         for (int64_t j = 0; j < o->T[l].n; ++j) {
             int64_t t = o->t_off[l] + j;
             int64_t z = o->tz[t], x = o->tx[t], y = o->ty[t];
-            double *acc = &o->tval[t * C];
-            for (int c = 0; c < C; ++c) acc[c] = 0.0;
+            for (int c = 0; c < C; ++c) acc[c] = 0.0f;
             int n = 0;
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b)
@@ -311,13 +314,12 @@ int ora_tree_fill_bf16(ora_t *o) {
                             if (ti < 0) { o->error = 2; return 2; }
                             v = &o->tval[ti * C];
                         }
-                        for (int c = 0; c < C; ++c) acc[c] += v[c];
+                        for (int c = 0; c < C; ++c) acc[c] = acc[c] + (float)v[c];
                         ++n;
                     }
-            for (int c = 0; c < C; ++c) acc[c] = round_bf16(acc[c] / (double)n);
+            for (int c = 0; c < C; ++c) o->tval[t * C + c] = round_bf16((double)(acc[c] / (float)n));
         }
-    }
-    return rc;
+    return 0;
 }
 
 void ora_get_tree(const ora_t *o, double *out) { memcpy(out, o->tval, sizeof(double) * (size_t)o->nt * (size_t)o->C); }
