@@ -189,6 +189,50 @@ apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particle
                                            const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                            float *grad_particles, float *grad_stencils, apr_stream_t stream);
 
+/* ---- Multi-channel convolution with bfloat16 features and weights (the APR CNN layer that Sec. 6
+ * proposes: several feature channels per particle, mixed by per-level learned filters). Features are
+ * bfloat16 (stored as uint16 bit patterns), channels-last; products are exact and accumulate in FP32
+ * on the tensor cores. Supported: channels = c_in = c_out = 16, k = 3. Pointers to features, weights,
+ * gradients and outputs must be 16-byte aligned. */
+
+/* BF16 tree restriction: as apr_tree_restrict, per channel, with the arithmetic of the BF16 layer:
+ * a node's in-grid children are summed in FP32 in (dz, dx, dy) order, divided by their count in FP32,
+ * and the quotient is rounded to bfloat16 (nearest, ties to even) before the next coarser level uses
+ * it. particles: device [N_p][channels] bf16; tree: device [N_t][channels] bf16, every entry written.
+ * Results are bit-exact. */
+apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, uint16_t *tree, int32_t channels,
+                                    apr_stream_t stream);
+
+/* Multi-channel APR convolution (Sec. 4.1 per output channel, summed over input channels): for every
+ * particle p at level l,
+ *   out[p][co] = sum_{ci} sum_{e in [-1,1]^3} weights[l - l_min][co][ci][e] * u_l(refl(i_p + e))[ci],
+ * with u_l and the boundary rule as in apr_convolve.
+ *   particles: device [N_p][c_in] bf16;  tree: device [N_t][c_in] bf16 from apr_tree_restrict_bf16;
+ *   weights:   device [(l_max-l_min+1)][c_out][c_in][k^3] bf16 ([z][x][y] taps, y fastest);
+ *   out:       device [N_p][c_out] float32, overwritten.
+ * Returns APR_ERR_UNSUPPORTED unless c_in = c_out = 16 and k = 3. A tensor-core wait that does not
+ * finish in bounded time records APR_ERR_TIMEOUT for apr_sync_status. */
+apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree, const uint16_t *weights,
+                             int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out, apr_stream_t stream);
+
+/* Scratch bytes of apr_convolve_mc_backward (tree gradient and per-block weight-gradient partials). */
+size_t apr_mc_backward_workspace_bytes(apr_handle_t h, int32_t c_in, int32_t c_out, int32_t k);
+
+/* Adjoint of apr_tree_restrict_bf16 followed by apr_convolve_mc, with the rounding of the tree taken
+ * as the identity (the derivative of the exact average). With g = grad_out:
+ *   grad_particles[q][ci] = sum over taps that read q (directly, or as the coarse fill of the next
+ *        finer level) of sum_co g_p[co] * weights[l][co][ci][e], plus the tree shares as in
+ *        apr_convolve_backward;
+ *   grad_weights[l][co][ci][e] = sum_{p at level l} g_p[co] * u_l(refl(i_p + e))[ci].
+ * grad_out: device [N_p][c_out] bf16 (the caller rounds the incoming FP32 gradient). grad_particles
+ * (device [N_p][c_in] float32) and grad_weights (device [L][c_out][c_in][k^3] float32) are
+ * overwritten; either may be NULL. workspace: apr_mc_backward_workspace_bytes bytes, 256-byte
+ * aligned. Results are deterministic (fixed summation order). */
+apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles, const uint16_t *tree,
+                                      const uint16_t *weights, int32_t c_in, int32_t c_out, int32_t k, int32_t bc,
+                                      const uint16_t *grad_out, float *grad_particles, float *grad_weights,
+                                      void *workspace, size_t workspace_bytes, apr_stream_t stream);
+
 /* Restricted stencils (Eq. restrict_stenc, K_{w_l} = R_l K_w P_l with block-average R_l and
  * piecewise-constant P_l): out[l - l_min][e] = sum_d w[d] * prod_axes c_s(d_a, e_a), where
  * c_s(d, e) = (1/s) #{x in [0, s): floor((x + d) / s) = e} and s = 2^(l_max - l). Host memory in and
@@ -198,8 +242,9 @@ apr_status_t apr_restrict_stencil(const float *w, int32_t k, int32_t l_max, int3
 /* Level-rescaled stencils (Eq. adapt_grad): out[l - l_min] = 2^-(l_max - l) * w. Host memory. */
 apr_status_t apr_rescale_stencil(const float *w, int32_t k, int32_t l_max, int32_t l_min, float *out);
 
-/* Wait for `stream`, then read and clear the handle's device error word. Returns APR_ERR_DEVICE if a
- * device-side check failed since the last call, else APR_OK (or APR_ERR_CUDA). */
+/* Wait for `stream`, then read and clear the handle's device error word. Returns APR_ERR_TIMEOUT if a
+ * bounded device wait gave up since the last call, APR_ERR_DEVICE if another device-side check
+ * failed, else APR_OK (or APR_ERR_CUDA). */
 apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream);
 
 const char *apr_status_string(apr_status_t s);

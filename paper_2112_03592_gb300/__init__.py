@@ -12,6 +12,10 @@ Functions with the C names:
     apr_convolve_backward(layout, particles, tree, stencils, k, grad_out[, bc])
                                                                   -> (grad_particles, grad_stencils)
       = apr_convolve_adjoint + apr_tree_restrict_adjoint + apr_convolve_stencil_grad
+    apr_tree_restrict_bf16(layout, particles[, tree])             -> tree      (bf16, 16 channels)
+    apr_convolve_mc(layout, particles, tree, weights[, bc, out])  -> out       (16 -> 16 channels, k = 3)
+    apr_convolve_mc_backward(layout, particles, tree, weights, grad_out[, bc])
+                                                                  -> (grad_particles, grad_weights)
     apr_restrict_stencil(w, l_max, l_min)                         -> [L][k^3]  (Eq. restrict_stenc)
     apr_rescale_stencil(w, l_max, l_min)                          -> [L][k^3]  (Eq. adapt_grad)
 plus ``AprConv`` (torch.autograd.Function): particles, stencils -> per-particle outputs.
@@ -28,7 +32,8 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
-           "apr_convolve_stencil_grad", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
+           "apr_convolve_stencil_grad", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
+           "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY"]
 
 
@@ -236,6 +241,74 @@ def apr_convolve_stencil_grad(layout: AprLayout, particles, tree, k, grad_out, b
         _dev_ptr(grad_stencils, "grad_stencils", layout.n_levels * k ** 3, torch.float32),
         ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
     return grad_stencils
+
+
+# ---- multi-channel, bfloat16 features (16 channels, k = 3)
+MC_CHANNELS = 16
+
+
+def apr_tree_restrict_bf16(layout: AprLayout, particles, tree=None, stream=None):
+    """BF16 tree [N_t][16] of particles [N_p][16] (FP32 averages rounded to bf16, level by level)."""
+    import torch
+    C = int(particles.shape[1])
+    _dev_ptr(particles, "particles", layout.n_particles * C, torch.bfloat16)
+    if tree is None:
+        tree = torch.empty((layout.n_tree, C), dtype=torch.bfloat16, device=particles.device)
+    _dev_ptr(tree, "tree", layout.n_tree * C, torch.bfloat16)
+    _abi.check("apr_tree_restrict_bf16", layout._lib.apr_tree_restrict_bf16(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()), C, _stream_ptr(stream)))
+    return tree
+
+
+def apr_convolve_mc(layout: AprLayout, particles, tree, weights, bc=APR_BC_REFLECT, out=None, stream=None):
+    """out[p][co] (float32) = sum_ci sum_e weights[l][co][ci][e] * u_l(...)[ci]; bf16 inputs."""
+    import torch
+    C = MC_CHANNELS
+    k = 3
+    _dev_ptr(particles, "particles", layout.n_particles * C, torch.bfloat16)
+    _dev_ptr(tree, "tree", layout.n_tree * C, torch.bfloat16)
+    _dev_ptr(weights, "weights", layout.n_levels * C * C * k ** 3, torch.bfloat16)
+    if out is None:
+        out = torch.empty((layout.n_particles, C), dtype=torch.float32, device=particles.device)
+    _dev_ptr(out, "out", layout.n_particles * C, torch.float32)
+    _abi.check("apr_convolve_mc", layout._lib.apr_convolve_mc(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
+        ctypes.c_void_p(weights.data_ptr()), C, C, k, int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_convolve_mc_backward(layout: AprLayout, particles, tree, weights, grad_out, bc=APR_BC_REFLECT,
+                             need_particles=True, need_weights=True, grad_particles=None, grad_weights=None,
+                             stream=None):
+    """(grad_particles [N_p][16] float32, grad_weights [L][16][16][27] float32); grad_out is bf16."""
+    import torch
+    C = MC_CHANNELS
+    k = 3
+    _dev_ptr(grad_out, "grad_out", layout.n_particles * C, torch.bfloat16)
+    _dev_ptr(weights, "weights", layout.n_levels * C * C * k ** 3, torch.bfloat16)
+    gp_ptr = gw_ptr = ctypes.c_void_p(0)
+    if need_particles:
+        if grad_particles is None:
+            grad_particles = torch.empty((layout.n_particles, C), dtype=torch.float32, device=grad_out.device)
+        gp_ptr = _dev_ptr(grad_particles, "grad_particles", layout.n_particles * C, torch.float32)
+    if need_weights:
+        _dev_ptr(particles, "particles", layout.n_particles * C, torch.bfloat16)
+        _dev_ptr(tree, "tree", layout.n_tree * C, torch.bfloat16)
+        if grad_weights is None:
+            grad_weights = torch.empty((layout.n_levels, C, C, k ** 3), dtype=torch.float32, device=grad_out.device)
+        gw_ptr = _dev_ptr(grad_weights, "grad_weights", layout.n_levels * C * C * k ** 3, torch.float32)
+    nbytes = int(layout._lib.apr_mc_backward_workspace_bytes(layout.handle, C, C, k))
+    key = ("mc", k)
+    ws = layout._ws.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=grad_out.device)
+        layout._ws[key] = ws
+    _abi.check("apr_convolve_mc_backward", layout._lib.apr_convolve_mc_backward(
+        layout.handle, ctypes.c_void_p(particles.data_ptr() if particles is not None else 0),
+        ctypes.c_void_p(tree.data_ptr() if tree is not None else 0), ctypes.c_void_p(weights.data_ptr()),
+        C, C, k, int(bc), ctypes.c_void_p(grad_out.data_ptr()), gp_ptr, gw_ptr,
+        ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
+    return (grad_particles if need_particles else None), (grad_weights if need_weights else None)
 
 
 def _stencil_stack(fn_name, w, l_max, l_min):

@@ -43,6 +43,10 @@ SIGNATURES = {
     "apr_tree_restrict_adjoint": (_I32, [_P, _P, _P, _P]),
     "apr_stencil_grad_workspace_bytes": (_SZ, [_P, _I32]),
     "apr_convolve_stencil_grad": (_I32, [_P, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
+    "apr_tree_restrict_bf16": (_I32, [_P, _P, _P, _I32, _P]),
+    "apr_convolve_mc": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
+    "apr_mc_backward_workspace_bytes": (_SZ, [_P, _I32, _I32, _I32]),
+    "apr_convolve_mc_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "apr_restrict_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
     "apr_rescale_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
     "apr_sync_status": (_I32, [_P, _P]),

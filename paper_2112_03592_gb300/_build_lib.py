@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 OUT = PKG / "_build"
 LIB = OUT / "libaprconv.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["apr_index.cpp", "apr_stencil.cpp", "apr_api.cu", "apr_kernels.cu", "apr_noalloc.cu"]
+SOURCES = ["apr_index.cpp", "apr_stencil.cpp", "apr_api.cu", "apr_kernels.cu", "apr_noalloc.cu", "apr_mc.cu"]
 
 
 def _nvcc() -> str:
@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 
 def _deps():
-    return [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list((ROOT / "include").glob("*.h"))
+    return [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list((ROOT / "include").glob("*.h"))
 
 
 def needs_build() -> bool:

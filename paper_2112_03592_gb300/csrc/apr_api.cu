@@ -23,18 +23,6 @@ cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, int n, f
 
 using namespace aprk;
 
-struct apr_handle_s {
-    HostIndex X;
-    bool host_only = false;
-    DevLayout L{};
-    Item *d_fwd = nullptr, *d_bwd = nullptr, *d_tree = nullptr;
-    int64_t *d_fwd_level_begin = nullptr;
-    uint32_t *d_row_ptr = nullptr, *d_trow_ptr = nullptr;
-    uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
-    unsigned *d_err = nullptr;
-    size_t dev_bytes = 0;
-};
-
 namespace {
 
 thread_local char g_last_msg[256] = "";
@@ -57,19 +45,19 @@ void free_device(apr_handle_s *h) {
         if (p) cudaFree(p);
 }
 
-apr_status_t cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return APR_OK;
-    if (e == cudaErrorMemoryAllocation) return APR_ERR_OOM;
-    snprintf(g_last_msg, sizeof(g_last_msg), "%s", cudaGetErrorString(e));
-    return APR_ERR_CUDA;
-}
-
 bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
 
 }  // namespace
 
 namespace aprk {
 void set_last_message(const char *msg) { snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg); }
+
+apr_status_t cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return APR_OK;
+    if (e == cudaErrorMemoryAllocation) return APR_ERR_OOM;
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", cudaGetErrorString(e));
+    return APR_ERR_CUDA;
+}
 }  // namespace aprk
 
 extern "C" {
@@ -332,7 +320,7 @@ apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream) {
     if (e != cudaSuccess) return cuda_status(e);
     if (v) {
         cudaMemset(h->d_err, 0, sizeof(unsigned));
-        return APR_ERR_DEVICE;
+        return (v & ERR_TIMEOUT) ? APR_ERR_TIMEOUT : APR_ERR_DEVICE;
     }
     return APR_OK;
 }

@@ -67,7 +67,7 @@ __device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *of
 
 // Block-wide exclusive scan of values held two per thread (entries 2t, 2t+1): writes pre[0..n]
 // (pre[n] = total). n <= 2*NT. Starts and ends with a barrier.
-__device__ void block_scan2(int c0, int c1, int n, int *pre, int *warp_tot) {
+__device__ inline void block_scan2(int c0, int c1, int n, int *pre, int *warp_tot) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = c0 + c1;
     int incl = s;

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "apr.h"
 
 namespace aprk {
@@ -67,9 +69,29 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &ou
 // Record a short reason for the last failure on this thread (read by apr_last_error_message).
 void set_last_message(const char *msg);
 
+// Bits of the device error word (DevLayout::err), read and cleared by apr_sync_status.
+constexpr unsigned ERR_DEVICE_CHECK = 1u;  // a device-side consistency check failed
+constexpr unsigned ERR_TIMEOUT = 2u;       // a bounded wait (tensor-core completion) gave up
+
+// Map a CUDA error to a status code, recording its message for apr_last_error_message.
+apr_status_t cuda_status(cudaError_t e);
+
 inline int64_t level_cells(int64_t D, int l_max, int l) {
     int64_t s = int64_t(1) << (l_max - l);
     return (D + s - 1) / s;
 }
 
 }  // namespace aprk
+
+// The object behind apr_handle_t: the host index and its device copy.
+struct apr_handle_s {
+    aprk::HostIndex X;
+    bool host_only = false;
+    aprk::DevLayout L{};
+    aprk::Item *d_fwd = nullptr, *d_bwd = nullptr, *d_tree = nullptr;
+    int64_t *d_fwd_level_begin = nullptr;
+    uint32_t *d_row_ptr = nullptr, *d_trow_ptr = nullptr;
+    uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
+    unsigned *d_err = nullptr;
+    size_t dev_bytes = 0;
+};

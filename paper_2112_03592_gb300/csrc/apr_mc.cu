@@ -1,0 +1,1123 @@
+// Multi-channel APR convolution with bfloat16 features and weights on the fifth-generation tensor
+// cores (tcgen05), FP32 accumulation: the per-level filters of an APR CNN layer (Sec. 6), with the
+// isotropic patch of Sec. 3.5 and the per-level convolution of Sec. 4.1 applied per channel pair.
+//
+// Work decomposition: every convolution work item (an 8 x 8-row, 64-cell tile of one level) is cut
+// into four 4 x 4-row sub-tiles. A CTA stages the sub-tile's patch (radius 1) with 16 channels per
+// cell in shared memory, lists the target cells, and runs the channel mixing as GEMMs:
+//   forward      D[target][co] += sum_e A_e[target][ci] W_e[ci][co]     (A_e gathered per tap)
+//   data adjoint D[dest][ci]   += sum_j sum_e G(q_j - e)[co] W_e[co][ci] (q_j: pre-images of dest)
+//   weights      D[(e,ci)][co] += sum_t U[t][(e,ci)] g_t[co]             (U: im2col of the targets)
+// The gathered A operand of the first two is written to tensor memory with tcgen05.st (one lane
+// per row, 8 columns per tap), B comes from shared memory, D lives in tensor memory. One thread
+// issues the MMAs; completion is signalled through an mbarrier whose waits are bounded in time.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "apr_device.cuh"
+#include "apr_internal.h"
+
+namespace aprk {
+namespace {
+
+using namespace dev;
+
+constexpr int MC = 16;                      // channels (c_in = c_out)
+constexpr int SZ = 4, SX = 4;               // sub-tile rows (z, x)
+constexpr int PZ = SZ + 2, PX = SX + 2, PY = BY + 2;
+constexpr int NPROW = PZ * PX;              // patch rows
+constexpr int NPC = NPROW * PY;             // patch cells
+constexpr int NIROW = SZ * SX;              // interior rows
+constexpr int MAXT = NIROW * BY;            // interior cells
+constexpr int NSUB = (TZ / SZ) * (TX / SX); // sub-tiles per work item
+constexpr int NTAP = 27;
+constexpr int WTAP = 512;                   // bytes of one tap's 16 x 16 bf16 weight block
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TM_A = 0;                // A operand: tap e in columns 8e .. 8e+7
+constexpr uint32_t TM_D = 224;              // accumulator: 16 columns
+constexpr int NSEG_F = 3 * NPROW;           // staging segments of the feature patch
+constexpr int WG_T = 16;                    // targets per weight-gradient GEMM step (one K step)
+constexpr int WG_MG = 64;                   // M groups of 8 rows allocated (54 used: 27 taps x 2)
+constexpr int WG_ROWS = NTAP * MC;          // 432 rows (e, ci) of the weight gradient
+static_assert(TZ % SZ == 0 && TX % SX == 0, "sub-tiles must divide the work-item tile");
+static_assert(SZ % 2 == 0 && SX % 2 == 0, "sub-tiles must be even-aligned (coarse cells)");
+static_assert(TM_A + 8 * NTAP <= TM_D && TM_D + 16 <= TMEM_COLS, "tensor-memory columns");
+static_assert(NPC < 65536 && MAXT <= 1024, "16-bit cell ids");
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte offset (stride
+// between core matrices along K) and stride-dimension byte offset (along M or N), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t((lbo & 0x3FFFF) >> 4) << 16) |
+           (uint64_t((sbo & 0x3FFFF) >> 4) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, M x N, A/B K-major unless *_mn.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn ? (1u << 15) : 0u) | ((uint32_t(N) >> 3) << 17) |
+           ((uint32_t(M) >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the mbarrier; gives up after about one second (or 2^24 polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
+// D (tensor memory) [+]= A (tensor memory) x B (shared memory descriptor)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                 "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+// D (tensor memory) [+]= A (shared memory descriptor) x B (shared memory descriptor)
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint4 &a, const uint4 &b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(a.x),
+                 "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Bounded-wait outcome shared by the block: on a timeout every thread leaves through the same path;
+// thread 0 records the error and waits once more (bounded) for the MMAs in flight.
+__device__ __forceinline__ bool block_timed_out(bool ok, uint64_t *bar, uint32_t parity, unsigned *err) {
+    const bool bad = __syncthreads_or(!ok) != 0;
+    if (bad && threadIdx.x == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        mbar_wait(bar, parity);
+    }
+    return bad;
+}
+
+// ---------------------------------------------------------------- geometry
+__device__ __forceinline__ int tap_off(int e) {  // patch-cell offset of tap e = ((dz+1)*3 + dx+1)*3 + dy+1
+    return (e / 9 - 1) * (PX * PY) + ((e / 3) % 3 - 1) * PY + (e % 3 - 1);
+}
+
+struct Sub {         // a sub-tile: level, interior origin, level grids
+    int l, z0, x0, y0, yb;
+    LevelGeo g, gc;  // level l and level l-1 (gc valid if l > l_min)
+};
+
+__device__ __forceinline__ bool sub_of(const DevLayout &L, const Item &it, int sub, Sub &s) {
+    s.l = it.l;
+    s.g = L.geo[it.l];
+    s.gc = it.l > L.l_min ? L.geo[it.l - 1] : s.g;
+    s.z0 = it.a * TZ + (sub / (TX / SX)) * SZ;
+    s.x0 = it.b * TX + (sub % (TX / SX)) * SX;
+    s.yb = it.yb;
+    s.y0 = it.yb * BY;
+    return s.z0 < s.g.dz && s.x0 < s.g.dx;
+}
+
+// Patch row pr = (iz, ix) covers level cells (z0-1+iz, x0-1+ix). 0: never read, 1: staged from the
+// (reflected) source row, 2: zero (outside the grid with zero boundary).
+__device__ __forceinline__ int row_mode(const Sub &s, int pr, int bc, int &rz, int &rx) {
+    const int z = s.z0 - 1 + pr / PX, x = s.x0 - 1 + pr % PX;
+    if (z > s.g.dz || x > s.g.dx) return 0;
+    const bool out = z < 0 || z >= s.g.dz || x < 0 || x >= s.g.dx;
+    if (out && bc == APR_BC_ZERO) return 2;
+    rz = reflect_idx(z, s.g.dz);
+    rx = reflect_idx(x, s.g.dx);
+    return 1;
+}
+
+// ---------------------------------------------------------------- feature patch staging
+struct McSlot {
+    int y;
+    uint4 a, b;
+};
+
+// Loads y and the two 16-byte halves of element i of segment sg (tree segments: [NPROW, 2 NPROW)).
+struct FeatLoader {
+    using Slot = McSlot;
+    const uint16_t *py, *ty;
+    const uint4 *pv, *tv;
+    __device__ __forceinline__ void operator()(int sg, int i, Slot &sl) const {
+        const bool t = sg >= NPROW && sg < 2 * NPROW;
+        sl.y = t ? int(ty[i]) : int(py[i]);
+        const uint4 *v = t ? tv : pv;
+        sl.a = v[2 * size_t(i)];
+        sl.b = v[2 * size_t(i) + 1];
+    }
+};
+
+struct FeatStage {
+    uint4 p0[NPC];  // channels 0-7 of every patch cell
+    uint4 p1[NPC];  // channels 8-15
+    int seg_lo[NSEG_F];
+    int pre[NSEG_F + 1];
+    int warp_tot[NWARP + 1];
+    unsigned short segid[SEGID_CAP];
+};
+
+// Fills the patch with u_l (Sec. 3.5) for the cells the sub-tile's targets read: level-l particles,
+// level-l tree nodes and level-(l-1) particles (each covering two cells per axis), reflected or
+// zero outside the grid. Segment s = kind * NPROW + patch row.
+__device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
+                               FeatStage &S) {
+    const int tid = threadIdx.x;
+    const int ylo = s.y0 - 1;
+    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
+    const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
+    int cnt[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int sg = 2 * tid + h;
+        cnt[h] = 0;
+        if (sg < NSEG_F) {
+            const int kind = sg / NPROW, pr = sg - kind * NPROW;
+            int rz = 0, rx = 0, lo = 0, hi = 0;
+            if (row_mode(s, pr, bc, rz, rx) == 1) {
+                if (kind == 0) {
+                    row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
+                } else if (kind == 1 && has_tree) {
+                    row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
+                } else if (kind == 2 && has_coarse) {
+                    const int cya = ya >> 1, cyb = min((yb + 1) >> 1, s.gc.dy);
+                    row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (rz >> 1) * s.gc.dx + (rx >> 1), cya,
+                              cyb, lo, hi);
+                }
+            }
+            S.seg_lo[sg] = lo;
+            cnt[h] = hi - lo;
+        }
+    }
+    block_scan2(cnt[0], cnt[1], NSEG_F, S.pre, S.warp_tot);
+    const FeatLoader loader{L.y, L.ty, vals, tree};
+    for_each_element(S.seg_lo, S.pre, NSEG_F, S.segid, loader, [&](int sg, int, const McSlot &sl) {
+        const int kind = sg / NPROW, pr = sg - kind * NPROW;
+        if (kind < 2) {
+            if (sl.y >= ya && sl.y < yb) {
+                const int c = pr * PY + sl.y - ylo;
+                S.p0[c] = sl.a;
+                S.p1[c] = sl.b;
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const int y = 2 * sl.y + f;
+                if (y >= ya && y < yb) {
+                    const int c = pr * PY + y - ylo;
+                    S.p0[c] = sl.a;
+                    S.p1[c] = sl.b;
+                }
+            }
+        }
+    });
+    // cells outside the grid: y mirrors of staged rows, whole rows for the zero boundary
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < NPROW * PY; i += NT) {
+        const int pr = i / PY, py = i - pr * PY;
+        int rz, rx;
+        const int m = row_mode(s, pr, bc, rz, rx);
+        const int y = ylo + py;
+        if (m == 2) {
+            S.p0[i] = z4;
+            S.p1[i] = z4;
+        } else if (m == 1 && (y == -1 || y == s.g.dy)) {
+            if (bc == APR_BC_ZERO) {
+                S.p0[i] = z4;
+                S.p1[i] = z4;
+            } else {
+                const int src = pr * PY + reflect_idx(y, s.g.dy) - ylo;  // in the patch: y = -1 -> 0, y = dy -> dy-1
+                S.p0[i] = S.p0[src];
+                S.p1[i] = S.p1[src];
+            }
+        }
+    }
+    block_sync();
+}
+
+// Target list of the sub-tile: the level-l particles of its interior, in particle order.
+struct Targets {
+    int idx[MAXT];
+    unsigned short cell[MAXT];
+    int row_lo[NIROW], row_base[NIROW + 1];
+};
+
+__device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        int lo = 0, cnt = 0;
+        if (lane < NIROW) {
+            const int z = s.z0 + lane / SX, x = s.x0 + lane % SX;
+            if (z < s.g.dz && x < s.g.dx) {
+                const int rr = z * s.g.dx + x;
+                lo = int(pblock(L, s.g, rr, s.yb));
+                cnt = int(pblock(L, s.g, rr, s.yb + 1)) - lo;
+            }
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < NIROW) {
+            T.row_lo[lane] = lo;
+            T.row_base[lane] = incl - cnt;
+        }
+        if (lane == NIROW - 1) T.row_base[NIROW] = incl;
+    }
+    block_sync();
+    for (int r = warp; r < NIROW; r += NWARP) {
+        const int iz = r / SX, ix = r % SX;
+        const int b = T.row_base[r], n = T.row_base[r + 1] - b;
+        for (int j = lane; j < n; j += 32) {
+            const int i = T.row_lo[r] + j;
+            T.idx[b + j] = i;
+            T.cell[b + j] = (unsigned short)(((iz + 1) * PX + ix + 1) * PY + int(L.y[i]) - s.y0 + 1);
+        }
+    }
+    const int n = T.row_base[NIROW];
+    block_sync();
+    return n;
+}
+
+// Weights of one level into the B layout of tap e: K-major core matrices of 8 rows x 16 bytes,
+// N-row group g and K chunk k at (2g + k) * 128 bytes (LBO 128, SBO 256). transpose = false: N = co,
+// K = ci (forward); transpose = true: N = ci, K = co (data adjoint).
+__device__ void load_weights(const uint16_t *W, int lev, bool transpose, unsigned char *wsm) {
+    const uint16_t *w = W + size_t(lev) * MC * MC * NTAP;
+    for (int gi = threadIdx.x; gi < MC * MC * NTAP; gi += NT) {
+        const int co = gi / (MC * NTAP), ci = (gi / NTAP) % MC, e = gi % NTAP;
+        const int n = transpose ? ci : co, k = transpose ? co : ci;
+        *reinterpret_cast<uint16_t *>(wsm + e * WTAP + ((n >> 3) * 2 + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = w[gi];
+    }
+    fence_async_smem();
+}
+
+// ---------------------------------------------------------------- BF16 tree restriction
+constexpr int TREE_WARPS = 4;
+
+struct TreeMcSmem {
+    uint4 child[TREE_WARPS][BY][8][2];  // per parent slot: 8 children (dz, dx, dy order), 16 channels
+    unsigned pres[TREE_WARPS][BY];
+};
+
+__global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                                           int n, const uint4 *__restrict__ vals,
+                                                                           uint4 *__restrict__ tree) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TreeMcSmem &S = *reinterpret_cast<TreeMcSmem *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * TREE_WARPS + warp;
+    if (bi >= n) return;
+    const Item it = items[bi];
+    const int l = it.l;
+    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+    const bool child_tree = l + 1 < L.l_max;
+    S.pres[warp][lane] = 0;
+    S.pres[warp][lane + 32] = 0;
+    __syncwarp();
+    const int cy0 = 2 * it.yb * BY;
+    for (int ab = 0; ab < 4; ++ab) {
+        const int cz = 2 * it.a + (ab >> 1), cx = 2 * it.b + (ab & 1);
+        if (cz >= gc.dz || cx >= gc.dx) continue;
+        const int rr = cz * gc.dx + cx;
+        for (int src = 0; src < (child_tree ? 2 : 1); ++src) {
+            const int lo = int(src ? tblock(L, gc, rr, 2 * it.yb) : pblock(L, gc, rr, 2 * it.yb));
+            const int hi = int(src ? tblock(L, gc, rr, 2 * it.yb + 2) : pblock(L, gc, rr, 2 * it.yb + 2));
+            const uint16_t *yv = src ? L.ty : L.y;
+            const uint4 *v = src ? tree : vals;
+            for (int i = lo + lane; i < hi; i += 32) {
+                const int cy = int(yv[i]) - cy0;  // in [0, 2 BY): exact block range
+                const int slot = ab * 2 + (cy & 1);
+                S.child[warp][cy >> 1][slot][0] = v[2 * size_t(i)];
+                S.child[warp][cy >> 1][slot][1] = v[2 * size_t(i) + 1];
+                atomicOr(&S.pres[warp][cy >> 1], 1u << slot);
+            }
+        }
+    }
+    __syncwarp();
+    const int rr = it.a * g.dx + it.b;
+    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
+    for (int t = tlo + lane; t < thi; t += 32) {
+        const int sl = int(L.ty[t]) - it.yb * BY;
+        const unsigned m = S.pres[warp][sl];
+        float acc[MC];
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[c] = 0.0f;
+        for (int k = 0; k < 8; ++k) {
+            if (!(m & (1u << k))) continue;
+            const uint4 h[2] = {S.child[warp][sl][k][0], S.child[warp][sl][k][1]};
+            const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(h);
+#pragma unroll
+            for (int c = 0; c < MC / 2; ++c) {
+                const float2 f = __bfloat1622float2(p[c]);
+                acc[2 * c] = __fadd_rn(acc[2 * c], f.x);
+                acc[2 * c + 1] = __fadd_rn(acc[2 * c + 1], f.y);
+            }
+        }
+        const int ny = int(L.ty[t]);
+        const int want = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * ny + 1 < gc.dy ? 2 : 1);
+        const int cnt = __popc(m);
+        if (cnt != want) atomicOr(L.err, ERR_DEVICE_CHECK);
+        const float nf = float(cnt ? cnt : 1);
+        uint4 o[2];
+        __nv_bfloat162 *q = reinterpret_cast<__nv_bfloat162 *>(o);
+#pragma unroll
+        for (int c = 0; c < MC / 2; ++c)
+            q[c] = __floats2bfloat162_rn(__fdiv_rn(acc[2 * c], nf), __fdiv_rn(acc[2 * c + 1], nf));
+        tree[2 * size_t(t)] = o[0];
+        tree[2 * size_t(t) + 1] = o[1];
+    }
+}
+
+// Transpose of the tree restriction for 16 FP32 gradient channels, one level (coarse to fine):
+// every child (particle or tree node of level l+1) gets its parent's gradient / #children added.
+__global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+                                                              float4 *__restrict__ gp, float4 *__restrict__ gt) {
+    __shared__ float4 share[NWARP][BY][MC / 4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * NWARP + warp;
+    if (bi >= n) return;
+    const Item it = items[bi];
+    const int l = it.l;
+    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+    const int rr = it.a * g.dx + it.b;
+    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
+    for (int k = lane; k < (thi - tlo) * (MC / 4); k += 32) {
+        const int t = tlo + k / (MC / 4), c = k % (MC / 4);
+        const int yv = L.ty[t];
+        const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
+        const float4 v = gt[size_t(t) * (MC / 4) + c];
+        const float f = float(cnt);
+        share[warp][yv - it.yb * BY][c] = make_float4(v.x / f, v.y / f, v.z / f, v.w / f);
+    }
+    __syncwarp();
+    const bool child_tree = l + 1 < L.l_max;
+    for (int ab = 0; ab < 4; ++ab) {
+        const int cz = 2 * it.a + (ab >> 1), cx = 2 * it.b + (ab & 1);
+        if (cz >= gc.dz || cx >= gc.dx) continue;
+        const int crr = cz * gc.dx + cx;
+        for (int src = 0; src < (child_tree ? 2 : 1); ++src) {
+            const int lo = int(src ? tblock(L, gc, crr, 2 * it.yb) : pblock(L, gc, crr, 2 * it.yb));
+            const int hi = int(src ? tblock(L, gc, crr, 2 * it.yb + 2) : pblock(L, gc, crr, 2 * it.yb + 2));
+            const uint16_t *yv = src ? L.ty : L.y;
+            float4 *dst = src ? gt : gp;
+            for (int k = lane; k < (hi - lo) * (MC / 4); k += 32) {
+                const int i = lo + k / (MC / 4), c = k % (MC / 4);
+                const float4 s = share[warp][(int(yv[i]) >> 1) - it.yb * BY][c];
+                float4 &d = dst[size_t(i) * (MC / 4) + c];
+                const float4 v = d;
+                d = make_float4(v.x + s.x, v.y + s.y, v.z + s.z, v.w + s.w);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- forward
+struct FwdSmem {
+    FeatStage st;
+    alignas(16) unsigned char w[NTAP * WTAP];
+    Targets tg;
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                       const uint4 *__restrict__ vals, const uint4 *__restrict__ tree,
+                                                       const uint16_t *__restrict__ W, int bc, float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FwdSmem &S = *reinterpret_cast<FwdSmem *>(smraw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Sub s;
+    if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
+    const int nt = list_targets(L, s, S.tg);
+    if (nt == 0) return;
+    load_weights(W, s.l - L.l_min, false, S.w);
+    stage_features(L, s, vals, tree, bc, S.st);
+    if (tid == 0) mbar_init(&S.bar);
+    if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
+    fence_async_smem();
+    tc_fence_before();
+    block_sync();
+    tc_fence_after();
+    const uint32_t tb = S.tmem;
+    const int q = warp & 3;
+    const uint32_t lane_base = uint32_t(32 * q) << 16;
+    const int e0 = warp < 4 ? 0 : 14, e1 = warp < 4 ? 14 : NTAP;
+    constexpr uint32_t idesc = idesc_bf16(128, 16, false);
+    uint32_t phase = 0;
+    for (int b0 = 0; b0 < nt; b0 += 128) {
+        const int t = b0 + 32 * q + lane;
+        const int cell = t < nt ? int(S.tg.cell[t]) : -1;
+        for (int e = e0; e < e1; ++e) {
+            uint4 a = make_uint4(0, 0, 0, 0), b = a;
+            if (cell >= 0) {
+                const int c = cell + tap_off(e);
+                a = S.st.p0[c];
+                b = S.st.p1[c];
+            }
+            tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        block_sync();
+        tc_fence_after();
+        if (tid == 0) {
+            for (int e = 0; e < NTAP; ++e)
+                mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc, e > 0);
+            mma_commit(&S.bar);
+        }
+        const bool ok = mbar_wait(&S.bar, phase);
+        if (block_timed_out(ok, &S.bar, phase, L.err)) break;
+        phase ^= 1;
+        tc_fence_after();
+        if (warp < 4) {
+            float v[16];
+            tmem_ld16(tb + lane_base + TM_D, v);
+            if (t < nt) {
+                float4 *o = reinterpret_cast<float4 *>(out + size_t(S.tg.idx[t]) * MC);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+        }
+        tc_fence_before();
+        block_sync();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    block_sync();
+    if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- data adjoint
+constexpr int NSEG_B = NPROW + 3 * NIROW;  // gradient rows, then interior particle / tree / coarse rows
+constexpr unsigned char SRC_NONE = 0xFF, SRC_P = 0, SRC_T = 1, SRC_C = 2;  // source kinds of a patch cell
+static_assert(SRC_P == 0 && SRC_T == 1, "interior particle / tree segments store their kind index");
+
+struct BwdSmem {
+    uint4 g0[NPC];  // bf16 gradient of the targets, channels 0-7 (zero elsewhere)
+    uint4 g1[NPC];
+    alignas(16) unsigned char w[NTAP * WTAP];
+    int srci[MAXT];                 // source of each interior cell: index ...
+    unsigned char srck[MAXT];       // ... and kind (particle, tree, coarse particle)
+    unsigned short dlist[MAXT];     // destinations: one-pre-image ones from the front, others from the back
+    unsigned tmask[NPROW][3];       // cells holding a target, per patch row (bits along y)
+    unsigned hot[NPROW][3];         // cells within distance 1 of a target
+    int seg_lo[NSEG_B];
+    int pre[NSEG_B + 1];
+    int warp_tot[NWARP + 1];
+    unsigned short segid[SEGID_CAP];
+    int n1, nn;
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ bool hot_at(const BwdSmem &S, int pz, int px, int py) {
+    return (S.hot[pz * PX + px][py >> 5] >> (py & 31)) & 1u;
+}
+
+// Pre-images along one axis of a destination whose first fine coordinate is u: its in-grid fine
+// cells (one, or two for a coarse particle) and the out-of-grid cells that reflect onto them.
+__device__ __forceinline__ int axis_pre(int u, bool coarse, int d, bool reflect, int *o) {
+    int n = 0;
+    o[n++] = u;
+    if (coarse && u + 1 < d) o[n++] = u + 1;
+    if (reflect) {
+        if (u == 0) o[n++] = -1;
+        if ((coarse ? min(u + 1, d - 1) : u) == d - 1) o[n++] = d;
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                            const uint16_t *__restrict__ W, int bc,
+                                                            const uint4 *__restrict__ gout, float *__restrict__ gp,
+                                                            float *__restrict__ gt) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    BwdSmem &S = *reinterpret_cast<BwdSmem *>(smraw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Sub s;
+    if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
+    const bool reflect = bc == APR_BC_REFLECT;
+    const int ylo = s.y0 - 1;
+    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);  // gradient rows: y range of the patch
+    const int yia = s.y0, yib = min(s.y0 + BY, s.g.dy);            // interior y range
+    const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < NPC; i += NT) {
+        S.g0[i] = z4;
+        S.g1[i] = z4;
+    }
+    for (int i = tid; i < MAXT; i += NT) S.srck[i] = SRC_NONE;
+    for (int i = tid; i < NPROW * 3; i += NT) (&S.tmask[0][0])[i] = 0;
+    if (tid == 0) {
+        S.n1 = 0;
+        S.nn = 0;
+    }
+    int cnt[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int sg = 2 * tid + h;
+        cnt[h] = 0;
+        if (sg < NSEG_B) {
+            int lo = 0, hi = 0;
+            if (sg < NPROW) {  // targets of the patch region (inside the grid only)
+                const int z = s.z0 - 1 + sg / PX, x = s.x0 - 1 + sg % PX;
+                if (z >= 0 && z < s.g.dz && x >= 0 && x < s.g.dx)
+                    row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, ya, yb, lo, hi);
+            } else {
+                const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
+                const int z = s.z0 + r / SX, x = s.x0 + r % SX;
+                if (z < s.g.dz && x < s.g.dx) {
+                    if (k == 0)
+                        row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
+                    else if (k == 1 && has_tree)
+                        row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
+                    else if (k == 2 && has_coarse)
+                        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (z >> 1) * s.gc.dx + (x >> 1),
+                                  yia >> 1, min((yib + 1) >> 1, s.gc.dy), lo, hi);
+                }
+            }
+            S.seg_lo[sg] = lo;
+            cnt[h] = hi - lo;
+        }
+    }
+    block_scan2(cnt[0], cnt[1], NSEG_B, S.pre, S.warp_tot);
+    struct Loader {
+        using Slot = McSlot;
+        const DevLayout *L;
+        const uint4 *gout;
+        __device__ void operator()(int sg, int i, Slot &sl) const {
+            const bool t = sg >= NPROW + NIROW && sg < NPROW + 2 * NIROW;
+            sl.y = t ? int(L->ty[i]) : int(L->y[i]);
+            if (sg < NPROW) {
+                sl.a = gout[2 * size_t(i)];
+                sl.b = gout[2 * size_t(i) + 1];
+            }
+        }
+    } loader{&L, gout};
+    for_each_element(S.seg_lo, S.pre, NSEG_B, S.segid, loader, [&](int sg, int i, const McSlot &sl) {
+        if (sg < NPROW) {
+            if (sl.y >= ya && sl.y < yb) {
+                const int py = sl.y - ylo;
+                S.g0[sg * PY + py] = sl.a;
+                S.g1[sg * PY + py] = sl.b;
+                atomicOr(&S.tmask[sg][py >> 5], 1u << (py & 31));
+            }
+            return;
+        }
+        const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
+        if (k < 2) {
+            if (sl.y >= yia && sl.y < yib) {
+                S.srck[r * BY + sl.y - s.y0] = (unsigned char)k;
+                S.srci[r * BY + sl.y - s.y0] = i;
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const int y = 2 * sl.y + f;
+                if (y >= yia && y < yib) {
+                    S.srck[r * BY + y - s.y0] = SRC_C;
+                    S.srci[r * BY + y - s.y0] = i;
+                }
+            }
+        }
+    });
+    // cells within distance 1 of a target: y dilation of each row, OR over the 3 x 3 neighbour rows
+    if (tid < NPROW) {
+        const int pz = tid / PX, px = tid % PX;
+        unsigned h[3] = {0, 0, 0};
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qz = pz + dz, qx = px + dx;
+                if (qz < 0 || qz >= PZ || qx < 0 || qx >= PX) continue;
+                const unsigned *m = S.tmask[qz * PX + qx];
+                h[0] |= m[0] | (m[0] << 1) | (m[0] >> 1) | (m[1] << 31);
+                h[1] |= m[1] | (m[1] << 1) | (m[1] >> 1) | (m[0] >> 31) | (m[2] << 31);
+                h[2] |= m[2] | (m[2] << 1) | (m[2] >> 1) | (m[1] >> 31);
+            }
+        S.hot[tid][0] = h[0];
+        S.hot[tid][1] = h[1];
+        S.hot[tid][2] = h[2];
+    }
+    block_sync();
+    // destinations: every particle / tree node of the interior, and every coarse particle (anchored
+    // at its first fine cell), that has a pre-image within distance 1 of a target
+    for (int ic = tid; ic < MAXT; ic += NT) {
+        const int r = ic / BY, iy = ic % BY;
+        const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
+        if (z >= s.g.dz || x >= s.g.dx || y >= s.g.dy) continue;
+        const int k = S.srck[ic];
+        if (k == SRC_NONE) {
+            if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
+            continue;
+        }
+        const bool coarse = k == SRC_C;
+        if (coarse && ((z | x | y) & 1)) continue;
+        int oz[4], ox[4], oy[4];
+        const int nz = axis_pre(z, coarse, s.g.dz, reflect, oz);
+        const int nx = axis_pre(x, coarse, s.g.dx, reflect, ox);
+        const int ny = axis_pre(y, coarse, s.g.dy, reflect, oy);
+        bool any = false;
+        for (int a = 0; a < nz && !any; ++a)
+            for (int b = 0; b < nx && !any; ++b)
+                for (int c = 0; c < ny && !any; ++c)
+                    any = hot_at(S, oz[a] - s.z0 + 1, ox[b] - s.x0 + 1, oy[c] - ylo);
+        if (!any) continue;
+        if (nz * nx * ny == 1)
+            S.dlist[atomicAdd(&S.n1, 1)] = (unsigned short)ic;
+        else
+            S.dlist[MAXT - 1 - atomicAdd(&S.nn, 1)] = (unsigned short)ic;
+    }
+    block_sync();
+    const int n1 = S.n1, nn = S.nn;
+    if (n1 + nn == 0) return;
+    load_weights(W, s.l - L.l_min, true, S.w);
+    if (tid == 0) mbar_init(&S.bar);
+    if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
+    fence_async_smem();
+    tc_fence_before();
+    block_sync();
+    tc_fence_after();
+    const uint32_t tb = S.tmem;
+    const int q = warp & 3;
+    const uint32_t lane_base = uint32_t(32 * q) << 16;
+    const int e0 = warp < 4 ? 0 : 14, e1 = warp < 4 ? 14 : NTAP;
+    constexpr uint32_t idesc = idesc_bf16(128, 16, false);
+    const int nb1 = (n1 + 127) / 128, nbn = (nn + 127) / 128;
+    uint32_t phase = 0;
+    for (int bk = 0; bk < nb1 + nbn; ++bk) {
+        // this thread's destination row
+        const int row = 32 * q + lane;
+        int ic = -1;
+        if (bk < nb1) {
+            if (bk * 128 + row < n1) ic = S.dlist[bk * 128 + row];
+        } else {
+            const int j = (bk - nb1) * 128 + row;
+            if (j < nn) ic = S.dlist[MAXT - 1 - j];
+        }
+        int oz[4], ox[4], oy[4], nz = 0, nx = 0, ny = 0;
+        if (ic >= 0) {
+            const int r = ic / BY;
+            const bool coarse = S.srck[ic] == SRC_C;
+            nz = axis_pre(s.z0 + r / SX, coarse, s.g.dz, reflect, oz);
+            nx = axis_pre(s.x0 + r % SX, coarse, s.g.dx, reflect, ox);
+            ny = axis_pre(s.y0 + ic % BY, coarse, s.g.dy, reflect, oy);
+        }
+        const int nq = nz * nx * ny;
+        bool failed = false;
+        for (int j = 0; __syncthreads_or(j < nq); ++j) {
+            int pz = -100, px = 0, py = 0;
+            if (j < nq) {
+                pz = oz[j / (nx * ny)] - s.z0 + 1;
+                px = ox[(j / ny) % nx] - s.x0 + 1;
+                py = oy[j % ny] - ylo;
+            }
+            for (int e = e0; e < e1; ++e) {
+                const int cz = pz - (e / 9 - 1), cx = px - ((e / 3) % 3 - 1), cy = py - (e % 3 - 1);
+                uint4 a = make_uint4(0, 0, 0, 0), b = a;
+                if (cz >= 0 && cz < PZ && cx >= 0 && cx < PX && cy >= 0 && cy < PY) {
+                    const int c = (cz * PX + cx) * PY + cy;
+                    a = S.g0[c];
+                    b = S.g1[c];
+                }
+                tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            block_sync();
+            tc_fence_after();
+            if (tid == 0) {
+                for (int e = 0; e < NTAP; ++e)
+                    mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc,
+                           (j > 0 || e > 0) ? 1u : 0u);
+                mma_commit(&S.bar);
+            }
+            const bool ok = mbar_wait(&S.bar, phase);
+            if (block_timed_out(ok, &S.bar, phase, L.err)) {
+                failed = true;
+                break;
+            }
+            phase ^= 1;
+            tc_fence_after();
+        }
+        if (failed) break;
+        if (warp < 4) {
+            float v[16];
+            tmem_ld16(tb + lane_base + TM_D, v);
+            if (ic >= 0) {
+                const int k = S.srck[ic];
+                const size_t idx = size_t(S.srci[ic]);
+                if (k == SRC_T) {
+                    float4 *o = reinterpret_cast<float4 *>(gt + idx * MC);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) red_add_v4(gp + idx * MC + 4 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                }
+            }
+        }
+        tc_fence_before();
+        block_sync();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    block_sync();
+    if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- weight gradient
+struct WgradSmem {
+    FeatStage st;
+    Targets tg;
+    alignas(16) unsigned char u[WG_MG * WG_T * 16];  // im2col of WG_T targets: group mg = 2e + h, target t at mg*256 + t*16
+    alignas(16) unsigned char gtile[2 * (WG_T / 8) * 128];  // g^T: co group g, target chunk k at (2g + k) * 128
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+struct WgradPlan {
+    int first[MAXL], last[MAXL];  // CTAs whose unit range meets each level (inclusive), -1 if none
+};
+
+// Persistent: CTA i handles units [i*U/G, (i+1)*U/G) (unit = work item x sub-tile, ordered by level)
+// and keeps one FP32 accumulator per level in tensor memory, flushed to partial[i + level index].
+__global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, const Item *__restrict__ items, int n_units,
+                                                         const uint4 *__restrict__ vals, const uint4 *__restrict__ tree,
+                                                         int bc, const uint4 *__restrict__ gout,
+                                                         float *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    WgradSmem &S = *reinterpret_cast<WgradSmem *>(smraw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x;
+    const int u0 = int((int64_t(blockIdx.x) * n_units) / G), u1 = int((int64_t(blockIdx.x + 1) * n_units) / G);
+    if (u0 >= u1) return;
+    if (tid == 0) mbar_init(&S.bar);
+    for (int i = tid; i < int(sizeof(S.u) / 16); i += NT) reinterpret_cast<uint4 *>(S.u)[i] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
+    tc_fence_before();
+    block_sync();
+    tc_fence_after();
+    const uint32_t tb = S.tmem;
+    const int q = warp & 3;
+    const uint32_t lane_base = uint32_t(32 * q) << 16;
+    constexpr uint32_t idesc = idesc_bf16(128, 16, true);
+    uint32_t phase = 0;
+    int cur_l = items[u0 / NSUB].l;
+    bool dirty = false, failed = false;
+    // writes the level's accumulator (zeros if nothing was accumulated) to partial[cta + level index];
+    // D block mb (rows 128 mb .. +127 of (e, ci)) lives in columns 16 mb .. 16 mb + 15
+    auto flush = [&]() {
+        if (warp < 4) {
+            float *dst = partial + size_t(blockIdx.x + cur_l - L.l_min) * WG_ROWS * MC;
+            for (int mb = 0; mb < 4; ++mb) {
+                float v[16];
+                tmem_ld16(tb + lane_base + 16 * mb, v);
+                const int row = 128 * mb + 32 * q + lane;
+                if (row < WG_ROWS) {
+                    float4 *o = reinterpret_cast<float4 *>(dst + size_t(row) * MC);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        o[c] = dirty ? make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3])
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        tc_fence_before();
+        block_sync();
+        tc_fence_after();
+    };
+    for (int u = u0; u < u1 && !failed; ++u) {
+        Sub s;
+        const Item it = items[u / NSUB];
+        if (it.l != cur_l) {
+            flush();
+            cur_l = it.l;
+            dirty = false;
+        }
+        if (!sub_of(L, it, u % NSUB, s)) continue;
+        const int nt = list_targets(L, s, S.tg);
+        if (nt == 0) continue;
+        stage_features(L, s, vals, tree, bc, S.st);
+        for (int t0 = 0; t0 < nt; t0 += WG_T) {
+            // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t
+            for (int i = tid; i < 2 * NTAP * WG_T; i += NT) {
+                const int mg = i / WG_T, t = i % WG_T, e = mg >> 1;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (t0 + t < nt) {
+                    const int c = int(S.tg.cell[t0 + t]) + tap_off(e);
+                    v = (mg & 1) ? S.st.p1[c] : S.st.p0[c];
+                }
+                *reinterpret_cast<uint4 *>(S.u + mg * (WG_T * 16) + t * 16) = v;
+            }
+            // g^T (N = co rows, K = targets), K-major core matrices
+            if (tid < 2 * WG_T) {
+                const int tt = tid >> 1, h = tid & 1, tg = t0 + tt;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (tg < nt) v = gout[2 * size_t(S.tg.idx[tg]) + h];
+                const uint16_t *p = reinterpret_cast<const uint16_t *>(&v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)  // co = 8h + j
+                    *reinterpret_cast<uint16_t *>(S.gtile + (h * (WG_T / 8) + (tt >> 3)) * 128 + j * 16 + (tt & 7) * 2) = p[j];
+            }
+            fence_async_smem();
+            tc_fence_before();
+            block_sync();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint64_t bd = sdesc(smem_u32(S.gtile), 128, (WG_T / 8) * 128);
+                for (int mb = 0; mb < 4; ++mb) {
+                    const uint64_t ad = sdesc(smem_u32(S.u + mb * 16 * (WG_T * 16)), 128, WG_T * 16);
+                    mma_ss(tb + 16 * mb, ad, bd, idesc, dirty ? 1u : 0u);
+                }
+                mma_commit(&S.bar);
+            }
+            const bool ok = mbar_wait(&S.bar, phase);
+            if (block_timed_out(ok, &S.bar, phase, L.err)) {
+                failed = true;
+                break;
+            }
+            phase ^= 1;
+            dirty = true;
+            tc_fence_after();
+        }
+    }
+    if (!failed) flush();
+    tc_fence_before();
+    block_sync();
+    if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
+}
+
+// grad_weights[lev][co][ci][e] = sum over the level's CTAs (in order) of partial[cta + lev][16e + ci][co]
+__global__ void mc_wgrad_reduce_kernel(const float *__restrict__ partial, WgradPlan plan, int n_levels,
+                                       float *__restrict__ gw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_levels * WG_ROWS * MC) return;
+    const int lev = i / (WG_ROWS * MC), r = i % (WG_ROWS * MC);
+    const int row = r / MC, co = r % MC;
+    float acc = 0.0f;
+    if (plan.first[lev] >= 0)
+        for (int c = plan.first[lev]; c <= plan.last[lev]; ++c) acc += partial[(size_t(c) + lev) * WG_ROWS * MC + r];
+    const int e = row / MC, ci = row % MC;
+    gw[((size_t(lev) * MC + co) * MC + ci) * NTAP + e] = acc;
+}
+
+// Each CTA of the tensor-core kernels holds 256 of the SM's 512 tensor-memory columns, so their
+// shared memory must admit exactly two CTAs per SM (228 KB per SM, 1 KB reserved per CTA).
+constexpr size_t kTwoPerSmMin = 76 * 1024, kTwoPerSmMax = 112 * 1024;
+static_assert(sizeof(FwdSmem) > kTwoPerSmMin && sizeof(FwdSmem) <= kTwoPerSmMax, "forward: two CTAs per SM");
+static_assert(sizeof(BwdSmem) > kTwoPerSmMin && sizeof(BwdSmem) <= kTwoPerSmMax, "data adjoint: two CTAs per SM");
+static_assert(sizeof(WgradSmem) > kTwoPerSmMin && sizeof(WgradSmem) <= kTwoPerSmMax, "weight gradient: two CTAs per SM");
+// operands of tensor-core descriptors and 16-byte vector accesses start on 16-byte boundaries
+static_assert(offsetof(FwdSmem, w) % 16 == 0 && offsetof(BwdSmem, w) % 16 == 0, "weights alignment");
+static_assert(offsetof(WgradSmem, u) % 16 == 0 && offsetof(WgradSmem, gtile) % 16 == 0, "operand alignment");
+static_assert(offsetof(BwdSmem, g1) % 16 == 0 && offsetof(FeatStage, p1) % 16 == 0, "patch alignment");
+static_assert(offsetof(FwdSmem, bar) % 8 == 0 && offsetof(BwdSmem, bar) % 8 == 0 && offsetof(WgradSmem, bar) % 8 == 0,
+              "mbarrier alignment");
+
+cudaError_t set_smem(const void *fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+int wgrad_ctas(int n_units) {
+    static int sms = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+    });
+    return std::max(1, std::min(n_units, 2 * sms));
+}
+
+bool mc_args_ok(int32_t c_in, int32_t c_out, int32_t k) { return c_in == MC && c_out == MC && k == 3; }
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+}  // namespace aprk
+
+using namespace aprk;
+
+extern "C" {
+
+apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, uint16_t *tree, int32_t channels,
+                                    apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (channels != MC) return APR_ERR_UNSUPPORTED;
+    const HostIndex &X = h->X;
+    if ((X.np && !particles) || (X.nt && !tree) || !aligned16(particles) || !aligned16(tree)) return APR_ERR_INVALID_ARG;
+    const size_t sm = sizeof(TreeMcSmem);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_tree_restrict_kernel), sm);
+    for (int l = X.l_max - 1; e == cudaSuccess && l >= X.l_min; --l) {
+        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        if (n > 0)
+            mc_tree_restrict_kernel<<<int((n + TREE_WARPS - 1) / TREE_WARPS), TREE_WARPS * 32, sm, stream>>>(
+                h->L, h->d_tree + b, int(n), reinterpret_cast<const uint4 *>(particles), reinterpret_cast<uint4 *>(tree));
+        e = cudaGetLastError();
+    }
+    return cuda_status(e);
+}
+
+apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree, const uint16_t *weights,
+                             int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!mc_args_ok(c_in, c_out, k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!weights || (X.np && (!particles || !out)) || (X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree) || !aligned16(out)) return APR_ERR_INVALID_ARG;
+    const size_t sm = sizeof(FwdSmem);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_fwd_kernel), sm);
+    const int n = int(X.fwd_items.size());
+    if (e == cudaSuccess && n > 0) {
+        mc_fwd_kernel<<<dim3(n, NSUB), NT, sm, stream>>>(h->L, h->d_fwd, reinterpret_cast<const uint4 *>(particles),
+                                                          reinterpret_cast<const uint4 *>(tree), weights, bc, out);
+        e = cudaGetLastError();
+    }
+    return cuda_status(e);
+}
+
+size_t apr_mc_backward_workspace_bytes(apr_handle_t h, int32_t c_in, int32_t c_out, int32_t k) {
+    if (!h || !mc_args_ok(c_in, c_out, k)) return 0;
+    const int L = h->X.l_max - h->X.l_min + 1;
+    const int units = int(h->X.fwd_items.size()) * NSUB;
+    const size_t gt = (size_t(h->X.nt) * MC * sizeof(float) + 255) / 256 * 256;
+    return gt + size_t(wgrad_ctas(units) + L) * WG_ROWS * MC * sizeof(float);
+}
+
+apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles, const uint16_t *tree,
+                                      const uint16_t *weights, int32_t c_in, int32_t c_out, int32_t k, int32_t bc,
+                                      const uint16_t *grad_out, float *grad_particles, float *grad_weights,
+                                      void *workspace, size_t workspace_bytes, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!mc_args_ok(c_in, c_out, k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!weights || (X.np && !grad_out)) return APR_ERR_INVALID_ARG;
+    if (grad_weights && ((X.np && !particles) || (X.nt && !tree))) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree) || !aligned16(grad_out) || !aligned16(grad_particles) ||
+        !aligned16(grad_weights))
+        return APR_ERR_INVALID_ARG;
+    const size_t need = apr_mc_backward_workspace_bytes(h, c_in, c_out, k);
+    if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return APR_ERR_INVALID_ARG;
+    const size_t gt_bytes = (size_t(X.nt) * MC * sizeof(float) + 255) / 256 * 256;
+    float *gt = static_cast<float *>(workspace);
+    float *partial = reinterpret_cast<float *>(static_cast<char *>(workspace) + gt_bytes);
+    const int n_levels = X.l_max - X.l_min + 1;
+    cudaError_t e = cudaSuccess;
+    if (grad_particles) {
+        if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * MC * sizeof(float), stream);
+        if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(gt, 0, size_t(X.nt) * MC * sizeof(float), stream);
+        if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void *>(mc_bwd_data_kernel), sizeof(BwdSmem));
+        const int n = int(X.bwd_items.size());
+        if (e == cudaSuccess && n > 0) {
+            mc_bwd_data_kernel<<<dim3(n, NSUB), NT, sizeof(BwdSmem), stream>>>(
+                h->L, h->d_bwd, weights, bc, reinterpret_cast<const uint4 *>(grad_out), grad_particles, gt);
+            e = cudaGetLastError();
+        }
+        for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
+            const int64_t b = X.tree_level_begin[l], nt = X.tree_level_begin[l + 1] - b;
+            if (nt > 0)
+                mc_tree_pushdown_kernel<<<int((nt + NWARP - 1) / NWARP), NT, 0, stream>>>(
+                    h->L, h->d_tree + b, int(nt), reinterpret_cast<float4 *>(grad_particles), reinterpret_cast<float4 *>(gt));
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && grad_weights) {
+        const int units = int(X.fwd_items.size()) * NSUB;
+        const int G = wgrad_ctas(units);
+        WgradPlan plan;
+        for (int i = 0; i < MAXL; ++i) plan.first[i] = plan.last[i] = -1;
+        auto cta_of = [&](int64_t u) {  // CTA c with c*units/G <= u < (c+1)*units/G
+            int c = int((u * G) / units);
+            while (c + 1 < G && (int64_t(c + 1) * units) / G <= u) ++c;
+            while (c > 0 && (int64_t(c) * units) / G > u) --c;
+            return c;
+        };
+        for (int lv = 0; lv < n_levels; ++lv) {
+            const int64_t ua = X.fwd_level_begin[X.l_min + lv] * NSUB, ub = X.fwd_level_begin[X.l_min + lv + 1] * NSUB;
+            if (ua >= ub) continue;
+            plan.first[lv] = cta_of(ua);
+            plan.last[lv] = cta_of(ub - 1);
+        }
+        e = set_smem(reinterpret_cast<const void *>(mc_wgrad_kernel), sizeof(WgradSmem));
+        if (e == cudaSuccess && units > 0) {
+            mc_wgrad_kernel<<<G, NT, sizeof(WgradSmem), stream>>>(h->L, h->d_fwd, units,
+                                                                  reinterpret_cast<const uint4 *>(particles),
+                                                                  reinterpret_cast<const uint4 *>(tree), bc,
+                                                                  reinterpret_cast<const uint4 *>(grad_out), partial);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            const int tot = n_levels * WG_ROWS * MC;
+            mc_wgrad_reduce_kernel<<<(tot + 255) / 256, 256, 0, stream>>>(partial, plan, n_levels, grad_weights);
+            e = cudaGetLastError();
+        }
+    }
+    return cuda_status(e);
+}
+
+}  // extern "C"
