@@ -312,6 +312,201 @@ def run_ours(args, rank, world):
     return rec
 
 
+MC_WORKLOAD = "blob256"
+MC_C = 16
+
+
+def mc_inputs(apr, seed=0):
+    """bfloat16-exact features (k/8 in [-8, 8]), weights ~ N(0, 1/432) rounded to bf16, upstream
+    gradients (k/8); returned as float64 arrays holding bf16 values."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    x = rng.integers(-64, 65, size=(apr.n_particles, MC_C)) / 8.0
+    w = torch.as_tensor(rng.normal(scale=432 ** -0.5, size=(apr.n_levels, MC_C, MC_C, 27)).astype(np.float32))
+    w = w.to(torch.bfloat16).to(torch.float64).numpy()
+    g = rng.integers(-64, 65, size=(apr.n_particles, MC_C)) / 8.0
+    return x, w, g
+
+
+def mc_algorithmic(apr, lay):
+    """Per launch of the multi-channel forward: bytes (features 32 B in, y 2 B, outputs 64 B out per
+    particle; tree 32 + 2 B per node; row pointers; weights) and tensor FLOPs (2 * 27 * 16 * 16 per
+    particle)."""
+    Np, Nt = apr.n_particles, lay.n_tree
+    Rp = int(apr.row_ptr.size - 1)
+    Rt = sum(apr.level_dims(l)[0] * apr.level_dims(l)[1] for l in range(apr.l_min, apr.l_max))
+    byts = Np * (32 + 2 + 64) + Nt * (32 + 2) + (Rp + Rt) * 4 + apr.n_levels * MC_C * MC_C * 27 * 2
+    flops = 2 * 27 * MC_C * MC_C * Np
+    return byts, flops
+
+
+def run_mc(args, rank, world, full=True):
+    """Multi-channel step on the 256^3 blob APR: BF16 tree + 16->16 convolution + its backward."""
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    apr = S.make_config(MC_WORKLOAD)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    Np = apr.n_particles
+    xh, wh, gh = mc_inputs(apr)
+    bf = lambda a: torch.as_tensor(a.astype(np.float32), device=dev).to(torch.bfloat16).contiguous()
+    x, w, g = bf(xh), bf(wh), bf(gh)
+    tree = torch.empty((lay.n_tree, MC_C), dtype=torch.bfloat16, device=dev)
+    out = torch.empty((Np, MC_C), device=dev)
+    gp = torch.empty((Np, MC_C), device=dev)
+    gw = torch.empty((apr.n_levels, MC_C, MC_C, 27), device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(e=None):
+        # BF16 tree | forward | data adjoint (+ tree push-down) | weight gradient
+        if e is not None:
+            e[0].record(stream)
+        G.apr_tree_restrict_bf16(lay, x, tree)
+        if e is not None:
+            e[1].record(stream)
+        G.apr_convolve_mc(lay, x, tree, w, G.APR_BC_REFLECT, out)
+        if e is not None:
+            e[2].record(stream)
+        G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_weights=False, grad_particles=gp)
+        if e is not None:
+            e[3].record(stream)
+        G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_particles=False, grad_weights=gw)
+        if e is not None:
+            e[4].record(stream)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clk = ClockSampler(dev.index).__enter__() if full else None
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        step(ev[i])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    if clk is not None:
+        time.sleep(0.12)
+        clk.__exit__()
+    lay.sync_status()
+    parts = [statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)) for j in range(4)]
+    step_ms = sum(parts)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    byts, flops = mc_algorithmic(apr, lay)
+    peaks, src = _peaks()
+    hbm, tc = float(peaks["hbm_gbs"]), float(peaks.get("bf16_tflops", 1900.0))
+    names = ["tree_restrict_bf16", "convolve_mc", "data_adjoint", "weight_grad"]
+    dom = max(range(1, 4), key=lambda j: parts[j])
+    n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
+    launches_per_step = n_tree_levels + 1 + 1 + n_tree_levels + 2
+    rec = {
+        "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
+        "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic (seeded 400-blob 256^3 image with Poisson noise -> APR; random bf16 features and weights)",
+        "config": {"workload": "blob APR 256^3 pixels, 16 -> 16 channels bf16 (FP32 accumulation), 3^3 per-level weights",
+                   "model": None, "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
+                   "step": "bf16 tree + convolve_mc + backward (data adjoint with tree push-down, weight gradient)",
+                   "l2": "flushed before every step (512 MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "step_ms_parts": {n: round(t, 5) for n, t in zip(names, parts)},
+        "roofline": {"kernel": {1: "mc_fwd_kernel (apr_convolve_mc)", 2: "mc_bwd_data_kernel (+ push-down)",
+                                3: "mc_wgrad_kernel (+ reduce)"}[dom],
+                     "bound": "hbm", "achieved": round(byts / (parts[dom] * 1e-3) / 1e9, 2), "peak": hbm, "unit": "GB/s",
+                     "frac": round(byts / (parts[dom] * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                     "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": byts,
+                     "tensor_tflops": round(flops / (parts[dom] * 1e-3) / 1e12, 2),
+                     "tensor_frac": round(flops / (parts[dom] * 1e-3) / 1e12 / tc, 4),
+                     "forward_frac": round(byts / (parts[1] * 1e-3) / 1e9 / hbm, 4),
+                     "forward_tensor_frac": round(flops / (parts[1] * 1e-3) / 1e12 / tc, 4)},
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if not full:
+        return rec
+    # end to end with host buffers: H2D of features and upstream gradient, D2H of outputs and grads
+    h_x, h_g = x.cpu().pin_memory(), g.cpu().pin_memory()
+    h_out, h_gp = torch.empty_like(out, device="cpu").pin_memory(), torch.empty_like(gp, device="cpu").pin_memory()
+    h_gw = torch.empty_like(gw, device="cpu").pin_memory()
+    d_x, d_g = torch.empty_like(x), torch.empty_like(g)
+
+    def e2e_step():
+        d_x.copy_(h_x, non_blocking=True)
+        d_g.copy_(h_g, non_blocking=True)
+        G.apr_tree_restrict_bf16(lay, d_x, tree)
+        G.apr_convolve_mc(lay, d_x, tree, w, G.APR_BC_REFLECT, out)
+        G.apr_convolve_mc_backward(lay, d_x, tree, w, d_g, G.APR_BC_REFLECT, grad_particles=gp, grad_weights=gw)
+        h_out.copy_(out, non_blocking=True)
+        h_gp.copy_(gp, non_blocking=True)
+        h_gw.copy_(gw, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = statistics.mean(e2e_ms)
+    rec["e2e"] = {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
+                  "h2d_bytes_per_step": int(h_x.numel() * 2 + h_g.numel() * 2),
+                  "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),
+                  "ms_per_step": round(e2e, 4)}
+    rec["clocks"] = clk.summary(t0, t1)
+    if rank == 0 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = mc_cpu_baseline(apr, xh, wh, gh, budget_s=args.cpu_budget)
+    return rec
+
+
+def mc_cpu_baseline(apr, x, w, g, budget_s=20.0):
+    """The FP64 oracle with 16 channels on a bounded sample: full BF16 tree fill, then forward and
+    backward of a random sample of output particles (rate per particle of the whole step)."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(apr, x)
+    t0 = time.perf_counter()
+    o.tree_bf16()
+    t_fill = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    n = 200
+    t0 = time.perf_counter()
+    s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+    o.conv(w, 3, sample=s, C_out=MC_C)
+    o.conv_backward(w, 3, g, sample=s, C_out=MC_C)
+    t_probe = time.perf_counter() - t0
+    n2 = int(min(apr.n_particles, max(n, n * (budget_s - t_fill) / max(t_probe, 1e-6) * 0.8)))
+    s = np.sort(rng.choice(apr.n_particles, n2, replace=False))
+    t0 = time.perf_counter()
+    o.conv(w, 3, sample=s, C_out=MC_C)
+    o.conv_backward(w, 3, g, sample=s, C_out=MC_C)
+    t_s = time.perf_counter() - t0
+    per = t_fill / apr.n_particles + t_s / n2
+    return {"value": round(1.0 / per / 1e9, 9), "unit": "Gparticles/s", "cores": 1, "kind": "oracle",
+            "sample": f"full bf16 tree fill ({t_fill:.2f} s, scaled by sample/N) + 16-channel forward and backward of "
+                      f"{n2} random output particles ({t_s:.2f} s), FP64, 1 thread"}
+
+
 def cpu_baseline(apr, st, gout, budget_s=20.0, sample_n=None):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the same step: the full
     tree fill, then forward and backward for a random sample of output particles. The tree fill
@@ -386,6 +581,45 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(val, 9), "unit": "Gparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_mc(args, rank, world):
+    """The oracle as the reference arm of the multi-channel workload (bounded sample per step)."""
+    import numpy as np
+
+    import aprsynth as S
+    import oracle
+    apr = S.make_config(MC_WORKLOAD)
+    x, w, g = mc_inputs(apr)
+    o = oracle.Oracle(apr, x)
+    rng = np.random.default_rng(1)
+    n = max(1, args.ref_sample // 10)
+    t_fill, t_samp = [], []
+    for i in range(args.warmup + args.steps):
+        s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+        t0 = time.perf_counter()
+        o.set_values(x)
+        o.tree_bf16()
+        t1 = time.perf_counter()
+        o.conv(w, 3, sample=s, C_out=MC_C)
+        o.conv_backward(w, 3, g, sample=s, C_out=MC_C)
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            t_fill.append(t1 - t0)
+            t_samp.append(t2 - t1)
+    per = statistics.mean(t_fill) / apr.n_particles + statistics.mean(t_samp) / n
+    val = 1.0 / per / 1e9
+    return {"metric": "APR conv Gparticles/s & pixel-equiv GB/s", "value": round(val, 9), "unit": "Gparticles/s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * (statistics.mean(t_fill) + statistics.mean(t_samp)), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded 400-blob 256^3 image with Poisson noise -> APR; random bf16 features and weights)",
+            "config": {"workload": "blob APR 256^3 pixels, 16 -> 16 channels bf16 (FP32 accumulation), 3^3 per-level weights",
+                       "step": f"oracle: full bf16 tree fill + 16-channel forward and backward of {n} random output "
+                               "particles; rate per particle = 1 / (fill time / N_p + sample time / sample size)"},
+            "cpu_baseline": {"value": round(val, 9), "unit": "Gparticles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} random output particles per step (plus the full bf16 tree fill)"},
+            "e2e": {"value": round(val, 9), "unit": "Gparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,6 +629,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=3000)
+    ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc"],
+                    help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step")
+    ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,14 +639,22 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        print(json.dumps(run_reference(args, rank, world)))
+        fn = run_reference_mc if args.workload == "blob256_mc" else run_reference
+        print(json.dumps(fn(args, rank, world)))
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    rec = run_ours(args, rank, world)
+    if args.workload == "blob256_mc":
+        rec = run_mc(args, rank, world, full=True)
+    else:
+        rec = run_ours(args, rank, world)
+        if not args.no_mc:
+            mc = run_mc(args, rank, world, full=False)
+            rec["multichannel"] = {k: mc[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "step_ms_parts",
+                                                      "roofline", "gpu_launches")}
     if rank == 0:
         print(json.dumps(rec))
     if world > 1:
