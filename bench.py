@@ -118,6 +118,18 @@ def recorded_traffic(kernel):
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank float over the process group (the step time every rank reports is the
+    slowest rank's); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algorithmic_bytes(apr, lay, k):
     """Bytes the method must move (no index overhead, no re-reads), per SURVEY-style accounting:
     conv forward  = N_p (4 in + 2 y + 4 out) + N_t (4 + 2) + (R_p + R_t) 4 + stencils
@@ -202,10 +214,7 @@ def run_ours(args, rank, world):
     parts = [[ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)] for j in range(5)]
     t_restrict, t_conv, t_adj, t_tadj, t_sgrad = parts
     step_ms = sum(sum(p) for p in parts) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, dev)
 
     # end to end through the public API with host buffers: H2D of the step's inputs (values,
     # upstream gradient), the step, D2H of its results (outputs, both gradients)
@@ -240,10 +249,7 @@ def run_ours(args, rank, world):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(e2e, dev)
 
     # forward-only pipeline (tree restriction + convolution), the paper's timed pipeline
     mean = lambda v: sum(v) / len(v)
@@ -402,10 +408,7 @@ def run_mc(args, rank, world, full=True):
     lay.sync_status()
     parts = [statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)) for j in range(4)]
     step_ms = sum(parts)
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, dev)
     byts, flops = mc_algorithmic(apr, lay)
     peaks, src = _peaks()
     hbm, tc = float(peaks["hbm_gbs"]), float(peaks.get("bf16_tflops", 1900.0))
@@ -467,7 +470,7 @@ def run_mc(args, rank, world, full=True):
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e = statistics.mean(e2e_ms)
+    e2e = max_over_ranks(statistics.mean(e2e_ms), dev)
     rec["e2e"] = {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
                   "h2d_bytes_per_step": int(h_x.numel() * 2 + h_g.numel() * 2),
                   "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),

@@ -66,6 +66,9 @@ typedef struct {
 #define APR_REQUIRE_BALANCE 2u   /* check the 2:1 balance the 5^3 convolution relies on */
 #define APR_HOST_ONLY 4u         /* build the index on the host only (no device memory): for
                                     inspecting the structure on machines without a GPU */
+#define APR_SUBDOMAIN 8u         /* the APR covers a block of a larger image (e.g. one z-slab of a
+                                    sharded APR): l_max may exceed ceil(log2(max dim)), the levels
+                                    being those of the enclosing image */
 
 /* Boundary modes of the convolution (the paper pads without naming a rule, Sec. 5.1) */
 #define APR_BC_REFLECT 0         /* half-sample symmetric reflection at each level's grid */

@@ -27,14 +27,15 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALANCE, APR_VALIDATE,  # noqa: F401
-                   AprError)
+from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALANCE, APR_SUBDOMAIN,  # noqa: F401
+                   APR_VALIDATE, AprError)
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
            "apr_convolve_stencil_grad", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
            "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
-           "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY"]
+           "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
+           "APR_SUBDOMAIN"]
 
 
 def _stream_ptr(stream=None):

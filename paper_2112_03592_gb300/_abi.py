@@ -10,7 +10,7 @@ _lib = None
 APR_OK = 0
 STATUS = {0: "APR_OK", 1: "APR_ERR_INVALID_ARG", 2: "APR_ERR_INVALID_LAYOUT", 3: "APR_ERR_UNSUPPORTED",
           4: "APR_ERR_OOM", 5: "APR_ERR_CUDA", 6: "APR_ERR_TIMEOUT", 7: "APR_ERR_DEVICE"}
-APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY = 1, 2, 4
+APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY, APR_SUBDOMAIN = 1, 2, 4, 8
 APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
 APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS = 4, 5

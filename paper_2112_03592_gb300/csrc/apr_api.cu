@@ -82,7 +82,7 @@ const char *apr_last_error_message(void) { return g_last_msg; }
 apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream, apr_handle_t *out) {
     if (!out) return APR_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!layout || (flags & ~(APR_VALIDATE | APR_REQUIRE_BALANCE | APR_HOST_ONLY))) return APR_ERR_INVALID_ARG;
+    if (!layout || (flags & ~(APR_VALIDATE | APR_REQUIRE_BALANCE | APR_HOST_ONLY | APR_SUBDOMAIN))) return APR_ERR_INVALID_ARG;
     apr_handle_s *h = new (std::nothrow) apr_handle_s();
     if (!h) return APR_ERR_OOM;
     const char *msg = "";

@@ -39,7 +39,10 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &X,
         maxd = std::max(maxd, L.dims[a]);
     }
     const int lmax = ceil_log2(maxd);
-    if (L.l_max != lmax) { *msg = "l_max must equal ceil(log2(max dim))"; return APR_ERR_INVALID_LAYOUT; }
+    if (L.l_max < lmax || (L.l_max != lmax && !(flags & APR_SUBDOMAIN))) {
+        *msg = "l_max must equal ceil(log2(max dim)) (or exceed it for APR_SUBDOMAIN)";
+        return APR_ERR_INVALID_LAYOUT;
+    }
     if (L.l_min < 0 || L.l_min > L.l_max || L.l_max >= MAXL) { *msg = "bad level range"; return APR_ERR_INVALID_ARG; }
 
     X.l_min = L.l_min;
