@@ -399,9 +399,9 @@ CONFIGS = {
     # 1024x1024x512 (z=512), 2000 blobs sigma 2-20; 5^3 Gaussian sigma=1.5
     "blob1024": dict(dims=(512, 1024, 1024), n_blobs=2000, sigma_range=(2.0, 20.0), seed=1,
                      E=0.1, sigma_floor=10.0, l_min=3, k=5, stencil_sigma=1.5, sigma_scale=1.5),
-    # 512^3 (Richardson-Lucy workload), 256^3 (multi-channel, ~1.0M particles)
-    "blob512": dict(dims=(512, 512, 512), n_blobs=250, sigma_range=(2.0, 20.0), seed=2,
-                    E=0.1, sigma_floor=10.0, l_min=3, k=5, stencil_sigma=1.5, sigma_scale=3.0),
+    # 512^3 (Richardson-Lucy workload, ~2.9M particles), 256^3 (multi-channel, ~1.0M particles)
+    "blob512": dict(dims=(512, 512, 512), n_blobs=200, sigma_range=(2.0, 20.0), seed=2,
+                    E=0.1, sigma_floor=10.0, l_min=3, k=5, stencil_sigma=1.5, sigma_scale=1.0),
     "blob256": dict(dims=(256, 256, 256), n_blobs=400, sigma_range=(2.0, 12.0), seed=3,
                     E=0.1, sigma_floor=10.0, l_min=2, k=3, stencil_sigma=1.0, sigma_scale=1.5),
 }

@@ -510,6 +510,156 @@ def mc_cpu_baseline(apr, x, w, g, budget_s=20.0):
                       f"{n2} random output particles ({t_s:.2f} s), FP64, 1 thread"}
 
 
+RL_WORKLOAD = "blob512"
+RL_ITERS = 20
+
+
+def run_rl(args, rank, world, full=True):
+    """Richardson-Lucy on the 512^3 blob APR: 20 iterations with the restricted 5^3 Gaussian PSF
+    (sigma 1.5) and its flip; one step = the whole 20-iteration deconvolution from i_0 = u."""
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    apr = S.make_config(RL_WORKLOAD)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    Np = apr.n_particles
+    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
+    st_h = G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
+    st = torch.as_tensor(st_h, device=dev)
+    u = torch.as_tensor(apr.values, device=dev)
+    est = torch.empty_like(u)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        est.copy_(u)
+        G.apr_richardson_lucy(lay, u, st, K, RL_ITERS, G.APR_BC_REFLECT, estimate=est)
+
+    clk = ClockSampler(dev.index).__enter__() if full else None
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t1 = time.perf_counter()
+    if clk is not None:
+        time.sleep(0.12)
+        clk.__exit__()
+    lay.sync_status()
+    step_ms = max_over_ranks(statistics.mean(ms), dev)
+    # one convolution alone, for the roofline of the dominant kernel (the fused-epilogue convolution)
+    tree = G.apr_tree_restrict(lay, u)
+    out = torch.empty_like(u)
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.apr_convolve(lay, u, tree, st, K, G.APR_BC_REFLECT, out)
+        b.record(stream)
+        b.synchronize()
+        ev.append(a.elapsed_time(b))
+    conv_ms = statistics.mean(ev)
+    conv_bytes, _ = algorithmic_bytes(apr, lay, K)
+    conv_bytes += Np * 4   # the fused epilogue reads one more value per particle
+    peaks, src = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
+    pix = float(np.prod(apr.dims))
+    rec = {
+        "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
+        "value": round(world * Np * RL_ITERS / (step_ms * 1e-3) / 1e9, 4),
+        "unit": "Gparticles/s (particle-iterations of Richardson-Lucy; 2 convolutions each)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded 200-blob 512^3 image with Poisson noise -> APR)",
+        "config": {"workload": "blob APR 512^3 pixels: 20 Richardson-Lucy iterations, restricted 5^3 Gaussian PSF sigma=1.5 and its flip",
+                   "model": None, "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
+                   "step": "20 iterations from i_0 = u (per iteration: 2 tree restrictions, 2 convolutions with fused divide / multiply)",
+                   "l2": "flushed before every step (512 MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "pixel_equiv_GBps_per_conv": round(pix * 4 * 2 * RL_ITERS / (step_ms * 1e-3) / 1e9, 2),
+        "roofline": {"kernel": "conv_fwd_kernel<2> (apr_convolve, one launch timed alone)", "bound": "hbm",
+                     "achieved": round(conv_bytes / (conv_ms * 1e-3) / 1e9, 2), "peak": hbm, "unit": "GB/s",
+                     "frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                     "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": conv_bytes,
+                     "conv_ms": round(conv_ms, 5)},
+        "gpu_launches": RL_ITERS * 2 * (n_tree_levels + 1) * args.steps,
+    }
+    if not full:
+        return rec
+    h_u, h_est = torch.as_tensor(apr.values).pin_memory(), torch.empty(Np).pin_memory()
+    d_u = torch.empty_like(u)
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_u.copy_(h_u, non_blocking=True)
+        est.copy_(d_u)
+        G.apr_richardson_lucy(lay, d_u, st, K, RL_ITERS, G.APR_BC_REFLECT, estimate=est)
+        h_est.copy_(est, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = max_over_ranks(statistics.mean(e2e), dev)
+    rec["e2e"] = {"value": round(world * Np * RL_ITERS / (e2e_ms * 1e-3) / 1e9, 4), "unit": rec["unit"],
+                  "h2d_bytes_per_step": int(h_u.numel() * 4), "d2h_bytes_per_step": int(h_est.numel() * 4),
+                  "ms_per_step": round(e2e_ms, 4)}
+    rec["clocks"] = clk.summary(t0, t1)
+    if rank == 0 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = rl_cpu_baseline(apr, st_h, budget_s=args.cpu_budget)
+    return rec
+
+
+def rl_cpu_baseline(apr, st, budget_s=20.0):
+    """The FP64 oracle's Richardson-Lucy iteration on a bounded sample: the full tree fill (twice per
+    iteration) and the two convolutions of one iteration evaluated for a random sample of output
+    particles; rate = particle-iterations per second."""
+    import numpy as np
+
+    import oracle
+    W = st.reshape(apr.n_levels, -1).astype(np.float64)
+    o = oracle.Oracle(apr)
+    t0 = time.perf_counter()
+    o.tree()
+    t_fill = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    n = 1000
+    s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+    t0 = time.perf_counter()
+    o.conv(W, K, sample=s)
+    t_probe = time.perf_counter() - t0
+    n2 = int(min(apr.n_particles, max(n, n * (budget_s - t_fill) / max(2 * t_probe, 1e-6) * 0.8)))
+    s = np.sort(rng.choice(apr.n_particles, n2, replace=False))
+    t0 = time.perf_counter()
+    o.conv(W, K, sample=s)
+    o.conv(W[:, ::-1].copy(), K, sample=s)
+    t_s = time.perf_counter() - t0
+    per = 2 * t_fill / apr.n_particles + t_s / n2
+    return {"value": round(1.0 / per / 1e9, 9), "unit": "Gparticles/s (particle-iterations)", "cores": 1,
+            "kind": "oracle",
+            "sample": f"full tree fill ({t_fill:.2f} s, counted twice per iteration, scaled by sample/N) + the two "
+                      f"convolutions of one iteration for {n2} random output particles ({t_s:.2f} s), FP64, 1 thread"}
+
+
 def cpu_baseline(apr, st, gout, budget_s=20.0, sample_n=None):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the same step: the full
     tree fill, then forward and backward for a random sample of output particles. The tree fill
@@ -623,6 +773,48 @@ def run_reference_mc(args, rank, world):
             "e2e": {"value": round(val, 9), "unit": "Gparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_rl(args, rank, world):
+    """The oracle as the reference arm of the Richardson-Lucy workload (bounded sample per step)."""
+    import numpy as np
+
+    import aprsynth as S
+    import oracle
+    apr = S.make_config(RL_WORKLOAD)
+    w = S.gaussian_stencil(K, SIGMA)
+    W = oracle.restrict_stencil(w.astype(np.float32).astype(np.float64), apr.l_max, apr.l_min).reshape(apr.n_levels, -1)
+    W_flip = W[:, ::-1].copy()
+    o = oracle.Oracle(apr)
+    rng = np.random.default_rng(1)
+    n = max(1, args.ref_sample // 3)
+    t_fill, t_samp = [], []
+    for i in range(args.warmup + args.steps):
+        s = np.sort(rng.choice(apr.n_particles, n, replace=False))
+        t0 = time.perf_counter()
+        o.set_values(apr.values)
+        o.tree()
+        t1 = time.perf_counter()
+        o.conv(W, K, sample=s)
+        o.conv(W_flip, K, sample=s)
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            t_fill.append(t1 - t0)
+            t_samp.append(t2 - t1)
+    per = 2 * statistics.mean(t_fill) / apr.n_particles + statistics.mean(t_samp) / n
+    val = 1.0 / per / 1e9
+    unit = "Gparticles/s (particle-iterations of Richardson-Lucy; 2 convolutions each)"
+    return {"metric": "APR conv Gparticles/s & pixel-equiv GB/s", "value": round(val, 9), "unit": unit,
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * (statistics.mean(t_fill) + statistics.mean(t_samp)), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded 200-blob 512^3 image with Poisson noise -> APR)",
+            "config": {"workload": "blob APR 512^3 pixels: 20 Richardson-Lucy iterations, restricted 5^3 Gaussian PSF sigma=1.5 and its flip",
+                       "step": f"oracle: one iteration's tree fill (counted twice) + its two convolutions for {n} random "
+                               "output particles; rate = particle-iterations per second"},
+            "cpu_baseline": {"value": round(val, 9), "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} random output particles per step (plus the full tree fill)"},
+            "e2e": {"value": round(val, 9), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,8 +824,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=3000)
-    ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc"],
-                    help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step")
+    ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc", "blob512_rl"],
+                    help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step; "
+                         "blob512_rl: 20 Richardson-Lucy iterations")
     ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -642,7 +835,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        fn = run_reference_mc if args.workload == "blob256_mc" else run_reference
+        fn = {"blob256_mc": run_reference_mc, "blob512_rl": run_reference_rl}.get(args.workload, run_reference)
         print(json.dumps(fn(args, rank, world)))
         return
     if world > 1:
@@ -652,6 +845,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "blob256_mc":
         rec = run_mc(args, rank, world, full=True)
+    elif args.workload == "blob512_rl":
+        rec = run_rl(args, rank, world, full=True)
     else:
         rec = run_ours(args, rank, world)
         if not args.no_mc:

@@ -192,6 +192,21 @@ apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particle
                                            const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                            float *grad_particles, float *grad_stencils, apr_stream_t stream);
 
+/* Richardson-Lucy deconvolution on the APR (Sec. 6.2): n_iter iterations of
+ *   i_{k+1} = i_k * ((u / (i_k (*) w)) (*) w_flip)
+ * where (*) is apr_convolve with the per-level stencils `stencils` (pass the restricted stencils of
+ * the PSF, apr_restrict_stencil, for the paper's scheme), w_flip is every level's stencil with its
+ * taps reversed in each dimension, and division and multiplication are per particle (the division
+ * gives 0 where the denominator is <= 0). Each iteration restricts the tree of i_k and of the ratio.
+ * The division and the multiplication run inside the convolution kernel's output write.
+ *   observed: device [N_p] float32 (u);  estimate: device [N_p] float32, in: i_0, out: i_n_iter;
+ *   stencils: device [L][k^3] float32;  k: 3 or 5;  bc as apr_convolve;
+ *   workspace: apr_rl_workspace_bytes(h) bytes, 256-byte aligned (a tree and a ratio buffer). */
+size_t apr_rl_workspace_bytes(apr_handle_t h);
+apr_status_t apr_richardson_lucy(apr_handle_t h, const float *observed, const float *stencils, int32_t k, int32_t bc,
+                                 int32_t n_iter, float *estimate, void *workspace, size_t workspace_bytes,
+                                 apr_stream_t stream);
+
 /* ---- Multi-channel convolution with bfloat16 features and weights (the APR CNN layer that Sec. 6
  * proposes: several feature channels per particle, mixed by per-level learned filters). Features are
  * bfloat16 (stored as uint16 bit patterns), channels-last; products are exact and accumulate in FP32

@@ -252,3 +252,23 @@ def restrict_stencil(w: np.ndarray, l_max: int, l_min: int) -> np.ndarray:
                 row[d + r, e + r] = M[i0, i0 + e]
         out[l - l_min] = np.einsum("abc,ai,bj,ck->ijk", w, row, row, row)
     return out
+
+
+def richardson_lucy(apr, observed, stencils, k, n_iter, bc=BC_REFLECT, estimate=None) -> np.ndarray:
+    """Richardson-Lucy on the APR (Sec. 6.2): i_{k+1} = i_k * ((u / (i_k (*) w)) (*) w_flip), with
+    (*) the APR convolution of Sec. 4.1 using the per-level stencils [L][k^3] and w_flip every
+    level's stencil with its taps reversed in each dimension. Division and multiplication are per
+    particle; a ratio whose denominator is <= 0 is 0 (the paper divides without a guard).
+    i_0 = observed unless `estimate` is given. FP64."""
+    u = np.asarray(observed, np.float64).reshape(-1)
+    i = u.copy() if estimate is None else np.asarray(estimate, np.float64).reshape(-1).copy()
+    W = np.asarray(stencils, np.float64).reshape(apr.n_levels, k ** 3)
+    W_flip = W[:, ::-1].copy()
+    o = Oracle(apr, i)
+    for _ in range(n_iter):
+        o.set_values(i)
+        c = o.conv(W, k, bc)[:, 0]
+        ratio = np.where(c > 0, u / np.where(c > 0, c, 1.0), 0.0)
+        o.set_values(ratio)
+        i = i * o.conv(W_flip, k, bc)[:, 0]
+    return i

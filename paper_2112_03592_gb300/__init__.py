@@ -12,6 +12,8 @@ Functions with the C names:
     apr_convolve_backward(layout, particles, tree, stencils, k, grad_out[, bc])
                                                                   -> (grad_particles, grad_stencils)
       = apr_convolve_adjoint + apr_tree_restrict_adjoint + apr_convolve_stencil_grad
+    apr_richardson_lucy(layout, observed, stencils, k, n_iter[, bc, estimate])
+                                                                  -> estimate  (Sec. 6.2)
     apr_tree_restrict_bf16(layout, particles[, tree])             -> tree      (bf16, 16 channels)
     apr_convolve_mc(layout, particles, tree, weights[, bc, out])  -> out       (16 -> 16 channels, k = 3)
     apr_convolve_mc_backward(layout, particles, tree, weights, grad_out[, bc])
@@ -32,7 +34,7 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
-           "apr_convolve_stencil_grad", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
+           "apr_convolve_stencil_grad", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
            "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
            "APR_SUBDOMAIN"]
@@ -242,6 +244,29 @@ def apr_convolve_stencil_grad(layout: AprLayout, particles, tree, k, grad_out, b
         _dev_ptr(grad_stencils, "grad_stencils", layout.n_levels * k ** 3, torch.float32),
         ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
     return grad_stencils
+
+
+def apr_richardson_lucy(layout: AprLayout, observed, stencils, k, n_iter, bc=APR_BC_REFLECT, estimate=None,
+                        stream=None):
+    """n_iter Richardson-Lucy updates i <- i * ((u / (i conv w)) conv w_flip) (Sec. 6.2) on the APR;
+    i_0 = observed unless `estimate` (updated in place) is given."""
+    import torch
+    _dev_ptr(observed, "observed", layout.n_particles, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    if estimate is None:
+        estimate = observed.clone()
+    _dev_ptr(estimate, "estimate", layout.n_particles, torch.float32)
+    nbytes = int(layout._lib.apr_rl_workspace_bytes(layout.handle))
+    key = ("rl",)
+    ws = layout._ws.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=observed.device)
+        layout._ws[key] = ws
+    _abi.check("apr_richardson_lucy", layout._lib.apr_richardson_lucy(
+        layout.handle, ctypes.c_void_p(observed.data_ptr()), ctypes.c_void_p(stencils.data_ptr()), int(k), int(bc),
+        int(n_iter), ctypes.c_void_p(estimate.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+        _stream_ptr(stream)))
+    return estimate
 
 
 # ---- multi-channel, bfloat16 features (16 channels, k = 3)

@@ -9,7 +9,8 @@
 
 namespace aprk {
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
-                            const float *tree, const float *st, int bc, float *out, cudaStream_t s);
+                            const float *tree, const float *st, int bc, float *out, cudaStream_t s,
+                            int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr);
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
                                  cudaStream_t s);
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
@@ -308,6 +309,42 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
         st = apr_convolve_stencil_grad(h, particles, tree, k, bc, grad_out, grad_stencils, partial,
                                        workspace_bytes - gt_bytes, stream);
     return st;
+}
+
+size_t apr_rl_workspace_bytes(apr_handle_t h) {
+    if (!h) return 0;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(size_t(h->X.nt) * sizeof(float)) + al(size_t(h->X.np) * sizeof(float));
+}
+
+apr_status_t apr_richardson_lucy(apr_handle_t h, const float *observed, const float *stencils, int32_t k, int32_t bc,
+                                 int32_t n_iter, float *estimate, void *workspace, size_t workspace_bytes,
+                                 apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (n_iter < 0 || !stencils || (X.np && (!observed || !estimate))) return APR_ERR_INVALID_ARG;
+    const size_t need = apr_rl_workspace_bytes(h);
+    if (need && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+        return APR_ERR_INVALID_ARG;
+    float *tree = static_cast<float *>(workspace);
+    float *ratio = reinterpret_cast<float *>(static_cast<char *>(workspace) + (size_t(X.nt) * sizeof(float) + 255) / 256 * 256);
+    const int n = int(X.fwd_items.size());
+    for (int it = 0; it < n_iter; ++it) {
+        // ratio = u / (i_k conv w); i_{k+1} = i_k * (ratio conv w_flipped)
+        apr_status_t st = apr_tree_restrict(h, estimate, tree, 1, stream);
+        if (st != APR_OK) return st;
+        cudaError_t e = launch_conv_fwd(k, h->L, h->d_fwd, n, estimate, tree, stencils, bc, ratio, stream, EPI_DIVIDE,
+                                        false, observed);
+        if (e != cudaSuccess) return cuda_status(e);
+        st = apr_tree_restrict(h, ratio, tree, 1, stream);
+        if (st != APR_OK) return st;
+        e = launch_conv_fwd(k, h->L, h->d_fwd, n, ratio, tree, stencils, bc, estimate, stream, EPI_MULTIPLY, true,
+                            estimate);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return APR_OK;
 }
 
 apr_status_t apr_sync_status(apr_handle_t h, apr_stream_t stream) {

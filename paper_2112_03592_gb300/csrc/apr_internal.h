@@ -69,6 +69,9 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &ou
 // Record a short reason for the last failure on this thread (read by apr_last_error_message).
 void set_last_message(const char *msg);
 
+// Epilogues of the convolution kernel (launch_conv_fwd)
+constexpr int EPI_PLAIN = 0, EPI_DIVIDE = 1, EPI_MULTIPLY = 2;
+
 // Bits of the device error word (DevLayout::err), read and cleared by apr_sync_status.
 constexpr unsigned ERR_DEVICE_CHECK = 1u;  // a device-side consistency check failed
 constexpr unsigned ERR_TIMEOUT = 2u;       // a bounded wait (tensor-core completion) gave up

@@ -299,6 +299,20 @@ __device__ __forceinline__ void windows_apply(const float *patch, const float *w
     }
 }
 
+// Per-particle epilogue of the convolution: the plain output, or the element-wise division and
+// multiplication of a Richardson-Lucy update (Sec. 6.2) fused into the write. aux may alias the
+// output (each particle's entry is read, then written, by the same thread).
+struct Epilogue {
+    int mode;                  // EPI_PLAIN, EPI_DIVIDE (aux[p] / acc, 0 if acc <= 0), EPI_MULTIPLY (aux[p] * acc)
+    bool flip;                 // taps in reversed order in every dimension (the flipped stencil)
+    const float *aux;
+    __device__ __forceinline__ float apply(int p, float acc) const {
+        if (mode == EPI_DIVIDE) return acc > 0.f ? __fdiv_rn(aux[p], acc) : 0.f;
+        if (mode == EPI_MULTIPLY) return aux[p] * acc;
+        return acc;
+    }
+};
+
 // ------------------------------------------------------------------------------------------------
 // APR convolution (Sec. 4.1; Sec. 5.2 with 8x8-row tiles and 64-cell y-blocks instead of the
 // paper's 4x4 / 8x8 warp grid with a sliding buffer).
@@ -308,18 +322,21 @@ __global__ void __launch_bounds__(NT, 3) conv_fwd_kernel(const DevLayout L, cons
                                                          const float *__restrict__ vals,
                                                          const float *__restrict__ tree,
                                                          const float *__restrict__ stencils, int bc,
-                                                         float *__restrict__ out) {
+                                                         float *out, const Epilogue epi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    load_taps<R>(stencils, it.l - L.l_min, false, S.w8);
+    load_taps<R>(stencils, it.l - L.l_min, epi.flip, S.w8);
     stage_patch<R>(L, it, vals, tree, bc, S);
     windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
         const unsigned m = S.wmask[w];
         const int first = S.wfirst[w];
 #pragma unroll
         for (int j = 0; j < WIN; ++j)
-            if ((m >> j) & 1u) out[first + __popc(m & ((1u << j) - 1u))] = acc[j];
+            if ((m >> j) & 1u) {
+                const int p = first + __popc(m & ((1u << j) - 1u));
+                out[p] = epi.apply(p, acc[j]);
+            }
     });
 }
 
@@ -826,11 +843,11 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 
 template <int R>
 cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
-                              const float *st, int bc, float *out, cudaStream_t s) {
+                              const float *st, int bc, float *out, const Epilogue &epi, cudaStream_t s) {
     const size_t sm = sizeof(PatchSmem<R>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_fwd_kernel<R>), sm);
     if (e != cudaSuccess) return e;
-    if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out);
+    if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out, epi);
     return cudaGetLastError();
 }
 
@@ -858,9 +875,11 @@ cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, c
 
 // ---- launch entry points used by the C ABI (apr_api.cu)
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
-                            const float *tree, const float *st, int bc, float *out, cudaStream_t s) {
-    return k == 3 ? launch_conv_fwd_t<1>(L, items, n, vals, tree, st, bc, out, s)
-                  : launch_conv_fwd_t<2>(L, items, n, vals, tree, st, bc, out, s);
+                            const float *tree, const float *st, int bc, float *out, cudaStream_t s, int epi_mode,
+                            bool flip, const float *aux) {
+    const Epilogue epi{epi_mode, flip, aux};
+    return k == 3 ? launch_conv_fwd_t<1>(L, items, n, vals, tree, st, bc, out, epi, s)
+                  : launch_conv_fwd_t<2>(L, items, n, vals, tree, st, bc, out, epi, s);
 }
 
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,

@@ -278,3 +278,46 @@ def test_bf16_tree_is_rounded_average_level_by_level():
     exact = Oracle(apr, vals).tree()
     fin = tc[:, 0] == apr.l_max - 1
     np.testing.assert_array_equal(t[fin], np.vectorize(oracle.round_bf16)(exact[fin]))
+
+
+# ---- Richardson-Lucy (Sec. 6.2)
+def test_rl_identity_psf_gives_observed_after_one_iteration():
+    apr = S.random_balanced_apr((12, 10, 20), 1, seed=31, p_fine=0.05)
+    rng = np.random.default_rng(2)
+    u = rng.uniform(1.0, 5.0, apr.n_particles)
+    i0 = rng.uniform(0.5, 2.0, apr.n_particles)
+    delta = np.zeros((apr.n_levels, 27))
+    delta[:, 13] = 1.0
+    got = oracle.richardson_lucy(apr, u, delta, 3, 1, estimate=i0)
+    np.testing.assert_allclose(got, u, rtol=1e-14)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_rl_on_pixels_equals_dense_rl(bc):
+    from scipy import ndimage
+    dims = (7, 9, 11)
+    apr = S.uniform_level_apr(dims, S.l_max_for(dims), l_min=2)
+    rng = np.random.default_rng(3)
+    u = rng.uniform(1.0, 10.0, apr.n_particles)
+    w = rng.uniform(0.0, 1.0, (3, 3, 3))          # non-symmetric: a missing flip fails
+    w /= w.sum()
+    W = np.zeros((apr.n_levels, 27))
+    W[:] = w.reshape(-1)
+    got = oracle.richardson_lucy(apr, u, W, 3, 3, bc=bc)
+    mode = "reflect" if bc == 0 else "constant"
+    U = u.reshape(dims)                             # all-finest APR: particle order = z, x, y raster
+    I = U.copy()
+    for _ in range(3):
+        c = ndimage.correlate(I, w, mode=mode, cval=0.0)
+        ratio = np.where(c > 0, U / np.where(c > 0, c, 1.0), 0.0)
+        I = I * ndimage.correlate(ratio, w[::-1, ::-1, ::-1], mode=mode, cval=0.0)
+    np.testing.assert_allclose(got, I.reshape(-1), rtol=1e-12)
+
+
+def test_rl_constant_image_is_a_fixed_point():
+    apr = S.random_balanced_apr((16, 16, 24), 1, seed=32, p_fine=0.03)
+    u = np.full(apr.n_particles, 4.5)
+    w = S.gaussian_stencil(5, 1.5)
+    W = oracle.restrict_stencil(w, apr.l_max, apr.l_min).reshape(apr.n_levels, -1)
+    got = oracle.richardson_lucy(apr, u, W, 5, 4)
+    np.testing.assert_allclose(got, u, rtol=1e-12)
