@@ -24,6 +24,12 @@ __device__ __forceinline__ void block_sync() {
     __syncthreads();
 }
 
+// Barrier of the two warps 2g and 2g+1 (named barrier 1 + g; barrier 0 is the block barrier).
+__device__ __forceinline__ void pair_sync(int g) {
+    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(64) : "memory");
+}
+
 __device__ __forceinline__ int reflect_idx(int i, int d) {
     // half-sample symmetric reflection into [0, d), repeated for grids smaller than the stencil
     const int p = 2 * d;
@@ -120,7 +126,7 @@ struct YVLoader {
 // takes a contiguous share of the chunk with strided lanes, issuing the loads of UNROLL elements
 // per thread before any of them is used. Trip counts depend on the warp only (lanes stay converged).
 // Ends with a block barrier.
-constexpr int SEGID_CAP = 4096;
+constexpr int SEGID_CAP = 2048;
 
 template <typename Load, typename Use>
 __device__ __forceinline__ void for_each_element(const int *seg_lo, const int *pre, int nseg, unsigned short *segid,

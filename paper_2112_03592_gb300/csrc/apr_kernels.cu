@@ -71,11 +71,13 @@ struct PatchSmem {
     int seg_meta[G::NSEG];               // patch row | kind << 8 | (interior row + 1) << 10
     int pre[(G::NSEG > NIW ? G::NSEG : NIW) + 1];
     int warp_tot[NWARP + 1];
-    float red[NWARP][32][WIN];           // partial window sums of the second half of the stencil rows
     unsigned wmask[NIW];                 // target bits of every window
     int wfirst[NIW];                     // first target (particle index) of every window
     unsigned short act[NIW];             // active windows, in window order
-    unsigned short segid[SEGID_CAP];     // segment of every staged element of the current chunk
+    union {                              // staging and window compute never overlap
+        unsigned short segid[SEGID_CAP]; // segment of every staged element of the current chunk
+        float red[NWARP / 2][32][WIN];   // partial window sums of the second half of the stencil rows
+    };
     int nact;
     int boundary;                        // the tile with its halo reaches outside the grid
 };
@@ -265,7 +267,9 @@ __device__ __forceinline__ int mirror_preimages(int c, int d, int *out) {
 
 // Stencil sums of the active windows act[0..nact) of a patch: warps 2v and 2v+1 take the same 32
 // windows, the first half of the stencil rows and the second half; the second writes its partial
-// sums to red[], the first adds them (fixed order) and calls emit(window, acc).
+// sums to red[], the first adds them (fixed order) and calls emit(window, acc). The two warps of a
+// pair synchronise with their own named barrier; callers that read what emit wrote from other warps
+// need a block barrier afterwards.
 template <int R, typename Emit>
 __device__ __forceinline__ void windows_apply(const float *patch, const float *w8, const unsigned short *act, int nact,
                                               float (*red)[32][WIN], Emit emit) {
@@ -288,14 +292,14 @@ __device__ __forceinline__ void windows_apply(const float *patch, const float *w
         }
         if (half == 1)
 #pragma unroll
-            for (int j = 0; j < WIN; ++j) red[warp][lane][j] = acc[j];
-        block_sync();
+            for (int j = 0; j < WIN; ++j) red[grp][lane][j] = acc[j];
+        pair_sync(grp);
         if (half == 0 && a < nact) {
 #pragma unroll
-            for (int j = 0; j < WIN; ++j) acc[j] += red[warp + 1][lane][j];
+            for (int j = 0; j < WIN; ++j) acc[j] += red[grp][lane][j];
             emit(w, acc);
         }
-        block_sync();
+        pair_sync(grp);
     }
 }
 
@@ -318,7 +322,7 @@ struct Epilogue {
 // paper's 4x4 / 8x8 warp grid with a sliding buffer).
 // ------------------------------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, 3) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
                                                          const float *__restrict__ vals,
                                                          const float *__restrict__ tree,
                                                          const float *__restrict__ stencils, int bc,
@@ -434,10 +438,12 @@ struct BwdSmem {
     int pre[(G::NROW + G::NRSEG > NIW ? G::NROW + G::NRSEG : NIW) + 1];
     int warp_tot[NWARP + 1];
     unsigned long long need[NIR];
-    float red[NWARP][32][WIN];
     unsigned char wmir[NIW];                  // window has cells with mirrored preimages
     unsigned short act[NIW];
-    unsigned short segid[SEGID_CAP];
+    union {                                   // staging / routing and window compute never overlap
+        unsigned short segid[SEGID_CAP];
+        float red[NWARP / 2][32][WIN];
+    };
     int nact;
 };
 
@@ -592,6 +598,7 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
     });
+    block_sync();
     // mirrored preimages (reflect only). Rows with mirrored z / x rows: one thread per active window
     // sums the windows of all mirrored row combinations (z', x') != (z, x) (same y cells) with the
     // window machinery; stencil rows outside the staged patch read zero, as the gradient outside the
@@ -836,6 +843,11 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
         dst[i] = v + share[warp][(yv >> 1) - y0];
     });
 }
+
+// Shared memory per block sets the blocks per SM (228 KB per SM, 1 KB reserved per block):
+// forward 4, data adjoint 3.
+static_assert(4 * (sizeof(PatchSmem<2>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
+static_assert(3 * (sizeof(BwdSmem<2>) + 1024) <= 228 * 1024, "data adjoint: three blocks per SM");
 
 cudaError_t set_smem(const void *fn, size_t bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
