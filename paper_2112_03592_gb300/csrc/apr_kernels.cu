@@ -41,10 +41,12 @@ struct Geo {
     static constexpr int PYS = (PY + 3) / 4 * 4;           // row stride, 16-byte multiple
     static constexpr int NROW = PZ * PX;
     static constexpr int NSEG = 3 * NROW;                  // particle, tree, coarser-particle source per row
+    static constexpr int NCZ = ((TZ + R - 1) >> 1) + ((R + 1) >> 1) + 1;  // level-(l-1) rows per axis under a patch
     static constexpr int NRSEG = 2 * NIR + NIR / 4;        // backward routing: particles, tree, coarser particles
     static_assert(WIN + 2 * R <= 12, "a window's taps must fit three 16-byte loads");
     static_assert((NWIN - 1) * WIN + 12 <= PYS, "window loads stay inside the row");
     static_assert(NSEG <= 2 * NT && NROW + NRSEG <= 2 * NT, "segments are scanned two per thread");
+    static_assert(NCZ * NCZ <= NROW && PZ < 15 && PX < 15, "once-staged coarse rows: segment count, 4-bit row fields");
 };
 
 // Deterministic compaction of the windows w (0 <= w < NIW) with flag(w) into act[0..*nact).
@@ -79,7 +81,6 @@ struct PatchSmem {
         float red[NWARP / 2][32][WIN];   // partial window sums of the second half of the stencil rows
     };
     int nact;
-    int boundary;                        // the tile with its halo reaches outside the grid
 };
 
 // Stage the forward patch of item `it` (Sec. 3.5): patch rows z in [z0-R, z0+TZ+R), x likewise, y in
@@ -104,25 +105,46 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
     }
     if (gwin)
         for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(gwin)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid == 0)
-        S.boundary = (z0 - R < 0 || x0 - R < 0 || yw < 0 || z0 + TZ + R > g.dz || x0 + TX + R > g.dx || yw + G::PY > g.dy);
 
-    // segment bounds, two per thread (entries 2t, 2t+1) for the scan
+    // segment bounds, two per thread (entries 2t, 2t+1) for the scan. Segments [0, NROW): level-l
+    // particles of every patch row, [NROW, 2 NROW): level-l tree nodes, [2 NROW, 3 NROW): level-(l-1)
+    // particles. Away from the grid boundary each level-(l-1) row is staged once and written to the
+    // (up to 2 x 2) patch rows it covers (NCZ^2 segments, kind 3); tiles reaching outside the grid
+    // stage one coarser row per patch row (kind 2), which follows the reflection of every row.
+    const bool boundary = z0 - R < 0 || x0 - R < 0 || yw < 0 || z0 + TZ + R > g.dz || x0 + TX + R > g.dx ||
+                          yw + G::PY > g.dy;
     int cnt[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int s = 2 * tid + h;
         if (s >= G::NSEG) break;
         const int kind = s / G::NROW, pr = s % G::NROW;
+        const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
+        int lo = 0, hi = 0;
+        if (kind == 2 && !boundary) {
+            // one level-(l-1) row (cz, cx) per segment; its fine rows 2cz + a, 2cx + b (a, b in {0, 1})
+            // sit at patch rows rz0 + a, rx0 + b (clipped to the patch)
+            int meta = 0;
+            if (pr < G::NCZ * G::NCZ && l > L.l_min) {
+                const LevelGeo gp = L.geo[l - 1];
+                const int cz = ((z0 - R) >> 1) + pr / G::NCZ, cx = ((x0 - R) >> 1) + pr % G::NCZ;
+                if (cz < gp.dz && cx < gp.dx)
+                    row_range(L.row_ptr, L.off, gp.row0, gp.off0, gp.nb, cz * gp.dx + cx, ylo >> 1, ((yhi - 1) >> 1) + 1,
+                              lo, hi);
+                meta = (2 * cz - (z0 - R) + 1) | ((2 * cx - (x0 - R) + 1) << 4) | (3 << 8);
+            }
+            S.seg_lo[s] = lo;
+            cnt[h] = hi - lo;
+            S.seg_meta[s] = meta;
+            continue;
+        }
         int z = z0 - R + pr / G::PX, x = x0 - R + pr % G::PX;
         const bool inside = z >= 0 && z < g.dz && x >= 0 && x < g.dx;
-        int lo = 0, hi = 0;
         if (inside || bc == APR_BC_REFLECT) {
             if (!inside) {
                 z = reflect_idx(z, g.dz);
                 x = reflect_idx(x, g.dx);
             }
-            const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
             const int rr = z * g.dx + x;
             if (kind == 0) {
                 row_range(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, ylo, yhi, lo, hi);
@@ -161,15 +183,29 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
                 atomicMin(&S.wfirst[w], i);
                 if (gwin) gwin[trow * BY + yr] = gout[i];
             }
-        } else {
+        } else if (kind == 2) {
             const int yy = 2 * s.y;  // first level-l cell of the coarser particle
             const int pos = yy - yw;
             if (pos >= 0 && pos < G::PY && yy < g.dy) prow[pos] = s.v;
             if (pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy) prow[pos + 1] = s.v;
+        } else {
+            // a level-(l-1) particle of a once-staged coarse row: its 2 x 2 x 2 fine cells
+            const int rz0 = (meta & 15) - 1, rx0 = ((meta >> 4) & 15) - 1;
+            const int yy = 2 * s.y, pos = yy - yw;
+            const bool c0 = pos >= 0 && pos < G::PY && yy < g.dy, c1 = pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy;
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int rz = rz0 + a, rx = rx0 + b;
+                    if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+                    float *q = S.patch + (rz * G::PX + rx) * G::PYS;
+                    if (c0) q[pos] = s.v;
+                    if (c1) q[pos + 1] = s.v;
+                }
         }
     });
-    block_sync();
-    if (S.boundary) {
+    if (boundary) {
         // rows outside the grid with zero boundary: zero; cells outside the grid in y (the first
         // max(0, -yw) and the last max(0, yw + PY - dy) of a row): mirror (reflect) or zero
         const int nlo = max(0, -yw), hi0 = min(G::PY, g.dy - yw);
@@ -534,13 +570,16 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     block_sync();
 
     // cells that need H: within R of a nonzero gradient, or (reflect) close enough to the grid
-    // boundary to have mirrored preimages; windows with any such cell are active
-    if (tid < NIR) {
-        const int ia = tid / TX, ib = tid % TX;
-        const int z = z0 + ia, x = x0 + ib;
+    // boundary to have mirrored preimages; windows with any such cell are active. Four threads per
+    // interior row, each over a quarter of the stencil rows; bit j of need[r] = interior cell j.
+    static_assert(NIR * 4 == NT, "four threads per interior row");
+    {
+        const int r = tid >> 2, q = tid & 3;
+        const int z = z0 + r / TX, x = x0 + r % TX;
+        const bool valid = z < g.dz && x < g.dx;
         unsigned long long m = 0ull;
         bool edge_zx = false;
-        if (z < g.dz && x < g.dx) {
+        if (valid) {
             // preimage rows of this row: itself and (reflect) the out-of-grid rows mirroring onto it
             int pz[2 * R + 1], px[2 * R + 1];
             int nz = 1, nx = 1;
@@ -553,39 +592,40 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
             edge_zx = nz > 1 || nx > 1;
             for (int iz = 0; iz < nz; ++iz)
                 for (int ix = 0; ix < nx; ++ix)
-                    for (int dz = 0; dz < 2 * R + 1; ++dz)
-                        for (int dx = 0; dx < 2 * R + 1; ++dx) {
-                            const int rz = pz[iz] - z0 + dz, rx = px[ix] - x0 + dx;  // patch row
-                            if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
-                            const int row = rz * G::PX + rx;
-                            const unsigned long long lo64 =
-                                (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
-                            const unsigned long long hi64 = S.rmask[row * 3 + 2];
-                            // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
-                            m |= lo64;
+                    for (int pr = q; pr < G::NPAIR; pr += 4) {
+                        const int rz = pz[iz] - z0 + pr / G::K, rx = px[ix] - x0 + pr % G::K;  // patch row
+                        if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+                        const int row = rz * G::PX + rx;
+                        const unsigned long long lo64 =
+                            (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
+                        const unsigned long long hi64 = S.rmask[row * 3 + 2];
+                        // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
+                        m |= lo64;
 #pragma unroll
-                            for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
-                        }
-            if (reflect)
-                for (int j = 0; j < BY; ++j)
-                    if (y0 + j < R || y0 + j >= g.dy - R) m |= 1ull << j;
+                        for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
+                    }
+        }
+        const unsigned mlo = unsigned(m), mhi = unsigned(m >> 32);
+        const unsigned olo = mlo | __shfl_xor_sync(0xffffffffu, mlo, 1), ohi = mhi | __shfl_xor_sync(0xffffffffu, mhi, 1);
+        m = (unsigned long long)(olo | __shfl_xor_sync(0xffffffffu, olo, 2)) |
+            ((unsigned long long)(ohi | __shfl_xor_sync(0xffffffffu, ohi, 2)) << 32);
+        if (q == 0) {
+            // cells inside the grid, and (reflect) cells within R of the y boundary of the grid
             const int nvalid = g.dy - y0;
-            if (nvalid < BY) m &= nvalid <= 0 ? 0ull : ((1ull << nvalid) - 1ull);
+            const unsigned long long vmask = nvalid >= BY ? ~0ull : (nvalid <= 0 ? 0ull : ((1ull << nvalid) - 1ull));
+            const int jl = R - y0, jh = g.dy - R - y0;
+            const unsigned long long ylow = jl <= 0 ? 0ull : (jl >= BY ? ~0ull : ((1ull << jl) - 1ull));
+            const unsigned long long yhigh = jh <= 0 ? ~0ull : (jh >= BY ? 0ull : (~0ull << jh));
+            const unsigned long long yedge = reflect && valid ? (ylow | yhigh) & vmask : 0ull;
+            m = valid ? (m | yedge) & vmask : 0ull;
+            // wmir: bit 0 = the row has mirrored rows (z or x), bit 1 = the window has cells within R
+            // of the y boundary
+#pragma unroll
+            for (int w = 0; w < NWIN; ++w)
+                S.wmir[r * NWIN + w] = (unsigned char)((reflect && valid && edge_zx ? 1 : 0) |
+                                                       (((yedge >> (w * WIN)) & 0xffull) ? 2 : 0));
+            S.need[r] = m;
         }
-        // wmir: bit 0 = the row has mirrored rows (z or x), bit 1 = the window has cells within R of the
-        // y boundary
-        for (int w = 0; w < NWIN; ++w) {
-            int mir = 0;
-            if (reflect && z < g.dz && x < g.dx) {
-                mir = edge_zx ? 1 : 0;
-                for (int j = 0; j < WIN; ++j) {
-                    const int yy = y0 + w * WIN + j;
-                    if (yy < g.dy && (yy < R || yy >= g.dy - R)) mir |= 2;
-                }
-            }
-            S.wmir[tid * NWIN + w] = (unsigned char)mir;
-        }
-        S.need[tid] = m;
     }
     block_sync();
     // (compact_windows reuses pre[] as scratch; the routing prefix is rebuilt from cnt[] below)
