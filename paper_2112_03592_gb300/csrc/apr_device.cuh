@@ -13,7 +13,7 @@ namespace dev {
 
 constexpr int NT = 256;                // threads per block of every kernel below
 constexpr int NWARP = NT / 32;
-constexpr int UNROLL = 8;              // element loads in flight per thread and staging step
+constexpr int UNROLL = 4;              // element loads in flight per thread and staging step
 static_assert(TZ % 2 == 0 && TX % 2 == 0, "tiles must be even-aligned (coarse cells)");
 
 // Block barrier. The warp is reconverged first: threads of one warp may reach this point at

@@ -103,8 +103,12 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
         S.wmask[i] = 0u;
         S.wfirst[i] = INT_MAX;
     }
-    if (gwin)
+    if (gwin) {
+        // stencil-gradient mode: every window cell enters the sums (non-targets with g = 0), so the
+        // patch cells no source covers must hold 0, not stale shared memory (0 * NaN = NaN)
         for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(gwin)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     // segment bounds, two per thread (entries 2t, 2t+1) for the scan. Segments [0, NROW): level-l
     // particles of every patch row, [NROW, 2 NROW): level-l tree nodes, [2 NROW, 3 NROW): level-(l-1)
@@ -242,13 +246,12 @@ __device__ void load_taps(const float *__restrict__ stencils, int l_idx, bool fl
 }
 
 // acc[j] += sum over stencil rows (dz, dx) = pairs [P0, P1) of sum_dy w8[(dz,dx)][dy] *
-// P[row (ia+dz, ib+dx)][col + j + dy], j < WIN. base points at P[row (ia, ib)][col]; the loop is
-// unrolled so every row offset is a constant.
+// P[row (ia+dz, ib+dx)][col + j + dy], j < WIN. base points at P[row (ia, ib)][col].
 template <int R, int P0, int P1>
 __device__ __forceinline__ void window_rows(const float *base, const float *w8, float acc[WIN]) {
     using G = Geo<R>;
-#pragma unroll
-    for (int pair = P0; pair < P1; ++pair) {
+#pragma unroll 1
+    for (int pair = P0; pair < P1; ++pair) {  // not unrolled: a smaller loop body keeps the instruction cache warm
         const int dz = pair / G::K, dx = pair % G::K;
         const float4 *src = reinterpret_cast<const float4 *>(base + (dz * G::PX + dx) * G::PYS);
         const float4 a0 = src[0], a1 = src[1], a2 = src[2];

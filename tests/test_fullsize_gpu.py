@@ -55,3 +55,46 @@ def test_fullsize_linearity_and_constant(big):
     out = G.apr_convolve(lay, c, tree, st, k)
     torch.cuda.synchronize()
     assert torch.max(torch.abs(out - 3.0)).item() <= 3.0 * 1e-5
+
+
+def test_fullsize_backward_identities(big):
+    """At full size: the stencil gradient and the particle gradient satisfy the identities of a
+    linear map, sum_l w_l . dL/dw_l = <g, out> = <x, dL/dx>, and are finite."""
+    apr, lay, _ = big
+    k = 5
+    st = torch.as_tensor(G.apr_restrict_stencil(S.gaussian_stencil(5, 1.5).astype(np.float32), apr.l_max, apr.l_min), device="cuda")
+    x = torch.as_tensor(apr.values, device="cuda")
+    g = torch.as_tensor(np.random.default_rng(3).normal(size=apr.n_particles).astype(np.float32), device="cuda")
+    tree = G.apr_tree_restrict(lay, x)
+    out = G.apr_convolve(lay, x, tree, st, k)
+    gp, gw = G.apr_convolve_backward(lay, x, tree, st, k, g)
+    torch.cuda.synchronize()
+    lay.sync_status()
+    gw64, gp64 = gw.double().cpu().numpy(), gp.double().cpu().numpy()
+    assert np.all(np.isfinite(gw64)) and np.all(np.isfinite(gp64))
+    o64, g64, x64 = out.double().cpu().numpy(), g.double().cpu().numpy(), x.double().cpu().numpy()
+    ref = float(np.dot(g64, o64))
+    scale = float(np.dot(np.abs(g64), np.abs(o64)))
+    assert abs(float(np.sum(st.double().cpu().numpy() * gw64)) - ref) <= 1e-5 * scale
+    assert abs(float(np.dot(x64, gp64)) - ref) <= 1e-5 * scale
+
+
+def test_fullsize_sampled_backward_parity(big):
+    """Gradients of a sampled set of outputs (dL/dout zero elsewhere) vs the oracle at full size."""
+    apr, lay, o = big
+    k = 5
+    st_h = G.apr_restrict_stencil(S.gaussian_stencil(5, 1.5).astype(np.float32), apr.l_max, apr.l_min)
+    st = torch.as_tensor(st_h, device="cuda")
+    x = torch.as_tensor(apr.values, device="cuda")
+    rng = np.random.default_rng(4)
+    sample = np.sort(rng.choice(apr.n_particles, 20000, replace=False))
+    g_full = np.zeros(apr.n_particles, np.float32)
+    g_full[sample] = rng.normal(size=sample.size).astype(np.float32)
+    tree = G.apr_tree_restrict(lay, x)
+    gp, gw = G.apr_convolve_backward(lay, x, tree, st, k, torch.as_tensor(g_full, device="cuda"))
+    torch.cuda.synchronize()
+    ref_gp, ref_gw = o.conv_backward(st_h.astype(np.float64), k, g_full.astype(np.float64), sample=sample)
+    got_gw = gw.double().cpu().numpy()
+    assert np.max(np.abs(got_gw - ref_gw.reshape(got_gw.shape))) <= 1e-5 * np.max(np.abs(ref_gw))
+    got_gp = gp.double().cpu().numpy()
+    assert np.max(np.abs(got_gp - ref_gp[:, 0])) <= 1e-5 * np.max(np.abs(ref_gp))
