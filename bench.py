@@ -118,6 +118,30 @@ def recorded_traffic(kernel):
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
+def make_replayers(fns, use_graph):
+    """The step's parts as CUDA graphs (one graph per part, replayed on the current stream), so the
+    timed region has no host launch gaps; the plain callables when use_graph is false. Each part
+    has run eagerly before (allocations, kernel attributes)."""
+    if not use_graph:
+        return list(fns)
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for f in fns:
+            f()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    out = []
+    for f in fns:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            f()
+        out.append(g.replay)
+    torch.cuda.synchronize()
+    return out
+
+
 def max_over_ranks(x: float, device=None) -> float:
     """Max of a per-rank float over the process group (the step time every rank reports is the
     slowest rank's); identity without a process group."""
@@ -170,25 +194,23 @@ def run_ours(args, rank, world):
 
     gtree = torch.empty(lay.n_tree, device=dev)
 
+    # tree restriction | convolution | convolution adjoint | tree adjoint | stencil gradient
+    parts_fns = [lambda: G.apr_tree_restrict(lay, vals, tree),
+                 lambda: G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out),
+                 lambda: G.apr_convolve_adjoint(lay, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_tree=gtree),
+                 lambda: G.apr_tree_restrict_adjoint(lay, gtree, gp),
+                 lambda: G.apr_convolve_stencil_grad(lay, vals, tree, K, gout, G.APR_BC_REFLECT, grad_stencils=gw)]
+    for f in parts_fns:
+        f()
+    run_part = make_replayers(parts_fns, not args.no_graph)
+
     def step(e=None):
-        # tree restriction | convolution | convolution adjoint | tree adjoint | stencil gradient
         if e is not None:
             e[0].record(stream)
-        G.apr_tree_restrict(lay, vals, tree)
-        if e is not None:
-            e[1].record(stream)
-        G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out)
-        if e is not None:
-            e[2].record(stream)
-        G.apr_convolve_adjoint(lay, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_tree=gtree)
-        if e is not None:
-            e[3].record(stream)
-        G.apr_tree_restrict_adjoint(lay, gtree, gp)
-        if e is not None:
-            e[4].record(stream)
-        G.apr_convolve_stencil_grad(lay, vals, tree, K, gout, G.APR_BC_REFLECT, grad_stencils=gw)
-        if e is not None:
-            e[5].record(stream)
+        for j, f in enumerate(run_part):
+            f()
+            if e is not None:
+                e[j + 1].record(stream)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     clk = ClockSampler(dev.index).__enter__()
@@ -223,15 +245,13 @@ def run_ours(args, rank, world):
     h_out = torch.empty(Np).pin_memory()
     h_gp = torch.empty(Np).pin_memory()
     h_gw = torch.empty_like(gw, device="cpu").pin_memory()
-    d_vals = torch.empty_like(vals)
-    d_gout = torch.empty_like(gout)
 
     def e2e_step():
-        d_vals.copy_(h_vals, non_blocking=True)
-        d_gout.copy_(h_gout, non_blocking=True)
-        G.apr_tree_restrict(lay, d_vals, tree)
-        G.apr_convolve(lay, d_vals, tree, st, K, G.APR_BC_REFLECT, out)
-        G.apr_convolve_backward(lay, d_vals, tree, st, K, d_gout, G.APR_BC_REFLECT, grad_particles=gp, grad_stencils=gw)
+        # the step's inputs land in the buffers the (captured) step reads
+        vals.copy_(h_vals, non_blocking=True)
+        gout.copy_(h_gout, non_blocking=True)
+        for f in run_part:
+            f()
         h_out.copy_(out, non_blocking=True)
         h_gp.copy_(gp, non_blocking=True)
         h_gw.copy_(gw, non_blocking=True)
@@ -288,6 +308,7 @@ def run_ours(args, rank, world):
                    "computational_ratio": round(float(np.prod(apr.dims)) / Np, 2),
                    "step": "tree restrict + convolve + convolve_backward (data + stencil grads)",
                    "l2": "flushed before every step (512 MB write, outside the step events)",
+                   "launch": "CUDA graphs (one per part)" if not args.no_graph else "eager",
                    "parallelism": f"replicas x{world}"},
         "pixel_equiv_GBps": round(world * pix_bytes / (step_ms * 1e-3) / 1e9, 2),
         "forward_pipeline": {"ms": round(fwd_ms, 5),
@@ -370,22 +391,22 @@ def run_mc(args, rank, world, full=True):
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # BF16 tree | forward | data adjoint (+ tree push-down) | weight gradient
+    parts_fns = [lambda: G.apr_tree_restrict_bf16(lay, x, tree),
+                 lambda: G.apr_convolve_mc(lay, x, tree, w, G.APR_BC_REFLECT, out),
+                 lambda: G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_weights=False, grad_particles=gp),
+                 lambda: G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_particles=False, grad_weights=gw)]
+    for f in parts_fns:
+        f()
+    run_part = make_replayers(parts_fns, not args.no_graph)
+
     def step(e=None):
-        # BF16 tree | forward | data adjoint (+ tree push-down) | weight gradient
         if e is not None:
             e[0].record(stream)
-        G.apr_tree_restrict_bf16(lay, x, tree)
-        if e is not None:
-            e[1].record(stream)
-        G.apr_convolve_mc(lay, x, tree, w, G.APR_BC_REFLECT, out)
-        if e is not None:
-            e[2].record(stream)
-        G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_weights=False, grad_particles=gp)
-        if e is not None:
-            e[3].record(stream)
-        G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT, need_particles=False, grad_weights=gw)
-        if e is not None:
-            e[4].record(stream)
+        for j, f in enumerate(run_part):
+            f()
+            if e is not None:
+                e[j + 1].record(stream)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     clk = ClockSampler(dev.index).__enter__() if full else None
@@ -427,6 +448,7 @@ def run_mc(args, rank, world, full=True):
                    "model": None, "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
                    "step": "bf16 tree + convolve_mc + backward (data adjoint with tree push-down, weight gradient)",
                    "l2": "flushed before every step (512 MB write, outside the step events)",
+                   "launch": "CUDA graphs (one per part)" if not args.no_graph else "eager",
                    "parallelism": f"replicas x{world}"},
         "step_ms_parts": {n: round(t, 5) for n, t in zip(names, parts)},
         "roofline": {"kernel": {1: "mc_fwd_kernel (apr_convolve_mc)", 2: "mc_bwd_data_kernel (+ push-down)",
@@ -446,14 +468,12 @@ def run_mc(args, rank, world, full=True):
     h_x, h_g = x.cpu().pin_memory(), g.cpu().pin_memory()
     h_out, h_gp = torch.empty_like(out, device="cpu").pin_memory(), torch.empty_like(gp, device="cpu").pin_memory()
     h_gw = torch.empty_like(gw, device="cpu").pin_memory()
-    d_x, d_g = torch.empty_like(x), torch.empty_like(g)
 
     def e2e_step():
-        d_x.copy_(h_x, non_blocking=True)
-        d_g.copy_(h_g, non_blocking=True)
-        G.apr_tree_restrict_bf16(lay, d_x, tree)
-        G.apr_convolve_mc(lay, d_x, tree, w, G.APR_BC_REFLECT, out)
-        G.apr_convolve_mc_backward(lay, d_x, tree, w, d_g, G.APR_BC_REFLECT, grad_particles=gp, grad_weights=gw)
+        x.copy_(h_x, non_blocking=True)
+        g.copy_(h_g, non_blocking=True)
+        for f in run_part:
+            f()
         h_out.copy_(out, non_blocking=True)
         h_gp.copy_(gp, non_blocking=True)
         h_gw.copy_(gw, non_blocking=True)
@@ -536,10 +556,12 @@ def run_rl(args, rank, world, full=True):
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def rl():
         est.copy_(u)
         G.apr_richardson_lucy(lay, u, st, K, RL_ITERS, G.APR_BC_REFLECT, estimate=est)
 
+    rl()
+    step = make_replayers([rl], not args.no_graph)[0]
     clk = ClockSampler(dev.index).__enter__() if full else None
     for _ in range(args.warmup):
         flush.zero_()
@@ -592,6 +614,7 @@ def run_rl(args, rank, world, full=True):
         "config": {"workload": "blob APR 512^3 pixels: 20 Richardson-Lucy iterations, restricted 5^3 Gaussian PSF sigma=1.5 and its flip",
                    "model": None, "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
                    "step": "20 iterations from i_0 = u (per iteration: 2 tree restrictions, 2 convolutions with fused divide / multiply)",
+                   "launch": "one CUDA graph for the 20 iterations" if not args.no_graph else "eager",
                    "l2": "flushed before every step (512 MB write, outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "pixel_equiv_GBps_per_conv": round(pix * 4 * 2 * RL_ITERS / (step_ms * 1e-3) / 1e9, 2),
@@ -605,15 +628,13 @@ def run_rl(args, rank, world, full=True):
     if not full:
         return rec
     h_u, h_est = torch.as_tensor(apr.values).pin_memory(), torch.empty(Np).pin_memory()
-    d_u = torch.empty_like(u)
     e2e = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        d_u.copy_(h_u, non_blocking=True)
-        est.copy_(d_u)
-        G.apr_richardson_lucy(lay, d_u, st, K, RL_ITERS, G.APR_BC_REFLECT, estimate=est)
+        u.copy_(h_u, non_blocking=True)
+        step()
         h_est.copy_(est, non_blocking=True)
         b.record(stream)
         b.synchronize()
@@ -828,6 +849,7 @@ def main():
                     help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step; "
                          "blob512_rl: 20 Richardson-Lucy iterations")
     ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -3,7 +3,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "apr_internal.h"
 
@@ -52,6 +54,20 @@ bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
 
 namespace aprk {
 void set_last_message(const char *msg) { snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg); }
+
+cudaError_t set_max_dynamic_smem(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == fn && d.second == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) done.emplace_back(fn, dev);
+    return e;
+}
 
 apr_status_t cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return APR_OK;

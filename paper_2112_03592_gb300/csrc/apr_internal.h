@@ -79,6 +79,10 @@ constexpr unsigned ERR_TIMEOUT = 2u;       // a bounded wait (tensor-core comple
 // Map a CUDA error to a status code, recording its message for apr_last_error_message.
 apr_status_t cuda_status(cudaError_t e);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per (kernel,
+// device): later calls make no CUDA call, so launches can be captured into CUDA graphs.
+cudaError_t set_max_dynamic_smem(const void *fn, size_t bytes);
+
 inline int64_t level_cells(int64_t D, int l_max, int l) {
     int64_t s = int64_t(1) << (l_max - l);
     return (D + s - 1) / s;

@@ -892,9 +892,7 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
 static_assert(4 * (sizeof(PatchSmem<2>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
 static_assert(3 * (sizeof(BwdSmem<2>) + 1024) <= 228 * 1024, "data adjoint: three blocks per SM");
 
-cudaError_t set_smem(const void *fn, size_t bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-}
+cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
 
 template <int R>
 cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,

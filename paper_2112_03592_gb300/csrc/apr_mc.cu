@@ -978,9 +978,7 @@ static_assert(offsetof(BwdSmem, g1) % 16 == 0 && offsetof(FeatStage, p1) % 16 ==
 static_assert(offsetof(FwdSmem, bar) % 8 == 0 && offsetof(BwdSmem, bar) % 8 == 0 && offsetof(WgradSmem, bar) % 8 == 0,
               "mbarrier alignment");
 
-cudaError_t set_smem(const void *fn, size_t bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-}
+cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
 
 int wgrad_ctas(int n_units) {
     static int sms = 0;
