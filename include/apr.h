@@ -130,6 +130,14 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
 apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                           int32_t k, int32_t bc, float *out, apr_stream_t stream);
 
+/* Gradient magnitude on the APR (Sec. 4.3): out[p] = sqrt(sum_{a=0..2} (w_a (*) u)_p^2), where (*) is
+ * apr_convolve with the a-th of three per-level stencil stacks (e.g. the Sobel derivative filters
+ * along z, x and y, rescaled per level by Eq. adapt_grad with apr_rescale_stencil). The patch is
+ * staged once for the three filters.
+ *   stencils: device [3][(l_max-l_min+1)][k^3] float32; other arguments as apr_convolve. */
+apr_status_t apr_gradient_magnitude(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                    int32_t k, int32_t bc, float *out, apr_stream_t stream);
+
 /* Scratch bytes apr_convolve_backward needs for stencil size k. */
 size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k);
 

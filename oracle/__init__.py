@@ -272,3 +272,15 @@ def richardson_lucy(apr, observed, stencils, k, n_iter, bc=BC_REFLECT, estimate=
         o.set_values(ratio)
         i = i * o.conv(W_flip, k, bc)[:, 0]
     return i
+
+
+def gradient_magnitude(apr, values, stencils3, k, bc=BC_REFLECT, sample=None) -> np.ndarray:
+    """sqrt(sum_a (w_a (*) u)^2) per particle for three stencil stacks [3][L][k^3] (Sec. 4.3: gradient
+    estimation with Sobel filters, level-rescaled by Eq. adapt_grad). FP64."""
+    W = np.asarray(stencils3, np.float64).reshape(3, apr.n_levels, k ** 3)
+    o = Oracle(apr, values)
+    acc = None
+    for a in range(3):
+        c = o.conv(W[a], k, bc, sample=sample)[:, 0]
+        acc = c * c if acc is None else acc + c * c
+    return np.sqrt(acc)

@@ -18,6 +18,7 @@ Functions with the C names:
     apr_convolve_mc(layout, particles, tree, weights[, bc, out])  -> out       (16 -> 16 channels, k = 3)
     apr_convolve_mc_backward(layout, particles, tree, weights, grad_out[, bc])
                                                                   -> (grad_particles, grad_weights)
+    apr_gradient_magnitude(layout, particles, tree, stencils3, k) -> |grad|    (Sec. 4.3, with sobel_stencils)
     apr_restrict_stencil(w, l_max, l_min)                         -> [L][k^3]  (Eq. restrict_stenc)
     apr_rescale_stencil(w, l_max, l_min)                          -> [L][k^3]  (Eq. adapt_grad)
 plus ``AprConv`` (torch.autograd.Function): particles, stencils -> per-particle outputs.
@@ -34,7 +35,7 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
-           "apr_convolve_stencil_grad", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
+           "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
            "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
            "APR_SUBDOMAIN"]
@@ -171,6 +172,36 @@ def apr_convolve(layout: AprLayout, particles, tree, stencils, k, bc=APR_BC_REFL
         layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
         ctypes.c_void_p(stencils.data_ptr()), int(k), int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def apr_gradient_magnitude(layout: AprLayout, particles, tree, stencils3, k, bc=APR_BC_REFLECT, out=None, stream=None):
+    """sqrt of the sum of squares of three convolutions (stencils3 [3][L][k^3], e.g. level-rescaled
+    Sobel filters along z, x, y; Sec. 4.3)."""
+    import torch
+    _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
+    _dev_ptr(tree, "tree", layout.n_tree, torch.float32)
+    _dev_ptr(stencils3, "stencils3", 3 * layout.n_levels * k ** 3, torch.float32)
+    if out is None:
+        out = torch.empty(layout.n_particles, dtype=torch.float32, device=particles.device)
+    _dev_ptr(out, "out", layout.n_particles, torch.float32)
+    _abi.check("apr_gradient_magnitude", layout._lib.apr_gradient_magnitude(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
+        ctypes.c_void_p(stencils3.data_ptr()), int(k), int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def sobel_stencils(k=3):
+    """Sobel derivative stencils [3][k][k][k] along z, x, y (central difference along the axis,
+    [1, 2, 1] smoothing across it, normalised so a linear ramp of slope 1 gives 1). Host, float32."""
+    if k != 3:
+        raise ValueError("Sobel stencils are 3x3x3")
+    d = np.array([-0.5, 0.0, 0.5])
+    sm = np.array([0.25, 0.5, 0.25])
+    out = np.zeros((3, 3, 3, 3))
+    out[0] = np.einsum("i,j,k->ijk", d, sm, sm)
+    out[1] = np.einsum("i,j,k->ijk", sm, d, sm)
+    out[2] = np.einsum("i,j,k->ijk", sm, sm, d)
+    return out.astype(np.float32)
 
 
 def apr_convolve_backward(layout: AprLayout, particles, tree, stencils, k, grad_out, bc=APR_BC_REFLECT,

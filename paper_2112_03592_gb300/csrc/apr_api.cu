@@ -15,6 +15,8 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
                             int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr);
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
                                  cudaStream_t s);
+cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
+                           const float *st, int bc, float *out, cudaStream_t s);
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
                             const float *gout, float *gp, float *gt, cudaStream_t s);
 cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int n, const float *vals,
@@ -243,6 +245,16 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
     if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
     const int n = int(h->X.fwd_items.size());
     return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
+}
+
+apr_status_t apr_gradient_magnitude(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                    int32_t k, int32_t bc, float *out, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    const int n = int(h->X.fwd_items.size());
+    return cuda_status(launch_gradmag(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
 }
 
 size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k) {

@@ -383,6 +383,43 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
     });
 }
 
+// Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
+// out[p] = sqrt(sum_a (w_a (*) u)_p^2) for three stencil stacks w_a (a = z, x, y) on one staged
+// patch. The three passes give each window to the same thread, which keeps the running sum of
+// squares in out[p].
+template <int R>
+__global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                             const float *__restrict__ vals,
+                                                             const float *__restrict__ tree,
+                                                             const float *__restrict__ stencils, int bc,
+                                                             float *__restrict__ out) {
+    using G = Geo<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
+    const Item it = items[blockIdx.x];
+    const int n_levels = L.l_max - L.l_min + 1;
+    load_taps<R>(stencils, it.l - L.l_min, false, S.w8);
+    stage_patch<R>(L, it, vals, tree, bc, S);
+    for (int a = 0; a < 3; ++a) {
+        if (a > 0) {
+            block_sync();
+            load_taps<R>(stencils + size_t(a) * n_levels * G::K3, it.l - L.l_min, false, S.w8);
+            block_sync();
+        }
+        windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
+            const unsigned m = S.wmask[w];
+            const int first = S.wfirst[w];
+#pragma unroll
+            for (int j = 0; j < WIN; ++j)
+                if ((m >> j) & 1u) {
+                    const int p = first + __popc(m & ((1u << j) - 1u));
+                    const float sq = acc[j] * acc[j];
+                    out[p] = a == 0 ? sq : (a == 1 ? out[p] + sq : sqrtf(out[p] + sq));
+                }
+        });
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Backward, stencil part: per work item, partial[e][item] = sum over its targets p of g_p *
 // u_l(p + e) (fixed order); stencil_grad_reduce_kernel then sums the items of every level.
@@ -933,6 +970,22 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
     const Epilogue epi{epi_mode, flip, aux};
     return k == 3 ? launch_conv_fwd_t<1>(L, items, n, vals, tree, st, bc, out, epi, s)
                   : launch_conv_fwd_t<2>(L, items, n, vals, tree, st, bc, out, epi, s);
+}
+
+template <int R>
+cudaError_t launch_gradmag_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
+                             const float *st, int bc, float *out, cudaStream_t s) {
+    const size_t sm = sizeof(PatchSmem<R>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_gradmag_kernel<R>), sm);
+    if (e != cudaSuccess) return e;
+    if (n > 0) conv_gradmag_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
+                           const float *st, int bc, float *out, cudaStream_t s) {
+    return k == 3 ? launch_gradmag_t<1>(L, items, n, vals, tree, st, bc, out, s)
+                  : launch_gradmag_t<2>(L, items, n, vals, tree, st, bc, out, s);
 }
 
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,

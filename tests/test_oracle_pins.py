@@ -321,3 +321,37 @@ def test_rl_constant_image_is_a_fixed_point():
     W = oracle.restrict_stencil(w, apr.l_max, apr.l_min).reshape(apr.n_levels, -1)
     got = oracle.richardson_lucy(apr, u, W, 5, 4)
     np.testing.assert_allclose(got, u, rtol=1e-12)
+
+
+# ---- gradient magnitude with level-rescaled Sobel stencils (Sec. 4.3, Eq. adapt_grad)
+def _sobel():
+    d, sm = np.array([-0.5, 0.0, 0.5]), np.array([0.25, 0.5, 0.25])
+    return np.stack([np.einsum("i,j,k->ijk", d, sm, sm), np.einsum("i,j,k->ijk", sm, d, sm),
+                     np.einsum("i,j,k->ijk", sm, sm, d)])
+
+
+@pytest.mark.parametrize("level", [None, 3])
+def test_gradient_magnitude_of_a_linear_ramp(level):
+    """A linear ramp has the same gradient everywhere: at pixels (all-finest APR) the Sobel estimate
+    is exact, and on a uniform coarse level the cell means are the ramp at the cell centres, so the
+    level-rescaled stencil (w / 2^(l_max - l)) recovers the pixel-unit gradient."""
+    dims = (16, 16, 32)
+    lmax = S.l_max_for(dims)
+    lev = lmax if level is None else level
+    apr = S.uniform_level_apr(dims, lev, l_min=min(lev, 2))
+    l, z, x, y = apr.particle_coords()
+    s = 1 << (lmax - lev)
+    alpha, beta, gamma = 0.7, -1.3, 0.4
+    # cell means of f = alpha*Z + beta*X + gamma*Y over the pixels of each cell (centres)
+    cz, cx, cy = (z + 0.5) * s - 0.5, (x + 0.5) * s - 0.5, (y + 0.5) * s - 0.5
+    vals = 5.0 + alpha * cz + beta * cx + gamma * cy
+    sob = _sobel().reshape(3, -1)
+    W = np.stack([np.stack([sob[a] * 2.0 ** -(lmax - lv) for lv in range(apr.l_min, apr.l_max + 1)]) for a in range(3)])
+    got = oracle.gradient_magnitude(apr, vals, W, 3)
+    dz, dx, dy = apr.level_dims(lev)
+    inner = (z >= 1) & (z < dz - 1) & (x >= 1) & (x < dx - 1) & (y >= 1) & (y < dy - 1)
+    np.testing.assert_allclose(got[inner], np.sqrt(alpha ** 2 + beta ** 2 + gamma ** 2), rtol=1e-12)
+    if level is not None:   # without the rescaling the coarse estimate is s times too large
+        W1 = np.stack([np.repeat(sob[a][None], apr.n_levels, 0) for a in range(3)])
+        g1 = oracle.gradient_magnitude(apr, vals, W1, 3)
+        np.testing.assert_allclose(g1[inner], s * np.sqrt(alpha ** 2 + beta ** 2 + gamma ** 2), rtol=1e-12)
