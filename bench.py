@@ -102,15 +102,26 @@ class ClockSampler:
                 else "warm-up and timed region (timed region shorter than the 50 ms sampling period)"}
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel source is
-    unchanged since that capture (sha1 prefix match); else None."""
+TRAFFIC_SOURCES = ["paper_2112_03592_gb300/csrc/apr_kernels.cu", "paper_2112_03592_gb300/csrc/apr_device.cuh"]
+
+
+def kernel_source_hash():
+    """sha1 prefix of the sources the single-channel kernels are built from."""
     import hashlib
+    h = hashlib.sha1()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel sources are
+    unchanged since that capture (sha1 prefix match); else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha1(f.read()).hexdigest()[:12]
+        sha = kernel_source_hash()
     except (OSError, KeyError, ValueError):
         return None
     if sha != rec.get("sha1_prefix"):
@@ -166,6 +177,40 @@ def algorithmic_bytes(apr, lay, k):
     conv = Np * 10 + Nt * 6 + (Rp + Rt) * 4 + st
     restrict = Np * 6 + Nt * 10 + (Rp + Rt) * 4
     return conv, restrict
+
+
+def dense_pixel_conv(dims, w, steps, flush, stream):
+    """Time a dense FP32 k^3 correlation of a pixel image of `dims` (cuDNN through torch conv3d,
+    TF32 disabled, zero padding); returns ms and pixel-equivalent GB/s, or None if it does not fit."""
+    import torch
+    import torch.nn.functional as F
+    prev = torch.backends.cudnn.allow_tf32
+    torch.backends.cudnn.allow_tf32 = False
+    try:
+        img = torch.rand((1, 1) + tuple(int(d) for d in dims), device=stream.device)
+        ker = torch.as_tensor(w, device=stream.device).reshape((1, 1) + w.shape)
+        pad = w.shape[0] // 2
+        out = F.conv3d(img, ker, padding=pad)
+        ts = []
+        for _ in range(max(3, steps)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = F.conv3d(img, ker, padding=pad)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts[1:])
+        nbytes = float(img.numel()) * 4
+        del img, out
+        torch.cuda.empty_cache()
+        return {"ms": round(ms, 4), "pixel_GBps": round(nbytes / (ms * 1e-3) / 1e9, 2),
+                "library": "cuDNN via torch.nn.functional.conv3d, FP32 (TF32 off), zero padding",
+                "note": "context for the pixel-equivalent metric; not part of the APR path"}
+    except RuntimeError as e:
+        return {"unavailable": str(e).splitlines()[0][:200]}
+    finally:
+        torch.backends.cudnn.allow_tf32 = prev
 
 
 def run_ours(args, rank, world):
@@ -289,6 +334,12 @@ def run_ours(args, rank, world):
         gm_ms.append(a.elapsed_time(b))
     gm_ms = statistics.mean(gm_ms)
 
+    # context: a dense FP32 5^3 convolution of the same-size pixel image with cuDNN (torch conv3d,
+    # TF32 off), the stand-in for the paper's dense pixel baseline (same pixel-equivalent metric)
+    dense = None
+    if not args.no_dense and world == 1:
+        dense = dense_pixel_conv(apr.dims, w, args.steps, flush, stream)
+
     # forward-only pipeline (tree restriction + convolution), the paper's timed pipeline
     mean = lambda v: sum(v) / len(v)
     fwd_ms = mean(t_restrict) + mean(t_conv)
@@ -333,6 +384,7 @@ def run_ours(args, rank, world):
                              "Gparticles_per_s": round(Np / (fwd_ms * 1e-3) / 1e9, 3),
                              "pixel_equiv_GBps": round(pix_bytes / (fwd_ms * 1e-3) / 1e9, 2),
                              "paper_context": "up to 1 TB/s pixel-equivalent on one RTX 2080 Max-Q (paper abstract)"},
+        "dense_pixel_conv": dense,
         "gradient_magnitude": {"ms": round(gm_ms, 5), "Gparticles_per_s": round(Np / (gm_ms * 1e-3) / 1e9, 3),
                                "filters": "3^3 Sobel along z, x, y, rescaled per level (Eq. adapt_grad)",
                                "hbm_frac_conv_bytes": round(algorithmic_bytes(apr, lay, 3)[0] / (gm_ms * 1e-3) / 1e9 / hbm, 4)},
@@ -871,6 +923,7 @@ def main():
                          "blob512_rl: 20 Richardson-Lucy iterations")
     ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense pixel convolution context timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
