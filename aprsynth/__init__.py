@@ -273,8 +273,15 @@ def _sum_pyramid(lam: np.ndarray, l_min, l_max):
     return sums, cnts
 
 
+class _Mean:
+    """Stands in for the noise generator: returns the mean itself (noise-free particle values)."""
+    @staticmethod
+    def poisson(v):
+        return v
+
+
 def apr_from_blobs(img: BlobImage, E=0.1, sigma_floor=10.0, l_min=2, seed_noise=None,
-                   name="", sigma_scale=1.0) -> AprInput:
+                   name="", sigma_scale=1.0, clean=False) -> AprInput:
     lam, amp = _blob_fields(img)
     l_max = l_max_for(img.dims)
     lreq = required_levels(lam, amp, E, sigma_floor, l_min, l_max, sigma_scale)
@@ -286,7 +293,7 @@ def apr_from_blobs(img: BlobImage, E=0.1, sigma_floor=10.0, l_min=2, seed_noise=
             return sums[l][z, x, y].astype(np.float64), 1.0
         return sums[l][z, x, y], cnts[l][z, x, y].astype(np.float64)
 
-    rng = np.random.default_rng(seed_noise if seed_noise is not None else 12345)
+    rng = _Mean() if clean else np.random.default_rng(seed_noise if seed_noise is not None else 12345)
     return apr_from_levels(lreq, l_min, l_max, lam_sum, rng, img.dims, name)
 
 
@@ -305,11 +312,7 @@ def uniform_level_apr(dims, level, values_fn=None, seed=0, l_min=None) -> AprInp
     def vals(l, z, x, y):
         return u[z, x, y], 1.0
 
-    class _Det:  # deterministic "poisson": return the mean itself
-        @staticmethod
-        def poisson(v):
-            return v
-    return apr_from_levels(lreq, l_min, l_max, vals, _Det(), dims, f"uniform{level}")
+    return apr_from_levels(lreq, l_min, l_max, vals, _Mean(), dims, f"uniform{level}")
 
 
 def random_balanced_apr(dims, l_min, seed=0, p_fine=0.04, values="uniform", name="") -> AprInput:
@@ -414,11 +417,12 @@ def _cache_dir():
     return pathlib.Path(os.environ.get("TMPDIR", "/tmp")) / "aprsynth_cache"
 
 
-def make_config(name: str, use_cache=True, **overrides) -> AprInput:
-    """Build (or load from the on-disk cache) the APR of a named workload."""
+def make_config(name: str, use_cache=True, clean=False, **overrides) -> AprInput:
+    """Build (or load from the on-disk cache) the APR of a named workload. clean=True: the same
+    particles with noise-free values (the mean intensity over each particle's pixels)."""
     cfg = dict(CONFIGS[name])
     cfg.update(overrides)
-    key = hashlib.sha1(repr(sorted(cfg.items())).encode()).hexdigest()[:12]
+    key = hashlib.sha1((repr(sorted(cfg.items())) + ("clean" if clean else "")).encode()).hexdigest()[:12]
     path = _cache_dir() / f"{name}_{key}.npz"
     if use_cache and path.exists():
         z = np.load(path)
@@ -427,7 +431,7 @@ def make_config(name: str, use_cache=True, **overrides) -> AprInput:
     img = blob_image(cfg["dims"], cfg["n_blobs"], cfg["sigma_range"], seed=cfg["seed"])
     apr = apr_from_blobs(img, E=cfg["E"], sigma_floor=cfg["sigma_floor"], l_min=cfg["l_min"],
                          seed_noise=cfg["seed"] + 1000, name=name,
-                         sigma_scale=cfg.get("sigma_scale", 1.0))
+                         sigma_scale=cfg.get("sigma_scale", 1.0), clean=clean)
     if use_cache:
         try:
             path.parent.mkdir(parents=True, exist_ok=True)

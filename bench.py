@@ -754,6 +754,110 @@ def rl_cpu_baseline(apr, st, budget_s=20.0):
                       f"convolutions of one iteration for {n2} random output particles ({t_s:.2f} s), FP64, 1 thread"}
 
 
+def pixels_per_particle(apr):
+    """Pixels each particle covers (cell edge 2^(l_max - l) per axis, clipped at the image edge)."""
+    import numpy as np
+    l, z, x, y = apr.particle_coords()
+    s = (1 << (apr.l_max - l)).astype(np.int64)
+    ext = [np.minimum(s, d - c * s) for c, d in zip((z, x, y), apr.dims)]
+    return (ext[0] * ext[1] * ext[2]).astype(np.float64)
+
+
+def run_surrogate(args, rank, world):
+    """APR CNN surrogate of 20 Richardson-Lucy iterations: trained on seeded 256^3 blob APRs, evaluated
+    on the 1024x1024x512 blob APR against the plain 20-iteration filter (time and PSNR)."""
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+    from paper_2112_03592_gb300.surrogate import AprCnn, psnr, train
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
+    flags = G.APR_VALIDATE | G.APR_REQUIRE_BALANCE
+    t0 = time.perf_counter()
+    samples = []
+    for i in range(args.sur_train):
+        a = S.make_config("blob256", seed=100 + i)
+        lay = G.AprLayout.from_apr(a, flags)
+        x = torch.as_tensor(a.values, device=dev)
+        st = torch.as_tensor(G.apr_restrict_stencil(w, a.l_max, a.l_min), device=dev)
+        t = G.apr_richardson_lucy(lay, x, st, K, RL_ITERS)
+        samples.append((lay, x, t, float(1.0 / float(x.mean()))))
+    t_data = time.perf_counter() - t0
+    model = AprCnn(4, n_dist=8, seed=0)
+    t0 = time.perf_counter()
+    hist = train(model, samples, args.sur_steps, lr=args.sur_lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    apr = S.make_config(WORKLOAD)
+    clean = S.make_config(WORKLOAD, clean=True)
+    lay = G.AprLayout.from_apr(apr, flags)
+    Np = apr.n_particles
+    x = torch.as_tensor(apr.values, device=dev)
+    st = torch.as_tensor(G.apr_restrict_stencil(w, apr.l_max, apr.l_min), device=dev)
+    scale = float(1.0 / float(x.mean()))
+    Wb = model.stack_weights(lay)
+    est = torch.empty_like(x)
+    holder = [None]
+
+    def rl():
+        est.copy_(x)
+        G.apr_richardson_lucy(lay, x, st, K, RL_ITERS, estimate=est)
+
+    def cnn():
+        holder[0] = model.forward(lay, x, scale, weights=Wb)
+
+    rl()
+    cnn()
+    run_rl_, run_cnn = make_replayers([rl, cnn], not args.no_graph)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(f):
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f()
+            b.record(stream)
+            b.synchronize()
+            if i >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    rl_ms = timed(run_rl_)
+    cnn_ms = timed(run_cnn)
+    y = holder[0]
+    wts = torch.as_tensor(pixels_per_particle(apr), device=dev)
+    ref_clean = torch.as_tensor(clean.values, device=dev)
+    rec = {
+        "metric": "surrogate vs iterative at PSNR",
+        "value": round(rl_ms / cnn_ms, 3), "unit": "x (time of 20 RL iterations / time of CNN inference)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(cnn_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (FP32 accumulation)",
+        "data": "synthetic (seeded blob images with Poisson noise -> APR); noise-free particle means as ground truth",
+        "config": {"workload": "4-layer APR CNN (16 ch bf16, 3^3 per-level weights, ReLU, residual) vs 20 Richardson-Lucy "
+                               "iterations (restricted 5^3 Gaussian PSF sigma=1.5), on the 1024x1024x512 blob APR",
+                   "n_particles": Np, "train": f"{args.sur_train} seeded 256^3 blob APRs, {args.sur_steps} Adam steps, "
+                                               f"lr {args.sur_lr}", "launch": "CUDA graphs" if not args.no_graph else "eager"},
+        "rl20_ms": round(rl_ms, 4), "cnn_ms": round(cnn_ms, 4),
+        "cnn_Gparticles_per_s": round(Np / (cnn_ms * 1e-3) / 1e9, 4),
+        "psnr_db": {"cnn_vs_rl20": round(psnr(y, est, wts), 3), "input_vs_rl20": round(psnr(x, est, wts), 3),
+                    "rl20_vs_clean": round(psnr(est, ref_clean, wts), 3), "cnn_vs_clean": round(psnr(y, ref_clean, wts), 3),
+                    "input_vs_clean": round(psnr(x, ref_clean, wts), 3),
+                    "weighting": "pixels covered by each particle (pixel-equivalent)"},
+        "training": {"loss_first": round(float(np.mean(hist[:10])), 6), "loss_last": round(float(np.mean(hist[-10:])), 6),
+                     "data_s": round(t_data, 1), "train_s": round(t_train, 1)},
+        "gpu_launches": None,
+    }
+    return rec
+
+
 def cpu_baseline(apr, st, gout, budget_s=20.0, sample_n=None):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the same step: the full
     tree fill, then forward and backward for a random sample of output particles. The tree fill
@@ -918,7 +1022,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=3000)
-    ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc", "blob512_rl"],
+    ap.add_argument("--sur-train", type=int, default=8, help="surrogate: training APRs")
+    ap.add_argument("--sur-steps", type=int, default=400, help="surrogate: Adam steps")
+    ap.add_argument("--sur-lr", type=float, default=2e-3, help="surrogate: learning rate")
+    ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc", "blob512_rl", "surrogate"],
                     help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step; "
                          "blob512_rl: 20 Richardson-Lucy iterations")
     ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
@@ -943,6 +1050,8 @@ def main():
         rec = run_mc(args, rank, world, full=True)
     elif args.workload == "blob512_rl":
         rec = run_rl(args, rank, world, full=True)
+    elif args.workload == "surrogate":
+        rec = run_surrogate(args, rank, world)
     else:
         rec = run_ours(args, rank, world)
         if not args.no_mc:

@@ -259,6 +259,28 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
                                       const uint16_t *grad_out, float *grad_particles, float *grad_weights,
                                       void *workspace, size_t workspace_bytes, apr_stream_t stream);
 
+/* ---- Element-wise layers of an APR CNN (Sec. 6: learned per-level filters) around apr_convolve_mc,
+ * on per-particle vectors of 16 channels (channels-last [n][16]). They need no handle; n is the
+ * number of particles (n_values the number of channel values). All return APR_ERR_INVALID_ARG for
+ * negative sizes or missing buffers. bf16 results are rounded to nearest, ties to even. */
+
+/* Input embedding: out[p][0] = bf16(scale * x[p]) (product rounded to float first), out[p][1..15] = 0. */
+apr_status_t apr_mc_embed_bf16(const float *x, int64_t n, float scale, uint16_t *out, apr_stream_t stream);
+
+/* Hidden activation: out[i] = bf16(max(in[i], 0)). */
+apr_status_t apr_mc_relu_bf16(const float *in, int64_t n_values, uint16_t *out, apr_stream_t stream);
+
+/* Its transpose (the bf16 rounding taken as the identity): grad_pre[i] = bf16(pre[i] > 0 ? grad_post[i] : 0). */
+apr_status_t apr_mc_relu_backward_bf16(const float *pre, const float *grad_post, int64_t n_values, uint16_t *grad_pre,
+                                       apr_stream_t stream);
+
+/* Residual read-out of the last layer: y[p] = x[p] + inv_scale * conv[p][0] (float32). */
+apr_status_t apr_mc_readout(const float *conv, const float *x, int64_t n, float inv_scale, float *y, apr_stream_t stream);
+
+/* Its transpose w.r.t. conv: grad_conv[p][0] = bf16(inv_scale * grad_y[p]), grad_conv[p][1..15] = 0. */
+apr_status_t apr_mc_readout_backward_bf16(const float *grad_y, int64_t n, float inv_scale, uint16_t *grad_conv,
+                                          apr_stream_t stream);
+
 /* Restricted stencils (Eq. restrict_stenc, K_{w_l} = R_l K_w P_l with block-average R_l and
  * piecewise-constant P_l): out[l - l_min][e] = sum_d w[d] * prod_axes c_s(d_a, e_a), where
  * c_s(d, e) = (1/s) #{x in [0, s): floor((x + d) / s) = e} and s = 2^(l_max - l). Host memory in and

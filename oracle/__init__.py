@@ -284,3 +284,63 @@ def gradient_magnitude(apr, values, stencils3, k, bc=BC_REFLECT, sample=None) ->
         c = o.conv(W[a], k, bc, sample=sample)[:, 0]
         acc = c * c if acc is None else acc + c * c
     return np.sqrt(acc)
+
+
+def round_bf16_array(v) -> np.ndarray:
+    """Element-wise bfloat16 rounding (to float32 first, then nearest-even on the upper 16 bits)."""
+    f = np.asarray(v, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    finite = (u & 0x7F800000) != 0x7F800000
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    out = np.where(finite, r, u.astype(np.uint32)).astype(np.uint32).view(np.float32)
+    return out.astype(np.float64)
+
+
+def cnn_forward(apr, x, weights, scale) -> np.ndarray:
+    """APR CNN (Sec. 6 outlook: learned per-level filters) with 16 bfloat16 channels: h_0 = embed(x)
+    (channel 0 = bf16(float32(scale) * x), others 0); for every layer i, c_i = 16 -> 16 APR
+    convolution of h_i (Sec. 4.1, per-level 3^3 weights, tree of bf16 features as tree_bf16), and
+    h_{i+1} = bf16(max(c_i, 0)) between layers; the output is y = x + c_last[:, 0] / scale. The
+    convolutions are FP64 on the bf16 values; the bf16 rounding points are those of the layer."""
+    x = np.asarray(x, np.float64).reshape(-1)
+    sc = np.float32(scale)
+    h = np.zeros((x.size, 16))
+    h[:, 0] = round_bf16_array(np.float32(sc) * x.astype(np.float32))
+    c = None
+    for i, W in enumerate(weights):
+        o = Oracle(apr, h)
+        o.tree_bf16()
+        c = o.conv(np.asarray(W, np.float64), 3, C_out=16)
+        if i + 1 < len(weights):
+            h = round_bf16_array(np.maximum(c, 0.0))
+    return x + c[:, 0] / float(sc)
+
+
+def cnn_backward(apr, x, weights, scale, grad_y):
+    """Weight gradients of cnn_forward for dL/dy = grad_y, every bf16 rounding taken as the identity
+    (its derivative is not defined): the transposes of the read-out, of each 16 -> 16 convolution
+    (conv_backward, through the tree) and of ReLU (mask c > 0), from the last layer down. FP64."""
+    x = np.asarray(x, np.float64).reshape(-1)
+    sc = np.float32(scale)
+    h = np.zeros((x.size, 16))
+    h[:, 0] = round_bf16_array(np.float32(sc) * x.astype(np.float32))
+    hs, cs = [], []
+    for i, W in enumerate(weights):
+        o = Oracle(apr, h)
+        o.tree_bf16()
+        c = o.conv(np.asarray(W, np.float64), 3, C_out=16)
+        hs.append(h)
+        cs.append(c)
+        if i + 1 < len(weights):
+            h = round_bf16_array(np.maximum(c, 0.0))
+    g = np.zeros((x.size, 16))
+    g[:, 0] = np.asarray(grad_y, np.float64).reshape(-1) / float(sc)
+    grads = [None] * len(weights)
+    for i in reversed(range(len(weights))):
+        o = Oracle(apr, hs[i])
+        o.tree_bf16()
+        gp, gw = o.conv_backward(np.asarray(weights[i], np.float64), 3, g, C_out=16)
+        grads[i] = gw
+        if i > 0:
+            g = gp * (cs[i - 1] > 0)
+    return grads

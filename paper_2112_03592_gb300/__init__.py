@@ -36,7 +36,8 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
            "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
-           "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
+           "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
+           "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
            "APR_SUBDOMAIN"]
 
@@ -366,6 +367,71 @@ def apr_convolve_mc_backward(layout: AprLayout, particles, tree, weights, grad_o
         C, C, k, int(bc), ctypes.c_void_p(grad_out.data_ptr()), gp_ptr, gw_ptr,
         ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)))
     return (grad_particles if need_particles else None), (grad_weights if need_weights else None)
+
+
+# ---- element-wise layers of the APR CNN (16 channels)
+def apr_mc_embed_bf16(x, scale, out=None, stream=None):
+    import torch
+    n = int(x.numel())
+    _dev_ptr(x, "x", n, torch.float32)
+    if out is None:
+        out = torch.empty((n, MC_CHANNELS), dtype=torch.bfloat16, device=x.device)
+    _dev_ptr(out, "out", n * MC_CHANNELS, torch.bfloat16)
+    _abi.check("apr_mc_embed_bf16", _abi.load().apr_mc_embed_bf16(
+        ctypes.c_void_p(x.data_ptr()), n, float(scale), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_mc_relu_bf16(inp, out=None, stream=None):
+    import torch
+    n = int(inp.numel())
+    _dev_ptr(inp, "in", n, torch.float32)
+    if out is None:
+        out = torch.empty(inp.shape, dtype=torch.bfloat16, device=inp.device)
+    _dev_ptr(out, "out", n, torch.bfloat16)
+    _abi.check("apr_mc_relu_bf16", _abi.load().apr_mc_relu_bf16(
+        ctypes.c_void_p(inp.data_ptr()), n, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_mc_relu_backward_bf16(pre, grad_post, out=None, stream=None):
+    import torch
+    n = int(pre.numel())
+    _dev_ptr(pre, "pre", n, torch.float32)
+    _dev_ptr(grad_post, "grad_post", n, torch.float32)
+    if out is None:
+        out = torch.empty(pre.shape, dtype=torch.bfloat16, device=pre.device)
+    _dev_ptr(out, "grad_pre", n, torch.bfloat16)
+    _abi.check("apr_mc_relu_backward_bf16", _abi.load().apr_mc_relu_backward_bf16(
+        ctypes.c_void_p(pre.data_ptr()), ctypes.c_void_p(grad_post.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+        _stream_ptr(stream)))
+    return out
+
+
+def apr_mc_readout(conv, x, inv_scale, out=None, stream=None):
+    import torch
+    n = int(x.numel())
+    _dev_ptr(conv, "conv", n * MC_CHANNELS, torch.float32)
+    _dev_ptr(x, "x", n, torch.float32)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+    _dev_ptr(out, "y", n, torch.float32)
+    _abi.check("apr_mc_readout", _abi.load().apr_mc_readout(
+        ctypes.c_void_p(conv.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, float(inv_scale),
+        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_mc_readout_backward_bf16(grad_y, inv_scale, out=None, stream=None):
+    import torch
+    n = int(grad_y.numel())
+    _dev_ptr(grad_y, "grad_y", n, torch.float32)
+    if out is None:
+        out = torch.empty((n, MC_CHANNELS), dtype=torch.bfloat16, device=grad_y.device)
+    _dev_ptr(out, "grad_conv", n * MC_CHANNELS, torch.bfloat16)
+    _abi.check("apr_mc_readout_backward_bf16", _abi.load().apr_mc_readout_backward_bf16(
+        ctypes.c_void_p(grad_y.data_ptr()), n, float(inv_scale), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def _stencil_stack(fn_name, w, l_max, l_min):

@@ -50,6 +50,11 @@ SIGNATURES = {
     "apr_convolve_mc": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
     "apr_mc_backward_workspace_bytes": (_SZ, [_P, _I32, _I32, _I32]),
     "apr_convolve_mc_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "apr_mc_embed_bf16": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
+    "apr_mc_relu_bf16": (_I32, [_P, _I64, _P, _P]),
+    "apr_mc_relu_backward_bf16": (_I32, [_P, _P, _I64, _P, _P]),
+    "apr_mc_readout": (_I32, [_P, _P, _I64, ctypes.c_float, _P, _P]),
+    "apr_mc_readout_backward_bf16": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
     "apr_restrict_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
     "apr_rescale_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
     "apr_sync_status": (_I32, [_P, _P]),

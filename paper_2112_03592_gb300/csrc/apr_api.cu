@@ -45,7 +45,7 @@ cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes) {
 
 void free_device(apr_handle_s *h) {
     void *ptrs[] = {h->d_fwd, h->d_bwd, h->d_tree, h->d_fwd_level_begin, h->d_row_ptr, h->d_trow_ptr,
-                    h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err};
+                    h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -139,6 +139,12 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
                 b += sizeof(unsigned);
                 e = cudaMemset(h->d_err, 0, sizeof(unsigned));
             }
+        }
+        if (e == cudaSuccess) {
+            // operand-layout copy of multi-channel weights: [2 (plain, transposed)][levels][27 * 16 * 16]
+            const size_t nb = size_t(2) * size_t(X.l_max - X.l_min + 1) * 27 * 16 * 16 * sizeof(uint16_t);
+            e = cudaMalloc(reinterpret_cast<void **>(&h->d_mcw), nb);
+            if (e == cudaSuccess) b += nb;
         }
         if (e != cudaSuccess) {
             st = cuda_status(e);

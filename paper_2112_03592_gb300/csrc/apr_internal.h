@@ -100,5 +100,6 @@ struct apr_handle_s {
     uint32_t *d_row_ptr = nullptr, *d_trow_ptr = nullptr;
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
+    uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
     size_t dev_bytes = 0;
 };

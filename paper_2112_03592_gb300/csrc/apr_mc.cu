@@ -40,6 +40,7 @@ constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t TM_A = 0;                // A operand: tap e in columns 8e .. 8e+7
 constexpr uint32_t TM_D = 224;              // accumulator: 16 columns
 constexpr int NSEG_F = 3 * NPROW;           // staging segments of the feature patch
+constexpr int NCZM = ((SZ + 1) >> 1) + 2;   // level-(l-1) rows per axis under a patch (even sub-tile origin)
 constexpr int WG_T = 16;                    // targets per weight-gradient GEMM step (one K step)
 constexpr int WG_MG = 64;                   // M groups of 8 rows allocated (54 used: 27 taps x 2)
 constexpr int WG_ROWS = NTAP * MC;          // 432 rows (e, ci) of the weight gradient
@@ -47,6 +48,7 @@ static_assert(TZ % SZ == 0 && TX % SX == 0, "sub-tiles must divide the work-item
 static_assert(SZ % 2 == 0 && SX % 2 == 0, "sub-tiles must be even-aligned (coarse cells)");
 static_assert(TM_A + 8 * NTAP <= TM_D && TM_D + 16 <= TMEM_COLS, "tensor-memory columns");
 static_assert(NPC < 65536 && MAXT <= 1024, "16-bit cell ids");
+static_assert(SZ == SX && NCZM * NCZM <= NPROW, "once-staged coarser rows fit the kind-2 segments");
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -227,6 +229,9 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
     const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
+    // all patch rows inside the grid: every coarser row is staged once (kind-2 segments then index the
+    // NCZM x NCZM level-(l-1) rows under the patch instead of the patch rows)
+    const bool inner = s.z0 >= 1 && s.x0 >= 1 && s.z0 + SZ + 1 <= s.g.dz && s.x0 + SX + 1 <= s.g.dx;
     int cnt[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -235,7 +240,15 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
         if (sg < NSEG_F) {
             const int kind = sg / NPROW, pr = sg - kind * NPROW;
             int rz = 0, rx = 0, lo = 0, hi = 0;
-            if (row_mode(s, pr, bc, rz, rx) == 1) {
+            if (kind == 2 && inner) {
+                // a level-(l-1) row staged once for the (up to) 2 x 2 patch rows it covers
+                if (pr < NCZM * NCZM && has_coarse) {
+                    const int cz = ((s.z0 - 1) >> 1) + pr / NCZM, cx = ((s.x0 - 1) >> 1) + pr % NCZM;
+                    const int cya = ya >> 1, cyb = min((yb + 1) >> 1, s.gc.dy);
+                    if (cz < s.gc.dz && cx < s.gc.dx)
+                        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, cz * s.gc.dx + cx, cya, cyb, lo, hi);
+                }
+            } else if (row_mode(s, pr, bc, rz, rx) == 1) {
                 if (kind == 0) {
                     row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
                 } else if (kind == 1 && has_tree) {
@@ -260,7 +273,7 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
                 S.p0[c] = sl.a;
                 S.p1[c] = sl.b;
             }
-        } else {
+        } else if (!inner) {
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const int y = 2 * sl.y + f;
@@ -269,6 +282,24 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
                     S.p0[c] = sl.a;
                     S.p1[c] = sl.b;
                 }
+            }
+        } else {
+            const int rz0 = 2 * (((s.z0 - 1) >> 1) + pr / NCZM) - (s.z0 - 1);
+            const int rx0 = 2 * (((s.x0 - 1) >> 1) + pr % NCZM) - (s.x0 - 1);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const int y = 2 * sl.y + f;
+                if (y < ya || y >= yb) continue;
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int pz = rz0 + a, px = rx0 + b;
+                        if (pz < 0 || pz >= PZ || px < 0 || px >= PX) continue;
+                        const int c = (pz * PX + px) * PY + y - ylo;
+                        S.p0[c] = sl.a;
+                        S.p1[c] = sl.b;
+                    }
             }
         }
     });
@@ -342,16 +373,28 @@ __device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
     return n;
 }
 
-// Weights of one level into the B layout of tap e: K-major core matrices of 8 rows x 16 bytes,
-// N-row group g and K chunk k at (2g + k) * 128 bytes (LBO 128, SBO 256). transpose = false: N = co,
-// K = ci (forward); transpose = true: N = ci, K = co (data adjoint).
-__device__ void load_weights(const uint16_t *W, int lev, bool transpose, unsigned char *wsm) {
-    const uint16_t *w = W + size_t(lev) * MC * MC * NTAP;
-    for (int gi = threadIdx.x; gi < MC * MC * NTAP; gi += NT) {
-        const int co = gi / (MC * NTAP), ci = (gi / NTAP) % MC, e = gi % NTAP;
-        const int n = transpose ? ci : co, k = transpose ? co : ci;
-        *reinterpret_cast<uint16_t *>(wsm + e * WTAP + ((n >> 3) * 2 + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = w[gi];
+// Weights of every level in the B-operand layout of each tap e: K-major core matrices of 8 rows x 16
+// bytes, N-row group g and K chunk k at (2g + k) * 128 bytes (LBO 128, SBO 256). transpose = 0:
+// N = co, K = ci (forward); transpose = 1: N = ci, K = co (data adjoint). One thread per destination
+// element of out[lev][e * 256 + ...], read from W[lev][co][ci][e].
+__global__ void mc_weight_layout_kernel(const uint16_t *__restrict__ W, int n_levels, int transpose,
+                                        uint16_t *__restrict__ out) {
+    constexpr int PER = MC * MC * NTAP;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n_levels * PER; d += gridDim.x * blockDim.x) {
+        const int lev = d / PER, r = d % PER;
+        const int e = r / (MC * MC), q = r % (MC * MC);
+        const int cm = q / 64, row = (q % 64) / 8, col = q % 8;
+        const int n = (cm >> 1) * 8 + row, k = (cm & 1) * 8 + col;
+        const int co = transpose ? k : n, ci = transpose ? n : k;
+        out[d] = W[((size_t(lev) * MC + co) * MC + ci) * NTAP + e];
     }
+}
+
+// One level's operand-layout weights (13 824 contiguous bytes) into shared memory.
+__device__ void load_weights(const uint16_t *wl, int lev, unsigned char *wsm) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(wl + size_t(lev) * MC * MC * NTAP);
+    uint4 *dst = reinterpret_cast<uint4 *>(wsm);
+    for (int i = threadIdx.x; i < NTAP * WTAP / 16; i += NT) dst[i] = src[i];
     fence_async_smem();
 }
 
@@ -494,7 +537,7 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
     const int nt = list_targets(L, s, S.tg);
     if (nt == 0) return;
-    load_weights(W, s.l - L.l_min, false, S.w);
+    load_weights(W, s.l - L.l_min, S.w);
     stage_features(L, s, vals, tree, bc, S.st);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
@@ -734,7 +777,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     block_sync();
     const int n1 = S.n1, nn = S.nn;
     if (n1 + nn == 0) return;
-    load_weights(W, s.l - L.l_min, true, S.w);
+    load_weights(W, s.l - L.l_min, S.w);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
     fence_async_smem();
@@ -1030,9 +1073,11 @@ apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const ui
     const size_t sm = sizeof(FwdSmem);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_fwd_kernel), sm);
     const int n = int(X.fwd_items.size());
+    const int nl = X.l_max - X.l_min + 1;
     if (e == cudaSuccess && n > 0) {
+        mc_weight_layout_kernel<<<(nl * MC * MC * NTAP + 255) / 256, 256, 0, stream>>>(weights, nl, 0, h->d_mcw);
         mc_fwd_kernel<<<dim3(n, NSUB), NT, sm, stream>>>(h->L, h->d_fwd, reinterpret_cast<const uint4 *>(particles),
-                                                          reinterpret_cast<const uint4 *>(tree), weights, bc, out);
+                                                          reinterpret_cast<const uint4 *>(tree), h->d_mcw, bc, out);
         e = cudaGetLastError();
     }
     return cuda_status(e);
@@ -1071,9 +1116,12 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
         if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(gt, 0, size_t(X.nt) * MC * sizeof(float), stream);
         if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void *>(mc_bwd_data_kernel), sizeof(BwdSmem));
         const int n = int(X.bwd_items.size());
+        const uint16_t *wt = h->d_mcw + size_t(n_levels) * MC * MC * NTAP;
         if (e == cudaSuccess && n > 0) {
+            mc_weight_layout_kernel<<<(n_levels * MC * MC * NTAP + 255) / 256, 256, 0, stream>>>(
+                weights, n_levels, 1, h->d_mcw + size_t(n_levels) * MC * MC * NTAP);
             mc_bwd_data_kernel<<<dim3(n, NSUB), NT, sizeof(BwdSmem), stream>>>(
-                h->L, h->d_bwd, weights, bc, reinterpret_cast<const uint4 *>(grad_out), grad_particles, gt);
+                h->L, h->d_bwd, wt, bc, reinterpret_cast<const uint4 *>(grad_out), grad_particles, gt);
             e = cudaGetLastError();
         }
         for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
