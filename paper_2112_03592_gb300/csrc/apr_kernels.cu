@@ -514,6 +514,7 @@ struct BwdSmem {
     int pre[(G::NROW + G::NRSEG > NIW ? G::NROW + G::NRSEG : NIW) + 1];
     int warp_tot[NWARP + 1];
     unsigned long long need[NIR];
+    int cpre[NIW + 1];                        // scratch of the window compaction
     unsigned char wmir[NIW];                  // window has cells with mirrored preimages
     unsigned short act[NIW];
     union {                                   // staging / routing and window compute never overlap
@@ -668,9 +669,9 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         }
     }
     block_sync();
-    // (compact_windows reuses pre[] as scratch; the routing prefix is rebuilt from cnt[] below)
+    // (the compaction has its own scratch: pre[] keeps the segment prefix for the routing pass)
     compact_windows([&](int w) { return ((S.need[w / NWIN] >> ((w % NWIN) * WIN)) & 0xffull) != 0ull; }, S.act,
-                    S.pre, S.warp_tot, &S.nact);
+                    S.cpre, S.warp_tot, &S.nact);
 
     // H = (flipped stencil) correlated with the gradient patch, at the active windows (c' = c term)
     windows_apply<R>(S.gpatch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
@@ -746,15 +747,8 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
         }
         block_sync();
     }
-    // prefix of the routing segments (entries rbase .. rbase + NRSEG): every thread still holds the
-    // counts of its entries 2t, 2t+1 in cnt[]
+    // routing: the sources of the interior cells, segments rbase .. rbase + NRSEG of the first scan
     const int rbase = G::NROW;
-    {
-        const int e0 = 2 * tid, e1 = 2 * tid + 1;
-        const int c0 = (e0 >= rbase && e0 < NSG) ? cnt[0] : 0;
-        const int c1 = (e1 >= rbase && e1 < NSG) ? cnt[1] : 0;
-        block_scan2(c0, c1, NSG, S.pre, S.warp_tot);
-    }
     const YLoader rl{L.y, L.ty, NIR, 2 * NIR};
     for_each_element(S.seg_lo + rbase, S.pre + rbase, G::NRSEG, S.segid, rl, [&](int seg, int i, SlotYV &s) {
         if (seg < NIR) {
