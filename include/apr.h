@@ -290,6 +290,13 @@ apr_status_t apr_restrict_stencil(const float *w, int32_t k, int32_t l_max, int3
 /* Level-rescaled stencils (Eq. adapt_grad): out[l - l_min] = 2^-(l_max - l) * w. Host memory. */
 apr_status_t apr_rescale_stencil(const float *w, int32_t k, int32_t l_max, int32_t l_min, float *out);
 
+/* Self-test of the device error path (no paper counterpart): launches one block that waits on a
+ * barrier nothing will complete, gives up after limit_us microseconds (1 .. 2 000 000) with the
+ * same bounded wait the tensor-core kernels use, and records the timeout in the handle's error word,
+ * so that the next apr_sync_status returns APR_ERR_TIMEOUT. No fault occurs; the handle and the
+ * CUDA context stay usable. */
+apr_status_t apr_selftest_bounded_wait(apr_handle_t h, uint32_t limit_us, apr_stream_t stream);
+
 /* Wait for `stream`, then read and clear the handle's device error word. Returns APR_ERR_TIMEOUT if a
  * bounded device wait gave up since the last call, APR_ERR_DEVICE if another device-side check
  * failed, else APR_OK (or APR_ERR_CUDA). */

@@ -57,6 +57,7 @@ SIGNATURES = {
     "apr_mc_readout_backward_bf16": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
     "apr_restrict_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
     "apr_rescale_stencil": (_I32, [_P, _I32, _I32, _I32, _P]),
+    "apr_selftest_bounded_wait": (_I32, [_P, _U32, _P]),
     "apr_sync_status": (_I32, [_P, _P]),
     "apr_status_string": (ctypes.c_char_p, [_I32]),
 }

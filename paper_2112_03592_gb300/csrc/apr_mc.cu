@@ -88,8 +88,9 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// Wait for phase `parity` of the mbarrier; gives up after about one second (or 2^24 polls).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier; gives up after limit_ns nanoseconds (default one second)
+// or 2^24 polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = 1000000000ull) {
     const uint32_t a = smem_u32(bar);
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 0; it < (1u << 24); ++it) {
@@ -100,7 +101,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (globaltimer() - t0 > 1000000000ull) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -156,6 +157,17 @@ __device__ __forceinline__ bool block_timed_out(bool ok, uint64_t *bar, uint32_t
         mbar_wait(bar, parity);
     }
     return bad;
+}
+
+// Self-test of the bounded-wait path: one block waits on an mbarrier that nothing arrives at, gives up
+// after limit_ns and records ERR_TIMEOUT, exactly as the tensor-core kernels do when their MMAs do
+// not complete. Nothing faults; the context stays usable.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, unsigned *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar);
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------- geometry
@@ -1043,6 +1055,12 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 using namespace aprk;
 
 extern "C" {
+
+apr_status_t apr_selftest_bounded_wait(apr_handle_t h, uint32_t limit_us, apr_stream_t stream) {
+    if (!h || h->host_only || limit_us == 0 || limit_us > 2000000u) return APR_ERR_INVALID_ARG;
+    bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(uint64_t(limit_us) * 1000ull, h->d_err);
+    return cuda_status(cudaGetLastError());
+}
 
 apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, uint16_t *tree, int32_t channels,
                                     apr_stream_t stream) {
