@@ -1035,6 +1035,9 @@ static_assert(offsetof(FwdSmem, bar) % 8 == 0 && offsetof(BwdSmem, bar) % 8 == 0
 
 cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
 
+// CTAs of the weight-gradient kernel: 8 per SM (2 resident at a time), so each CTA accumulates a
+// short chain of tensor-core MMAs (about 1/8 of an SM's share of the units) before its partial sum
+// is written; the fixed-order reduction then adds the partials in FP32.
 int wgrad_ctas(int n_units) {
     static int sms = 0;
     static std::once_flag once;
@@ -1043,7 +1046,7 @@ int wgrad_ctas(int n_units) {
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 152;
     });
-    return std::max(1, std::min(n_units, 2 * sms));
+    return std::max(1, std::min(n_units, 8 * sms));
 }
 
 bool mc_args_ok(int32_t c_in, int32_t c_out, int32_t k) { return c_in == MC && c_out == MC && k == 3; }

@@ -142,3 +142,29 @@ def test_partition_and_balance_violations_rejected():
     S.validate_apr(unb, check_balance=False)
     _build(_layout(unb), flags=G.APR_VALIDATE | G.APR_HOST_ONLY)     # a valid partition ...
     _expect(2, _layout(unb), flags=HOST)                             # ... but not 2:1 balanced
+
+
+def test_compute_calls_reject_bad_arguments_without_a_device():
+    """Argument checks run before any launch: host-only handles, null buffers, unsupported sizes and
+    flags return their status codes on a machine without a GPU."""
+    import ctypes
+    apr = S.random_balanced_apr((8, 8, 16), 0, seed=1, p_fine=0.05)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE | G.APR_HOST_ONLY)
+    lib, h = lay._lib, lay.handle
+    P = ctypes.c_void_p
+    dummy = P(16)
+    inv = 1  # APR_ERR_INVALID_ARG
+    assert lib.apr_convolve(h, dummy, dummy, dummy, 3, 0, dummy, P(0)) == inv          # host-only handle
+    assert lib.apr_gradient_magnitude(h, dummy, dummy, dummy, 3, 0, dummy, P(0)) == inv
+    assert lib.apr_richardson_lucy(h, dummy, dummy, 3, 0, 2, dummy, dummy, 1 << 20, P(0)) == inv
+    assert lib.apr_convolve_mc(h, dummy, dummy, dummy, 16, 16, 3, 0, dummy, P(0)) == inv
+    assert lib.apr_tree_restrict_bf16(h, dummy, dummy, 16, P(0)) == inv
+    assert lib.apr_selftest_bounded_wait(h, 1000, P(0)) == inv
+    assert lib.apr_mc_relu_bf16(P(0), 10, dummy, P(0)) == inv                           # null input
+    assert lib.apr_mc_embed_bf16(dummy, -1, ctypes.c_float(1.0), dummy, P(0)) == inv   # negative size
+    assert lib.apr_mc_readout(P(0), dummy, 4, ctypes.c_float(1.0), dummy, P(0)) == inv
+    assert lib.apr_mc_backward_workspace_bytes(h, 8, 16, 3) == 0                        # unsupported shape
+    assert lib.apr_restrict_stencil(dummy, 7, 9, 2, dummy) == 3                          # k = 7 unsupported
+    bad = _abi.AprHostLayout()
+    out = P()
+    assert lib.apr_build_device(ctypes.byref(bad), 1 << 7, P(0), ctypes.byref(out)) == inv  # unknown flag
