@@ -271,8 +271,8 @@ template <int R>
 __device__ __forceinline__ void window_rows_checked(const float *patch, const float *w8, int ia, int ib, int col,
                                                     float acc[WIN]) {
     using G = Geo<R>;
-#pragma unroll
-    for (int pair = 0; pair < G::NPAIR; ++pair) {
+#pragma unroll 1
+    for (int pair = 0; pair < G::NPAIR; ++pair) {  // boundary tiles only: kept small for the instruction cache
         const int dz = pair / G::K, dx = pair % G::K;
         const int rz = ia + dz, rx = ib + dx;
         if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
@@ -728,9 +728,9 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
                         // taps e with c' - e inside the staged window (the rest reads zero gradient)
                         const int cz = pz[iz] - (z0 - R), cx = px[ix] - (x0 - R), cy = py[iy] - yw;
                         const int ey0 = max(-R, cy - G::PY + 1), ey1 = min(R, cy);
-#pragma unroll
+#pragma unroll 1
                         for (int ez = -R; ez <= R; ++ez)
-#pragma unroll
+#pragma unroll 1
                             for (int ex = -R; ex <= R; ++ex) {
                                 const int sz = cz - ez, sx = cx - ex;
                                 if (sz < 0 || sz >= G::PZ || sx < 0 || sx >= G::PX) continue;
