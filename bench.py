@@ -602,6 +602,10 @@ def mc_cpu_baseline(apr, x, w, g, budget_s=20.0):
                       f"{apr.n_particles} outputs; FP64, 1 thread"}
 
 
+RL_WORKLOAD = "blob512"
+RL_ITERS = 20
+
+
 def run_rl(args, rank, world, full=True):
     """Richardson-Lucy on the 512^3 blob APR: 20 iterations with the restricted 5^3 Gaussian PSF
     (sigma 1.5) and its flip; one step = the whole 20-iteration deconvolution from i_0 = u."""
@@ -1040,7 +1044,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=3000)
     ap.add_argument("--sur-train", type=int, default=8, help="surrogate: training APRs")
-    ap.add_argument("--sur-steps", type=int, default=400, help="surrogate: Adam steps")
+    ap.add_argument("--sur-steps", type=int, default=1500, help="surrogate: Adam steps")
     ap.add_argument("--sur-lr", type=float, default=2e-3, help="surrogate: learning rate")
     ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc", "blob512_rl", "surrogate"],
                     help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step; "
