@@ -166,7 +166,7 @@ def max_over_ranks(x: float, device=None) -> float:
 
 
 def algorithmic_bytes(apr, lay, k):
-    """Bytes the method must move (no index overhead, no re-reads), per SURVEY-style accounting:
+    """Bytes the method must move (no index overhead, no re-reads):
     conv forward  = N_p (4 in + 2 y + 4 out) + N_t (4 + 2) + (R_p + R_t) 4 + stencils
     tree restrict = N_p (4 + 2) + N_t (4 write + 2) + (R_p + R_t) 4   (tree read-back of finer levels ~ N_t 4)
     """

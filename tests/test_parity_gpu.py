@@ -10,7 +10,7 @@ from paper_2112_03592_gb300 import _abi
 
 pytestmark = pytest.mark.gpu
 FLAGS = G.APR_VALIDATE | G.APR_REQUIRE_BALANCE
-REL = 1e-5    # FP32 vs FP64: max relative error (positive data), spec bound
+REL = 1e-5    # FP32 vs FP64: max relative error (positive data)
 NORM = 1e-5   # sign-mixed data: max |diff| / max |reference|
 
 
