@@ -115,7 +115,7 @@ apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size
  * level l+1 or a tree node of level l+1 (average downsampling, Sec. 2.3).
  *   particles: device [N_p][channels] float32 (channels-last), read only.
  *   tree:      device [N_t][channels] float32, written (every entry).
- * channels: 1 .. 64. */
+ * channels: 1 .. 64 (APR_ERR_INVALID_ARG otherwise); each channel is averaged on its own. */
 apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tree, int32_t channels,
                                apr_stream_t stream);
 

@@ -14,7 +14,7 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s,
                             int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr);
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int C = 1, int ch = 0);
 cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                            const float *st, int bc, float *out, cudaStream_t s);
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
@@ -232,13 +232,15 @@ apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size
 apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tree, int32_t channels,
                                apr_stream_t stream) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;
-    if (channels != 1) return APR_ERR_UNSUPPORTED;
+    if (channels < 1 || channels > 64) return APR_ERR_INVALID_ARG;
     if ((!particles && h->X.np) || (!tree && h->X.nt)) return APR_ERR_INVALID_ARG;
     const HostIndex &X = h->X;
     for (int l = X.l_max - 1; l >= X.l_min; --l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-        cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, int(n), particles, tree, stream);
-        if (e != cudaSuccess) return cuda_status(e);
+        for (int c = 0; c < channels; ++c) {  // channels-last values: one strided pass per channel
+            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, int(n), particles, tree, stream, channels, c);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
     }
     return APR_OK;
 }

@@ -804,7 +804,8 @@ __device__ __forceinline__ void child_segment(const DevLayout &L, const Item &it
 // Warp-level flattened loop over the children: f(segment, index, y, value), values read from vp
 // (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use.
 template <typename F>
-__device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f) {
+__device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f,
+                                              int C = 1, int c = 0) {
     const int lane = threadIdx.x & 31;
     int incl = n;
 #pragma unroll
@@ -843,7 +844,7 @@ __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n,
                 sg[u] = s;
                 ix[u] = slo + (e - sex);
                 yv[u] = s >= 4 ? int(L.ty[ix[u]]) : int(L.y[ix[u]]);
-                vv[u] = s >= 4 ? vt[ix[u]] : vp[ix[u]];
+                vv[u] = s >= 4 ? vt[size_t(ix[u]) * C + c] : vp[size_t(ix[u]) * C + c];
             }
         }
 #pragma unroll
@@ -856,7 +857,7 @@ __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n,
 // parent, then every node averages its in-grid slots in a fixed order.
 __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items, int n,
                                                            const float *__restrict__ vals,
-                                                           float *__restrict__ tree) {
+                                                           float *__restrict__ tree, int C, int ch) {
     __shared__ float slot[NWARP][8][BY];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * NWARP + warp;
@@ -872,7 +873,7 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
     float(*sl)[BY] = slot[warp];
     warp_children(L, lo, cn, vals, tree, [&](int s, int, int yv, float v) {
         sl[(s & 3) * 2 + (yv & 1)][(yv >> 1) - y0] = v;
-    });
+    }, C, ch);
     __syncwarp();
     for (int t = tlo + lane; t < thi; t += 32) {
         const int yv = L.ty[t];
@@ -886,7 +887,7 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
                 ++cnt;
             }
         }
-        tree[t] = s / float(cnt);
+        tree[size_t(t) * C + ch] = s / float(cnt);
     }
 }
 
@@ -983,8 +984,8 @@ cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, 
 }
 
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
-                                 cudaStream_t s) {
-    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, vals, tree);
+                                 cudaStream_t s, int C, int ch) {
+    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, vals, tree, C, ch);
     return cudaGetLastError();
 }
 

@@ -196,3 +196,14 @@ def test_convolve_adjoint_dot_product():
     lhs = float(np.dot(out.cpu().double().numpy(), y))
     rhs = float(np.dot(x, gp.cpu().double().numpy()) + np.dot(t, gt.cpu().double().numpy()))
     assert abs(lhs - rhs) <= 1e-5 * max(1.0, abs(lhs)), (lhs, rhs)
+
+
+@pytest.mark.parametrize("C", [2, 5])
+def test_tree_restrict_multichannel_fp32(C):
+    apr = CASES["rand_ragged"]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    vals = np.random.default_rng(C).uniform(1.0, 9.0, size=(apr.n_particles, C))
+    tree = G.apr_tree_restrict(lay, dev(vals.astype(np.float32))).cpu().numpy()
+    ref = oracle.Oracle(apr, vals.astype(np.float32)).tree()
+    assert tree.shape == ref.shape
+    assert_rel(tree, ref)
