@@ -355,3 +355,19 @@ def test_gradient_magnitude_of_a_linear_ramp(level):
         W1 = np.stack([np.repeat(sob[a][None], apr.n_levels, 0) for a in range(3)])
         g1 = oracle.gradient_magnitude(apr, vals, W1, 3)
         np.testing.assert_allclose(g1[inner], s * np.sqrt(alpha ** 2 + beta ** 2 + gamma ** 2), rtol=1e-12)
+
+
+def test_multichannel_conv_on_pixels_equals_channel_sum_of_dense_correlations():
+    """With 16 channels on an all-finest APR, out[co] = sum_ci correlate(x[ci], W[co][ci]) (reflect)."""
+    dims = (6, 7, 9)
+    apr = S.uniform_level_apr(dims, S.l_max_for(dims), l_min=2)
+    rng = np.random.default_rng(11)
+    C = 16
+    x = rng.normal(size=(apr.n_particles, C))
+    W = rng.normal(size=(apr.n_levels, C, C, 27))
+    got = Oracle(apr, x).conv(W, 3, C_out=C)
+    lev = apr.l_max - apr.l_min
+    X = x.reshape(dims + (C,))
+    for co in range(0, C, 5):
+        ref = sum(ndi.correlate(X[..., ci], W[lev, co, ci].reshape(3, 3, 3), mode="reflect") for ci in range(C))
+        np.testing.assert_allclose(got[:, co], ref.reshape(-1), rtol=1e-10, atol=1e-10)
