@@ -831,6 +831,7 @@ def run_surrogate(args, rank, world):
 
     rl_ms = timed(run_rl_)
     cnn_ms = timed(run_cnn)
+    n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
     y = holder[0]
     wts = torch.as_tensor(pixels_per_particle(apr), device=dev)
     ref_clean = torch.as_tensor(clean.values, device=dev)
@@ -852,7 +853,9 @@ def run_surrogate(args, rank, world):
                     "weighting": "pixels covered by each particle (pixel-equivalent)"},
         "training": {"loss_first": round(float(np.mean(hist[:10])), 6), "loss_last": round(float(np.mean(hist[-10:])), 6),
                      "data_s": round(t_data, 1), "train_s": round(t_train, 1)},
-        "gpu_launches": None,
+        # per CNN inference: embedding, 4 x (tree restriction per level, weight layout, convolution;
+        # hidden ReLUs fused into the convolution), read-out; per RL run: 2 x (tree + convolution) per iteration
+        "gpu_launches": (2 + 4 * (n_tree_levels + 2) + RL_ITERS * 2 * (n_tree_levels + 1)) * args.steps,
     }
     return rec
 

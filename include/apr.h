@@ -241,6 +241,13 @@ apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, u
 apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree, const uint16_t *weights,
                              int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out, apr_stream_t stream);
 
+/* apr_convolve_mc with the hidden-layer activation of an APR CNN fused into the write:
+ * out[p][co] = bf16(max(conv[p][co], 0)) (device [N_p][c_out] bf16), instead of the float32 result.
+ * For inference (the backward needs the float32 pre-activation). */
+apr_status_t apr_convolve_mc_relu_bf16(apr_handle_t h, const uint16_t *particles, const uint16_t *tree,
+                                       const uint16_t *weights, int32_t c_in, int32_t c_out, int32_t k, int32_t bc,
+                                       uint16_t *out, apr_stream_t stream);
+
 /* Scratch bytes of apr_convolve_mc_backward (tree gradient and per-block weight-gradient partials). */
 size_t apr_mc_backward_workspace_bytes(apr_handle_t h, int32_t c_in, int32_t c_out, int32_t k);
 

@@ -35,7 +35,7 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
-           "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_backward",
+           "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_relu_bf16", "apr_convolve_mc_backward",
            "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
            "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
@@ -330,6 +330,23 @@ def apr_convolve_mc(layout: AprLayout, particles, tree, weights, bc=APR_BC_REFLE
         out = torch.empty((layout.n_particles, C), dtype=torch.float32, device=particles.device)
     _dev_ptr(out, "out", layout.n_particles * C, torch.float32)
     _abi.check("apr_convolve_mc", layout._lib.apr_convolve_mc(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
+        ctypes.c_void_p(weights.data_ptr()), C, C, k, int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_convolve_mc_relu_bf16(layout: AprLayout, particles, tree, weights, bc=APR_BC_REFLECT, out=None, stream=None):
+    """bf16(max(apr_convolve_mc(...), 0)) [N_p][16]: a hidden CNN layer with the ReLU fused (inference)."""
+    import torch
+    C = MC_CHANNELS
+    k = 3
+    _dev_ptr(particles, "particles", layout.n_particles * C, torch.bfloat16)
+    _dev_ptr(tree, "tree", layout.n_tree * C, torch.bfloat16)
+    _dev_ptr(weights, "weights", layout.n_levels * C * C * k ** 3, torch.bfloat16)
+    if out is None:
+        out = torch.empty((layout.n_particles, C), dtype=torch.bfloat16, device=particles.device)
+    _dev_ptr(out, "out", layout.n_particles * C, torch.bfloat16)
+    _abi.check("apr_convolve_mc_relu_bf16", layout._lib.apr_convolve_mc_relu_bf16(
         layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
         ctypes.c_void_p(weights.data_ptr()), C, C, k, int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out

@@ -48,6 +48,7 @@ SIGNATURES = {
     "apr_richardson_lucy": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "apr_tree_restrict_bf16": (_I32, [_P, _P, _P, _I32, _P]),
     "apr_convolve_mc": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
+    "apr_convolve_mc_relu_bf16": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
     "apr_mc_backward_workspace_bytes": (_SZ, [_P, _I32, _I32, _I32]),
     "apr_convolve_mc_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "apr_mc_embed_bf16": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),

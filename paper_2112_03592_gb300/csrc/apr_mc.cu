@@ -539,9 +539,12 @@ struct FwdSmem {
     uint32_t tmem;
 };
 
+// out (float32 [N][16]) receives the convolution; if out_bf16 is given instead, it receives
+// bf16(max(conv, 0)), the next layer's input in an APR CNN (the ReLU fused into the write).
 __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
                                                        const uint4 *__restrict__ vals, const uint4 *__restrict__ tree,
-                                                       const uint16_t *__restrict__ W, int bc, float *__restrict__ out) {
+                                                       const uint16_t *__restrict__ W, int bc, float *__restrict__ out,
+                                                       uint4 *__restrict__ out_bf16) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FwdSmem &S = *reinterpret_cast<FwdSmem *>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -592,9 +595,18 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
             float v[16];
             tmem_ld16(tb + lane_base + TM_D, v);
             if (t < nt) {
-                float4 *o = reinterpret_cast<float4 *>(out + size_t(S.tg.idx[t]) * MC);
+                if (out_bf16) {
+                    uint4 r[2];
+                    __nv_bfloat162 *b2 = reinterpret_cast<__nv_bfloat162 *>(r);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    for (int k = 0; k < MC / 2; ++k) b2[k] = __floats2bfloat162_rn(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f));
+                    out_bf16[2 * size_t(S.tg.idx[t])] = r[0];
+                    out_bf16[2 * size_t(S.tg.idx[t]) + 1] = r[1];
+                } else {
+                    float4 *o = reinterpret_cast<float4 *>(out + size_t(S.tg.idx[t]) * MC);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                }
             }
         }
         tc_fence_before();
@@ -1083,14 +1095,15 @@ apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, u
     return cuda_status(e);
 }
 
-apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree, const uint16_t *weights,
-                             int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out, apr_stream_t stream) {
+static apr_status_t convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree,
+                                const uint16_t *weights, int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out,
+                                uint16_t *out_bf16, apr_stream_t stream) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;
     if (!mc_args_ok(c_in, c_out, k)) return APR_ERR_UNSUPPORTED;
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     const HostIndex &X = h->X;
-    if (!weights || (X.np && (!particles || !out)) || (X.nt && !tree)) return APR_ERR_INVALID_ARG;
-    if (!aligned16(particles) || !aligned16(tree) || !aligned16(out)) return APR_ERR_INVALID_ARG;
+    if (!weights || (X.np && (!particles || (!out && !out_bf16))) || (X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree) || !aligned16(out) || !aligned16(out_bf16)) return APR_ERR_INVALID_ARG;
     const size_t sm = sizeof(FwdSmem);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_fwd_kernel), sm);
     const int n = int(X.fwd_items.size());
@@ -1098,10 +1111,24 @@ apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const ui
     if (e == cudaSuccess && n > 0) {
         mc_weight_layout_kernel<<<(nl * MC * MC * NTAP + 255) / 256, 256, 0, stream>>>(weights, nl, 0, h->d_mcw);
         mc_fwd_kernel<<<dim3(n, NSUB), NT, sm, stream>>>(h->L, h->d_fwd, reinterpret_cast<const uint4 *>(particles),
-                                                          reinterpret_cast<const uint4 *>(tree), h->d_mcw, bc, out);
+                                                          reinterpret_cast<const uint4 *>(tree), h->d_mcw, bc, out,
+                                                          reinterpret_cast<uint4 *>(out_bf16));
         e = cudaGetLastError();
     }
     return cuda_status(e);
+}
+
+apr_status_t apr_convolve_mc(apr_handle_t h, const uint16_t *particles, const uint16_t *tree, const uint16_t *weights,
+                             int32_t c_in, int32_t c_out, int32_t k, int32_t bc, float *out, apr_stream_t stream) {
+    if (!out && h && h->X.np) return APR_ERR_INVALID_ARG;
+    return convolve_mc(h, particles, tree, weights, c_in, c_out, k, bc, out, nullptr, stream);
+}
+
+apr_status_t apr_convolve_mc_relu_bf16(apr_handle_t h, const uint16_t *particles, const uint16_t *tree,
+                                       const uint16_t *weights, int32_t c_in, int32_t c_out, int32_t k, int32_t bc,
+                                       uint16_t *out, apr_stream_t stream) {
+    if (!out && h && h->X.np) return APR_ERR_INVALID_ARG;
+    return convolve_mc(h, particles, tree, weights, c_in, c_out, k, bc, nullptr, out, stream);
 }
 
 size_t apr_mc_backward_workspace_bytes(apr_handle_t h, int32_t c_in, int32_t c_out, int32_t k) {

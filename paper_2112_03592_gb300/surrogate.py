@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import math
 
-from . import (apr_convolve_mc, apr_convolve_mc_backward, apr_mc_embed_bf16, apr_mc_readout,
+from . import (apr_convolve_mc, apr_convolve_mc_backward, apr_convolve_mc_relu_bf16, apr_mc_embed_bf16, apr_mc_readout,
                apr_mc_readout_backward_bf16, apr_mc_relu_backward_bf16, apr_mc_relu_bf16, apr_tree_restrict_bf16)
 
 C = 16
@@ -52,6 +52,9 @@ class AprCnn:
         c = None
         for i in range(self.n_layers):
             tree = apr_tree_restrict_bf16(layout, h)
+            if not keep and i + 1 < self.n_layers:
+                h = apr_convolve_mc_relu_bf16(layout, h, tree, Wb[i])   # inference: ReLU fused into the write
+                continue
             c = apr_convolve_mc(layout, h, tree, Wb[i])
             if keep:
                 saved.append((h, tree, c))

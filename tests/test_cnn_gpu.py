@@ -86,3 +86,16 @@ def test_cnn_training_reduces_loss():
     model = AprCnn(4, seed=0)
     hist = train(model, [(lay, x, target, float(1.0 / x.mean()))], steps=60, lr=3e-3)
     assert np.isfinite(hist).all() and np.mean(hist[-10:]) < 0.5 * np.mean(hist[:5])
+
+
+def test_fused_relu_layer_equals_convolution_then_relu():
+    apr = CASES["rand_ragged"]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    rng = np.random.default_rng(5)
+    x = torch.as_tensor((rng.integers(-64, 65, size=(apr.n_particles, 16)) / 8.0).astype(np.float32), device="cuda").to(torch.bfloat16)
+    w = torch.as_tensor(rng.normal(scale=0.1, size=(apr.n_levels, 16, 16, 27)).astype(np.float32), device="cuda").to(torch.bfloat16)
+    tree = G.apr_tree_restrict_bf16(lay, x)
+    fused = G.apr_convolve_mc_relu_bf16(lay, x, tree, w)
+    plain = G.apr_mc_relu_bf16(G.apr_convolve_mc(lay, x, tree, w))
+    torch.cuda.synchronize()
+    assert torch.equal(fused, plain)
