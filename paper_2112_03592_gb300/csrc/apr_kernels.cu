@@ -230,19 +230,37 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
     compact_windows([&](int w) { return S.wmask[w] != 0u; }, S.act, S.pre, S.warp_tot, &S.nact);
 }
 
-// Stencil taps of level l into w8[pair][0..K), optionally flipped (the transpose uses w[-e]).
-template <int R>
+// Stencil taps of level l into w8[pair][0..K), optionally flipped (the transpose uses w[-e]). The
+// stack holds (2 RS + 1)^3 taps per level; with R < RS the central (2 R + 1)^3 of them are loaded.
+template <int R, int RS = R>
 __device__ void load_taps(const float *__restrict__ stencils, int l_idx, bool flip, float *w8) {
     using G = Geo<R>;
+    constexpr int KS = 2 * RS + 1, KS3 = KS * KS * KS, D = RS - R;
     for (int i = threadIdx.x; i < G::NPAIR * 8; i += NT) {
         const int pair = i / 8, t = i % 8;
         float v = 0.f;
         if (t < G::K) {
-            const int e = pair * G::K + t;
-            v = stencils[l_idx * G::K3 + (flip ? G::K3 - 1 - e : e)];
+            const int e = ((pair / G::K + D) * KS + (pair % G::K + D)) * KS + (t + D);
+            v = stencils[l_idx * KS3 + (flip ? KS3 - 1 - e : e)];
         }
         w8[i] = v;
     }
+}
+
+// True on every thread if all taps of level l_idx of a 5^3 stack outside its central 3^3 are zero.
+// Such a level is convolved with radius 1: a restricted 5^3 stencil (Eq. restrict_stenc) has support
+// 2 ceil(2 / s) + 1 = 3 cells per axis at every level with cell edge s >= 2, i.e. below l_max. The
+// result is the same linear map (the skipped products are 0 * u); only its FP32 summation order
+// differs. Called by all threads of the block (a block barrier).
+__device__ __forceinline__ bool outer_taps_zero5(const float *__restrict__ stencils, int l_idx) {
+    const int t = threadIdx.x;
+    bool nz = false;
+    if (t < 125) {
+        const int a = t / 25, b = (t / 5) % 5, c = t % 5;
+        const bool outer = a == 0 || a == 4 || b == 0 || b == 4 || c == 0 || c == 4;
+        nz = outer && stencils[l_idx * 125 + t] != 0.f;
+    }
+    return __syncthreads_or(nz) == 0;
 }
 
 // acc[j] += sum over stencil rows (dz, dx) = pairs [P0, P1) of sum_dy w8[(dz,dx)][dy] *
@@ -360,16 +378,13 @@ struct Epilogue {
 // APR convolution (Sec. 4.1; Sec. 5.2 with 8x8-row tiles and 64-cell y-blocks instead of the
 // paper's 4x4 / 8x8 warp grid with a sliding buffer).
 // ------------------------------------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                         const float *__restrict__ vals,
-                                                         const float *__restrict__ tree,
-                                                         const float *__restrict__ stencils, int bc,
-                                                         float *out, const Epilogue epi) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// One forward tile with stencil radius R from a stack of radius RS >= R.
+template <int R, int RS>
+__device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, const float *__restrict__ vals,
+                                              const float *__restrict__ tree, const float *__restrict__ stencils,
+                                              int bc, float *out, const Epilogue &epi, unsigned char *smem_raw) {
     PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
-    const Item it = items[blockIdx.x];
-    load_taps<R>(stencils, it.l - L.l_min, epi.flip, S.w8);
+    load_taps<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w8);
     stage_patch<R>(L, it, vals, tree, bc, S);
     windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
         const unsigned m = S.wmask[w];
@@ -381,6 +396,23 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
                 out[p] = epi.apply(p, acc[j]);
             }
     });
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                         const float *__restrict__ vals,
+                                                         const float *__restrict__ tree,
+                                                         const float *__restrict__ stencils, int bc,
+                                                         float *out, const Epilogue epi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Item it = items[blockIdx.x];
+    if constexpr (R == 2) {
+        if (outer_taps_zero5(stencils, it.l - L.l_min)) {
+            conv_fwd_tile<1, 2>(L, it, vals, tree, stencils, bc, out, epi, smem_raw);
+            return;
+        }
+    }
+    conv_fwd_tile<R, R>(L, it, vals, tree, stencils, bc, out, epi, smem_raw);
 }
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
@@ -534,23 +566,22 @@ struct YLoader {
     }
 };
 
-template <int R>
-__global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                              const float *__restrict__ stencils, int bc,
-                                                              const float *__restrict__ gout,
-                                                              float *__restrict__ gp, float *__restrict__ gt) {
+// One data-adjoint tile with stencil radius R from a stack of radius RS >= R.
+template <int R, int RS>
+__device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Item &it,
+                                                   const float *__restrict__ stencils, int bc,
+                                                   const float *__restrict__ gout, float *__restrict__ gp,
+                                                   float *__restrict__ gt, unsigned char *smem_raw) {
     using G = Geo<R>;
     constexpr int NSG = G::NROW + G::NRSEG;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem<R> &S = *reinterpret_cast<BwdSmem<R> *>(smem_raw);
-    const Item it = items[blockIdx.x];
     const int l = it.l, tid = threadIdx.x;
     const LevelGeo g = L.geo[l];
     const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY;
     const int yw = y0 - R;
     const bool reflect = bc == APR_BC_REFLECT;
 
-    load_taps<R>(stencils, l - L.l_min, true, S.w8);
+    load_taps<R, RS>(stencils, l - L.l_min, true, S.w8);
     for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.gpatch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(S.H)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < G::NROW * 3; i += NT) S.rmask[i] = 0u;
@@ -777,6 +808,22 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     });
 }
 
+template <int R>
+__global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                              const float *__restrict__ stencils, int bc,
+                                                              const float *__restrict__ gout,
+                                                              float *__restrict__ gp, float *__restrict__ gt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Item it = items[blockIdx.x];
+    if constexpr (R == 2) {
+        if (outer_taps_zero5(stencils, it.l - L.l_min)) {
+            conv_bwd_data_tile<1, 2>(L, it, stencils, bc, gout, gp, gt, smem_raw);
+            return;
+        }
+    }
+    conv_bwd_data_tile<R, R>(L, it, stencils, bc, gout, gp, gt, smem_raw);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Tree kernels, one warp per tree brick (l, z, x, yb), eight bricks per block. The children of the
 // brick's nodes live in the 2x2 child rows of level l+1, y-blocks 2yb and 2yb+1 (lanes 0..3:
@@ -923,6 +970,8 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
 // forward 4, data adjoint 3.
 static_assert(4 * (sizeof(PatchSmem<2>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
 static_assert(3 * (sizeof(BwdSmem<2>) + 1024) <= 228 * 1024, "data adjoint: three blocks per SM");
+static_assert(sizeof(PatchSmem<1>) <= sizeof(PatchSmem<2>) && sizeof(BwdSmem<1>) <= sizeof(BwdSmem<2>),
+              "radius-1 tiles run inside the radius-2 launch");
 
 cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
 

@@ -27,7 +27,19 @@ def stencil_stack(apr, k, mode, seed=0):
         w = S.gaussian_stencil(k, 1.0 if k == 3 else 1.5).astype(np.float32)
         return G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
     rng = np.random.default_rng(seed)
-    return rng.normal(size=(L, k ** 3)).astype(np.float32)
+    st = rng.normal(size=(L, k ** 3)).astype(np.float32)
+    if mode == "mixed_shell" and k == 5:
+        # even level indices: zero outside the central 3^3 (computed with radius 1); level 1: zero
+        # outside the core except one corner tap (radius 2); the rest: all taps
+        w = st.reshape(L, 5, 5, 5)
+        for i in range(L):
+            if i % 2 == 0 or i == 1:
+                core = w[i, 1:4, 1:4, 1:4].copy()
+                w[i] = 0.0
+                w[i, 1:4, 1:4, 1:4] = core
+        if L > 1:
+            w[1, 0, 0, 0] = 0.5
+    return st
 
 
 def gpu_forward(apr, st, k, bc):
@@ -81,14 +93,14 @@ def test_tree_restrict_matches_oracle(case):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("k", [3, 5])
 @pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
-@pytest.mark.parametrize("mode", ["gauss", "restricted", "random"])
+@pytest.mark.parametrize("mode", ["gauss", "restricted", "random", "mixed_shell"])
 def test_convolve_matches_oracle(case, k, bc, mode):
     apr = CASES[case]()
     st = stencil_stack(apr, k, mode, seed=k + 10 * bc)
     _, _, _, out = gpu_forward(apr, st, k, bc)
     ref = oracle.Oracle(apr).conv(st.astype(np.float64), k, bc=bc)[:, 0]
     got = out.cpu().numpy()
-    if mode == "random" or bc == G.APR_BC_ZERO:
+    if mode in ("random", "mixed_shell") or bc == G.APR_BC_ZERO:
         assert_norm(got, ref)
     else:
         assert_rel(got, ref)
@@ -106,9 +118,10 @@ def test_constant_image_stays_constant():
 @pytest.mark.parametrize("case", ["blob64", "rand_ragged", "rand_thin", "tiny"])
 @pytest.mark.parametrize("k", [3, 5])
 @pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
-def test_backward_matches_oracle(case, k, bc):
+@pytest.mark.parametrize("mode", ["random", "restricted", "mixed_shell"])
+def test_backward_matches_oracle(case, k, bc, mode):
     apr = CASES[case]()
-    st = stencil_stack(apr, k, "random", seed=3)
+    st = stencil_stack(apr, k, mode, seed=3)
     lay, v, tree, _ = gpu_forward(apr, st, k, bc)
     g = np.random.default_rng(1).normal(size=apr.n_particles).astype(np.float32)
     gp, gw = G.apr_convolve_backward(lay, v, tree, dev(st), k, dev(g), bc)
