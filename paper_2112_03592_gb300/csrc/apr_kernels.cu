@@ -86,12 +86,11 @@ struct PatchSmem {
 // Stage the forward patch of item `it` (Sec. 3.5): patch rows z in [z0-R, z0+TZ+R), x likewise, y in
 // [y0-R, y0+BY+R); rows outside the grid are reflected rows (or zeros), cells outside the grid in y
 // are reflected cells (or zeros). Marks the target windows (level-l particles of the interior rows in
-// y-block yb) and lists the active ones. If gwin is given, also stores dL/dout of every target at
-// gwin[row * BY + (y - y0)] (zero elsewhere).
+// y-block yb) and lists the active ones. zero_fill: cells no source covers hold 0 (the stencil
+// gradient reads every cell of a window), not stale shared memory.
 template <int R>
 __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__restrict__ vals,
-                            const float *__restrict__ tree, int bc, PatchSmem<R> &S,
-                            const float *__restrict__ gout = nullptr, float *gwin = nullptr) {
+                            const float *__restrict__ tree, int bc, PatchSmem<R> &S, bool zero_fill = false) {
     using G = Geo<R>;
     const int tid = threadIdx.x;
     const int l = it.l;
@@ -103,12 +102,8 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
         S.wmask[i] = 0u;
         S.wfirst[i] = INT_MAX;
     }
-    if (gwin) {
-        // stencil-gradient mode: every window cell enters the sums (non-targets with g = 0), so the
-        // patch cells no source covers must hold 0, not stale shared memory (0 * NaN = NaN)
-        for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(gwin)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zero_fill)
         for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
 
     // segment bounds, two per thread (entries 2t, 2t+1) for the scan. Segments [0, NROW): level-l
     // particles of every patch row, [NROW, 2 NROW): level-l tree nodes, [2 NROW, 3 NROW): level-(l-1)
@@ -185,7 +180,6 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
                 const int w = trow * NWIN + yr / WIN;
                 atomicOr(&S.wmask[w], 1u << (yr % WIN));
                 atomicMin(&S.wfirst[w], i);
-                if (gwin) gwin[trow * BY + yr] = gout[i];
             }
         } else if (kind == 2) {
             const int yy = 2 * s.y;  // first level-l cell of the coarser particle
@@ -457,24 +451,18 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
 // u_l(p + e) (fixed order); stencil_grad_reduce_kernel then sums the items of every level.
 // ------------------------------------------------------------------------------------------------
 template <int R>
-struct StencilGradSmem {
-    PatchSmem<R> P;
-    __align__(16) float gwin[NIR * BY];
-    float red[(NT / Geo<R>::NPAIR) * Geo<R>::NPAIR * Geo<R>::K];
-};
-
-template <int R>
-__global__ void __launch_bounds__(NT, 2) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
                                                                  int n_items, const float *__restrict__ vals,
                                                                  const float *__restrict__ tree, int bc,
                                                                  const float *__restrict__ gout,
                                                                  float *__restrict__ partial) {
     using G = Geo<R>;
     constexpr int NGRP = NT / G::NPAIR;
+    static_assert(NGRP * G::NPAIR * G::K <= G::NROW * G::PYS, "partials fit in the patch");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StencilGradSmem<R> &S = *reinterpret_cast<StencilGradSmem<R> *>(smem_raw);
+    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    stage_patch<R>(L, it, vals, tree, bc, S.P, gout, S.gwin);
+    stage_patch<R>(L, it, vals, tree, bc, S, true);
     const int tid = threadIdx.x;
     const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
     float acc[G::K];
@@ -482,28 +470,38 @@ __global__ void __launch_bounds__(NT, 2) conv_bwd_stencil_kernel(const DevLayout
     for (int t = 0; t < G::K; ++t) acc[t] = 0.f;
     if (grp < NGRP) {
         const int dz = pair / G::K, dx = pair % G::K;
-        for (int a = grp; a < S.P.nact; a += NGRP) {
-            const int w = S.P.act[a], r = w / NWIN, col = (w % NWIN) * WIN;
+        for (int a = grp; a < S.nact; a += NGRP) {
+            const int w = S.act[a], r = w / NWIN, col = (w % NWIN) * WIN;
             const int ia = r / TX, ib = r % TX;
-            const float4 *src = reinterpret_cast<const float4 *>(S.P.patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + col);
+            const float4 *src = reinterpret_cast<const float4 *>(S.patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + col);
             const float4 a0 = src[0], a1 = src[1], a2 = src[2];
             const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-            const float4 *gs = reinterpret_cast<const float4 *>(S.gwin + r * BY + col);
-            const float4 g0 = gs[0], g1 = gs[1];
-            const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            // dL/dout of the window's targets: consecutive particles from wfirst (0 at other cells)
+            const unsigned m = S.wmask[w];
+            const float *gs = gout + S.wfirst[w];
+            float gg[WIN];
+            int c = 0;
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) {
+                gg[j] = 0.f;
+                if ((m >> j) & 1u) gg[j] = gs[c++];
+            }
 #pragma unroll
             for (int t = 0; t < G::K; ++t)
 #pragma unroll
                 for (int j = 0; j < WIN; ++j) acc[t] = fmaf(gg[j], v[j + t], acc[t]);
         }
-#pragma unroll
-        for (int t = 0; t < G::K; ++t) S.red[(grp * G::NPAIR + pair) * G::K + t] = acc[t];
     }
+    block_sync();   // the partials reuse the patch
+    float *red = S.patch;
+    if (grp < NGRP)
+#pragma unroll
+        for (int t = 0; t < G::K; ++t) red[(grp * G::NPAIR + pair) * G::K + t] = acc[t];
     block_sync();
     if (tid < G::K3) {
         const int pr = tid / G::K, t = tid % G::K;
         float s = 0.f;
-        for (int q = 0; q < NGRP; ++q) s += S.red[(q * G::NPAIR + pr) * G::K + t];
+        for (int q = 0; q < NGRP; ++q) s += red[(q * G::NPAIR + pr) * G::K + t];
         partial[size_t(tid) * n_items + blockIdx.x] = s;
     }
 }
@@ -998,7 +996,7 @@ cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int n, cons
 template <int R>
 cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, const float *vals,
                                  const float *tree, int bc, const float *gout, float *partial, cudaStream_t s) {
-    const size_t sm = sizeof(StencilGradSmem<R>);
+    const size_t sm = sizeof(PatchSmem<R>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_stencil_kernel<R>), sm);
     if (e != cudaSuccess) return e;
     if (n > 0) conv_bwd_stencil_kernel<R><<<n, NT, sm, s>>>(L, items, n, vals, tree, bc, gout, partial);
