@@ -122,9 +122,9 @@ struct YVLoader {
 
 // Flattened loop over the elements of nseg segments (segment s: global indices seg_lo[s] ..
 // seg_lo[s] + pre[s+1] - pre[s]), in chunks of SEGID_CAP elements. For every chunk, the threads
-// first write the segment id of each element into segid[] (one thread per segment), then every warp
-// takes a contiguous share of the chunk with strided lanes, issuing the loads of UNROLL elements
-// per thread before any of them is used. Trip counts depend on the warp only (lanes stay converged).
+// first write the segment id of each element into segid[] (one thread per segment), then the warps
+// take groups of 32 consecutive elements in turn, each lane issuing the loads of UNROLL elements
+// before any of them is used. Trip counts depend on the warp only (lanes stay converged).
 // Ends with a block barrier.
 constexpr int SEGID_CAP = 2048;
 
@@ -140,14 +140,15 @@ __device__ __forceinline__ void for_each_element(const int *seg_lo, const int *p
             for (int e = a; e < b; ++e) segid[e - c0] = (unsigned short)sg;
         }
         block_sync();
-        const int share = (c1 - c0 + NWARP - 1) / NWARP;
-        const int ea = c0 + warp * share, eb = min(c1, ea + share);
-        for (int base = ea; base < eb; base += 32 * UNROLL) {
+        // warp w takes the 32-element groups w, w + NWARP, w + 2 NWARP, ..., UNROLL groups per
+        // step, so every warp gets a mix of the segment kinds (their per-element work differs)
+        const int eb = c1;
+        for (int base = c0 + warp * 32; base < eb; base += NWARP * 32 * UNROLL) {
             int sg[UNROLL], ix[UNROLL];
             typename Load::Slot slot[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                const int eu = base + lane + 32 * u;
+                const int eu = base + lane + NWARP * 32 * u;
                 sg[u] = -1;
                 ix[u] = 0;
                 if (eu < eb) {
