@@ -3,6 +3,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -48,6 +49,11 @@ void free_device(apr_handle_s *h) {
                     h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int i = 0; i < 4; ++i) {
+        if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
+        if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
+        if (h->d_plan_pre[i]) cudaFree(h->d_plan_pre[i]);
+    }
 }
 
 bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
@@ -120,6 +126,17 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
     h->host_only = (flags & APR_HOST_ONLY) != 0;
     if (!h->host_only) {
         (void)stream;  // uploads are synchronous: the index is built once
+        bool plans_ok = false;
+        try {
+            plans_ok = build_plans(h->X);
+        } catch (const std::exception &) {
+            plans_ok = false;
+        }
+        if (!plans_ok) {
+            snprintf(g_last_msg, sizeof(g_last_msg), "host allocation failed (tile plans)");
+            delete h;
+            return APR_ERR_OOM;
+        }
         const HostIndex &X = h->X;
         cudaError_t e = cudaSuccess;
         size_t &b = h->dev_bytes;
@@ -133,6 +150,12 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+            const HostPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
+            e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
+            if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
+            if (e == cudaSuccess) e = upload(&h->d_plan_pre[i], P.pre.data(), P.pre.size(), b);
+        }
         if (e == cudaSuccess) {
             e = cudaMalloc(reinterpret_cast<void **>(&h->d_err), sizeof(unsigned));
             if (e == cudaSuccess) {
@@ -163,6 +186,15 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         L.l_min = X.l_min;
         L.l_max = X.l_max;
         for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
+        for (int i = 0; i < 2; ++i) {
+            L.fplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i], h->d_plan_pre[i]};
+            L.bplan[i] = PlanView{h->d_plan_hdr[2 + i], h->d_plan_ent[2 + i], h->d_plan_pre[2 + i]};
+        }
+        // the plans live on the device now; the host copies are not needed again
+        for (int i = 0; i < 2; ++i) {
+            h->X.fplan[i] = HostPlan{};
+            h->X.bplan[i] = HostPlan{};
+        }
     }
     *out = h;
     return APR_OK;

@@ -30,7 +30,10 @@ __device__ __forceinline__ void pair_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(64) : "memory");
 }
 
-__device__ __forceinline__ int reflect_idx(int i, int d) {
+__host__ __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+__host__ __device__ __forceinline__ int reflect_idx(int i, int d) {
     // half-sample symmetric reflection into [0, d), repeated for grids smaller than the stencil
     const int p = 2 * d;
     int m = i % p;
@@ -39,8 +42,8 @@ __device__ __forceinline__ int reflect_idx(int i, int d) {
 }
 
 // First element of y-block j of a row (particles or tree); j >= nb gives the row end.
-__device__ __forceinline__ uint32_t blk_start(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb,
-                                              int rr, int j) {
+__host__ __device__ __forceinline__ uint32_t blk_start(const uint32_t *rp, const uint16_t *off, int row0, int off0,
+                                                       int nb, int rr, int j) {
     if (j >= nb) return rp[row0 + rr + 1];
     return rp[row0 + rr] + off[off0 + rr * nb + j];
 }
@@ -56,8 +59,8 @@ __device__ __forceinline__ uint32_t tblock(const DevLayout &L, const LevelGeo &g
 // Index range [lo, hi) of a row containing every element with y in [ya, yb) (ya < yb), plus at
 // most BY/2 extra elements on each side (callers filter by y). Uses the per-block offsets only:
 // at most BY - ra elements of block ja lie at or after ya, at most rb elements of block jb before yb.
-__device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb, int rr,
-                                          int ya, int yb, int &lo, int &hi) {
+__host__ __device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *off, int row0, int off0, int nb,
+                                                   int rr, int ya, int yb, int &lo, int &hi) {
     const int rs = int(rp[row0 + rr]), re = int(rp[row0 + rr + 1]);
     const int ja = ya / BY, ra = ya - ja * BY;
     const int jb = yb / BY, rb = yb - jb * BY;
@@ -65,10 +68,10 @@ __device__ __forceinline__ void row_range(const uint32_t *rp, const uint16_t *of
                          : int(blk_start(rp, off, row0, off0, nb, rr, ja + 1)) - (BY - ra);
     int b = rb <= BY / 2 ? int(blk_start(rp, off, row0, off0, nb, rr, jb)) + rb
                          : int(blk_start(rp, off, row0, off0, nb, rr, jb + 1));
-    a = max(a, rs);
-    b = min(b, re);
+    a = imax(a, rs);
+    b = imin(b, re);
     lo = a;
-    hi = max(a, b);
+    hi = imax(a, b);
 }
 
 // Block-wide exclusive scan of values held two per thread (entries 2t, 2t+1): writes pre[0..n]

@@ -30,6 +30,27 @@ struct LevelGeo {
     int32_t toff0;
 };
 
+// Tile plans: per work item, the non-empty source segments of its staged patch (index range of one
+// row's elements) in the kernels' segment order, built once per APR on the host. For each item,
+// hdr = {first entry, count}; entries [first, first + count) hold {lo, meta}; pre[first + k] is the
+// number of elements of the item's entries before entry k (pre[first + count] = the total).
+struct PlanHdr {
+    int32_t first, count;
+};
+struct PlanEnt {
+    int32_t lo, meta;
+};
+struct PlanView {
+    const PlanHdr *hdr;
+    const PlanEnt *ent;
+    const int32_t *pre;
+};
+struct HostPlan {
+    std::vector<PlanHdr> hdr;
+    std::vector<PlanEnt> ent;
+    std::vector<int32_t> pre;
+};
+
 // Everything a kernel needs to walk the index (device pointers).
 struct DevLayout {
     const uint32_t *row_ptr;   // [R+1]
@@ -41,6 +62,8 @@ struct DevLayout {
     unsigned *err;
     int32_t l_min, l_max;
     LevelGeo geo[MAXL];
+    PlanView fplan[2];   // forward tiles (fwd_items), stencil radius 1 and 2
+    PlanView bplan[2];   // data-adjoint tiles (bwd_items), stencil radius 1 and 2
 };
 
 struct Item {  // a work item: level, tile (or row) coordinates, y block
@@ -60,11 +83,16 @@ struct HostIndex {
     std::vector<Item> tree_items;             // non-empty (l, z, x, yb) tree bricks, by level
     int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
     int64_t tree_level_begin[MAXL + 1] = {};
+    HostPlan fplan[2], bplan[2];              // tile plans (build_plans), radius 1 and 2
 };
 
 // Builds and validates the index from the host layout. Returns APR_OK or an error code; `msg`
 // receives a short reason on failure.
 apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
+
+// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu); false if a host
+// allocation failed.
+bool build_plans(HostIndex &X);
 
 // Record a short reason for the last failure on this thread (read by apr_last_error_message).
 void set_last_message(const char *msg);
@@ -101,5 +129,8 @@ struct apr_handle_s {
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
+    aprk::PlanHdr *d_plan_hdr[4] = {};   // tile plans: forward radius 1, 2; adjoint radius 1, 2
+    aprk::PlanEnt *d_plan_ent[4] = {};
+    int32_t *d_plan_pre[4] = {};
     size_t dev_bytes = 0;
 };

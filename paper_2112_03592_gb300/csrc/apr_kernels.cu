@@ -19,35 +19,13 @@
 
 #include "apr_device.cuh"
 #include "apr_internal.h"
+#include "apr_tile.cuh"
 
 namespace aprk {
 
 namespace {
 
 using namespace dev;
-
-constexpr int WIN = 8;                 // y cells per compute window
-constexpr int NWIN = BY / WIN;         // windows per interior row
-constexpr int NIR = TZ * TX;           // interior rows of a tile
-constexpr int NIW = NIR * NWIN;        // window slots of a tile
-static_assert(NIW == 2 * NT, "window slots are scanned two per thread");
-
-template <int R>
-struct Geo {
-    static constexpr int K = 2 * R + 1;
-    static constexpr int K3 = K * K * K;
-    static constexpr int NPAIR = K * K;                    // (dz, dx) pairs
-    static constexpr int PZ = TZ + 2 * R, PX = TX + 2 * R, PY = BY + 2 * R;
-    static constexpr int PYS = (PY + 3) / 4 * 4;           // row stride, 16-byte multiple
-    static constexpr int NROW = PZ * PX;
-    static constexpr int NSEG = 3 * NROW;                  // particle, tree, coarser-particle source per row
-    static constexpr int NCZ = ((TZ + R - 1) >> 1) + ((R + 1) >> 1) + 1;  // level-(l-1) rows per axis under a patch
-    static constexpr int NRSEG = 2 * NIR + NIR / 4;        // backward routing: particles, tree, coarser particles
-    static_assert(WIN + 2 * R <= 12, "a window's taps must fit three 16-byte loads");
-    static_assert((NWIN - 1) * WIN + 12 <= PYS, "window loads stay inside the row");
-    static_assert(NSEG <= 2 * NT && NROW + NRSEG <= 2 * NT, "segments are scanned two per thread");
-    static_assert(NCZ * NCZ <= NROW && PZ < 15 && PX < 15, "once-staged coarse rows: segment count, 4-bit row fields");
-};
 
 // Deterministic compaction of the windows w (0 <= w < NIW) with flag(w) into act[0..*nact).
 template <typename Flag>
@@ -60,6 +38,20 @@ __device__ __forceinline__ void compact_windows(Flag flag, unsigned short *act, 
     if (tid == 0) *nact = pre[NIW];
     block_sync();
 }
+
+// Loads y and value of element i of segment seg: tree nodes for segments of kind 1, particles
+// otherwise (kinds from the segments' meta words).
+struct MetaYVLoader {
+    using Slot = SlotYV;
+    const uint16_t *py, *ty;
+    const float *pv, *tv;
+    const int *meta;
+    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
+        const bool t = meta_kind(meta[seg]) == 1;
+        s.y = t ? int(ty[i]) : int(py[i]);
+        s.v = t ? tv[i] : pv[i];
+    }
+};
 
 // ------------------------------------------------------------------------------------------------
 // Shared-memory image of a staged forward tile.
@@ -89,7 +81,7 @@ struct PatchSmem {
 // y-block yb) and lists the active ones. zero_fill: cells no source covers hold 0 (the stencil
 // gradient reads every cell of a window), not stale shared memory.
 template <int R>
-__device__ void stage_patch(const DevLayout &L, const Item &it, const float *__restrict__ vals,
+__device__ void stage_patch(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
                             const float *__restrict__ tree, int bc, PatchSmem<R> &S, bool zero_fill = false) {
     using G = Geo<R>;
     const int tid = threadIdx.x;
@@ -105,75 +97,40 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, const float *__r
     if (zero_fill)
         for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // segment bounds, two per thread (entries 2t, 2t+1) for the scan. Segments [0, NROW): level-l
-    // particles of every patch row, [NROW, 2 NROW): level-l tree nodes, [2 NROW, 3 NROW): level-(l-1)
-    // particles. Away from the grid boundary each level-(l-1) row is staged once and written to the
-    // (up to 2 x 2) patch rows it covers (NCZ^2 segments, kind 3); tiles reaching outside the grid
-    // stage one coarser row per patch row (kind 2), which follows the reflection of every row.
-    const bool boundary = z0 - R < 0 || x0 - R < 0 || yw < 0 || z0 + TZ + R > g.dz || x0 + TX + R > g.dx ||
-                          yw + G::PY > g.dy;
-    int cnt[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int s = 2 * tid + h;
-        if (s >= G::NSEG) break;
-        const int kind = s / G::NROW, pr = s % G::NROW;
-        const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
-        int lo = 0, hi = 0;
-        if (kind == 2 && !boundary) {
-            // one level-(l-1) row (cz, cx) per segment; its fine rows 2cz + a, 2cx + b (a, b in {0, 1})
-            // sit at patch rows rz0 + a, rx0 + b (clipped to the patch)
-            int meta = 0;
-            if (pr < G::NCZ * G::NCZ && l > L.l_min) {
-                const LevelGeo gp = L.geo[l - 1];
-                const int cz = ((z0 - R) >> 1) + pr / G::NCZ, cx = ((x0 - R) >> 1) + pr % G::NCZ;
-                if (cz < gp.dz && cx < gp.dx)
-                    row_range(L.row_ptr, L.off, gp.row0, gp.off0, gp.nb, cz * gp.dx + cx, ylo >> 1, ((yhi - 1) >> 1) + 1,
-                              lo, hi);
-                meta = (2 * cz - (z0 - R) + 1) | ((2 * cx - (x0 - R) + 1) << 4) | (3 << 8);
-            }
-            S.seg_lo[s] = lo;
-            cnt[h] = hi - lo;
-            S.seg_meta[s] = meta;
-            continue;
-        }
-        int z = z0 - R + pr / G::PX, x = x0 - R + pr % G::PX;
-        const bool inside = z >= 0 && z < g.dz && x >= 0 && x < g.dx;
-        if (inside || bc == APR_BC_REFLECT) {
-            if (!inside) {
-                z = reflect_idx(z, g.dz);
-                x = reflect_idx(x, g.dx);
-            }
-            const int rr = z * g.dx + x;
-            if (kind == 0) {
-                row_range(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, ylo, yhi, lo, hi);
-            } else if (kind == 1) {
-                if (l < L.l_max) row_range(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, ylo, yhi, lo, hi);
-            } else if (l > L.l_min) {
-                const LevelGeo gp = L.geo[l - 1];
-                const int prr = (z >> 1) * gp.dx + (x >> 1);
-                row_range(L.row_ptr, L.off, gp.row0, gp.off0, gp.nb, prr, ylo >> 1, ((yhi - 1) >> 1) + 1, lo, hi);
-            }
-        }
-        S.seg_lo[s] = lo;
-        cnt[h] = hi - lo;
-        // interior row of a particle segment whose particles are targets (+1; 0: none)
-        const int a = pr / G::PX - R, b = pr % G::PX - R;
-        const int trow = (kind == 0 && a >= 0 && a < TZ && b >= 0 && b < TX && z0 + a < g.dz && x0 + b < g.dx)
-                             ? a * TX + b + 1 : 0;
-        S.seg_meta[s] = pr | (kind << 8) | (trow << 10);
+    // the tile's non-empty source segments (fwd_segment, listed once per APR in the tile plan). With
+    // zero boundary the segments of rows outside the grid are dropped and the rest rescanned.
+    const bool boundary = fwd_tile_at_boundary<R>(L, it);
+    const PlanView P = L.fplan[R - 1];
+    const PlanHdr hd = P.hdr[tile];
+    const int nseg = hd.count;
+    for (int k = tid; k < nseg; k += NT) {
+        const PlanEnt e = P.ent[hd.first + k];
+        S.seg_lo[k] = e.lo;
+        S.seg_meta[k] = e.meta;
     }
-    block_scan2(cnt[0], cnt[1], G::NSEG, S.pre, S.warp_tot);
+    if (bc == APR_BC_REFLECT || !boundary) {
+        for (int k = tid; k <= nseg; k += NT) S.pre[k] = P.pre[hd.first + k];
+        block_sync();
+    } else {
+        int cnt[2] = {0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * tid + h;
+            if (k < nseg && !(P.ent[hd.first + k].meta & META_REFL))
+                cnt[h] = P.pre[hd.first + k + 1] - P.pre[hd.first + k];
+        }
+        block_scan2(cnt[0], cnt[1], nseg, S.pre, S.warp_tot);
+    }
 
-    const YVLoader ld{L.y, L.ty, vals, tree, G::NROW, 2 * G::NROW};
-    for_each_element(S.seg_lo, S.pre, G::NSEG, S.segid, ld, [&](int seg, int i, SlotYV &s) {
+    const MetaYVLoader ld{L.y, L.ty, vals, tree, S.seg_meta};
+    for_each_element(S.seg_lo, S.pre, nseg, S.segid, ld, [&](int seg, int i, SlotYV &s) {
         const int meta = S.seg_meta[seg];
-        const int kind = (meta >> 8) & 3;
+        const int kind = meta_kind(meta);
         float *prow = S.patch + (meta & 255) * G::PYS;
         if (kind < 2) {
             const int pos = s.y - yw;
             if (pos >= 0 && pos < G::PY) prow[pos] = s.v;
-            const int trow = (meta >> 10) - 1;
+            const int trow = meta_trow(meta);
             const int yr = s.y - y0;
             if (trow >= 0 && yr >= 0 && yr < BY) {
                 // a target: level-l particle of an interior row inside y-block yb
@@ -374,12 +331,12 @@ struct Epilogue {
 // ------------------------------------------------------------------------------------------------
 // One forward tile with stencil radius R from a stack of radius RS >= R.
 template <int R, int RS>
-__device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, const float *__restrict__ vals,
+__device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
                                               const float *__restrict__ tree, const float *__restrict__ stencils,
                                               int bc, float *out, const Epilogue &epi, unsigned char *smem_raw) {
     PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
     load_taps<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w8);
-    stage_patch<R>(L, it, vals, tree, bc, S);
+    stage_patch<R>(L, it, tile, vals, tree, bc, S);
     windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
         const unsigned m = S.wmask[w];
         const int first = S.wfirst[w];
@@ -402,11 +359,11 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
     const Item it = items[blockIdx.x];
     if constexpr (R == 2) {
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_fwd_tile<1, 2>(L, it, vals, tree, stencils, bc, out, epi, smem_raw);
+            conv_fwd_tile<1, 2>(L, it, blockIdx.x, vals, tree, stencils, bc, out, epi, smem_raw);
             return;
         }
     }
-    conv_fwd_tile<R, R>(L, it, vals, tree, stencils, bc, out, epi, smem_raw);
+    conv_fwd_tile<R, R>(L, it, blockIdx.x, vals, tree, stencils, bc, out, epi, smem_raw);
 }
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
@@ -425,7 +382,7 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
     const Item it = items[blockIdx.x];
     const int n_levels = L.l_max - L.l_min + 1;
     load_taps<R>(stencils, it.l - L.l_min, false, S.w8);
-    stage_patch<R>(L, it, vals, tree, bc, S);
+    stage_patch<R>(L, it, blockIdx.x, vals, tree, bc, S);
     for (int a = 0; a < 3; ++a) {
         if (a > 0) {
             block_sync();
@@ -462,7 +419,7 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    stage_patch<R>(L, it, vals, tree, bc, S, true);
+    stage_patch<R>(L, it, blockIdx.x, vals, tree, bc, S, true);
     const int tid = threadIdx.x;
     const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
     float acc[G::K];
@@ -542,6 +499,7 @@ struct BwdSmem {
     unsigned rmask[G::NROW * 3];              // nonzero-gradient columns of every patch row
     int seg_lo[G::NROW + G::NRSEG];
     int pre[(G::NROW + G::NRSEG > NIW ? G::NROW + G::NRSEG : NIW) + 1];
+    unsigned short smeta[G::NROW + G::NRSEG];  // segment's index in its group (patch row, routing index)
     int warp_tot[NWARP + 1];
     unsigned long long need[NIR];
     int cpre[NIW + 1];                        // scratch of the window compaction
@@ -554,24 +512,25 @@ struct BwdSmem {
     int nact;
 };
 
-struct YLoader {
+// y of element i of routing segment seg (routing index q = q_of[seg]: tree nodes for NIR <= q < 2 NIR).
+struct RouteYLoader {
     using Slot = SlotYV;
     const uint16_t *py, *ty;
-    int t0, t1;
+    const unsigned short *q_of;
     __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
-        s.y = (seg >= t0 && seg < t1) ? int(ty[i]) : int(py[i]);
+        const int q = q_of[seg];
+        s.y = (q >= NIR && q < 2 * NIR) ? int(ty[i]) : int(py[i]);
         s.v = 0.f;
     }
 };
 
 // One data-adjoint tile with stencil radius R from a stack of radius RS >= R.
 template <int R, int RS>
-__device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Item &it,
+__device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Item &it, int tile,
                                                    const float *__restrict__ stencils, int bc,
                                                    const float *__restrict__ gout, float *__restrict__ gp,
                                                    float *__restrict__ gt, unsigned char *smem_raw) {
     using G = Geo<R>;
-    constexpr int NSG = G::NROW + G::NRSEG;
     BwdSmem<R> &S = *reinterpret_cast<BwdSmem<R> *>(smem_raw);
     const int l = it.l, tid = threadIdx.x;
     const LevelGeo g = L.geo[l];
@@ -584,57 +543,28 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(S.H)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < G::NROW * 3; i += NT) S.rmask[i] = 0u;
 
-    // segments: gradient rows (in-grid patch rows, no reflection: g is zero outside the grid), then the
-    // sources of the interior cells: particles and tree nodes of the interior rows in y-block yb, and
-    // the coarser particles of the interior (TZ/2 x TX/2 parent rows, parent y in [y0/2, y0/2+BY/2))
-    int cnt[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int s = 2 * tid + h;
-        if (s >= NSG) break;
-        int lo = 0, hi = 0;
-        if (s < G::NROW) {
-            const int z = z0 - R + s / G::PX, x = x0 - R + s % G::PX;
-            if (z >= 0 && z < g.dz && x >= 0 && x < g.dx) {
-                const int ylo = max(yw, 0), yhi = min(yw + G::PY, g.dy);
-                row_range(L.row_ptr, L.off, g.row0, g.off0, g.nb, z * g.dx + x, ylo, yhi, lo, hi);
-            }
-        } else {
-            const int q = s - G::NROW;
-            if (q < 2 * NIR) {
-                const int r = q % NIR;
-                const int z = z0 + r / TX, x = x0 + r % TX;
-                if (z < g.dz && x < g.dx) {
-                    const int rr = z * g.dx + x;
-                    if (q < NIR) {
-                        lo = int(pblock(L, g, rr, it.yb));
-                        hi = int(pblock(L, g, rr, it.yb + 1));
-                    } else if (l < L.l_max) {
-                        lo = int(tblock(L, g, rr, it.yb));
-                        hi = int(tblock(L, g, rr, it.yb + 1));
-                    }
-                }
-            } else if (l > L.l_min) {
-                const int r = q - 2 * NIR;
-                const LevelGeo gq = L.geo[l - 1];
-                const int pz = z0 / 2 + r / (TX / 2), px = x0 / 2 + r % (TX / 2);
-                if (pz < gq.dz && px < gq.dx)
-                    row_range(L.row_ptr, L.off, gq.row0, gq.off0, gq.nb, pz * gq.dx + px, y0 / 2,
-                              min(y0 / 2 + BY / 2, gq.dy), lo, hi);
-            }
-        }
-        S.seg_lo[s] = lo;
-        cnt[h] = hi - lo;
+    // the tile's non-empty segments (bwd_segment, listed once per APR in the tile plan): n1 gradient
+    // rows (in-grid patch rows, no reflection: g is zero outside the grid), then n2 sources of the
+    // interior cells (particles and tree nodes of the interior rows in y-block yb, coarser particles)
+    const PlanView P = L.bplan[R - 1];
+    const PlanHdr hd = P.hdr[tile];
+    const int n1 = hd.count & 0xffff, n2 = hd.count >> 16;
+    for (int k = tid; k < n1 + n2; k += NT) {
+        const PlanEnt e = P.ent[hd.first + k];
+        S.seg_lo[k] = e.lo;
+        S.smeta[k] = (unsigned short)e.meta;
     }
-    block_scan2(cnt[0], cnt[1], NSG, S.pre, S.warp_tot);
+    for (int k = tid; k <= n1 + n2; k += NT) S.pre[k] = P.pre[hd.first + k];
+    block_sync();
 
     // gradient patch and its occupancy masks (the first NROW segments)
     const YVLoader gl{L.y, L.ty, gout, gout, 0, 0};
-    for_each_element(S.seg_lo, S.pre, G::NROW, S.segid, gl, [&](int seg, int, SlotYV &s) {
+    for_each_element(S.seg_lo, S.pre, n1, S.segid, gl, [&](int seg, int, SlotYV &s) {
         const int pos = s.y - yw;
         if (pos >= 0 && pos < G::PY) {
-            S.gpatch[seg * G::PYS + pos] = s.v;
-            atomicOr(&S.rmask[seg * 3 + (pos >> 5)], 1u << (pos & 31));
+            const int row = S.smeta[seg];
+            S.gpatch[row * G::PYS + pos] = s.v;
+            atomicOr(&S.rmask[row * 3 + (pos >> 5)], 1u << (pos & 31));
         }
     });
     block_sync();
@@ -776,18 +706,18 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         }
         block_sync();
     }
-    // routing: the sources of the interior cells, segments rbase .. rbase + NRSEG of the first scan
-    const int rbase = G::NROW;
-    const YLoader rl{L.y, L.ty, NIR, 2 * NIR};
-    for_each_element(S.seg_lo + rbase, S.pre + rbase, G::NRSEG, S.segid, rl, [&](int seg, int i, SlotYV &s) {
-        if (seg < NIR) {
-            const float h = S.H[seg * BY + (s.y - y0)];
+    // routing: the sources of the interior cells, plan entries n1 .. n1 + n2 (routing index q)
+    const RouteYLoader rl{L.y, L.ty, S.smeta + n1};
+    for_each_element(S.seg_lo + n1, S.pre + n1, n2, S.segid, rl, [&](int seg, int i, SlotYV &s) {
+        const int q = S.smeta[n1 + seg];
+        if (q < NIR) {
+            const float h = S.H[q * BY + (s.y - y0)];
             if (h != 0.f) atomicAdd(&gp[i], h);
-        } else if (seg < 2 * NIR) {
-            const float h = S.H[(seg - NIR) * BY + (s.y - y0)];
+        } else if (q < 2 * NIR) {
+            const float h = S.H[(q - NIR) * BY + (s.y - y0)];
             if (h != 0.f) gt[i] = h;
         } else {
-            const int r = seg - 2 * NIR;
+            const int r = q - 2 * NIR;
             const int j0 = 2 * s.y - y0;  // first level-l cell column of the coarser particle
             if (j0 < 0 || j0 >= BY) return;
             const int pa = r / (TX / 2), pb = r % (TX / 2);
@@ -815,11 +745,11 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     const Item it = items[blockIdx.x];
     if constexpr (R == 2) {
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_bwd_data_tile<1, 2>(L, it, stencils, bc, gout, gp, gt, smem_raw);
+            conv_bwd_data_tile<1, 2>(L, it, blockIdx.x, stencils, bc, gout, gp, gt, smem_raw);
             return;
         }
     }
-    conv_bwd_data_tile<R, R>(L, it, stencils, bc, gout, gp, gt, smem_raw);
+    conv_bwd_data_tile<R, R>(L, it, blockIdx.x, stencils, bc, gout, gp, gt, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -1,0 +1,116 @@
+// Tile plans (host): for every forward and data-adjoint work item and both stencil radii, the
+// non-empty source segments of the item's patch, listed once per APR so that the kernels read them
+// with one coalesced load instead of evaluating every row's offsets (and a block scan) per call.
+// The segments are those of fwd_segment / bwd_segment (apr_tile.cuh), evaluated here on the host
+// copy of the index.
+#include <thread>
+#include <vector>
+
+#include "apr_tile.cuh"
+
+namespace aprk {
+namespace {
+
+using namespace dev;
+
+DevLayout host_view(const HostIndex &X) {
+    DevLayout L{};
+    L.row_ptr = X.row_ptr.data();
+    L.y = X.y.data();
+    L.off = X.off.data();
+    L.trow_ptr = X.trow_ptr.data();
+    L.ty = X.ty.data();
+    L.toff = X.toff.data();
+    L.l_min = X.l_min;
+    L.l_max = X.l_max;
+    for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
+    return L;
+}
+
+// Appends one item's entries: pre holds the running element count; the slot after the last entry
+// holds the item's total.
+struct Appender {
+    HostPlan &P;
+    int first = 0, total = 0;
+    void begin() {
+        first = int(P.ent.size());
+        total = 0;
+    }
+    void add(int lo, int hi, int meta) {
+        if (hi <= lo) return;
+        P.ent.push_back(PlanEnt{lo, meta});
+        P.pre.push_back(total);
+        total += hi - lo;
+    }
+    int end() {
+        const int n = int(P.ent.size()) - first;
+        P.ent.push_back(PlanEnt{0, 0});
+        P.pre.push_back(total);
+        return n;
+    }
+};
+
+template <int R>
+void fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+    using G = Geo<R>;
+    P.hdr.assign(items.size(), PlanHdr{0, 0});
+    Appender ap{P};
+    for (size_t t = 0; t < items.size(); ++t) {
+        const Item &it = items[t];
+        const bool bnd = fwd_tile_at_boundary<R>(L, it);
+        ap.begin();
+        for (int s = 0; s < G::NSEG; ++s) {
+            int lo, hi, meta;
+            fwd_segment<R>(L, it, bnd, s, lo, hi, meta);
+            ap.add(lo, hi, meta);
+        }
+        P.hdr[t] = PlanHdr{ap.first, ap.end()};
+    }
+}
+
+// Adjoint items: count = n1 | n2 << 16 (gradient rows, then routing segments); meta = the segment's
+// index within its group (patch row, routing index q).
+template <int R>
+void bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+    using G = Geo<R>;
+    P.hdr.assign(items.size(), PlanHdr{0, 0});
+    Appender ap{P};
+    for (size_t t = 0; t < items.size(); ++t) {
+        const Item &it = items[t];
+        ap.begin();
+        int n1 = 0;
+        for (int s = 0; s < G::NROW + G::NRSEG; ++s) {
+            int lo, hi;
+            bwd_segment<R>(L, it, s, lo, hi);
+            const int before = int(P.ent.size());
+            ap.add(lo, hi, s < G::NROW ? s : s - G::NROW);
+            if (s < G::NROW && int(P.ent.size()) > before) ++n1;
+        }
+        const int n = ap.end();
+        P.hdr[t] = PlanHdr{ap.first, n1 | ((n - n1) << 16)};
+    }
+}
+
+}  // namespace
+
+bool build_plans(HostIndex &X) {
+    const DevLayout L = host_view(X);
+    bool ok[4] = {true, true, true, true};
+    auto guarded = [&ok](int i, auto f) {
+        return [&ok, i, f] {
+            try {
+                f();
+            } catch (...) {  // host allocation failure: reported by the caller
+                ok[i] = false;
+            }
+        };
+    };
+    std::thread t[4] = {std::thread(guarded(0, [&] { fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
+                        std::thread(guarded(1, [&] { fwd_plan<2>(L, X.fwd_items, X.fplan[1]); })),
+                        std::thread(guarded(2, [&] { bwd_plan<1>(L, X.bwd_items, X.bplan[0]); })),
+                        std::thread(guarded(3, [&] { bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }))};
+    for (auto &th : t) th.join();
+    return ok[0] && ok[1] && ok[2] && ok[3];
+}
+
+}  // namespace aprk
