@@ -3,7 +3,6 @@
 
 #include <cstdio>
 #include <cstring>
-#include <exception>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -52,7 +51,6 @@ void free_device(apr_handle_s *h) {
     for (int i = 0; i < 4; ++i) {
         if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
         if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
-        if (h->d_plan_pre[i]) cudaFree(h->d_plan_pre[i]);
     }
 }
 
@@ -126,16 +124,12 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
     h->host_only = (flags & APR_HOST_ONLY) != 0;
     if (!h->host_only) {
         (void)stream;  // uploads are synchronous: the index is built once
-        bool plans_ok = false;
-        try {
-            plans_ok = build_plans(h->X);
-        } catch (const std::exception &) {
-            plans_ok = false;
-        }
-        if (!plans_ok) {
-            snprintf(g_last_msg, sizeof(g_last_msg), "host allocation failed (tile plans)");
+        const apr_status_t pst = build_plans(h->X);
+        if (pst != APR_OK) {
+            snprintf(g_last_msg, sizeof(g_last_msg), "%s", pst == APR_ERR_OOM ? "host allocation failed (tile plans)"
+                                                                                : "tile with too many staged elements");
             delete h;
-            return APR_ERR_OOM;
+            return pst;
         }
         const HostIndex &X = h->X;
         cudaError_t e = cudaSuccess;
@@ -154,7 +148,6 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
             const HostPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
             e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
             if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
-            if (e == cudaSuccess) e = upload(&h->d_plan_pre[i], P.pre.data(), P.pre.size(), b);
         }
         if (e == cudaSuccess) {
             e = cudaMalloc(reinterpret_cast<void **>(&h->d_err), sizeof(unsigned));
@@ -187,8 +180,8 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         L.l_max = X.l_max;
         for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
         for (int i = 0; i < 2; ++i) {
-            L.fplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i], h->d_plan_pre[i]};
-            L.bplan[i] = PlanView{h->d_plan_hdr[2 + i], h->d_plan_ent[2 + i], h->d_plan_pre[2 + i]};
+            L.fplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i]};
+            L.bplan[i] = PlanView{h->d_plan_hdr[2 + i], h->d_plan_ent[2 + i]};
         }
         // the plans live on the device now; the host copies are not needed again
         for (int i = 0; i < 2; ++i) {

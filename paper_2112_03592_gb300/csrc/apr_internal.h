@@ -32,23 +32,23 @@ struct LevelGeo {
 
 // Tile plans: per work item, the non-empty source segments of its staged patch (index range of one
 // row's elements) in the kernels' segment order, built once per APR on the host. For each item,
-// hdr = {first entry, count}; entries [first, first + count) hold {lo, meta}; pre[first + k] is the
-// number of elements of the item's entries before entry k (pre[first + count] = the total).
+// hdr = {first entry, count}; entries [first, first + count) hold {lo, meta, pre}, pre = the number
+// of elements of the item's entries before this one; entry first + count holds the total in pre.
 struct PlanHdr {
     int32_t first, count;
 };
 struct PlanEnt {
-    int32_t lo, meta;
+    int32_t lo;
+    uint16_t meta, pre;
 };
+static_assert(sizeof(PlanEnt) == 8, "plan entries are 8-byte words");
 struct PlanView {
     const PlanHdr *hdr;
     const PlanEnt *ent;
-    const int32_t *pre;
 };
 struct HostPlan {
     std::vector<PlanHdr> hdr;
     std::vector<PlanEnt> ent;
-    std::vector<int32_t> pre;
 };
 
 // Everything a kernel needs to walk the index (device pointers).
@@ -90,9 +90,9 @@ struct HostIndex {
 // receives a short reason on failure.
 apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
 
-// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu); false if a host
-// allocation failed.
-bool build_plans(HostIndex &X);
+// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu). Returns APR_OK,
+// APR_ERR_OOM (host allocation) or APR_ERR_UNSUPPORTED (a tile with 65536 or more staged elements).
+apr_status_t build_plans(HostIndex &X);
 
 // Record a short reason for the last failure on this thread (read by apr_last_error_message).
 void set_last_message(const char *msg);
@@ -131,6 +131,5 @@ struct apr_handle_s {
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
     aprk::PlanHdr *d_plan_hdr[4] = {};   // tile plans: forward radius 1, 2; adjoint radius 1, 2
     aprk::PlanEnt *d_plan_ent[4] = {};
-    int32_t *d_plan_pre[4] = {};
     size_t dev_bytes = 0;
 };

@@ -103,21 +103,26 @@ __device__ void stage_patch(const DevLayout &L, const Item &it, int tile, const 
     const PlanView P = L.fplan[R - 1];
     const PlanHdr hd = P.hdr[tile];
     const int nseg = hd.count;
-    for (int k = tid; k < nseg; k += NT) {
+    const bool rescan = bc != APR_BC_REFLECT && boundary;
+    for (int k = tid; k <= nseg; k += NT) {
         const PlanEnt e = P.ent[hd.first + k];
-        S.seg_lo[k] = e.lo;
-        S.seg_meta[k] = e.meta;
+        if (k < nseg) {
+            S.seg_lo[k] = e.lo;
+            S.seg_meta[k] = with_trow<R>(g, it, e.meta);
+        }
+        if (!rescan) S.pre[k] = e.pre;
     }
-    if (bc == APR_BC_REFLECT || !boundary) {
-        for (int k = tid; k <= nseg; k += NT) S.pre[k] = P.pre[hd.first + k];
+    if (!rescan) {
         block_sync();
     } else {
         int cnt[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * tid + h;
-            if (k < nseg && !(P.ent[hd.first + k].meta & META_REFL))
-                cnt[h] = P.pre[hd.first + k + 1] - P.pre[hd.first + k];
+            if (k < nseg) {
+                const PlanEnt e = P.ent[hd.first + k];
+                if (!(e.meta & META_REFL)) cnt[h] = int(P.ent[hd.first + k + 1].pre) - int(e.pre);
+            }
         }
         block_scan2(cnt[0], cnt[1], nseg, S.pre, S.warp_tot);
     }
@@ -549,12 +554,14 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     const PlanView P = L.bplan[R - 1];
     const PlanHdr hd = P.hdr[tile];
     const int n1 = hd.count & 0xffff, n2 = hd.count >> 16;
-    for (int k = tid; k < n1 + n2; k += NT) {
+    for (int k = tid; k <= n1 + n2; k += NT) {
         const PlanEnt e = P.ent[hd.first + k];
-        S.seg_lo[k] = e.lo;
-        S.smeta[k] = (unsigned short)e.meta;
+        if (k < n1 + n2) {
+            S.seg_lo[k] = e.lo;
+            S.smeta[k] = e.meta;
+        }
+        S.pre[k] = e.pre;
     }
-    for (int k = tid; k <= n1 + n2; k += NT) S.pre[k] = P.pre[hd.first + k];
     block_sync();
 
     // gradient patch and its occupancy masks (the first NROW segments)

@@ -28,30 +28,31 @@ DevLayout host_view(const HostIndex &X) {
 }
 
 // Appends one item's entries: pre holds the running element count; the slot after the last entry
-// holds the item's total.
+// holds the item's total. Totals above 65535 (not reachable with 8x8-row tiles and 64-cell y-blocks:
+// at most 3 (8 + 2R)^2 rows of at most 2 BY + 2R elements) set `overflow`.
 struct Appender {
     HostPlan &P;
     int first = 0, total = 0;
+    bool overflow = false;
     void begin() {
         first = int(P.ent.size());
         total = 0;
     }
     void add(int lo, int hi, int meta) {
         if (hi <= lo) return;
-        P.ent.push_back(PlanEnt{lo, meta});
-        P.pre.push_back(total);
+        P.ent.push_back(PlanEnt{lo, uint16_t(meta), uint16_t(total)});
         total += hi - lo;
+        if (total > 65535) overflow = true;
     }
     int end() {
         const int n = int(P.ent.size()) - first;
-        P.ent.push_back(PlanEnt{0, 0});
-        P.pre.push_back(total);
+        P.ent.push_back(PlanEnt{0, 0, uint16_t(total)});
         return n;
     }
 };
 
 template <int R>
-void fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+bool fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
     using G = Geo<R>;
     P.hdr.assign(items.size(), PlanHdr{0, 0});
     Appender ap{P};
@@ -66,12 +67,13 @@ void fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
         }
         P.hdr[t] = PlanHdr{ap.first, ap.end()};
     }
+    return !ap.overflow;
 }
 
 // Adjoint items: count = n1 | n2 << 16 (gradient rows, then routing segments); meta = the segment's
 // index within its group (patch row, routing index q).
 template <int R>
-void bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
     using G = Geo<R>;
     P.hdr.assign(items.size(), PlanHdr{0, 0});
     Appender ap{P};
@@ -89,28 +91,31 @@ void bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
         const int n = ap.end();
         P.hdr[t] = PlanHdr{ap.first, n1 | ((n - n1) << 16)};
     }
+    return !ap.overflow;
 }
 
 }  // namespace
 
-bool build_plans(HostIndex &X) {
+apr_status_t build_plans(HostIndex &X) {
     const DevLayout L = host_view(X);
-    bool ok[4] = {true, true, true, true};
-    auto guarded = [&ok](int i, auto f) {
-        return [&ok, i, f] {
+    apr_status_t st[4] = {APR_OK, APR_OK, APR_OK, APR_OK};
+    auto guarded = [&st](int i, auto f) {
+        return [&st, i, f] {
             try {
-                f();
-            } catch (...) {  // host allocation failure: reported by the caller
-                ok[i] = false;
+                if (!f()) st[i] = APR_ERR_UNSUPPORTED;
+            } catch (...) {  // host allocation failure
+                st[i] = APR_ERR_OOM;
             }
         };
     };
-    std::thread t[4] = {std::thread(guarded(0, [&] { fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
-                        std::thread(guarded(1, [&] { fwd_plan<2>(L, X.fwd_items, X.fplan[1]); })),
-                        std::thread(guarded(2, [&] { bwd_plan<1>(L, X.bwd_items, X.bplan[0]); })),
-                        std::thread(guarded(3, [&] { bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }))};
+    std::thread t[4] = {std::thread(guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
+                        std::thread(guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); })),
+                        std::thread(guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); })),
+                        std::thread(guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }))};
     for (auto &th : t) th.join();
-    return ok[0] && ok[1] && ok[2] && ok[3];
+    for (apr_status_t s : st)
+        if (s != APR_OK) return s;
+    return APR_OK;
 }
 
 }  // namespace aprk

@@ -30,15 +30,26 @@ struct Geo {
     static_assert((NWIN - 1) * WIN + 12 <= PYS, "window loads stay inside the row");
     static_assert(NSEG <= 2 * NT && NROW + NRSEG <= 2 * NT, "segments are scanned two per thread");
     static_assert(NCZ * NCZ <= NROW && PZ < 15 && PX < 15, "once-staged coarse rows: segment count, 4-bit row fields");
-    static_assert(NROW < 256 && NIR < 127, "meta fields: 8-bit patch row, 7-bit interior row");
+    static_assert(NROW < 256 && NIR < 127 && NROW + NRSEG < 65536, "meta fields: 8-bit patch row, 7-bit interior row");
 };
 
-// meta of a forward segment of kinds 0-2: patch row | kind << 8 | (interior row + 1) << 10, plus
-// META_REFL if the patch row lies outside the grid (the segment holds the reflected row; with zero
-// boundary it is empty). Kind 3: (first covered patch row z + 1) | (x + 1) << 4 | 3 << 8.
-constexpr int META_REFL = 1 << 20;
+// meta of a forward segment of kinds 0-2: patch row | kind << 8, plus META_REFL if the patch row lies
+// outside the grid (the segment holds the reflected row; with zero boundary it is empty); kind 3:
+// (first covered patch row z + 1) | (x + 1) << 4 | 3 << 8. These 11 bits are what a plan stores;
+// with_trow adds (interior row + 1) << 11 for the particle segments of interior rows.
+constexpr int META_REFL = 1 << 10;
 __host__ __device__ __forceinline__ int meta_kind(int meta) { return (meta >> 8) & 3; }
-__host__ __device__ __forceinline__ int meta_trow(int meta) { return ((meta >> 10) & 127) - 1; }
+__host__ __device__ __forceinline__ int meta_trow(int meta) { return ((meta >> 11) & 127) - 1; }
+
+template <int R>
+__host__ __device__ __forceinline__ int with_trow(const LevelGeo &g, const Item &it, int meta) {
+    using G = Geo<R>;
+    if (meta_kind(meta) != 0) return meta;
+    const int pr = meta & 255;
+    const int a = pr / G::PX - R, b = pr % G::PX - R;
+    const bool target = a >= 0 && a < TZ && b >= 0 && b < TX && it.a * TZ + a < g.dz && it.b * TX + b < g.dx;
+    return target ? meta | ((a * TX + b + 1) << 11) : meta;
+}
 
 // Whether the forward patch of item it (rows z0-R .. z0+TZ+R, x likewise, y y0-R .. y0+BY+R) reaches
 // outside the level grid.
@@ -96,11 +107,7 @@ __host__ __device__ inline void fwd_segment(const DevLayout &L, const Item &it, 
         const int prr = (z >> 1) * gp.dx + (x >> 1);
         row_range(L.row_ptr, L.off, gp.row0, gp.off0, gp.nb, prr, ylo >> 1, ((yhi - 1) >> 1) + 1, lo, hi);
     }
-    // interior row of a particle segment whose particles are targets (+1; 0: none)
-    const int a = pr / G::PX - R, b = pr % G::PX - R;
-    const int trow = (kind == 0 && a >= 0 && a < TZ && b >= 0 && b < TX && z0 + a < g.dz && x0 + b < g.dx)
-                         ? a * TX + b + 1 : 0;
-    meta = pr | (kind << 8) | (trow << 10) | (inside ? 0 : META_REFL);
+    meta = pr | (kind << 8) | (inside ? 0 : META_REFL);
 }
 
 // Segment s of the data-adjoint tile of item it. [0, NROW): gradient rows, the level-l particles of
