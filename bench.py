@@ -102,7 +102,8 @@ class ClockSampler:
                 else "warm-up and timed region (timed region shorter than the 50 ms sampling period)"}
 
 
-TRAFFIC_SOURCES = ["paper_2112_03592_gb300/csrc/apr_kernels.cu", "paper_2112_03592_gb300/csrc/apr_device.cuh"]
+TRAFFIC_SOURCES = ["paper_2112_03592_gb300/csrc/apr_kernels.cu", "paper_2112_03592_gb300/csrc/apr_device.cuh",
+                   "paper_2112_03592_gb300/csrc/apr_tile.cuh", "paper_2112_03592_gb300/csrc/apr_plan.cu"]
 
 
 def kernel_source_hash():
