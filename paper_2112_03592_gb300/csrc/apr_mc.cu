@@ -232,19 +232,23 @@ struct FeatStage {
     unsigned short segid[SEGID_CAP];
 };
 
-// Fills the patch with u_l (Sec. 3.5) for the cells the sub-tile's targets read: level-l particles,
-// level-l tree nodes and level-(l-1) particles (each covering two cells per axis), reflected or
-// zero outside the grid. Segment s = kind * NPROW + patch row.
-__device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
-                               FeatStage &S) {
+// Staging of the feature patch with u_l (Sec. 3.5) for the cells the sub-tile's targets read:
+// level-l particles, level-l tree nodes and level-(l-1) particles (each covering two cells per
+// axis), reflected or zero outside the grid. Segment s = kind * NPROW + patch row. All patch rows
+// inside the grid: every coarser row is staged once (kind-2 segments then index the NCZM x NCZM
+// level-(l-1) rows under the patch instead of the patch rows).
+__device__ __forceinline__ bool sub_inner(const Sub &s) {
+    return s.z0 >= 1 && s.x0 >= 1 && s.z0 + SZ + 1 <= s.g.dz && s.x0 + SX + 1 <= s.g.dx;
+}
+
+// Segment bounds: writes seg_lo, returns the two counts of this thread's segments (2t, 2t+1) for the
+// scan; no barrier.
+__device__ __forceinline__ void feature_segments(const DevLayout &L, const Sub &s, int bc, FeatStage &S, int cnt[2]) {
     const int tid = threadIdx.x;
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
     const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
-    // all patch rows inside the grid: every coarser row is staged once (kind-2 segments then index the
-    // NCZM x NCZM level-(l-1) rows under the patch instead of the patch rows)
-    const bool inner = s.z0 >= 1 && s.x0 >= 1 && s.z0 + SZ + 1 <= s.g.dz && s.x0 + SX + 1 <= s.g.dx;
-    int cnt[2];
+    const bool inner = sub_inner(s);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int sg = 2 * tid + h;
@@ -275,7 +279,15 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
             cnt[h] = hi - lo;
         }
     }
-    block_scan2(cnt[0], cnt[1], NSEG_F, S.pre, S.warp_tot);
+}
+
+// Element loads and patch writes after the segment scan (S.pre); ends with a block barrier.
+__device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
+                                 FeatStage &S) {
+    const int tid = threadIdx.x;
+    const int ylo = s.y0 - 1;
+    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
+    const bool inner = sub_inner(s);
     const FeatLoader loader{L.y, L.ty, vals, tree};
     for_each_element(S.seg_lo, S.pre, NSEG_F, S.segid, loader, [&](int sg, int, const McSlot &sl) {
         const int kind = sg / NPROW, pr = sg - kind * NPROW;
@@ -339,6 +351,14 @@ __device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *va
     block_sync();
 }
 
+__device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
+                               FeatStage &S) {
+    int cnt[2];
+    feature_segments(L, s, bc, S, cnt);
+    block_scan2(cnt[0], cnt[1], NSEG_F, S.pre, S.warp_tot);
+    feature_elements(L, s, vals, tree, bc, S);
+}
+
 // Target list of the sub-tile: the level-l particles of its interior, in particle order.
 struct Targets {
     int idx[MAXT];
@@ -346,7 +366,8 @@ struct Targets {
     int row_lo[NIROW], row_base[NIROW + 1];
 };
 
-__device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
+// Row offsets of the targets (warp 0; no barrier).
+__device__ __forceinline__ void target_rows(const DevLayout &L, const Sub &s, Targets &T) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         int lo = 0, cnt = 0;
@@ -370,7 +391,11 @@ __device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
         }
         if (lane == NIROW - 1) T.row_base[NIROW] = incl;
     }
-    block_sync();
+}
+
+// Target indices and patch cells from the row offsets (after a barrier); ends with a barrier.
+__device__ __forceinline__ void target_fill(const DevLayout &L, const Sub &s, Targets &T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < NIROW; r += NWARP) {
         const int iz = r / SX, ix = r % SX;
         const int b = T.row_base[r], n = T.row_base[r + 1] - b;
@@ -380,8 +405,14 @@ __device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
             T.cell[b + j] = (unsigned short)(((iz + 1) * PX + ix + 1) * PY + int(L.y[i]) - s.y0 + 1);
         }
     }
-    const int n = T.row_base[NIROW];
     block_sync();
+}
+
+__device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
+    target_rows(L, s, T);
+    block_sync();
+    const int n = T.row_base[NIROW];
+    target_fill(L, s, T);
     return n;
 }
 
@@ -402,11 +433,23 @@ __global__ void mc_weight_layout_kernel(const uint16_t *__restrict__ W, int n_le
     }
 }
 
-// One level's operand-layout weights (13 824 contiguous bytes) into shared memory.
-__device__ void load_weights(const uint16_t *wl, int lev, unsigned char *wsm) {
+// One level's operand-layout weights (13 824 contiguous bytes) into shared memory, in two halves: the
+// loads into registers (four 16-byte words per thread) early, the stores into shared memory later,
+// so the loads' latency overlaps other work.
+constexpr int WV = NTAP * WTAP / 16;  // 16-byte words of one level's weights
+static_assert(WV <= 4 * NT, "four weight words per thread");
+
+__device__ __forceinline__ void preload_weights(const uint16_t *wl, int lev, uint4 (&w)[4]) {
     const uint4 *src = reinterpret_cast<const uint4 *>(wl + size_t(lev) * MC * MC * NTAP);
-    uint4 *dst = reinterpret_cast<uint4 *>(wsm);
-    for (int i = threadIdx.x; i < NTAP * WTAP / 16; i += NT) dst[i] = src[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (threadIdx.x + k * NT < WV) w[k] = src[threadIdx.x + k * NT];
+}
+
+__device__ __forceinline__ void store_weights(const uint4 (&w)[4], unsigned char *wsm) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (threadIdx.x + k * NT < WV) reinterpret_cast<uint4 *>(wsm)[threadIdx.x + k * NT] = w[k];
     fence_async_smem();
 }
 
@@ -550,10 +593,19 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Sub s;
     if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
-    const int nt = list_targets(L, s, S.tg);
+    // the level's weights, the feature segments' and the targets' row offsets are loaded in the same
+    // round (the weights are held in registers until the patch is staged)
+    uint4 wreg[4];
+    preload_weights(W, s.l - L.l_min, wreg);
+    int cnt[2];
+    feature_segments(L, s, bc, S.st, cnt);
+    target_rows(L, s, S.tg);
+    block_scan2(cnt[0], cnt[1], NSEG_F, S.st.pre, S.st.warp_tot);
+    const int nt = S.tg.row_base[NIROW];
     if (nt == 0) return;
-    load_weights(W, s.l - L.l_min, S.w);
-    stage_features(L, s, vals, tree, bc, S.st);
+    target_fill(L, s, S.tg);
+    feature_elements(L, s, vals, tree, bc, S.st);
+    store_weights(wreg, S.w);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
     fence_async_smem();
@@ -667,6 +719,10 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Sub s;
     if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
+    // the level's (transposed) weights are loaded now and held in registers until the destination
+    // list is known, so their latency overlaps the staging
+    uint4 wreg[4];
+    preload_weights(W, s.l - L.l_min, wreg);
     const bool reflect = bc == APR_BC_REFLECT;
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);  // gradient rows: y range of the patch
@@ -801,7 +857,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     block_sync();
     const int n1 = S.n1, nn = S.nn;
     if (n1 + nn == 0) return;
-    load_weights(W, s.l - L.l_min, S.w);
+    store_weights(wreg, S.w);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
     fence_async_smem();
