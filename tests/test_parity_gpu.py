@@ -75,6 +75,9 @@ CASES = {
     "all_max": lambda: S.uniform_level_apr((9, 17, 70), 7, l_min=2),
     "uniform_coarse": lambda: S.uniform_level_apr((32, 32, 32), 3, l_min=3),
     "tiny": lambda: S.random_balanced_apr((2, 3, 5), 0, seed=9, p_fine=0.3),
+    "single": lambda: S.uniform_level_apr((1, 1, 1), 0, l_min=0),
+    "row": lambda: S.random_balanced_apr((1, 1, 200), 0, seed=13, p_fine=0.05),
+    "plane": lambda: S.random_balanced_apr((1, 37, 90), 1, seed=14, p_fine=0.03),
 }
 
 
@@ -106,6 +109,19 @@ def test_convolve_matches_oracle(case, k, bc, mode):
         assert_rel(got, ref)
 
 
+@pytest.mark.parametrize("k", [3, 5])
+def test_single_particle_closed_form(k):
+    # a 1-cell grid reflects every neighbour onto the cell itself: out = v * sum(w); zero boundary
+    # keeps only the centre tap
+    apr = CASES["single"]()
+    w = np.random.default_rng(k).normal(size=(1, k ** 3)).astype(np.float32)
+    v = float(apr.values[0])
+    for bc, ref in ((G.APR_BC_REFLECT, v * float(w.astype(np.float64).sum())),
+                    (G.APR_BC_ZERO, v * float(w[0, k ** 3 // 2]))):
+        _, _, _, out = gpu_forward(apr, w, k, bc)
+        assert abs(float(out.cpu()[0]) - ref) <= 1e-5 * max(abs(ref), 1e-30) + 1e-6 * abs(v) * float(np.abs(w).sum())
+
+
 def test_constant_image_stays_constant():
     apr = S.random_balanced_apr((24, 20, 130), 1, seed=4, values="const")
     for k in (3, 5):
@@ -115,7 +131,7 @@ def test_constant_image_stays_constant():
         assert_rel(out.cpu().numpy(), np.full(out.numel(), 7.25))
 
 
-@pytest.mark.parametrize("case", ["blob64", "rand_ragged", "rand_thin", "tiny"])
+@pytest.mark.parametrize("case", ["blob64", "rand_ragged", "rand_thin", "tiny", "single", "row", "plane"])
 @pytest.mark.parametrize("k", [3, 5])
 @pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
 @pytest.mark.parametrize("mode", ["random", "restricted", "mixed_shell"])
