@@ -48,7 +48,7 @@ void free_device(apr_handle_s *h) {
                     h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 6; ++i) {
         if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
         if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
     }
@@ -144,8 +144,8 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-            const HostPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+            const HostPlan &P = i < 2 ? X.fplan[i] : i < 4 ? X.bplan[i - 2] : i == 4 ? X.mcfplan : X.mcbplan;
             e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
             if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
         }
@@ -183,11 +183,15 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
             L.fplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i]};
             L.bplan[i] = PlanView{h->d_plan_hdr[2 + i], h->d_plan_ent[2 + i]};
         }
+        L.mcfplan = PlanView{h->d_plan_hdr[4], h->d_plan_ent[4]};
+        L.mcbplan = PlanView{h->d_plan_hdr[5], h->d_plan_ent[5]};
         // the plans live on the device now; the host copies are not needed again
         for (int i = 0; i < 2; ++i) {
             h->X.fplan[i] = HostPlan{};
             h->X.bplan[i] = HostPlan{};
         }
+        h->X.mcfplan = HostPlan{};
+        h->X.mcbplan = HostPlan{};
     }
     *out = h;
     return APR_OK;

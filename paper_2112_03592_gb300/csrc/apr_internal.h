@@ -64,6 +64,8 @@ struct DevLayout {
     LevelGeo geo[MAXL];
     PlanView fplan[2];   // forward tiles (fwd_items), stencil radius 1 and 2
     PlanView bplan[2];   // data-adjoint tiles (bwd_items), stencil radius 1 and 2
+    PlanView mcfplan;    // multi-channel feature patches of the sub-tiles of fwd_items
+    PlanView mcbplan;    // multi-channel data-adjoint sub-tiles of bwd_items
 };
 
 struct Item {  // a work item: level, tile (or row) coordinates, y block
@@ -84,15 +86,21 @@ struct HostIndex {
     int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
     int64_t tree_level_begin[MAXL + 1] = {};
     HostPlan fplan[2], bplan[2];              // tile plans (build_plans), radius 1 and 2
+    HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
 };
 
 // Builds and validates the index from the host layout. Returns APR_OK or an error code; `msg`
 // receives a short reason on failure.
 apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
 
-// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu). Returns APR_OK,
-// APR_ERR_OOM (host allocation) or APR_ERR_UNSUPPORTED (a tile with 65536 or more staged elements).
+// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu), the
+// multi-channel ones included. Returns APR_OK, APR_ERR_OOM (host allocation) or
+// APR_ERR_UNSUPPORTED (a tile with 65536 or more staged elements).
 apr_status_t build_plans(HostIndex &X);
+// The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
+bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
+// DevLayout over the host copy of X's index (for host code that walks it like a kernel).
+DevLayout host_layout_view(const HostIndex &X);
 
 // Record a short reason for the last failure on this thread (read by apr_last_error_message).
 void set_last_message(const char *msg);
@@ -129,7 +137,8 @@ struct apr_handle_s {
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
-    aprk::PlanHdr *d_plan_hdr[4] = {};   // tile plans: forward radius 1, 2; adjoint radius 1, 2
-    aprk::PlanEnt *d_plan_ent[4] = {};
+    // tile plans: forward radius 1, 2; adjoint radius 1, 2; multi-channel feature, adjoint
+    aprk::PlanHdr *d_plan_hdr[6] = {};
+    aprk::PlanEnt *d_plan_ent[6] = {};
     size_t dev_bytes = 0;
 };

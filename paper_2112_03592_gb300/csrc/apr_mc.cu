@@ -180,7 +180,7 @@ struct Sub {         // a sub-tile: level, interior origin, level grids
     LevelGeo g, gc;  // level l and level l-1 (gc valid if l > l_min)
 };
 
-__device__ __forceinline__ bool sub_of(const DevLayout &L, const Item &it, int sub, Sub &s) {
+__host__ __device__ __forceinline__ bool sub_of(const DevLayout &L, const Item &it, int sub, Sub &s) {
     s.l = it.l;
     s.g = L.geo[it.l];
     s.gc = it.l > L.l_min ? L.geo[it.l - 1] : s.g;
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool sub_of(const DevLayout &L, const Item &it, int s
 
 // Patch row pr = (iz, ix) covers level cells (z0-1+iz, x0-1+ix). 0: never read, 1: staged from the
 // (reflected) source row, 2: zero (outside the grid with zero boundary).
-__device__ __forceinline__ int row_mode(const Sub &s, int pr, int bc, int &rz, int &rx) {
+__host__ __device__ __forceinline__ int row_mode(const Sub &s, int pr, int bc, int &rz, int &rx) {
     const int z = s.z0 - 1 + pr / PX, x = s.x0 - 1 + pr % PX;
     if (z > s.g.dz || x > s.g.dx) return 0;
     const bool out = z < 0 || z >= s.g.dz || x < 0 || x >= s.g.dx;
@@ -209,13 +209,18 @@ struct McSlot {
     uint4 a, b;
 };
 
-// Loads y and the two 16-byte halves of element i of segment sg (tree segments: [NPROW, 2 NPROW)).
+// Loads y and the two 16-byte halves of element i of plan entry sg (segment og = meta & MC_SEG;
+// tree segments: [NPROW, 2 NPROW)).
+constexpr int MC_SEG = 255;           // plan meta: segment index; bit 8 = the patch row is outside the grid
+constexpr int MC_REFL = 256;
 struct FeatLoader {
     using Slot = McSlot;
     const uint16_t *py, *ty;
     const uint4 *pv, *tv;
+    const unsigned short *meta;
     __device__ __forceinline__ void operator()(int sg, int i, Slot &sl) const {
-        const bool t = sg >= NPROW && sg < 2 * NPROW;
+        const int og = meta[sg] & MC_SEG;
+        const bool t = og >= NPROW && og < 2 * NPROW;
         sl.y = t ? int(ty[i]) : int(py[i]);
         const uint4 *v = t ? tv : pv;
         sl.a = v[2 * size_t(i)];
@@ -228,6 +233,7 @@ struct FeatStage {
     uint4 p1[NPC];  // channels 8-15
     int seg_lo[NSEG_F];
     int pre[NSEG_F + 1];
+    unsigned short smeta[NSEG_F];  // plan meta of every entry
     int warp_tot[NWARP + 1];
     unsigned short segid[SEGID_CAP];
 };
@@ -237,60 +243,91 @@ struct FeatStage {
 // axis), reflected or zero outside the grid. Segment s = kind * NPROW + patch row. All patch rows
 // inside the grid: every coarser row is staged once (kind-2 segments then index the NCZM x NCZM
 // level-(l-1) rows under the patch instead of the patch rows).
-__device__ __forceinline__ bool sub_inner(const Sub &s) {
+__host__ __device__ __forceinline__ bool sub_inner(const Sub &s) {
     return s.z0 >= 1 && s.x0 >= 1 && s.z0 + SZ + 1 <= s.g.dz && s.x0 + SX + 1 <= s.g.dx;
 }
 
-// Segment bounds: writes seg_lo, returns the two counts of this thread's segments (2t, 2t+1) for the
-// scan; no barrier.
-__device__ __forceinline__ void feature_segments(const DevLayout &L, const Sub &s, int bc, FeatStage &S, int cnt[2]) {
-    const int tid = threadIdx.x;
+// Feature segment sg of sub-tile s with the reflecting boundary: index range [lo, hi) of one row's
+// elements; refl: the patch row lies outside the grid (with zero boundary the segment is empty).
+__host__ __device__ inline void feat_segment(const DevLayout &L, const Sub &s, int sg, int &lo, int &hi, bool &refl) {
     const int ylo = s.y0 - 1;
-    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
+    const int ya = imax(ylo, 0), yb = imin(s.y0 + BY + 1, s.g.dy);
     const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
-    const bool inner = sub_inner(s);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int sg = 2 * tid + h;
-        cnt[h] = 0;
-        if (sg < NSEG_F) {
-            const int kind = sg / NPROW, pr = sg - kind * NPROW;
-            int rz = 0, rx = 0, lo = 0, hi = 0;
-            if (kind == 2 && inner) {
-                // a level-(l-1) row staged once for the (up to) 2 x 2 patch rows it covers
-                if (pr < NCZM * NCZM && has_coarse) {
-                    const int cz = ((s.z0 - 1) >> 1) + pr / NCZM, cx = ((s.x0 - 1) >> 1) + pr % NCZM;
-                    const int cya = ya >> 1, cyb = min((yb + 1) >> 1, s.gc.dy);
-                    if (cz < s.gc.dz && cx < s.gc.dx)
-                        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, cz * s.gc.dx + cx, cya, cyb, lo, hi);
-                }
-            } else if (row_mode(s, pr, bc, rz, rx) == 1) {
-                if (kind == 0) {
-                    row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
-                } else if (kind == 1 && has_tree) {
-                    row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
-                } else if (kind == 2 && has_coarse) {
-                    const int cya = ya >> 1, cyb = min((yb + 1) >> 1, s.gc.dy);
-                    row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (rz >> 1) * s.gc.dx + (rx >> 1), cya,
-                              cyb, lo, hi);
-                }
-            }
-            S.seg_lo[sg] = lo;
-            cnt[h] = hi - lo;
+    const int kind = sg / NPROW, pr = sg - kind * NPROW;
+    lo = 0;
+    hi = 0;
+    refl = false;
+    if (kind == 2 && sub_inner(s)) {
+        // a level-(l-1) row staged once for the (up to) 2 x 2 patch rows it covers
+        if (pr < NCZM * NCZM && has_coarse) {
+            const int cz = ((s.z0 - 1) >> 1) + pr / NCZM, cx = ((s.x0 - 1) >> 1) + pr % NCZM;
+            const int cya = ya >> 1, cyb = imin((yb + 1) >> 1, s.gc.dy);
+            if (cz < s.gc.dz && cx < s.gc.dx)
+                row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, cz * s.gc.dx + cx, cya, cyb, lo, hi);
         }
+        return;
+    }
+    int rz = 0, rx = 0;
+    if (row_mode(s, pr, APR_BC_REFLECT, rz, rx) != 1) return;
+    const int z = s.z0 - 1 + pr / PX, x = s.x0 - 1 + pr % PX;
+    refl = z < 0 || z >= s.g.dz || x < 0 || x >= s.g.dx;
+    if (kind == 0) {
+        row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
+    } else if (kind == 1 && has_tree) {
+        row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, rz * s.g.dx + rx, ya, yb, lo, hi);
+    } else if (kind == 2 && has_coarse) {
+        const int cya = ya >> 1, cyb = imin((yb + 1) >> 1, s.gc.dy);
+        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (rz >> 1) * s.gc.dx + (rx >> 1), cya, cyb, lo, hi);
     }
 }
 
-// Element loads and patch writes after the segment scan (S.pre); ends with a block barrier.
+// Reads a sub-tile's plan (entries taken by threads t0, t0 + 1, ...; threads below t0 are free for
+// other loads) into seg_lo / smeta / pre and returns the entry count. drop_refl (zero boundary on a
+// sub-tile with rows outside the grid): the entries flagged MC_REFL are emptied and the counts
+// rescanned by all threads. Ends with a block barrier.
+__device__ __forceinline__ int load_mc_plan(const PlanView &P, int tile, int t0, bool drop_refl, int *seg_lo,
+                                            unsigned short *smeta, int *pre, int *warp_tot) {
+    const int tid = threadIdx.x;
+    const PlanHdr hd = P.hdr[tile];
+    const int n = hd.count;
+    if (tid >= t0)
+        for (int k = tid - t0; k <= n; k += NT - t0) {
+            const PlanEnt e = P.ent[hd.first + k];
+            if (k < n) {
+                seg_lo[k] = e.lo;
+                smeta[k] = e.meta;
+            }
+            if (!drop_refl) pre[k] = e.pre;
+        }
+    if (!drop_refl) {
+        block_sync();
+        return n;
+    }
+    int cnt[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = 2 * tid + h;
+        if (k < n) {
+            const PlanEnt e = P.ent[hd.first + k];
+            if (!(e.meta & MC_REFL)) cnt[h] = int(P.ent[hd.first + k + 1].pre) - int(e.pre);
+        }
+    }
+    block_scan2(cnt[0], cnt[1], n, pre, warp_tot);
+    return n;
+}
+
+// Element loads and patch writes for the nseg plan entries in S (after load_mc_plan); ends with a
+// block barrier.
 __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
-                                 FeatStage &S) {
+                                 int nseg, FeatStage &S) {
     const int tid = threadIdx.x;
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
     const bool inner = sub_inner(s);
-    const FeatLoader loader{L.y, L.ty, vals, tree};
-    for_each_element(S.seg_lo, S.pre, NSEG_F, S.segid, loader, [&](int sg, int, const McSlot &sl) {
-        const int kind = sg / NPROW, pr = sg - kind * NPROW;
+    const FeatLoader loader{L.y, L.ty, vals, tree, S.smeta};
+    for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int sg, int, const McSlot &sl) {
+        const int og = S.smeta[sg] & MC_SEG;
+        const int kind = og / NPROW, pr = og - kind * NPROW;
         if (kind < 2) {
             if (sl.y >= ya && sl.y < yb) {
                 const int c = pr * PY + sl.y - ylo;
@@ -351,12 +388,12 @@ __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *
     block_sync();
 }
 
-__device__ void stage_features(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
-                               FeatStage &S) {
-    int cnt[2];
-    feature_segments(L, s, bc, S, cnt);
-    block_scan2(cnt[0], cnt[1], NSEG_F, S.pre, S.warp_tot);
-    feature_elements(L, s, vals, tree, bc, S);
+// The whole staging of sub-tile `tile` (index into the feature plan: item * NSUB + sub).
+__device__ void stage_features(const DevLayout &L, const Sub &s, int tile, const uint4 *vals, const uint4 *tree,
+                               int bc, FeatStage &S) {
+    const int n = load_mc_plan(L.mcfplan, tile, 0, bc != APR_BC_REFLECT && !sub_inner(s), S.seg_lo, S.smeta, S.pre,
+                               S.warp_tot);
+    feature_elements(L, s, vals, tree, bc, n, S);
 }
 
 // Target list of the sub-tile: the level-l particles of its interior, in particle order.
@@ -597,14 +634,14 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     // round (the weights are held in registers until the patch is staged)
     uint4 wreg[4];
     preload_weights(W, s.l - L.l_min, wreg);
-    int cnt[2];
-    feature_segments(L, s, bc, S.st, cnt);
-    target_rows(L, s, S.tg);
-    block_scan2(cnt[0], cnt[1], NSEG_F, S.st.pre, S.st.warp_tot);
+    target_rows(L, s, S.tg);   // warp 0, while the other warps read the plan
+    const int nseg = load_mc_plan(L.mcfplan, blockIdx.x * NSUB + blockIdx.y, 32,
+                                  bc != APR_BC_REFLECT && !sub_inner(s), S.st.seg_lo, S.st.smeta, S.st.pre,
+                                  S.st.warp_tot);
     const int nt = S.tg.row_base[NIROW];
     if (nt == 0) return;
     target_fill(L, s, S.tg);
-    feature_elements(L, s, vals, tree, bc, S.st);
+    feature_elements(L, s, vals, tree, bc, nseg, S.st);
     store_weights(wreg, S.w);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
@@ -686,12 +723,41 @@ struct BwdSmem {
     unsigned hot[NPROW][3];         // cells within distance 1 of a target
     int seg_lo[NSEG_B];
     int pre[NSEG_B + 1];
+    unsigned short smeta[NSEG_B];  // plan meta (segment index) of every entry
     int warp_tot[NWARP + 1];
     unsigned short segid[SEGID_CAP];
     int n1, nn;
     uint64_t bar;
     uint32_t tmem;
 };
+
+// Segment sg of the data-adjoint sub-tile s: [0, NPROW) the targets of the patch rows (inside the
+// grid only; y in the patch window), then per interior row the level-l particles, the level-l tree
+// nodes and the level-(l-1) particles over the interior y range.
+__host__ __device__ inline void adj_segment(const DevLayout &L, const Sub &s, int sg, int &lo, int &hi) {
+    const int ylo = s.y0 - 1;
+    const int ya = imax(ylo, 0), yb = imin(s.y0 + BY + 1, s.g.dy);
+    const int yia = s.y0, yib = imin(s.y0 + BY, s.g.dy);
+    const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
+    lo = 0;
+    hi = 0;
+    if (sg < NPROW) {
+        const int z = s.z0 - 1 + sg / PX, x = s.x0 - 1 + sg % PX;
+        if (z >= 0 && z < s.g.dz && x >= 0 && x < s.g.dx)
+            row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, ya, yb, lo, hi);
+        return;
+    }
+    const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
+    const int z = s.z0 + r / SX, x = s.x0 + r % SX;
+    if (z >= s.g.dz || x >= s.g.dx) return;
+    if (k == 0)
+        row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
+    else if (k == 1 && has_tree)
+        row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
+    else if (k == 2 && has_coarse)
+        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (z >> 1) * s.gc.dx + (x >> 1), yia >> 1,
+                  imin((yib + 1) >> 1, s.gc.dy), lo, hi);
+}
 
 __device__ __forceinline__ bool hot_at(const BwdSmem &S, int pz, int px, int py) {
     return (S.hot[pz * PX + px][py >> 5] >> (py & 31)) & 1u;
@@ -727,7 +793,6 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);  // gradient rows: y range of the patch
     const int yia = s.y0, yib = min(s.y0 + BY, s.g.dy);            // interior y range
-    const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
     const uint4 z4 = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < NPC; i += NT) {
         S.g0[i] = z4;
@@ -739,40 +804,16 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
         S.n1 = 0;
         S.nn = 0;
     }
-    int cnt[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int sg = 2 * tid + h;
-        cnt[h] = 0;
-        if (sg < NSEG_B) {
-            int lo = 0, hi = 0;
-            if (sg < NPROW) {  // targets of the patch region (inside the grid only)
-                const int z = s.z0 - 1 + sg / PX, x = s.x0 - 1 + sg % PX;
-                if (z >= 0 && z < s.g.dz && x >= 0 && x < s.g.dx)
-                    row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, ya, yb, lo, hi);
-            } else {
-                const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
-                const int z = s.z0 + r / SX, x = s.x0 + r % SX;
-                if (z < s.g.dz && x < s.g.dx) {
-                    if (k == 0)
-                        row_range(L.row_ptr, L.off, s.g.row0, s.g.off0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
-                    else if (k == 1 && has_tree)
-                        row_range(L.trow_ptr, L.toff, s.g.trow0, s.g.toff0, s.g.nb, z * s.g.dx + x, yia, yib, lo, hi);
-                    else if (k == 2 && has_coarse)
-                        row_range(L.row_ptr, L.off, s.gc.row0, s.gc.off0, s.gc.nb, (z >> 1) * s.gc.dx + (x >> 1),
-                                  yia >> 1, min((yib + 1) >> 1, s.gc.dy), lo, hi);
-                }
-            }
-            S.seg_lo[sg] = lo;
-            cnt[h] = hi - lo;
-        }
-    }
-    block_scan2(cnt[0], cnt[1], NSEG_B, S.pre, S.warp_tot);
+    const int nseg = load_mc_plan(L.mcbplan, blockIdx.x * NSUB + blockIdx.y, 0, false, S.seg_lo, S.smeta, S.pre,
+                                  S.warp_tot);
+
     struct Loader {
         using Slot = McSlot;
         const DevLayout *L;
         const uint4 *gout;
-        __device__ void operator()(int sg, int i, Slot &sl) const {
+        const unsigned short *meta;
+        __device__ void operator()(int k, int i, Slot &sl) const {
+            const int sg = meta[k];
             const bool t = sg >= NPROW + NIROW && sg < NPROW + 2 * NIROW;
             sl.y = t ? int(L->ty[i]) : int(L->y[i]);
             if (sg < NPROW) {
@@ -780,8 +821,9 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                 sl.b = gout[2 * size_t(i) + 1];
             }
         }
-    } loader{&L, gout};
-    for_each_element(S.seg_lo, S.pre, NSEG_B, S.segid, loader, [&](int sg, int i, const McSlot &sl) {
+    } loader{&L, gout, S.smeta};
+    for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int ent, int i, const McSlot &sl) {
+        const int sg = S.smeta[ent];
         if (sg < NPROW) {
             if (sl.y >= ya && sl.y < yb) {
                 const int py = sl.y - ylo;
@@ -1024,7 +1066,7 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
         if (!sub_of(L, it, u % NSUB, s)) continue;
         const int nt = list_targets(L, s, S.tg);
         if (nt == 0) continue;
-        stage_features(L, s, vals, tree, bc, S.st);
+        stage_features(L, s, u, vals, tree, bc, S.st);
         for (int t0 = 0; t0 < nt; t0 += WG_T) {
             // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t
             for (int i = tid; i < 2 * NTAP * WG_T; i += NT) {
@@ -1121,6 +1163,42 @@ bool mc_args_ok(int32_t c_in, int32_t c_out, int32_t k) { return c_in == MC && c
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 }  // namespace
+
+// Multi-channel sub-tile plans (host): for every sub-tile (item * NSUB + sub) the non-empty feature
+// segments (fwd_items; meta = segment index | MC_REFL for rows outside the grid) and the non-empty
+// data-adjoint segments (bwd_items; meta = segment index). Entries as in the single-channel plans.
+bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj) {
+    bool ok = true;
+    auto build = [&](const std::vector<Item> &items, HostPlan &P, bool features) {
+        P.hdr.assign(items.size() * NSUB, PlanHdr{0, 0});
+        P.ent.clear();
+        for (size_t t = 0; t < items.size(); ++t)
+            for (int sub = 0; sub < NSUB; ++sub) {
+                const int first = int(P.ent.size());
+                int total = 0;
+                Sub s;
+                if (sub_of(L, items[t], sub, s)) {
+                    const int nseg = features ? NSEG_F : NSEG_B;
+                    for (int sg = 0; sg < nseg; ++sg) {
+                        int lo = 0, hi = 0;
+                        bool refl = false;
+                        if (features) feat_segment(L, s, sg, lo, hi, refl);
+                        else adj_segment(L, s, sg, lo, hi);
+                        if (hi <= lo) continue;
+                        P.ent.push_back(PlanEnt{lo, uint16_t(sg | (refl ? MC_REFL : 0)), uint16_t(total)});
+                        total += hi - lo;
+                        if (total > 65535) ok = false;
+                    }
+                }
+                P.hdr[t * NSUB + sub] = PlanHdr{first, int(P.ent.size()) - first};
+                P.ent.push_back(PlanEnt{0, 0, uint16_t(total)});
+            }
+    };
+    build(X.fwd_items, feat, true);
+    build(X.bwd_items, adj, false);
+    return ok;
+}
+
 }  // namespace aprk
 
 using namespace aprk;

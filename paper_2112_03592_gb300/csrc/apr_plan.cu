@@ -9,11 +9,8 @@
 #include "apr_tile.cuh"
 
 namespace aprk {
-namespace {
 
-using namespace dev;
-
-DevLayout host_view(const HostIndex &X) {
+DevLayout host_layout_view(const HostIndex &X) {
     DevLayout L{};
     L.row_ptr = X.row_ptr.data();
     L.y = X.y.data();
@@ -26,6 +23,10 @@ DevLayout host_view(const HostIndex &X) {
     for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
     return L;
 }
+
+namespace {
+
+using namespace dev;
 
 // Appends one item's entries: pre holds the running element count; the slot after the last entry
 // holds the item's total. Totals above 65535 (not reachable with 8x8-row tiles and 64-cell y-blocks:
@@ -97,8 +98,8 @@ bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
 }  // namespace
 
 apr_status_t build_plans(HostIndex &X) {
-    const DevLayout L = host_view(X);
-    apr_status_t st[4] = {APR_OK, APR_OK, APR_OK, APR_OK};
+    const DevLayout L = host_layout_view(X);
+    apr_status_t st[5] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
     auto guarded = [&st](int i, auto f) {
         return [&st, i, f] {
             try {
@@ -108,10 +109,11 @@ apr_status_t build_plans(HostIndex &X) {
             }
         };
     };
-    std::thread t[4] = {std::thread(guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
+    std::thread t[5] = {std::thread(guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
                         std::thread(guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); })),
                         std::thread(guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); })),
-                        std::thread(guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }))};
+                        std::thread(guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); })),
+                        std::thread(guarded(4, [&] { return build_mc_plans(L, X, X.mcfplan, X.mcbplan); }))};
     for (auto &th : t) th.join();
     for (apr_status_t s : st)
         if (s != APR_OK) return s;
