@@ -92,8 +92,9 @@ typedef struct {
  * paragraph). The tree structure (which nodes exist) is derived from the particle cells; its
  * values are computed later by apr_tree_restrict. y indices are stored as uint16. For every tile
  * the host also lists the non-empty source segments of its staged patch (tile plans, for stencil
- * radius 1 and 2), so the convolution kernels never evaluate row offsets per call; on a
- * 1024x1024x512 image with 8 M particles the plans take about 120 MB of the handle's memory.
+ * radius 1 and 2 and for the multi-channel sub-tiles), so the convolution kernels never evaluate
+ * row offsets per call; on a 1024x1024x512 image with 8 M particles the plans take about 195 MB of
+ * the handle's memory.
  * Allocates device memory (cudaMalloc) owned by *out; returns APR_ERR_INVALID_LAYOUT when the
  * arrays are inconsistent (row sizes, y order and range, and with the flags the partition and the
  * balance), APR_ERR_OOM on allocation failure. *out is NULL on error. */
