@@ -224,7 +224,9 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     apr = S.make_config(WORKLOAD)
+    t_build = time.perf_counter()
     lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    t_build = time.perf_counter() - t_build
     w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
     st_h = G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
     Np = apr.n_particles
@@ -429,6 +431,7 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "wall_s_timed_region": round(wall, 4),
         "layout_bytes": lay.layout_bytes(),
+        "layout_build_s": round(t_build, 3),   # once per APR: validation, index, work lists, tile plans, upload
     }
     if rank == 0 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(apr, st_h, gout.cpu().numpy(), budget_s=args.cpu_budget)
