@@ -3,6 +3,7 @@
 // with one coalesced load instead of evaluating every row's offsets (and a block scan) per call.
 // The segments are those of fwd_segment / bwd_segment (apr_tile.cuh), evaluated here on the host
 // copy of the index.
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -109,12 +110,25 @@ apr_status_t build_plans(HostIndex &X) {
             }
         };
     };
-    std::thread t[5] = {std::thread(guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); })),
-                        std::thread(guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); })),
-                        std::thread(guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); })),
-                        std::thread(guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); })),
-                        std::thread(guarded(4, [&] { return build_mc_plans(L, X, X.mcfplan, X.mcbplan); }))};
-    for (auto &th : t) th.join();
+    std::function<void()> jobs[5] = {guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); }),
+                                     guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); }),
+                                     guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); }),
+                                     guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }),
+                                     guarded(4, [&] { return build_mc_plans(L, X, X.mcfplan, X.mcbplan); })};
+    // one thread per plan; a job whose thread cannot be started runs here
+    std::vector<std::thread> threads;
+    try {
+        threads.reserve(5);
+    } catch (...) {  // the jobs then run here
+    }
+    for (auto &job : jobs) {
+        try {
+            threads.emplace_back(job);
+        } catch (...) {
+            job();
+        }
+    }
+    for (auto &th : threads) th.join();
     for (apr_status_t s : st)
         if (s != APR_OK) return s;
     return APR_OK;
