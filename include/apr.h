@@ -134,6 +134,14 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
 apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                           int32_t k, int32_t bc, float *out, apr_stream_t stream);
 
+/* apr_tree_restrict into `workspace` followed by apr_convolve, for callers that do not keep the tree
+ * (the paper's pipeline: restriction, then convolution). workspace: caller-owned device memory of at
+ * least apr_convolve_auto_workspace_bytes(h) bytes, 4-byte aligned; it holds the tree values [N_t]
+ * afterwards. APR_ERR_INVALID_ARG if it is missing or too small; otherwise as the two calls. */
+size_t apr_convolve_auto_workspace_bytes(apr_handle_t h);
+apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const float *stencils, int32_t k, int32_t bc,
+                               float *out, void *workspace, size_t workspace_bytes, apr_stream_t stream);
+
 /* Gradient magnitude on the APR (Sec. 4.3): out[p] = sqrt(sum_{a=0..2} (w_a (*) u)_p^2), where (*) is
  * apr_convolve with the a-th of three per-level stencil stacks (e.g. the Sobel derivative filters
  * along z, x and y, rescaled per level by Eq. adapt_grad with apr_rescale_stencil). The patch is

@@ -33,7 +33,7 @@ from . import _abi
 from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALANCE, APR_SUBDOMAIN,  # noqa: F401
                    APR_VALIDATE, AprError)
 
-__all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve",
+__all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve", "apr_convolve_auto",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
            "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_relu_bf16", "apr_convolve_mc_backward",
            "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
@@ -172,6 +172,26 @@ def apr_convolve(layout: AprLayout, particles, tree, stencils, k, bc=APR_BC_REFL
     _abi.check("apr_convolve", layout._lib.apr_convolve(
         layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
         ctypes.c_void_p(stencils.data_ptr()), int(k), int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def apr_convolve_auto(layout: AprLayout, particles, stencils, k, bc=APR_BC_REFLECT, out=None, workspace=None,
+                      stream=None):
+    """Tree restriction into a workspace, then apr_convolve (one call; the tree is not kept)."""
+    import torch
+    _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    if out is None:
+        out = torch.empty(layout.n_particles, dtype=torch.float32, device=particles.device)
+    _dev_ptr(out, "out", layout.n_particles, torch.float32)
+    nbytes = int(layout._lib.apr_convolve_auto_workspace_bytes(layout.handle))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=particles.device)
+    _abi.check("apr_convolve_auto", layout._lib.apr_convolve_auto(
+        layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(stencils.data_ptr()), int(k), int(bc),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel() *
+                                                                                         workspace.element_size()),
+        _stream_ptr(stream)))
     return out
 
 

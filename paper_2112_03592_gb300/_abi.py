@@ -36,6 +36,8 @@ SIGNATURES = {
     "apr_export_structure": (_I32, [_P, _I32, _P, _SZ]),
     "apr_tree_restrict": (_I32, [_P, _P, _P, _I32, _P]),
     "apr_convolve": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _P]),
+    "apr_convolve_auto_workspace_bytes": (_SZ, [_P]),
+    "apr_convolve_auto": (_I32, [_P, _P, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "apr_gradient_magnitude": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _P]),
     "apr_backward_workspace_bytes": (_SZ, [_P, _I32]),
     "apr_convolve_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),

@@ -284,6 +284,22 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
     return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
 }
 
+size_t apr_convolve_auto_workspace_bytes(apr_handle_t h) {
+    return h ? size_t(h->X.nt > 0 ? h->X.nt : 1) * sizeof(float) : 0;
+}
+
+apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const float *stencils, int32_t k, int32_t bc,
+                               float *out, void *workspace, size_t workspace_bytes, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < apr_convolve_auto_workspace_bytes(h) ||
+        reinterpret_cast<uintptr_t>(workspace) % alignof(float) != 0)
+        return APR_ERR_INVALID_ARG;
+    float *tree = static_cast<float *>(workspace);
+    const apr_status_t st = apr_tree_restrict(h, particles, tree, 1, stream);
+    if (st != APR_OK) return st;
+    return apr_convolve(h, particles, tree, stencils, k, bc, out, stream);
+}
+
 apr_status_t apr_gradient_magnitude(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                                     int32_t k, int32_t bc, float *out, apr_stream_t stream) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;

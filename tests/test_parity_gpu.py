@@ -236,3 +236,17 @@ def test_tree_restrict_multichannel_fp32(C):
     ref = oracle.Oracle(apr, vals.astype(np.float32)).tree()
     assert tree.shape == ref.shape
     assert_rel(tree, ref)
+
+
+@pytest.mark.parametrize("bc", [G.APR_BC_REFLECT, G.APR_BC_ZERO])
+def test_convolve_auto_equals_restrict_then_convolve(bc):
+    apr = CASES["rand_ragged"]()
+    st = dev(stencil_stack(apr, 5, "restricted"))
+    lay, v, tree, out = gpu_forward(apr, st.cpu().numpy(), 5, bc)
+    auto = G.apr_convolve_auto(lay, v, st, 5, bc)
+    torch.cuda.synchronize()
+    assert torch.equal(auto, out)
+    small = torch.empty(max(lay.n_tree * 4 - 4, 0), dtype=torch.uint8, device="cuda")
+    if lay.n_tree > 0:
+        with pytest.raises(RuntimeError):
+            G.apr_convolve_auto(lay, v, st, 5, bc, workspace=small)
