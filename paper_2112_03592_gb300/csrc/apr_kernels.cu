@@ -3,15 +3,17 @@
 // Data layout in device memory (built by apr_index.cpp, Sec. 3.1 Alg. 1 extended):
 //   row_ptr[R+1] (uint32), y[N_p] (uint16), off[rows * nb] (uint16): for every row (l, z, x) and
 //   y-block j of BY cells, the offset of the row's first particle with y >= j*BY. The tree has the
-//   same three arrays. A work item names a tile of TZ x TX rows and one y-block of one level.
+//   same three arrays. A work item names a tile of TZ x TX rows and one y-block of one level; its
+//   tile plan (apr_plan.cu) lists the non-empty source segments of its patch.
 //
 // Convolution-type kernels stage an isotropic level-l patch (Sec. 3.5) of the tile plus an R-cell
 // halo in shared memory: same-level particles directly, the level-(l-1) particle of each remaining
 // cell piecewise-constant, and finer content through the level-l tree node (Sec. 4.1, Fig.
 // treeconv). The source elements of all patch rows are loaded in one flattened, unrolled loop
 // (consecutive lanes on consecutive particles, several loads in flight per thread), then the
-// stencil is applied to 8-cell windows along y that hold target particles, four threads per window,
-// with 16-byte shared-memory loads.
+// stencil is applied to 8-cell windows along y that hold target particles, two threads per window
+// (one lane in each warp of a pair, each over half of the stencil rows), with 16-byte shared-memory
+// loads. A 5^3 stack whose level has zero taps outside the central 3^3 is applied with radius 1.
 #include <cuda_runtime.h>
 
 #include <climits>

@@ -2,7 +2,7 @@
 // non-empty source segments of the item's patch, listed once per APR so that the kernels read them
 // with one coalesced load instead of evaluating every row's offsets (and a block scan) per call.
 // The segments are those of fwd_segment / bwd_segment (apr_tile.cuh), evaluated here on the host
-// copy of the index.
+// copy of the index; the multi-channel sub-tile plans come from build_mc_plans (apr_mc.cu).
 #include <functional>
 #include <thread>
 #include <vector>
