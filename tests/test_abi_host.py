@@ -156,6 +156,9 @@ def test_compute_calls_reject_bad_arguments_without_a_device():
     inv = 1  # APR_ERR_INVALID_ARG
     assert lib.apr_convolve(h, dummy, dummy, dummy, 3, 0, dummy, P(0)) == inv          # host-only handle
     assert lib.apr_gradient_magnitude(h, dummy, dummy, dummy, 3, 0, dummy, P(0)) == inv
+    assert lib.apr_convolve_auto(h, dummy, dummy, 3, 0, dummy, dummy, 1 << 20, P(0)) == inv
+    assert lib.apr_convolve_auto_workspace_bytes(h) == 4 * max(lay.n_tree, 1)
+    assert lib.apr_convolve_mc_relu_bf16(h, dummy, dummy, dummy, 16, 16, 3, 0, dummy, P(0)) == inv
     assert lib.apr_richardson_lucy(h, dummy, dummy, 3, 0, 2, dummy, dummy, 1 << 20, P(0)) == inv
     assert lib.apr_convolve_mc(h, dummy, dummy, dummy, 16, 16, 3, 0, dummy, P(0)) == inv
     assert lib.apr_tree_restrict_bf16(h, dummy, dummy, 16, P(0)) == inv
