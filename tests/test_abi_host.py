@@ -82,6 +82,28 @@ def test_restrict_and_rescale_stencils_vs_oracle():
         G.apr_restrict_stencil(np.ones((7, 7, 7), np.float32), 5, 1)
 
 
+def test_restricted_5cubed_stencils_have_3cubed_support_below_l_max():
+    """Eq. restrict_stenc with cell edge s >= 2 maps a 5^3 stencil to support 2 ceil(2/s) + 1 = 3 per
+    axis: the library's restricted stack is exactly zero outside the central 3^3 on every level below
+    l_max (the condition under which the convolution kernels apply radius-1 tiles), and so is the
+    oracle's independent construction; at l_max the stencil is unchanged and its outer taps are not
+    zero."""
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.1, 1.0, size=(5, 5, 5)).astype(np.float32)
+    l_max, l_min = 10, 3
+    a = G.apr_restrict_stencil(w, l_max, l_min).reshape(-1, 5, 5, 5)
+    b = oracle.restrict_stencil(w.astype(np.float64), l_max, l_min).reshape(-1, 5, 5, 5)
+    shell = np.ones((5, 5, 5), bool)
+    shell[1:4, 1:4, 1:4] = False
+    for i, l in enumerate(range(l_min, l_max + 1)):
+        if l < l_max:
+            assert np.all(a[i][shell] == 0.0) and np.all(b[i][shell] == 0.0), l
+            assert np.all(a[i][~shell] != 0.0)
+        else:
+            np.testing.assert_array_equal(a[i], w)
+            assert np.all(a[i][shell] != 0.0)
+
+
 # ---------------------------------------------------------------------------- invalid layouts
 def _layout(apr, **kw):
     d = dict(dims=apr.dims, l_min=apr.l_min, l_max=apr.l_max, row_ptr=apr.row_ptr.copy(), y_idx=apr.y_idx.copy())
