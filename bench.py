@@ -535,7 +535,9 @@ def run_mc(args, rank, world, full=True):
     names = ["tree_restrict_bf16", "convolve_mc", "data_adjoint", "weight_grad"]
     dom = max(range(1, 4), key=lambda j: parts[j])
     n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
-    launches_per_step = n_tree_levels + 1 + 1 + n_tree_levels + 2
+    # per step: BF16 tree (one launch per level), weight layout + forward, weight layout + data
+    # adjoint, push-down (one per level), weight gradient + its reduction
+    launches_per_step = n_tree_levels + 2 + 2 + n_tree_levels + 2
     rec = {
         "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
         "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
