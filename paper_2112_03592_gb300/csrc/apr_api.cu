@@ -32,29 +32,46 @@ namespace {
 
 thread_local char g_last_msg[256] = "";
 
+// Device copy of n elements, the allocation rounded up to a multiple of `pad` elements (zeroed
+// tail): the y arrays are read in aligned 8-element packets.
 template <typename T>
-cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes) {
+cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes, size_t pad = 1) {
     *dst = nullptr;
-    const size_t b = (n ? n : 1) * sizeof(T);
+    const size_t na = ((n ? n : 1) + pad - 1) / pad * pad;
+    const size_t b = na * sizeof(T);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), b);
     if (e != cudaSuccess) return e;
     bytes += b;
     if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && na > n) e = cudaMemset(*dst + n, 0, (na - n) * sizeof(T));
     return e;
 }
+
+// Staged value arrays (particles and tree values of the forward-type calls) are read in 16-byte
+// vectors: their base addresses must be 16-byte aligned.
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 void free_device(apr_handle_s *h) {
     void *ptrs[] = {h->d_fwd, h->d_bwd, h->d_tree, h->d_fwd_level_begin, h->d_row_ptr, h->d_trow_ptr,
                     h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
         if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (h->d_fplan_hdr[i]) cudaFree(h->d_fplan_hdr[i]);
+        if (h->d_fplan_ent[i]) cudaFree(h->d_fplan_ent[i]);
     }
 }
 
 bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
+
+apr_status_t misaligned() {
+    aprk::set_last_message("staged value arrays (particles, tree values) must be 16-byte aligned");
+    return APR_ERR_INVALID_ARG;
+}
 
 }  // namespace
 
@@ -127,7 +144,7 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         const apr_status_t pst = build_plans(h->X);
         if (pst != APR_OK) {
             snprintf(g_last_msg, sizeof(g_last_msg), "%s", pst == APR_ERR_OOM ? "host allocation failed (tile plans)"
-                                                                                : "tile with too many staged elements");
+                                                                                : "tile with too many staged elements, or more than 2^28 particles or tree nodes");
             delete h;
             return pst;
         }
@@ -135,17 +152,21 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         cudaError_t e = cudaSuccess;
         size_t &b = h->dev_bytes;
         if (e == cudaSuccess) e = upload(&h->d_row_ptr, X.row_ptr.data(), X.row_ptr.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_y, X.y.data(), X.y.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_y, X.y.data(), X.y.size(), b, 8);
         if (e == cudaSuccess) e = upload(&h->d_off, X.off.data(), X.off.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_trow_ptr, X.trow_ptr.data(), X.trow_ptr.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_ty, X.ty.data(), X.ty.size(), b);
+        if (e == cudaSuccess) e = upload(&h->d_ty, X.ty.data(), X.ty.size(), b, 8);
         if (e == cudaSuccess) e = upload(&h->d_toff, X.toff.data(), X.toff.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_fwd, X.fwd_items.data(), X.fwd_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
-        for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
-            const HostPlan &P = i < 2 ? X.fplan[i] : i < 4 ? X.bplan[i - 2] : i == 4 ? X.mcfplan : X.mcbplan;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = upload(&h->d_fplan_hdr[i], X.fplan[i].hdr.data(), X.fplan[i].hdr.size(), b);
+            if (e == cudaSuccess) e = upload(&h->d_fplan_ent[i], X.fplan[i].ent.data(), X.fplan[i].ent.size(), b);
+        }
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+            const HostPlan &P = i < 2 ? X.bplan[i] : i == 2 ? X.mcfplan : X.mcbplan;
             e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
             if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
         }
@@ -176,18 +197,20 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         L.ty = h->d_ty;
         L.toff = h->d_toff;
         L.err = h->d_err;
+        L.np = int32_t(X.np);
+        L.nt = int32_t(X.nt);
         L.l_min = X.l_min;
         L.l_max = X.l_max;
         for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
         for (int i = 0; i < 2; ++i) {
-            L.fplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i]};
-            L.bplan[i] = PlanView{h->d_plan_hdr[2 + i], h->d_plan_ent[2 + i]};
+            L.fplan[i] = FPlanView{h->d_fplan_hdr[i], h->d_fplan_ent[i]};
+            L.bplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i]};
         }
-        L.mcfplan = PlanView{h->d_plan_hdr[4], h->d_plan_ent[4]};
-        L.mcbplan = PlanView{h->d_plan_hdr[5], h->d_plan_ent[5]};
+        L.mcfplan = PlanView{h->d_plan_hdr[2], h->d_plan_ent[2]};
+        L.mcbplan = PlanView{h->d_plan_hdr[3], h->d_plan_ent[3]};
         // the plans live on the device now; the host copies are not needed again
         for (int i = 0; i < 2; ++i) {
-            h->X.fplan[i] = HostPlan{};
+            h->X.fplan[i] = HostFPlan{};
             h->X.bplan[i] = HostPlan{};
         }
         h->X.mcfplan = HostPlan{};
@@ -280,6 +303,7 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
     if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree)) return misaligned();
     const int n = int(h->X.fwd_items.size());
     return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
 }
@@ -292,7 +316,7 @@ apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const flo
                                float *out, void *workspace, size_t workspace_bytes, apr_stream_t stream) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < apr_convolve_auto_workspace_bytes(h) ||
-        reinterpret_cast<uintptr_t>(workspace) % alignof(float) != 0)
+        !aligned16(workspace))
         return APR_ERR_INVALID_ARG;
     float *tree = static_cast<float *>(workspace);
     const apr_status_t st = apr_tree_restrict(h, particles, tree, 1, stream);
@@ -306,6 +330,7 @@ apr_status_t apr_gradient_magnitude(apr_handle_t h, const float *particles, cons
     if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree)) return misaligned();
     const int n = int(h->X.fwd_items.size());
     return cuda_status(launch_gradmag(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
 }
@@ -356,6 +381,7 @@ apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, c
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     const HostIndex &X = h->X;
     if (!grad_stencils || (X.np && (!particles || !grad_out)) || (X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree)) return misaligned();
     const size_t need = apr_stencil_grad_workspace_bytes(h, k);
     if (need && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255))) return APR_ERR_INVALID_ARG;
     const int n = int(X.fwd_items.size());
@@ -406,6 +432,7 @@ apr_status_t apr_richardson_lucy(apr_handle_t h, const float *observed, const fl
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     const HostIndex &X = h->X;
     if (n_iter < 0 || !stencils || (X.np && (!observed || !estimate))) return APR_ERR_INVALID_ARG;
+    if (!aligned16(estimate)) return misaligned();
     const size_t need = apr_rl_workspace_bytes(h);
     if (need && (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)))
         return APR_ERR_INVALID_ARG;

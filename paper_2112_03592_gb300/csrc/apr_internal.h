@@ -50,6 +50,14 @@ struct HostPlan {
     std::vector<PlanHdr> hdr;
     std::vector<PlanEnt> ent;
 };
+struct FPlanView {     // forward tile plans (apr_tile.cuh: FPlanEnt)
+    const PlanHdr *hdr;
+    const uint2 *ent;
+};
+struct HostFPlan {
+    std::vector<PlanHdr> hdr;
+    std::vector<uint2> ent;
+};
 
 // Everything a kernel needs to walk the index (device pointers).
 struct DevLayout {
@@ -60,9 +68,10 @@ struct DevLayout {
     const uint16_t *ty;        // [N_t]
     const uint16_t *toff;
     unsigned *err;
+    int32_t np, nt;            // particles, tree nodes (value array lengths)
     int32_t l_min, l_max;
     LevelGeo geo[MAXL];
-    PlanView fplan[2];   // forward tiles (fwd_items), stencil radius 1 and 2
+    FPlanView fplan[2];  // forward tiles (fwd_items), stencil radius 1 and 2
     PlanView bplan[2];   // data-adjoint tiles (bwd_items), stencil radius 1 and 2
     PlanView mcfplan;    // multi-channel feature patches of the sub-tiles of fwd_items
     PlanView mcbplan;    // multi-channel data-adjoint sub-tiles of bwd_items
@@ -85,7 +94,8 @@ struct HostIndex {
     std::vector<Item> tree_items;             // non-empty (l, z, x, yb) tree bricks, by level
     int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
     int64_t tree_level_begin[MAXL + 1] = {};
-    HostPlan fplan[2], bplan[2];              // tile plans (build_plans), radius 1 and 2
+    HostFPlan fplan[2];                       // forward tile plans (build_plans), radius 1 and 2
+    HostPlan bplan[2];                        // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
 };
 
@@ -93,8 +103,8 @@ struct HostIndex {
 // receives a short reason on failure.
 apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &out, const char **msg);
 
-// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu), the
-// multi-channel ones included. Returns APR_OK, APR_ERR_OOM (host allocation) or
+// Builds the tile plans of X's forward and data-adjoint work items (apr_plan.cu) and the
+// multi-channel sub-tile plans. Returns APR_OK, APR_ERR_OOM (host allocation) or
 // APR_ERR_UNSUPPORTED (a tile with 65536 or more staged elements).
 apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
@@ -137,8 +147,10 @@ struct apr_handle_s {
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
-    // tile plans: forward radius 1, 2; adjoint radius 1, 2; multi-channel feature, adjoint
-    aprk::PlanHdr *d_plan_hdr[6] = {};
-    aprk::PlanEnt *d_plan_ent[6] = {};
+    // tile plans: adjoint radius 1, 2; multi-channel feature, adjoint
+    aprk::PlanHdr *d_plan_hdr[4] = {};
+    aprk::PlanEnt *d_plan_ent[4] = {};
+    aprk::PlanHdr *d_fplan_hdr[2] = {};   // forward radius 1, 2
+    uint2 *d_fplan_ent[2] = {};
     size_t dev_bytes = 0;
 };

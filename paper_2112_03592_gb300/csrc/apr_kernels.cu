@@ -41,153 +41,6 @@ __device__ __forceinline__ void compact_windows(Flag flag, unsigned short *act, 
     block_sync();
 }
 
-// Loads y and value of element i of segment seg: tree nodes for segments of kind 1, particles
-// otherwise (kinds from the segments' meta words).
-struct MetaYVLoader {
-    using Slot = SlotYV;
-    const uint16_t *py, *ty;
-    const float *pv, *tv;
-    const int *meta;
-    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
-        const bool t = meta_kind(meta[seg]) == 1;
-        s.y = t ? int(ty[i]) : int(py[i]);
-        s.v = t ? tv[i] : pv[i];
-    }
-};
-
-// ------------------------------------------------------------------------------------------------
-// Shared-memory image of a staged forward tile.
-// ------------------------------------------------------------------------------------------------
-template <int R>
-struct PatchSmem {
-    using G = Geo<R>;
-    float patch[G::NROW * G::PYS];       // first member: 16-byte aligned
-    __align__(16) float w8[G::NPAIR * 8];  // taps of every (dz, dx) pair, padded to 8
-    int seg_lo[G::NSEG];
-    int seg_meta[G::NSEG];               // patch row | kind << 8 | (interior row + 1) << 10
-    int pre[(G::NSEG > NIW ? G::NSEG : NIW) + 1];
-    int warp_tot[NWARP + 1];
-    unsigned wmask[NIW];                 // target bits of every window
-    int wfirst[NIW];                     // first target (particle index) of every window
-    unsigned short act[NIW];             // active windows, in window order
-    union {                              // staging and window compute never overlap
-        unsigned short segid[SEGID_CAP]; // segment of every staged element of the current chunk
-        float red[NWARP / 2][32][WIN];   // partial window sums of the second half of the stencil rows
-    };
-    int nact;
-};
-
-// Stage the forward patch of item `it` (Sec. 3.5): patch rows z in [z0-R, z0+TZ+R), x likewise, y in
-// [y0-R, y0+BY+R); rows outside the grid are reflected rows (or zeros), cells outside the grid in y
-// are reflected cells (or zeros). Marks the target windows (level-l particles of the interior rows in
-// y-block yb) and lists the active ones. zero_fill: cells no source covers hold 0 (the stencil
-// gradient reads every cell of a window), not stale shared memory.
-template <int R>
-__device__ void stage_patch(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
-                            const float *__restrict__ tree, int bc, PatchSmem<R> &S, bool zero_fill = false) {
-    using G = Geo<R>;
-    const int tid = threadIdx.x;
-    const int l = it.l;
-    const LevelGeo g = L.geo[l];
-    const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY;
-    const int yw = y0 - R;  // level y of patch column 0
-
-    for (int i = tid; i < NIW; i += NT) {
-        S.wmask[i] = 0u;
-        S.wfirst[i] = INT_MAX;
-    }
-    if (zero_fill)
-        for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    // the tile's non-empty source segments (fwd_segment, listed once per APR in the tile plan). With
-    // zero boundary the segments of rows outside the grid are dropped and the rest rescanned.
-    const bool boundary = fwd_tile_at_boundary<R>(L, it);
-    const PlanView P = L.fplan[R - 1];
-    const PlanHdr hd = P.hdr[tile];
-    const int nseg = hd.count;
-    const bool rescan = bc != APR_BC_REFLECT && boundary;
-    for (int k = tid; k <= nseg; k += NT) {
-        const PlanEnt e = P.ent[hd.first + k];
-        if (k < nseg) {
-            S.seg_lo[k] = e.lo;
-            S.seg_meta[k] = with_trow<R>(g, it, e.meta);
-        }
-        if (!rescan) S.pre[k] = e.pre;
-    }
-    if (!rescan) {
-        block_sync();
-    } else {
-        int cnt[2] = {0, 0};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = 2 * tid + h;
-            if (k < nseg) {
-                const PlanEnt e = P.ent[hd.first + k];
-                if (!(e.meta & META_REFL)) cnt[h] = int(P.ent[hd.first + k + 1].pre) - int(e.pre);
-            }
-        }
-        block_scan2(cnt[0], cnt[1], nseg, S.pre, S.warp_tot);
-    }
-
-    const MetaYVLoader ld{L.y, L.ty, vals, tree, S.seg_meta};
-    for_each_element(S.seg_lo, S.pre, nseg, S.segid, ld, [&](int seg, int i, SlotYV &s) {
-        const int meta = S.seg_meta[seg];
-        const int kind = meta_kind(meta);
-        float *prow = S.patch + (meta & 255) * G::PYS;
-        if (kind < 2) {
-            const int pos = s.y - yw;
-            if (pos >= 0 && pos < G::PY) prow[pos] = s.v;
-            const int trow = meta_trow(meta);
-            const int yr = s.y - y0;
-            if (trow >= 0 && yr >= 0 && yr < BY) {
-                // a target: level-l particle of an interior row inside y-block yb
-                const int w = trow * NWIN + yr / WIN;
-                atomicOr(&S.wmask[w], 1u << (yr % WIN));
-                atomicMin(&S.wfirst[w], i);
-            }
-        } else if (kind == 2) {
-            const int yy = 2 * s.y;  // first level-l cell of the coarser particle
-            const int pos = yy - yw;
-            if (pos >= 0 && pos < G::PY && yy < g.dy) prow[pos] = s.v;
-            if (pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy) prow[pos + 1] = s.v;
-        } else {
-            // a level-(l-1) particle of a once-staged coarse row: its 2 x 2 x 2 fine cells
-            const int rz0 = (meta & 15) - 1, rx0 = ((meta >> 4) & 15) - 1;
-            const int yy = 2 * s.y, pos = yy - yw;
-            const bool c0 = pos >= 0 && pos < G::PY && yy < g.dy, c1 = pos + 1 >= 0 && pos + 1 < G::PY && yy + 1 < g.dy;
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int rz = rz0 + a, rx = rx0 + b;
-                    if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
-                    float *q = S.patch + (rz * G::PX + rx) * G::PYS;
-                    if (c0) q[pos] = s.v;
-                    if (c1) q[pos + 1] = s.v;
-                }
-        }
-    });
-    if (boundary) {
-        // rows outside the grid with zero boundary: zero; cells outside the grid in y (the first
-        // max(0, -yw) and the last max(0, yw + PY - dy) of a row): mirror (reflect) or zero
-        const int nlo = max(0, -yw), hi0 = min(G::PY, g.dy - yw);
-        for (int pr = tid; pr < G::NROW; pr += NT) {
-            const int z = z0 - R + pr / G::PX, x = x0 - R + pr % G::PX;
-            float *prow = S.patch + pr * G::PYS;
-            if (bc != APR_BC_REFLECT && (z < 0 || z >= g.dz || x < 0 || x >= g.dx)) {
-                for (int pos = 0; pos < G::PY; ++pos) prow[pos] = 0.f;
-                continue;
-            }
-            for (int pos = 0; pos < nlo; ++pos)
-                prow[pos] = bc == APR_BC_REFLECT ? prow[reflect_idx(yw + pos, g.dy) - yw] : 0.f;
-            for (int pos = hi0; pos < G::PY; ++pos)
-                prow[pos] = bc == APR_BC_REFLECT ? prow[reflect_idx(yw + pos, g.dy) - yw] : 0.f;
-        }
-    }
-    block_sync();
-    compact_windows([&](int w) { return S.wmask[w] != 0u; }, S.act, S.pre, S.warp_tot, &S.nact);
-}
-
 // Stencil taps of level l into w8[pair][0..K), optionally flipped (the transpose uses w[-e]). The
 // stack holds (2 RS + 1)^3 taps per level; with R < RS the central (2 R + 1)^3 of them are loaded.
 template <int R, int RS = R>
@@ -333,6 +186,337 @@ struct Epilogue {
 };
 
 // ------------------------------------------------------------------------------------------------
+// Staged forward patch (convolution, gradient magnitude, stencil gradient).
+//
+// The sources of every patch row (Sec. 3.5: level-l particles, level-l tree nodes, level-(l-1)
+// particles) are index ranges [lo, lo + n) of the APR's arrays (fwd_segment). They are read as
+// 8-element packets aligned to 8 elements: one 16-byte load of y and two of values per packet, with
+// the elements outside the range masked (the y arrays are padded to a multiple of 8 elements; the
+// last packet of a value array is read element by element up to the array's end). A packet ->
+// segment table per chunk of packets replaces any per-element bookkeeping; the occupancy of the
+// target rows is OR-ed per packet.
+// ------------------------------------------------------------------------------------------------
+constexpr int PCAP = 1024;  // packets per staging chunk
+
+// Floats per stencil row in the paired-tap layout: taps (w0, w0, w1, w1, ...), padded to 16 bytes.
+template <int R>
+__host__ __device__ constexpr int w2_stride() {
+    return ((2 * R + 1) + 1) / 2 * 4;
+}
+
+template <int R, int NS>
+struct FwdSmem {
+    using G = Geo<R>;
+    float patch[G::NROW * G::PYS];             // first member: 16-byte aligned
+    __align__(16) float w2[NS][G::NPAIR * w2_stride<R>()];  // paired taps of NS stencil stacks
+    int seg_lo[G::NSEG];                        // first element of segment s
+    unsigned seg_nm[G::NSEG];                   // element count | segment meta << 8 (with_trow)
+    int pre[G::NSEG + 1];                       // packet prefix over the segments
+    int warp_tot[NWARP + 1];
+    unsigned long long rmask[NIR];              // targets of interior row r: bit j = cell y0 + j
+    int rfirst[NIR];                            // first target (particle index) of interior row r
+    unsigned short act[NIW];                    // windows holding targets, in window order
+    unsigned short pseg[PCAP];                  // segment of every packet of the current chunk
+    int nact;
+};
+
+// Targets of window w (bit j = cell j of the window) and the particle index of its first target.
+template <typename S>
+__device__ __forceinline__ unsigned win_mask(const S &sm, int w) {
+    return unsigned(sm.rmask[w / NWIN] >> ((w % NWIN) * WIN)) & 0xffu;
+}
+template <typename S>
+__device__ __forceinline__ int win_first(const S &sm, int w) {
+    const unsigned long long m = sm.rmask[w / NWIN];
+    return sm.rfirst[w / NWIN] + __popcll(m & ((1ull << ((w % NWIN) * WIN)) - 1ull));
+}
+
+// Writes the valid elements of one packet (elements i0 .. i0+7; valid: lo <= i < lo + n) into the
+// patch. Kinds 0, 1: one cell each (and, for level-l particles of interior rows, a target bit);
+// kind 2: the two level-l cells of a level-(l-1) particle in its patch row; kind 3: its 2 x 2 x 2
+// cells in the (up to) 2 x 2 patch rows of a once-staged level-(l-1) row.
+template <int R, int NS>
+__device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0, const uint4 &yq, const float4 &va,
+                                             const float4 &vb, int dy, int yw, int y0) {
+    using G = Geo<R>;
+    const int lo = S.seg_lo[seg];
+    const unsigned nm = S.seg_nm[seg];
+    const int n = int(nm & 255u), meta = int(nm >> 8);
+    const int kind = meta_kind(meta);
+    const int yv[8] = {int(yq.x & 0xffffu), int(yq.x >> 16), int(yq.y & 0xffffu), int(yq.y >> 16),
+                       int(yq.z & 0xffffu), int(yq.z >> 16), int(yq.w & 0xffffu), int(yq.w >> 16)};
+    const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+    if (kind < 2) {
+        float *prow = S.patch + (meta & 255) * G::PYS;
+        const int trow = meta_trow(meta);
+        unsigned long long bits = 0ull;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = unsigned(i0 + j - lo) < unsigned(n);
+            const int pos = yv[j] - yw;
+            if (ok && unsigned(pos) < unsigned(G::PY)) prow[pos] = vv[j];
+            const int yr = yv[j] - y0;
+            if (ok && unsigned(yr) < unsigned(BY)) bits |= 1ull << yr;
+        }
+        if (trow >= 0 && bits) atomicOr(&S.rmask[trow], bits);
+    } else if (kind == 2) {
+        float *prow = S.patch + (meta & 255) * G::PYS;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (unsigned(i0 + j - lo) >= unsigned(n)) continue;
+            const int yy = 2 * yv[j], pos = yy - yw;
+            if (unsigned(pos) < unsigned(G::PY) && yy < dy) prow[pos] = vv[j];
+            if (unsigned(pos + 1) < unsigned(G::PY) && yy + 1 < dy) prow[pos + 1] = vv[j];
+        }
+    } else {
+        const int rz0 = (meta & 15) - 1, rx0 = ((meta >> 4) & 15) - 1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (unsigned(i0 + j - lo) >= unsigned(n)) continue;
+            const int yy = 2 * yv[j], pos = yy - yw;
+            const bool c0 = unsigned(pos) < unsigned(G::PY) && yy < dy;
+            const bool c1 = unsigned(pos + 1) < unsigned(G::PY) && yy + 1 < dy;
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int rz = rz0 + a, rx = rx0 + b;
+                    if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+                    float *q = S.patch + (rz * G::PX + rx) * G::PYS;
+                    if (c0) q[pos] = vv[j];
+                    if (c1) q[pos + 1] = vv[j];
+                }
+        }
+    }
+}
+
+// Stage the forward patch of item `it` (Sec. 3.5): patch rows z in [z0-R, z0+TZ+R), x likewise, y in
+// [y0-R, y0+BY+R); rows outside the grid hold the reflected rows (or zeros), cells outside the grid
+// in y the reflected cells (or zeros); cells no source covers (possible only in layouts not checked
+// for 2:1 balance) hold 0. Also records the target rows (rmask, rfirst) and lists the windows that
+// hold targets (act, nact). Ends with a block barrier.
+template <int R, int NS>
+__device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
+                          const float *__restrict__ tree, int bc, FwdSmem<R, NS> &S) {
+    using G = Geo<R>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const LevelGeo g = L.geo[it.l];
+    const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY, yw = y0 - R;
+    const bool boundary = fwd_tile_at_boundary<R>(L, it);
+    const bool reflect = bc == APR_BC_REFLECT;
+
+    for (int i = tid; i < G::NROW * G::PYS / 4; i += NT)
+        reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < NIR) {
+        const int z = z0 + tid / TX, x = x0 + tid % TX;
+        S.rmask[tid] = 0ull;
+        S.rfirst[tid] = (z < g.dz && x < g.dx) ? int(pblock(L, g, z * g.dx + x, it.yb)) : 0;
+    }
+    // the tile's non-empty segments and their packet prefixes (fwd_segment, listed once per APR in
+    // the tile plan); with zero boundary the segments of rows outside the grid are skipped (their
+    // cells stay 0)
+    const FPlanView FP = L.fplan[R - 1];
+    const PlanHdr hd = FP.hdr[tile];
+    const int nseg = hd.count;
+    for (int k = tid; k <= nseg; k += NT) {
+        const uint2 raw = FP.ent[hd.first + k];
+        const FPlanEnt e{raw.x, raw.y};
+        if (k < nseg) {
+            const int meta = fplan_meta(e);
+            const bool drop = !reflect && (meta & META_REFL);
+            S.seg_lo[k] = fplan_lo(e);
+            S.seg_nm[k] = unsigned(drop ? 0 : fplan_n(e)) | (unsigned(with_trow<R>(g, it, meta)) << 8);
+        }
+        S.pre[k] = fplan_pre(e);
+    }
+    block_sync();
+
+    const int P = S.pre[nseg];
+    for (int c0 = 0; c0 < P; c0 += PCAP) {
+        const int c1 = min(P, c0 + PCAP);
+        for (int s = tid; s < nseg; s += NT) {
+            const int a = max(S.pre[s], c0), b = min(S.pre[s + 1], c1);
+            for (int p = a; p < b; ++p) S.pseg[p - c0] = (unsigned short)s;
+        }
+        block_sync();
+        // two packets per thread and step: the loads of both are issued before either is placed
+        for (int p0 = c0 + tid; p0 < c1; p0 += 2 * NT) {
+            uint4 yq[2];
+            float4 va[2], vb[2];
+            int sg[2], i0[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int p = p0 + u * NT;
+                sg[u] = -1;
+                i0[u] = 0;
+                if (p < c1) {
+                    const int s = S.pseg[p - c0];
+                    const bool t = meta_kind(int(S.seg_nm[s] >> 8)) == 1;
+                    const int g8 = (S.seg_lo[s] >> 3) + (p - S.pre[s]);
+                    const uint4 *yt = reinterpret_cast<const uint4 *>(t ? L.ty : L.y);
+                    const float *vs = t ? tree : vals;
+                    yq[u] = __ldg(yt + g8);
+                    if (8 * g8 + 8 <= (t ? L.nt : L.np)) {
+                        va[u] = __ldg(reinterpret_cast<const float4 *>(vs) + 2 * g8);
+                        vb[u] = __ldg(reinterpret_cast<const float4 *>(vs) + 2 * g8 + 1);
+                    } else {
+                        float e[8];
+                        const int nv = (t ? L.nt : L.np) - 8 * g8;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) e[j] = j < nv ? vs[8 * g8 + j] : 0.f;
+                        va[u] = make_float4(e[0], e[1], e[2], e[3]);
+                        vb[u] = make_float4(e[4], e[5], e[6], e[7]);
+                    }
+                    sg[u] = s;
+                    i0[u] = 8 * g8;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (sg[u] >= 0) place_packet<R, NS>(S, sg[u], i0[u], yq[u], va[u], vb[u], g.dy, yw, y0);
+        }
+        block_sync();
+    }
+    if (boundary && reflect) {
+        // cells outside the grid in y (the first max(0, -yw), the last from dy - yw on): mirrored from
+        // the in-grid cells of the same row
+        const int nlo = max(0, -yw), hi0 = min(G::PY, g.dy - yw), per = nlo + (G::PY - hi0);
+        if (per > 0) {
+            for (int task = tid; task < G::NROW * per; task += NT) {
+                const int pr = task / per, q = task - pr * per;
+                const int pos = q < nlo ? q : hi0 + (q - nlo);
+                float *prow = S.patch + pr * G::PYS;
+                prow[pos] = prow[reflect_idx(yw + pos, g.dy) - yw];
+            }
+            block_sync();
+        }
+    }
+    // windows holding targets, in window order (rows of warps 0 and 1)
+    if (tid < NIR) {
+        const unsigned long long m = S.rmask[tid];
+        unsigned am = 0u;
+#pragma unroll
+        for (int w = 0; w < NWIN; ++w) am |= ((m >> (w * WIN)) & 0xffull) ? (1u << w) : 0u;
+        const int c = __popc(am);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) S.warp_tot[warp] = incl;
+        pair_sync(0);
+        int k = (warp == 1 ? S.warp_tot[0] : 0) + incl - c;
+#pragma unroll
+        for (int w = 0; w < NWIN; ++w)
+            if ((am >> w) & 1u) S.act[k++] = (unsigned short)(tid * NWIN + w);
+        if (tid == NIR - 1) S.nact = k;
+    }
+    block_sync();
+}
+
+// Stencil taps of level l_idx in the paired layout w2[pair][2t], w2[pair][2t+1] = w[pair][t],
+// optionally flipped. The stack holds (2 RS + 1)^3 taps per level; with R < RS the central
+// (2 R + 1)^3 of them are loaded.
+template <int R, int RS = R>
+__device__ void load_taps2(const float *__restrict__ stencils, int l_idx, bool flip, float *w2) {
+    using G = Geo<R>;
+    constexpr int KS = 2 * RS + 1, KS3 = KS * KS * KS, D = RS - R, WS = w2_stride<R>();
+    for (int i = threadIdx.x; i < G::NPAIR * WS; i += NT) {
+        const int pair = i / WS, t = (i % WS) / 2;
+        float v = 0.f;
+        if (t < G::K) {
+            const int e = ((pair / G::K + D) * KS + (pair % G::K + D)) * KS + (t + D);
+            v = stencils[l_idx * KS3 + (flip ? KS3 - 1 - e : e)];
+        }
+        w2[i] = v;
+    }
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Partial window sums over the stencil rows pair = sub, sub + 2, ... (the two lanes of a window take
+// alternate rows): acc[j] = sum_rows sum_t w[row][t] * P[row][col + j + t], j < WIN. Paired FP32
+// FMAs: even taps update (acc_{2i}, acc_{2i+1}) from the aligned value pairs (v_{2i+t}, v_{2i+t+1}),
+// odd taps update separate pairs (o_{2m-1}, o_{2m}) from (v_{2m-1+t}, v_{2m+t}), also aligned; the
+// two are added at the end (o_{-1} and o_8 are unused).
+template <int R>
+__device__ __forceinline__ void window_part2(const float *patch, const float *w2, int w, int sub, float acc[WIN]) {
+    using G = Geo<R>;
+    constexpr int WS = w2_stride<R>();
+    const int r = w / NWIN;
+    const float *base = patch + ((r / TX) * G::PX + (r % TX)) * G::PYS + (w % NWIN) * WIN;
+    float2 E[4], O[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) O[i] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int pair = sub; pair < G::NPAIR; pair += 2) {  // not unrolled: keeps the instruction cache warm
+        const int dz = pair / G::K, dx = pair - dz * G::K;
+        const float4 *src = reinterpret_cast<const float4 *>(base + (dz * G::PX + dx) * G::PYS);
+        const float4 q0 = src[0], q1 = src[1], q2 = src[2];
+        const float2 V[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                             make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+        const float4 *wq = reinterpret_cast<const float4 *>(w2 + pair * WS);
+        const float4 wa = wq[0], wb = wq[1];
+        const float2 W0 = make_float2(wa.x, wa.y), W1 = make_float2(wa.z, wa.w), W2 = make_float2(wb.x, wb.y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) E[i] = ffma2(W0, V[i], E[i]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) E[i] = ffma2(W2, V[i + 1], E[i]);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) O[m] = ffma2(W1, V[m], O[m]);
+        if constexpr (R == 2) {
+            const float4 wc = wq[2];
+            const float2 W3 = make_float2(wb.z, wb.w), W4 = make_float2(wc.x, wc.y);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) E[i] = ffma2(W4, V[i + 2], E[i]);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) O[m] = ffma2(W3, V[m + 1], O[m]);
+        }
+    }
+    acc[0] = E[0].x + O[0].y;
+    acc[1] = E[0].y + O[1].x;
+    acc[2] = E[1].x + O[1].y;
+    acc[3] = E[1].y + O[2].x;
+    acc[4] = E[2].x + O[2].y;
+    acc[5] = E[2].y + O[3].x;
+    acc[6] = E[3].x + O[3].y;
+    acc[7] = E[3].y + O[4].x;
+}
+
+// Window sums of the active windows act[0..nact): two adjacent lanes per window over alternate
+// stencil rows, then a reduce-scatter between them (lane 0 of the pair keeps outputs 0..3, lane 1
+// outputs 4..7; the sum of the two halves is commutative, so the result is deterministic).
+// emit(w, j0, own[4]) receives outputs j0 .. j0+3 of window w.
+template <int R, typename Emit>
+__device__ __forceinline__ void fwd_windows(const float *patch, const float *w2, const unsigned short *act, int nact,
+                                            Emit emit) {
+    const int sub = threadIdx.x & 1;
+    for (int base = 0; base < nact; base += NT / 2) {
+        const int a = base + (threadIdx.x >> 1);
+        const bool valid = a < nact;
+        const int w = valid ? act[a] : 0;
+        float acc[WIN];
+        if (valid) {
+            window_part2<R>(patch, w2, w, sub, acc);
+        } else {
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
+        }
+        float own[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float send = sub ? acc[k] : acc[4 + k];
+            const float keep = sub ? acc[4 + k] : acc[k];
+            own[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+        if (valid) emit(w, 4 * sub, own);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // APR convolution (Sec. 4.1; Sec. 5.2 with 8x8-row tiles and 64-cell y-blocks instead of the
 // paper's 4x4 / 8x8 warp grid with a sliding buffer).
 // ------------------------------------------------------------------------------------------------
@@ -341,17 +525,17 @@ template <int R, int RS>
 __device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
                                               const float *__restrict__ tree, const float *__restrict__ stencils,
                                               int bc, float *out, const Epilogue &epi, unsigned char *smem_raw) {
-    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
-    load_taps<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w8);
-    stage_patch<R>(L, it, tile, vals, tree, bc, S);
-    windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
-        const unsigned m = S.wmask[w];
-        const int first = S.wfirst[w];
+    FwdSmem<R, 1> &S = *reinterpret_cast<FwdSmem<R, 1> *>(smem_raw);
+    load_taps2<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w2[0]);
+    stage_fwd<R, 1>(L, it, tile, vals, tree, bc, S);
+    fwd_windows<R>(S.patch, S.w2[0], S.act, S.nact, [&](int w, int j0, const float *own) {
+        const unsigned m = win_mask(S, w);
+        int p = win_first(S, w) + __popc(m & ((1u << j0) - 1u));
 #pragma unroll
-        for (int j = 0; j < WIN; ++j)
-            if ((m >> j) & 1u) {
-                const int p = first + __popc(m & ((1u << j) - 1u));
-                out[p] = epi.apply(p, acc[j]);
+        for (int k = 0; k < 4; ++k)
+            if ((m >> (j0 + k)) & 1u) {
+                out[p] = epi.apply(p, own[k]);
+                ++p;
             }
     });
 }
@@ -375,8 +559,7 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
 // out[p] = sqrt(sum_a (w_a (*) u)_p^2) for three stencil stacks w_a (a = z, x, y) on one staged
-// patch. The three passes give each window to the same thread, which keeps the running sum of
-// squares in out[p].
+// patch; each window's three sums are taken by the same two lanes in turn.
 template <int R>
 __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, const Item *__restrict__ items,
                                                              const float *__restrict__ vals,
@@ -385,28 +568,46 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
                                                              float *__restrict__ out) {
     using G = Geo<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
+    FwdSmem<R, 3> &S = *reinterpret_cast<FwdSmem<R, 3> *>(smem_raw);
     const Item it = items[blockIdx.x];
     const int n_levels = L.l_max - L.l_min + 1;
-    load_taps<R>(stencils, it.l - L.l_min, false, S.w8);
-    stage_patch<R>(L, it, blockIdx.x, vals, tree, bc, S);
-    for (int a = 0; a < 3; ++a) {
-        if (a > 0) {
-            block_sync();
-            load_taps<R>(stencils + size_t(a) * n_levels * G::K3, it.l - L.l_min, false, S.w8);
-            block_sync();
-        }
-        windows_apply<R>(S.patch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
-            const unsigned m = S.wmask[w];
-            const int first = S.wfirst[w];
+#pragma unroll 1
+    for (int a = 0; a < 3; ++a) load_taps2<R>(stencils + size_t(a) * n_levels * G::K3, it.l - L.l_min, false, S.w2[a]);
+    stage_fwd<R, 3>(L, it, blockIdx.x, vals, tree, bc, S);
+    const int sub = threadIdx.x & 1;
+    for (int base = 0; base < S.nact; base += NT / 2) {
+        const int ai = base + (threadIdx.x >> 1);
+        const bool valid = ai < S.nact;
+        const int w = valid ? S.act[ai] : 0;
+        float sq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int a = 0; a < 3; ++a) {
+            float acc[WIN];
+            if (valid) {
+                window_part2<R>(S.patch, S.w2[a], w, sub, acc);
+            } else {
 #pragma unroll
-            for (int j = 0; j < WIN; ++j)
-                if ((m >> j) & 1u) {
-                    const int p = first + __popc(m & ((1u << j) - 1u));
-                    const float sq = acc[j] * acc[j];
-                    out[p] = a == 0 ? sq : (a == 1 ? out[p] + sq : sqrtf(out[p] + sq));
+                for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float send = sub ? acc[k] : acc[4 + k];
+                const float keep = sub ? acc[4 + k] : acc[k];
+                const float v = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+                sq[k] = fmaf(v, v, sq[k]);
+            }
+        }
+        if (valid) {
+            const unsigned m = win_mask(S, w);
+            const int j0 = 4 * sub;
+            int p = win_first(S, w) + __popc(m & ((1u << j0) - 1u));
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((m >> (j0 + k)) & 1u) {
+                    out[p] = sqrtf(sq[k]);
+                    ++p;
                 }
-        });
+        }
     }
 }
 
@@ -424,9 +625,9 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
     constexpr int NGRP = NT / G::NPAIR;
     static_assert(NGRP * G::NPAIR * G::K <= G::NROW * G::PYS, "partials fit in the patch");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PatchSmem<R> &S = *reinterpret_cast<PatchSmem<R> *>(smem_raw);
+    FwdSmem<R, 1> &S = *reinterpret_cast<FwdSmem<R, 1> *>(smem_raw);
     const Item it = items[blockIdx.x];
-    stage_patch<R>(L, it, blockIdx.x, vals, tree, bc, S, true);
+    stage_fwd<R, 1>(L, it, blockIdx.x, vals, tree, bc, S);
     const int tid = threadIdx.x;
     const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
     float acc[G::K];
@@ -440,9 +641,9 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
             const float4 *src = reinterpret_cast<const float4 *>(S.patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + col);
             const float4 a0 = src[0], a1 = src[1], a2 = src[2];
             const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-            // dL/dout of the window's targets: consecutive particles from wfirst (0 at other cells)
-            const unsigned m = S.wmask[w];
-            const float *gs = gout + S.wfirst[w];
+            // dL/dout of the window's targets: consecutive particles from its first target (0 at other cells)
+            const unsigned m = win_mask(S, w);
+            const float *gs = gout + win_first(S, w);
             float gg[WIN];
             int c = 0;
 #pragma unroll
@@ -469,7 +670,6 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
         partial[size_t(tid) * n_items + blockIdx.x] = s;
     }
 }
-
 // grad_w[l][e] = sum over the level's items of partial[e][item], fixed-order block reduction.
 __global__ void __launch_bounds__(NT) stencil_grad_reduce_kernel(const float *__restrict__ partial, int n_items,
                                                                  const int64_t *__restrict__ level_begin,
@@ -905,9 +1105,10 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
 
 // Shared memory per block sets the blocks per SM (228 KB per SM, 1 KB reserved per block):
 // forward 4, data adjoint 3.
-static_assert(4 * (sizeof(PatchSmem<2>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
+static_assert(4 * (sizeof(FwdSmem<2, 1>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
+static_assert(4 * (sizeof(FwdSmem<2, 3>) + 1024) <= 228 * 1024, "gradient magnitude: four blocks per SM");
 static_assert(3 * (sizeof(BwdSmem<2>) + 1024) <= 228 * 1024, "data adjoint: three blocks per SM");
-static_assert(sizeof(PatchSmem<1>) <= sizeof(PatchSmem<2>) && sizeof(BwdSmem<1>) <= sizeof(BwdSmem<2>),
+static_assert(sizeof(FwdSmem<1, 1>) <= sizeof(FwdSmem<2, 1>) && sizeof(BwdSmem<1>) <= sizeof(BwdSmem<2>),
               "radius-1 tiles run inside the radius-2 launch");
 
 cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
@@ -915,7 +1116,7 @@ cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem
 template <int R>
 cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                               const float *st, int bc, float *out, const Epilogue &epi, cudaStream_t s) {
-    const size_t sm = sizeof(PatchSmem<R>);
+    const size_t sm = sizeof(FwdSmem<R, 1>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_fwd_kernel<R>), sm);
     if (e != cudaSuccess) return e;
     if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out, epi);
@@ -935,7 +1136,7 @@ cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int n, cons
 template <int R>
 cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, const float *vals,
                                  const float *tree, int bc, const float *gout, float *partial, cudaStream_t s) {
-    const size_t sm = sizeof(PatchSmem<R>);
+    const size_t sm = sizeof(FwdSmem<R, 1>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_stencil_kernel<R>), sm);
     if (e != cudaSuccess) return e;
     if (n > 0) conv_bwd_stencil_kernel<R><<<n, NT, sm, s>>>(L, items, n, vals, tree, bc, gout, partial);
@@ -956,7 +1157,7 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
 template <int R>
 cudaError_t launch_gradmag_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                              const float *st, int bc, float *out, cudaStream_t s) {
-    const size_t sm = sizeof(PatchSmem<R>);
+    const size_t sm = sizeof(FwdSmem<R, 3>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_gradmag_kernel<R>), sm);
     if (e != cudaSuccess) return e;
     if (n > 0) conv_gradmag_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out);

@@ -2,7 +2,8 @@
 // non-empty source segments of the item's patch, listed once per APR so that the kernels read them
 // with one coalesced load instead of evaluating every row's offsets (and a block scan) per call.
 // The segments are those of fwd_segment / bwd_segment (apr_tile.cuh), evaluated here on the host
-// copy of the index; the multi-channel sub-tile plans come from build_mc_plans (apr_mc.cu).
+// copy of the index; forward entries carry the prefix of their 8-element packets. The multi-channel
+// sub-tile plans come from build_mc_plans (apr_mc.cu).
 #include <functional>
 #include <thread>
 #include <vector>
@@ -19,6 +20,8 @@ DevLayout host_layout_view(const HostIndex &X) {
     L.trow_ptr = X.trow_ptr.data();
     L.ty = X.ty.data();
     L.toff = X.toff.data();
+    L.np = int32_t(X.np);
+    L.nt = int32_t(X.nt);
     L.l_min = X.l_min;
     L.l_max = X.l_max;
     for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
@@ -53,23 +56,35 @@ struct Appender {
     }
 };
 
+// Forward items: the non-empty segments with their packet prefixes; the entry after an item's
+// segments holds its packet total. Totals above 65535 (not reachable: at most 3 (8 + 2R)^2
+// segments of at most 2 BY + 2R elements, i.e. fewer than 10 000 packets) set `overflow`.
 template <int R>
-bool fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+bool fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostFPlan &P) {
     using G = Geo<R>;
     P.hdr.assign(items.size(), PlanHdr{0, 0});
-    Appender ap{P};
+    P.ent.clear();
+    bool overflow = false;
     for (size_t t = 0; t < items.size(); ++t) {
         const Item &it = items[t];
         const bool bnd = fwd_tile_at_boundary<R>(L, it);
-        ap.begin();
+        const int first = int(P.ent.size());
+        int total = 0;
         for (int s = 0; s < G::NSEG; ++s) {
             int lo, hi, meta;
             fwd_segment<R>(L, it, bnd, s, lo, hi, meta);
-            ap.add(lo, hi, meta);
+            if (hi <= lo) continue;
+            if (hi - lo > 255) overflow = true;
+            const FPlanEnt e = fplan_encode(lo, hi - lo, meta, total);
+            P.ent.push_back(uint2{e.w0, e.w1});
+            total += packets_of(lo, hi - lo);
+            if (total > 65535) overflow = true;
         }
-        P.hdr[t] = PlanHdr{ap.first, ap.end()};
+        const FPlanEnt e = fplan_encode(0, 0, 0, total);
+        P.ent.push_back(uint2{e.w0, e.w1});
+        P.hdr[t] = PlanHdr{first, int(P.ent.size()) - 1 - first};
     }
-    return !ap.overflow;
+    return !overflow;
 }
 
 // Adjoint items: count = n1 | n2 << 16 (gradient rows, then routing segments); meta = the segment's
@@ -100,6 +115,7 @@ bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
 
 apr_status_t build_plans(HostIndex &X) {
     const DevLayout L = host_layout_view(X);
+    if (X.np >= FPLAN_MAX_INDEX || X.nt >= FPLAN_MAX_INDEX) return APR_ERR_UNSUPPORTED;
     apr_status_t st[5] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
     auto guarded = [&st](int i, auto f) {
         return [&st, i, f] {

@@ -51,6 +51,25 @@ __host__ __device__ __forceinline__ int with_trow(const LevelGeo &g, const Item 
     return target ? meta | ((a * TX + b + 1) << 11) : meta;
 }
 
+// Forward tile plans: per work item and stencil radius, the non-empty segments of fwd_segment in
+// segment order, each with the prefix of 8-element packets before it (the packets of segment
+// [lo, lo + n) are the aligned groups lo >> 3 .. (lo + n - 1) >> 3). An item's entries are followed
+// by one entry whose prefix is the item's packet total. Two 32-bit words:
+//   w0 = lo (28 bits) | n[3:0] << 28,   w1 = packet prefix (16 bits) | meta (11 bits) << 16 | n[7:4] << 27.
+struct FPlanEnt {
+    uint32_t w0, w1;
+};
+constexpr int64_t FPLAN_MAX_INDEX = int64_t(1) << 28;  // particles and tree nodes an index may hold
+__host__ __device__ __forceinline__ FPlanEnt fplan_encode(int lo, int n, int meta, int ppre) {
+    return FPlanEnt{uint32_t(lo) | (uint32_t(n & 15) << 28),
+                    uint32_t(ppre & 0xffff) | (uint32_t(meta & 0x7ff) << 16) | (uint32_t(n >> 4) << 27)};
+}
+__host__ __device__ __forceinline__ int fplan_lo(const FPlanEnt &e) { return int(e.w0 & 0x0fffffffu); }
+__host__ __device__ __forceinline__ int fplan_n(const FPlanEnt &e) { return int(e.w0 >> 28) | int((e.w1 >> 27) << 4); }
+__host__ __device__ __forceinline__ int fplan_meta(const FPlanEnt &e) { return int((e.w1 >> 16) & 0x7ffu); }
+__host__ __device__ __forceinline__ int fplan_pre(const FPlanEnt &e) { return int(e.w1 & 0xffffu); }
+__host__ __device__ __forceinline__ int packets_of(int lo, int n) { return n > 0 ? ((lo + n + 7) >> 3) - (lo >> 3) : 0; }
+
 // Whether the forward patch of item it (rows z0-R .. z0+TZ+R, x likewise, y y0-R .. y0+BY+R) reaches
 // outside the level grid.
 template <int R>
