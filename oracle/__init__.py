@@ -296,51 +296,75 @@ def round_bf16_array(v) -> np.ndarray:
     return out.astype(np.float64)
 
 
-def cnn_forward(apr, x, weights, scale) -> np.ndarray:
+def _cnn_layer_input(apr, h, rounding):
+    """Oracle over the features h with its APR tree filled: the bf16 tree (tree_bf16) of the
+    network, or, with rounding off, the FP64 tree of Sec. 3.4."""
+    o = Oracle(apr, h)
+    if rounding:
+        o.tree_bf16()
+    else:
+        o.tree()
+    return o
+
+
+def cnn_forward(apr, x, weights, scale, rounding=True) -> np.ndarray:
     """APR CNN (Sec. 6 outlook: learned per-level filters) with 16 bfloat16 channels: h_0 = embed(x)
     (channel 0 = bf16(float32(scale) * x), others 0); for every layer i, c_i = 16 -> 16 APR
     convolution of h_i (Sec. 4.1, per-level 3^3 weights, tree of bf16 features as tree_bf16), and
     h_{i+1} = bf16(max(c_i, 0)) between layers; the output is y = x + c_last[:, 0] / scale. The
-    convolutions are FP64 on the bf16 values; the bf16 rounding points are those of the layer."""
+    convolutions are FP64 on the bf16 values; the bf16 rounding points are those of the layer.
+
+    rounding=False (a test hook) removes every bf16 rounding (embedding, activations, tree): the
+    same network in FP64, a piecewise-linear map whose derivative cnn_backward computes."""
     x = np.asarray(x, np.float64).reshape(-1)
     sc = np.float32(scale)
+    rnd = round_bf16_array if rounding else (lambda a: np.asarray(a, np.float64))
     h = np.zeros((x.size, 16))
-    h[:, 0] = round_bf16_array(np.float32(sc) * x.astype(np.float32))
+    h[:, 0] = rnd(np.float32(sc) * x.astype(np.float32)) if rounding else float(sc) * x
     c = None
     for i, W in enumerate(weights):
-        o = Oracle(apr, h)
-        o.tree_bf16()
+        o = _cnn_layer_input(apr, h, rounding)
         c = o.conv(np.asarray(W, np.float64), 3, C_out=16)
         if i + 1 < len(weights):
-            h = round_bf16_array(np.maximum(c, 0.0))
+            h = rnd(np.maximum(c, 0.0))
     return x + c[:, 0] / float(sc)
 
 
-def cnn_backward(apr, x, weights, scale, grad_y):
+def cnn_backward(apr, x, weights, scale, grad_y, rounding=True):
     """Weight gradients of cnn_forward for dL/dy = grad_y, every bf16 rounding taken as the identity
     (its derivative is not defined): the transposes of the read-out, of each 16 -> 16 convolution
-    (conv_backward, through the tree) and of ReLU (mask c > 0), from the last layer down. FP64."""
+    (conv_backward, through the tree) and of ReLU (mask c > 0: zero derivative at 0), from the last
+    layer down. FP64. rounding=False: the activations are those of cnn_forward(rounding=False), so
+    the result is the exact gradient of that piecewise-linear network."""
     x = np.asarray(x, np.float64).reshape(-1)
     sc = np.float32(scale)
+    rnd = round_bf16_array if rounding else (lambda a: np.asarray(a, np.float64))
     h = np.zeros((x.size, 16))
-    h[:, 0] = round_bf16_array(np.float32(sc) * x.astype(np.float32))
+    h[:, 0] = rnd(np.float32(sc) * x.astype(np.float32)) if rounding else float(sc) * x
     hs, cs = [], []
     for i, W in enumerate(weights):
-        o = Oracle(apr, h)
-        o.tree_bf16()
+        o = _cnn_layer_input(apr, h, rounding)
         c = o.conv(np.asarray(W, np.float64), 3, C_out=16)
         hs.append(h)
         cs.append(c)
         if i + 1 < len(weights):
-            h = round_bf16_array(np.maximum(c, 0.0))
+            h = rnd(np.maximum(c, 0.0))
     g = np.zeros((x.size, 16))
     g[:, 0] = np.asarray(grad_y, np.float64).reshape(-1) / float(sc)
     grads = [None] * len(weights)
     for i in reversed(range(len(weights))):
-        o = Oracle(apr, hs[i])
-        o.tree_bf16()
+        o = _cnn_layer_input(apr, hs[i], rounding)
         gp, gw = o.conv_backward(np.asarray(weights[i], np.float64), 3, g, C_out=16)
         grads[i] = gw
         if i > 0:
             g = gp * (cs[i - 1] > 0)
     return grads
+
+
+def cnn_layers(apr, h, W, relu):
+    """One layer of cnn_forward on given bf16 features h [N][16] (a test aid for layer-by-layer
+    comparison): c = the 16 -> 16 APR convolution of h over the bf16 tree of h (FP64), returned as
+    is (relu=False) or as bf16(max(c, 0)) (relu=True)."""
+    o = _cnn_layer_input(apr, np.asarray(h, np.float64), True)
+    c = o.conv(np.asarray(W, np.float64), 3, C_out=16)
+    return round_bf16_array(np.maximum(c, 0.0)) if relu else c

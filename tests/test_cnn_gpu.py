@@ -1,5 +1,6 @@
 """APR CNN (16 bf16 channels, 3^3 per-level weights, ReLU, residual read-out): element-wise kernels
-bit for bit, the network's forward and weight gradients vs the FP64 oracle network."""
+bit for bit, every layer of the network against the oracle fed the GPU's own bf16 inputs (1e-5), and
+the whole network's forward and weight gradients vs the FP64 oracle network as a sanity bound."""
 import numpy as np
 import pytest
 import torch
@@ -62,8 +63,9 @@ def test_cnn_forward_and_gradients_match_oracle(case):
     torch.cuda.synchronize()
     lay.sync_status()
     ref_y = oracle.cnn_forward(apr, x, Wh, scale)
-    # the residual branch carries the network's arithmetic: bf16 rounding decisions taken on FP32
-    # (GPU) and FP64 (oracle) values can differ by one bf16 unit at a few activations
+    # end to end only as a sanity bound (the layer-by-layer test holds each step to 1e-5): bf16
+    # rounding decisions taken on FP32 (GPU) and FP64 (oracle) values can differ by one bf16 unit at
+    # a few activations, and those differences propagate
     d_got = y.double().cpu().numpy() - x
     d_ref = ref_y - x
     err = np.max(np.abs(d_got - d_ref)) / np.max(np.abs(d_ref))
@@ -73,6 +75,68 @@ def test_cnn_forward_and_gradients_match_oracle(case):
         gg = gg.double().cpu().numpy()
         e = np.max(np.abs(gg - rg)) / np.max(np.abs(rg))
         assert np.all(np.isfinite(gg)) and e <= 2e-2, f"layer {i} weight gradient normwise error {e:.3e}"
+
+
+def _nerr(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert np.all(np.isfinite(got))
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cnn_layer_by_layer_matches_oracle(case):
+    """Every step of the network on the GPU against the oracle fed the GPU's own bf16 inputs of that
+    step: embedding and activations bit for bit, bf16 trees bit for bit, each convolution and each
+    convolution transpose (data and weight gradients) normwise 1e-5, read-out and its transpose bit
+    for bit. Layer order, level indexing and the read-out scale are fixed by this chain."""
+    apr = CASES[case]()
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    x = apr.values.astype(np.float32)
+    scale = float(np.float32(1.0 / x.mean()))
+    model = AprCnn(4, seed=1)
+    Wb = model.stack_weights(lay)
+    Wh = [w.float().cpu().numpy().astype(np.float64) for w in Wb]
+    y = model.forward(lay, f32(x), scale, keep=True, weights=Wb)
+    torch.cuda.synchronize()
+    lay.sync_status()
+    _, _, _, saved = model._saved
+    host = lambda t: t.float().cpu().numpy().astype(np.float64)
+    ref_h0 = np.zeros((apr.n_particles, 16))
+    ref_h0[:, 0] = oracle.round_bf16_array(np.float32(scale) * x)
+    np.testing.assert_array_equal(host(saved[0][0]), ref_h0)
+    for i, (h, tree, c) in enumerate(saved):
+        hh = host(h)
+        o = oracle.Oracle(apr, hh)
+        np.testing.assert_array_equal(host(tree), o.tree_bf16())
+        e = _nerr(host(c), o.conv(Wh[i], 3, C_out=16))
+        assert e <= 1e-5, f"layer {i} convolution normwise error {e:.3e}"
+        if i + 1 < len(saved):
+            np.testing.assert_array_equal(host(saved[i + 1][0]), oracle.round_bf16_array(np.maximum(host(c), 0.0)))
+    c_last = saved[-1][2].float().cpu().numpy()
+    inv = np.float32(1.0 / scale)  # the FP32 factor the read-out receives
+    np.testing.assert_array_equal(y.cpu().numpy(), (x + inv * c_last[:, 0]).astype(np.float32))
+    # backward, step by step
+    gy = np.random.default_rng(2).normal(size=apr.n_particles).astype(np.float32)
+    g = G.apr_mc_readout_backward_bf16(f32(gy), float(inv))
+    ref_g = np.zeros((apr.n_particles, 16))
+    ref_g[:, 0] = oracle.round_bf16_array(inv * gy)
+    np.testing.assert_array_equal(host(g), ref_g)
+    for i in reversed(range(len(saved))):
+        h, tree, _ = saved[i]
+        gp, gw = G.apr_convolve_mc_backward(lay, h, tree, Wb[i], g, need_particles=i > 0)
+        torch.cuda.synchronize()
+        o = oracle.Oracle(apr, host(h))
+        o.tree_bf16()
+        rp, rw = o.conv_backward(Wh[i], 3, host(g), C_out=16)
+        e = _nerr(gw.double().cpu().numpy(), rw)
+        assert e <= 1e-5, f"layer {i} weight gradient normwise error {e:.3e}"
+        if i > 0:
+            e = _nerr(gp.double().cpu().numpy(), rp)
+            assert e <= 1e-5, f"layer {i} data gradient normwise error {e:.3e}"
+            g = G.apr_mc_relu_backward_bf16(saved[i - 1][2], gp)
+            c_prev = saved[i - 1][2].float().cpu().numpy()
+            np.testing.assert_array_equal(host(g), oracle.round_bf16_array(np.where(c_prev > 0, gp.cpu().numpy(), 0)))
 
 
 def test_cnn_training_reduces_loss():

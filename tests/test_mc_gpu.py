@@ -106,3 +106,26 @@ def test_mc_rejects_unsupported_shapes():
     assert lib.apr_convolve_mc(lay.handle, p(x), p(t), p(w), 16, 16, 3, 7, p(out), s) == 1   # bad bc
     assert lib.apr_convolve_mc(lay.handle, p(x) + 2, p(t), p(w), 16, 16, 3, 0, p(out), s) == 1  # misaligned
     assert lib.apr_tree_restrict_bf16(lay.handle, p(x), p(t), 8, s) == 3
+
+
+def test_bf16_tree_golden_two_levels_up():
+    """The hand-derived bf16 tree of tests/golden/tree_bf16.txt (FP32 accumulation in child order
+    loses a term that the exact average keeps) in channel 0, bit for bit on the GPU."""
+    from test_oracle_cnn_pins import _golden_bf16_tree
+    child, root = _golden_bf16_tree()
+    ps = []
+    for z in range(4):
+        for x in range(4):
+            for y in range(4):
+                ps.append((2, z, x, y, child[(z // 2, x // 2, y // 2)]))
+    apr = S.apr_from_particles((4, 4, 4), 0, ps)
+    lay = G.AprLayout.from_apr(apr, FLAGS)
+    xm = np.zeros((apr.n_particles, C))
+    xm[:, 0] = apr.values
+    tree = G.apr_tree_restrict_bf16(lay, to_bf16(xm)).float().cpu().numpy()
+    torch.cuda.synchronize()
+    ref = oracle.Oracle(apr, xm).tree_bf16()
+    np.testing.assert_array_equal(tree.astype(np.float64), ref)
+    tc = oracle.Oracle(apr, xm).tree_coords()
+    i0 = [i for i, c in enumerate(tc) if tuple(int(v) for v in c) == (0, 0, 0, 0)][0]
+    assert tree[i0, 0] == root[(0, 0, 0, 0)]
