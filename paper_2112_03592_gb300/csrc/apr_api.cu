@@ -56,11 +56,11 @@ void free_device(apr_handle_s *h) {
                     h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
         if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
         if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (h->d_fplan_hdr[i]) cudaFree(h->d_fplan_hdr[i]);
         if (h->d_fplan_ent[i]) cudaFree(h->d_fplan_ent[i]);
     }
@@ -161,12 +161,13 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
         if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-            e = upload(&h->d_fplan_hdr[i], X.fplan[i].hdr.data(), X.fplan[i].hdr.size(), b);
-            if (e == cudaSuccess) e = upload(&h->d_fplan_ent[i], X.fplan[i].ent.data(), X.fplan[i].ent.size(), b);
-        }
         for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-            const HostPlan &P = i < 2 ? X.bplan[i] : i == 2 ? X.mcfplan : X.mcbplan;
+            const HostFPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
+            e = upload(&h->d_fplan_hdr[i], P.hdr.data(), P.hdr.size(), b);
+            if (e == cudaSuccess) e = upload(&h->d_fplan_ent[i], P.ent.data(), P.ent.size(), b);
+        }
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            const HostPlan &P = i == 0 ? X.mcfplan : X.mcbplan;
             e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
             if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
         }
@@ -204,14 +205,14 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         for (int l = 0; l < MAXL; ++l) L.geo[l] = X.geo[l];
         for (int i = 0; i < 2; ++i) {
             L.fplan[i] = FPlanView{h->d_fplan_hdr[i], h->d_fplan_ent[i]};
-            L.bplan[i] = PlanView{h->d_plan_hdr[i], h->d_plan_ent[i]};
+            L.bplan[i] = FPlanView{h->d_fplan_hdr[2 + i], h->d_fplan_ent[2 + i]};
         }
-        L.mcfplan = PlanView{h->d_plan_hdr[2], h->d_plan_ent[2]};
-        L.mcbplan = PlanView{h->d_plan_hdr[3], h->d_plan_ent[3]};
+        L.mcfplan = PlanView{h->d_plan_hdr[0], h->d_plan_ent[0]};
+        L.mcbplan = PlanView{h->d_plan_hdr[1], h->d_plan_ent[1]};
         // the plans live on the device now; the host copies are not needed again
         for (int i = 0; i < 2; ++i) {
             h->X.fplan[i] = HostFPlan{};
-            h->X.bplan[i] = HostPlan{};
+            h->X.bplan[i] = HostFPlan{};
         }
         h->X.mcfplan = HostPlan{};
         h->X.mcbplan = HostPlan{};

@@ -72,7 +72,7 @@ struct DevLayout {
     int32_t l_min, l_max;
     LevelGeo geo[MAXL];
     FPlanView fplan[2];  // forward tiles (fwd_items), stencil radius 1 and 2
-    PlanView bplan[2];   // data-adjoint tiles (bwd_items), stencil radius 1 and 2
+    FPlanView bplan[2];  // data-adjoint tiles (bwd_items), stencil radius 1 and 2
     PlanView mcfplan;    // multi-channel feature patches of the sub-tiles of fwd_items
     PlanView mcbplan;    // multi-channel data-adjoint sub-tiles of bwd_items
 };
@@ -95,7 +95,7 @@ struct HostIndex {
     int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
     int64_t tree_level_begin[MAXL + 1] = {};
     HostFPlan fplan[2];                       // forward tile plans (build_plans), radius 1 and 2
-    HostPlan bplan[2];                        // data-adjoint tile plans (build_plans), radius 1 and 2
+    HostFPlan bplan[2];                       // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
 };
 
@@ -147,10 +147,10 @@ struct apr_handle_s {
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
-    // tile plans: adjoint radius 1, 2; multi-channel feature, adjoint
-    aprk::PlanHdr *d_plan_hdr[4] = {};
-    aprk::PlanEnt *d_plan_ent[4] = {};
-    aprk::PlanHdr *d_fplan_hdr[2] = {};   // forward radius 1, 2
-    uint2 *d_fplan_ent[2] = {};
+    // tile plans: multi-channel feature, adjoint
+    aprk::PlanHdr *d_plan_hdr[2] = {};
+    aprk::PlanEnt *d_plan_ent[2] = {};
+    aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
+    uint2 *d_fplan_ent[4] = {};
     size_t dev_bytes = 0;
 };

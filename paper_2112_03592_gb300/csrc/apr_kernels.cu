@@ -29,35 +29,6 @@ namespace {
 
 using namespace dev;
 
-// Deterministic compaction of the windows w (0 <= w < NIW) with flag(w) into act[0..*nact).
-template <typename Flag>
-__device__ __forceinline__ void compact_windows(Flag flag, unsigned short *act, int *pre, int *warp_tot, int *nact) {
-    const int tid = threadIdx.x;
-    const int f0 = flag(2 * tid) ? 1 : 0, f1 = flag(2 * tid + 1) ? 1 : 0;
-    block_scan2(f0, f1, NIW, pre, warp_tot);
-    if (f0) act[pre[2 * tid]] = (unsigned short)(2 * tid);
-    if (f1) act[pre[2 * tid + 1]] = (unsigned short)(2 * tid + 1);
-    if (tid == 0) *nact = pre[NIW];
-    block_sync();
-}
-
-// Stencil taps of level l into w8[pair][0..K), optionally flipped (the transpose uses w[-e]). The
-// stack holds (2 RS + 1)^3 taps per level; with R < RS the central (2 R + 1)^3 of them are loaded.
-template <int R, int RS = R>
-__device__ void load_taps(const float *__restrict__ stencils, int l_idx, bool flip, float *w8) {
-    using G = Geo<R>;
-    constexpr int KS = 2 * RS + 1, KS3 = KS * KS * KS, D = RS - R;
-    for (int i = threadIdx.x; i < G::NPAIR * 8; i += NT) {
-        const int pair = i / 8, t = i % 8;
-        float v = 0.f;
-        if (t < G::K) {
-            const int e = ((pair / G::K + D) * KS + (pair % G::K + D)) * KS + (t + D);
-            v = stencils[l_idx * KS3 + (flip ? KS3 - 1 - e : e)];
-        }
-        w8[i] = v;
-    }
-}
-
 // True on every thread if all taps of level l_idx of a 5^3 stack outside its central 3^3 are zero.
 // Such a level is convolved with radius 1: a restricted 5^3 stencil (Eq. restrict_stenc) has support
 // 2 ceil(2 / s) + 1 = 3 cells per axis at every level with cell edge s >= 2, i.e. below l_max. The
@@ -74,49 +45,6 @@ __device__ __forceinline__ bool outer_taps_zero5(const float *__restrict__ stenc
     return __syncthreads_or(nz) == 0;
 }
 
-// acc[j] += sum over stencil rows (dz, dx) = pairs [P0, P1) of sum_dy w8[(dz,dx)][dy] *
-// P[row (ia+dz, ib+dx)][col + j + dy], j < WIN. base points at P[row (ia, ib)][col].
-template <int R, int P0, int P1>
-__device__ __forceinline__ void window_rows(const float *base, const float *w8, float acc[WIN]) {
-    using G = Geo<R>;
-#pragma unroll 1
-    for (int pair = P0; pair < P1; ++pair) {  // not unrolled: a smaller loop body keeps the instruction cache warm
-        const int dz = pair / G::K, dx = pair % G::K;
-        const float4 *src = reinterpret_cast<const float4 *>(base + (dz * G::PX + dx) * G::PYS);
-        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-        const float4 wa = *reinterpret_cast<const float4 *>(w8 + pair * 8);
-        const float wt[5] = {wa.x, wa.y, wa.z, wa.w, w8[pair * 8 + 4]};
-#pragma unroll
-        for (int j = 0; j < WIN; ++j)
-#pragma unroll
-            for (int t = 0; t < G::K; ++t) acc[j] = fmaf(wt[t], v[j + t], acc[j]);
-    }
-}
-
-// Like window_rows over all stencil rows, for a window whose centre row (ia, ib) may lie outside
-// the tile interior (a mirrored row): stencil rows that fall outside the staged patch read zero.
-template <int R>
-__device__ __forceinline__ void window_rows_checked(const float *patch, const float *w8, int ia, int ib, int col,
-                                                    float acc[WIN]) {
-    using G = Geo<R>;
-#pragma unroll 1
-    for (int pair = 0; pair < G::NPAIR; ++pair) {  // boundary tiles only: kept small for the instruction cache
-        const int dz = pair / G::K, dx = pair % G::K;
-        const int rz = ia + dz, rx = ib + dx;
-        if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
-        const float4 *src = reinterpret_cast<const float4 *>(patch + (rz * G::PX + rx) * G::PYS + col);
-        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-        const float4 wa = *reinterpret_cast<const float4 *>(w8 + pair * 8);
-        const float wt[5] = {wa.x, wa.y, wa.z, wa.w, w8[pair * 8 + 4]};
-#pragma unroll
-        for (int j = 0; j < WIN; ++j)
-#pragma unroll
-            for (int t = 0; t < G::K; ++t) acc[j] = fmaf(wt[t], v[j + t], acc[j]);
-    }
-}
-
 // Positions v in [-R, d + R) outside [0, d) that reflect onto c (at most 2R). Returns the count.
 template <int R>
 __device__ __forceinline__ int mirror_preimages(int c, int d, int *out) {
@@ -131,44 +59,6 @@ __device__ __forceinline__ int mirror_preimages(int c, int d, int *out) {
     for (int v = d; v < d + R; ++v)
         if (reflect_idx(v, d) == c) out[n++] = v;
     return n;
-}
-
-// Stencil sums of the active windows act[0..nact) of a patch: warps 2v and 2v+1 take the same 32
-// windows, the first half of the stencil rows and the second half; the second writes its partial
-// sums to red[], the first adds them (fixed order) and calls emit(window, acc). The two warps of a
-// pair synchronise with their own named barrier; callers that read what emit wrote from other warps
-// need a block barrier afterwards.
-template <int R, typename Emit>
-__device__ __forceinline__ void windows_apply(const float *patch, const float *w8, const unsigned short *act, int nact,
-                                              float (*red)[32][WIN], Emit emit) {
-    using G = Geo<R>;
-    constexpr int HALF = (G::NPAIR + 1) / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = warp & 1, grp = warp >> 1;
-    for (int base = 0; base < nact; base += 32 * (NWARP / 2)) {
-        const int a = base + grp * 32 + lane;
-        float acc[WIN];
-#pragma unroll
-        for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
-        int w = 0;
-        if (a < nact) {
-            w = act[a];
-            const int r = w / NWIN;
-            const float *b = patch + ((r / TX) * G::PX + (r % TX)) * G::PYS + (w % NWIN) * WIN;
-            if (half == 0) window_rows<R, 0, HALF>(b, w8, acc);
-            else window_rows<R, HALF, G::NPAIR>(b, w8, acc);
-        }
-        if (half == 1)
-#pragma unroll
-            for (int j = 0; j < WIN; ++j) red[grp][lane][j] = acc[j];
-        pair_sync(grp);
-        if (half == 0 && a < nact) {
-#pragma unroll
-            for (int j = 0; j < WIN; ++j) acc[j] += red[grp][lane][j];
-            emit(w, acc);
-        }
-        pair_sync(grp);
-    }
 }
 
 // Per-particle epilogue of the convolution: the plain output, or the element-wise division and
@@ -247,18 +137,26 @@ __device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0,
                        int(yq.z & 0xffffu), int(yq.z >> 16), int(yq.w & 0xffffu), int(yq.w >> 16)};
     const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
     if (kind < 2) {
+        // the plan lists only elements whose cell lies in the patch window (0 <= y - yw < PY)
         float *prow = S.patch + (meta & 255) * G::PYS;
-        const int trow = meta_trow(meta);
-        unsigned long long bits = 0ull;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const bool ok = unsigned(i0 + j - lo) < unsigned(n);
-            const int pos = yv[j] - yw;
-            if (ok && unsigned(pos) < unsigned(G::PY)) prow[pos] = vv[j];
-            const int yr = yv[j] - y0;
-            if (ok && unsigned(yr) < unsigned(BY)) bits |= 1ull << yr;
+        for (int j = 0; j < 8; ++j)
+            if (unsigned(i0 + j - lo) < unsigned(n)) prow[yv[j] - yw] = vv[j];
+        const int trow = meta_trow(meta);
+        if (trow >= 0) {
+            unsigned b0 = 0u, b1 = 0u;  // target bits of cells y0 .. y0+31 and y0+32 .. y0+63
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int yr = yv[j] - y0;
+                if (unsigned(i0 + j - lo) < unsigned(n) && unsigned(yr) < unsigned(BY)) {
+                    if (yr < 32) b0 |= 1u << yr;
+                    else b1 |= 1u << (yr - 32);
+                }
+            }
+            unsigned *rm = reinterpret_cast<unsigned *>(&S.rmask[trow]);
+            if (b0) atomicOr(rm, b0);
+            if (b1) atomicOr(rm + 1, b1);
         }
-        if (trow >= 0 && bits) atomicOr(&S.rmask[trow], bits);
     } else if (kind == 2) {
         float *prow = S.patch + (meta & 255) * G::PYS;
 #pragma unroll
@@ -700,36 +598,114 @@ __global__ void __launch_bounds__(NT) stencil_grad_reduce_kernel(const float *__
 template <int R>
 struct BwdSmem {
     using G = Geo<R>;
+    static constexpr int NS = G::NROW + G::NRSEG;  // plan segments: gradient rows, routing
     float gpatch[G::NROW * G::PYS];
     __align__(16) float H[NIR * BY];
-    __align__(16) float w8[G::NPAIR * 8];     // flipped taps: w8[pair][t] = w[K3 - 1 - (pair*K + t)]
-    unsigned rmask[G::NROW * 3];              // nonzero-gradient columns of every patch row
-    int seg_lo[G::NROW + G::NRSEG];
-    int pre[(G::NROW + G::NRSEG > NIW ? G::NROW + G::NRSEG : NIW) + 1];
-    unsigned short smeta[G::NROW + G::NRSEG];  // segment's index in its group (patch row, routing index)
-    int warp_tot[NWARP + 1];
+    __align__(16) float w2[G::NPAIR * w2_stride<R>()];  // flipped taps, paired layout
+    unsigned occ[G::NROW * 3];                 // nonzero-gradient columns of every patch row (68 bits)
+    unsigned long long dil[G::NROW];           // interior columns within R (in y) of a gradient column
     unsigned long long need[NIR];
-    int cpre[NIW + 1];                        // scratch of the window compaction
-    unsigned char wmir[NIW];                  // window has cells with mirrored preimages
+    int seg_lo[NS];
+    unsigned seg_nm[NS];                       // element count | routing / patch-row index << 8
+    int pre[NS + 1];                           // packet prefix
+    int warp_tot[NWARP + 1];
+    unsigned char wmir[NIW];                   // window has cells with mirrored preimages
     unsigned short act[NIW];
-    union {                                   // staging / routing and window compute never overlap
-        unsigned short segid[SEGID_CAP];
-        float red[NWARP / 2][32][WIN];
-    };
+    unsigned short pseg[PCAP];
     int nact;
 };
 
-// y of element i of routing segment seg (routing index q = q_of[seg]: tree nodes for NIR <= q < 2 NIR).
-struct RouteYLoader {
-    using Slot = SlotYV;
-    const uint16_t *py, *ty;
-    const unsigned short *q_of;
-    __device__ __forceinline__ void operator()(int seg, int i, Slot &s) const {
-        const int q = q_of[seg];
-        s.y = (q >= NIR && q < 2 * NIR) ? int(ty[i]) : int(py[i]);
-        s.v = 0.f;
+// The packets of segments [s0, s0 + ns) (packet prefixes in pre[s0 .. s0 + ns]): loads y (from ty for
+// segments with tree(seg), else from py) and, with vals, the values of 8 elements per packet, then
+// calls use(seg, i0, yq, va, vb, mask) with the packet's valid-element mask. Chunks of PCAP packets;
+// ends with a block barrier.
+template <typename Tree, typename Use>
+__device__ __forceinline__ void for_each_packet(const int *seg_lo, const unsigned *seg_nm, const int *pre, int s0,
+                                                int ns, unsigned short *pseg, const uint16_t *py, const uint16_t *ty,
+                                                Tree tree, const float *vals, int nvals, Use use) {
+    const int tid = threadIdx.x;
+    const int P0 = pre[s0], P1 = pre[s0 + ns];
+    for (int c0 = P0; c0 < P1; c0 += PCAP) {
+        const int c1 = min(P1, c0 + PCAP);
+        for (int s = s0 + tid; s < s0 + ns; s += NT) {
+            const int a = max(pre[s], c0), b = min(pre[s + 1], c1);
+            for (int p = a; p < b; ++p) pseg[p - c0] = (unsigned short)s;
+        }
+        block_sync();
+        for (int p0 = c0 + tid; p0 < c1; p0 += 2 * NT) {
+            uint4 yq[2];
+            float4 va[2], vb[2];
+            int sg[2], i0[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int p = p0 + u * NT;
+                sg[u] = -1;
+                i0[u] = 0;
+                va[u] = vb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (p < c1) {
+                    const int s = pseg[p - c0];
+                    const int g8 = (seg_lo[s] >> 3) + (p - pre[s]);
+                    yq[u] = __ldg(reinterpret_cast<const uint4 *>(tree(s) ? ty : py) + g8);
+                    if (vals) {
+                        if (8 * g8 + 8 <= nvals) {
+                            va[u] = __ldg(reinterpret_cast<const float4 *>(vals) + 2 * g8);
+                            vb[u] = __ldg(reinterpret_cast<const float4 *>(vals) + 2 * g8 + 1);
+                        } else {
+                            float e[8];
+                            const int nv = nvals - 8 * g8;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) e[j] = j < nv ? vals[8 * g8 + j] : 0.f;
+                            va[u] = make_float4(e[0], e[1], e[2], e[3]);
+                            vb[u] = make_float4(e[4], e[5], e[6], e[7]);
+                        }
+                    }
+                    sg[u] = s;
+                    i0[u] = 8 * g8;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (sg[u] < 0) continue;
+                const int lo = seg_lo[sg[u]], n = int(seg_nm[sg[u]] & 255u);
+                unsigned m = 0u;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m |= (unsigned(i0[u] + j - lo) < unsigned(n) ? 1u : 0u) << j;
+                use(sg[u], i0[u], yq[u], va[u], vb[u], m);
+            }
+        }
+        block_sync();
     }
-};
+}
+
+__device__ __forceinline__ void unpack_y(const uint4 &q, int y[8]) {
+    y[0] = int(q.x & 0xffffu), y[1] = int(q.x >> 16), y[2] = int(q.y & 0xffffu), y[3] = int(q.y >> 16);
+    y[4] = int(q.z & 0xffffu), y[5] = int(q.z >> 16), y[6] = int(q.w & 0xffffu), y[7] = int(q.w >> 16);
+}
+
+// Like window_part2 over all stencil rows, one lane per window, for a window whose centre row (ia,
+// ib) of the patch may lie outside the tile interior (a mirrored row): stencil rows outside the
+// staged patch read zero. Boundary tiles only.
+template <int R>
+__device__ __forceinline__ void window_checked2(const float *patch, const float *w2, int ia, int ib, int col,
+                                                float acc[WIN]) {
+    using G = Geo<R>;
+    constexpr int WS = w2_stride<R>();
+#pragma unroll 1
+    for (int pair = 0; pair < G::NPAIR; ++pair) {
+        const int dz = pair / G::K, dx = pair % G::K;
+        const int rz = ia + dz, rx = ib + dx;
+        if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+        const float4 *src = reinterpret_cast<const float4 *>(patch + (rz * G::PX + rx) * G::PYS + col);
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+#pragma unroll
+        for (int t = 0; t < G::K; ++t) {
+            const float wt = w2[pair * WS + 2 * t];
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) acc[j] = fmaf(wt, v[j + t], acc[j]);
+        }
+    }
+}
 
 // One data-adjoint tile with stencil radius R from a stack of radius RS >= R.
 template <int R, int RS>
@@ -738,44 +714,67 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                                                    const float *__restrict__ gout, float *__restrict__ gp,
                                                    float *__restrict__ gt, unsigned char *smem_raw) {
     using G = Geo<R>;
+    constexpr int WS = w2_stride<R>();
     BwdSmem<R> &S = *reinterpret_cast<BwdSmem<R> *>(smem_raw);
-    const int l = it.l, tid = threadIdx.x;
+    const int l = it.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const LevelGeo g = L.geo[l];
     const int z0 = it.a * TZ, x0 = it.b * TX, y0 = it.yb * BY;
     const int yw = y0 - R;
     const bool reflect = bc == APR_BC_REFLECT;
 
-    load_taps<R, RS>(stencils, l - L.l_min, true, S.w8);
+    load_taps2<R, RS>(stencils, l - L.l_min, true, S.w2);
     for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.gpatch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(S.H)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = tid; i < G::NROW * 3; i += NT) S.rmask[i] = 0u;
+    for (int i = tid; i < G::NROW * 3; i += NT) S.occ[i] = 0u;
 
     // the tile's non-empty segments (bwd_segment, listed once per APR in the tile plan): n1 gradient
-    // rows (in-grid patch rows, no reflection: g is zero outside the grid), then n2 sources of the
-    // interior cells (particles and tree nodes of the interior rows in y-block yb, coarser particles)
-    const PlanView P = L.bplan[R - 1];
+    // rows (in-grid patch rows, trimmed to the patch window; no reflection: g is zero outside the
+    // grid), then n2 sources of the interior cells (particles and tree nodes of the interior rows in
+    // y-block yb, level-(l-1) particles over the interior)
+    const FPlanView P = L.bplan[R - 1];
     const PlanHdr hd = P.hdr[tile];
     const int n1 = hd.count & 0xffff, n2 = hd.count >> 16;
     for (int k = tid; k <= n1 + n2; k += NT) {
-        const PlanEnt e = P.ent[hd.first + k];
+        const uint2 raw = P.ent[hd.first + k];
+        const FPlanEnt e{raw.x, raw.y};
         if (k < n1 + n2) {
-            S.seg_lo[k] = e.lo;
-            S.smeta[k] = e.meta;
+            S.seg_lo[k] = fplan_lo(e);
+            S.seg_nm[k] = unsigned(fplan_n(e)) | (unsigned(fplan_meta(e)) << 8);
         }
-        S.pre[k] = e.pre;
+        S.pre[k] = fplan_pre(e);
     }
     block_sync();
 
-    // gradient patch and its occupancy masks (the first NROW segments)
-    const YVLoader gl{L.y, L.ty, gout, gout, 0, 0};
-    for_each_element(S.seg_lo, S.pre, n1, S.segid, gl, [&](int seg, int, SlotYV &s) {
-        const int pos = s.y - yw;
-        if (pos >= 0 && pos < G::PY) {
-            const int row = S.smeta[seg];
-            S.gpatch[row * G::PYS + pos] = s.v;
-            atomicOr(&S.rmask[row * 3 + (pos >> 5)], 1u << (pos & 31));
-        }
-    });
+    // gradient patch and its occupancy (the first n1 segments; one patch row per segment)
+    for_each_packet(S.seg_lo, S.seg_nm, S.pre, 0, n1, S.pseg, L.y, L.ty, [](int) { return false; }, gout, L.np,
+                    [&](int seg, int, const uint4 &yq, const float4 &va, const float4 &vb, unsigned m) {
+                        const int row = int(S.seg_nm[seg] >> 8);
+                        float *prow = S.gpatch + row * G::PYS;
+                        int yv[8];
+                        unpack_y(yq, yv);
+                        const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+                        unsigned o[3] = {0u, 0u, 0u};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (!((m >> j) & 1u)) continue;
+                            const int pos = yv[j] - yw;
+                            prow[pos] = vv[j];
+                            o[pos >> 5] |= 1u << (pos & 31);
+                        }
+#pragma unroll
+                        for (int wd = 0; wd < 3; ++wd)
+                            if (o[wd]) atomicOr(&S.occ[row * 3 + wd], o[wd]);
+                    });
+    // y-dilation of every patch row: interior column j <-> patch column j + R, needed if any of the
+    // patch columns j .. j + 2R holds a gradient
+    for (int row = tid; row < G::NROW; row += NT) {
+        const unsigned long long lo64 = (unsigned long long)S.occ[row * 3] | ((unsigned long long)S.occ[row * 3 + 1] << 32);
+        const unsigned long long hi64 = S.occ[row * 3 + 2];
+        unsigned long long m = lo64;
+#pragma unroll
+        for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
+        S.dil[row] = m;
+    }
     block_sync();
 
     // cells that need H: within R of a nonzero gradient, or (reflect) close enough to the grid
@@ -789,7 +788,6 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         unsigned long long m = 0ull;
         bool edge_zx = false;
         if (valid) {
-            // preimage rows of this row: itself and (reflect) the out-of-grid rows mirroring onto it
             int pz[2 * R + 1], px[2 * R + 1];
             int nz = 1, nx = 1;
             pz[0] = z;
@@ -804,14 +802,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                     for (int pr = q; pr < G::NPAIR; pr += 4) {
                         const int rz = pz[iz] - z0 + pr / G::K, rx = px[ix] - x0 + pr % G::K;  // patch row
                         if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
-                        const int row = rz * G::PX + rx;
-                        const unsigned long long lo64 =
-                            (unsigned long long)S.rmask[row * 3] | ((unsigned long long)S.rmask[row * 3 + 1] << 32);
-                        const unsigned long long hi64 = S.rmask[row * 3 + 2];
-                        // interior column j <-> patch column j + R: needed if any of columns j .. j + 2R
-                        m |= lo64;
-#pragma unroll
-                        for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
+                        m |= S.dil[rz * G::PX + rx];
                     }
         }
         const unsigned mlo = unsigned(m), mhi = unsigned(m >> 32);
@@ -837,21 +828,38 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         }
     }
     block_sync();
-    // (the compaction has its own scratch: pre[] keeps the segment prefix for the routing pass)
-    compact_windows([&](int w) { return ((S.need[w / NWIN] >> ((w % NWIN) * WIN)) & 0xffull) != 0ull; }, S.act,
-                    S.cpre, S.warp_tot, &S.nact);
+    // active windows, in window order (rows of warps 0 and 1)
+    if (tid < NIR) {
+        const unsigned long long m = S.need[tid];
+        unsigned am = 0u;
+#pragma unroll
+        for (int w = 0; w < NWIN; ++w) am |= ((m >> (w * WIN)) & 0xffull) ? (1u << w) : 0u;
+        const int c = __popc(am);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) S.warp_tot[warp] = incl;
+        pair_sync(0);
+        int k = (warp == 1 ? S.warp_tot[0] : 0) + incl - c;
+#pragma unroll
+        for (int w = 0; w < NWIN; ++w)
+            if ((am >> w) & 1u) S.act[k++] = (unsigned short)(tid * NWIN + w);
+        if (tid == NIR - 1) S.nact = k;
+    }
+    block_sync();
 
     // H = (flipped stencil) correlated with the gradient patch, at the active windows (c' = c term)
-    windows_apply<R>(S.gpatch, S.w8, S.act, S.nact, S.red, [&](int w, const float *acc) {
-        float4 *dst = reinterpret_cast<float4 *>(S.H + (w / NWIN) * BY + (w % NWIN) * WIN);
-        dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    fwd_windows<R>(S.gpatch, S.w2, S.act, S.nact, [&](int w, int j0, const float *own) {
+        *reinterpret_cast<float4 *>(S.H + (w / NWIN) * BY + (w % NWIN) * WIN + j0) = make_float4(own[0], own[1], own[2], own[3]);
     });
     block_sync();
     // mirrored preimages (reflect only). Rows with mirrored z / x rows: one thread per active window
-    // sums the windows of all mirrored row combinations (z', x') != (z, x) (same y cells) with the
-    // window machinery; stencil rows outside the staged patch read zero, as the gradient outside the
-    // grid is zero. Cells within R of the y boundary then add the combinations whose y is mirrored.
+    // sums the windows of all mirrored row combinations (z', x') != (z, x) (same y cells); stencil
+    // rows outside the staged patch read zero, as the gradient outside the grid is zero. Cells within
+    // R of the y boundary then add the combinations whose y is mirrored.
     if (reflect) {
         for (int a = tid; a < S.nact; a += NT) {
             const int w = S.act[a];
@@ -867,7 +875,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
             for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
             for (int iz = 0; iz < nz; ++iz)
                 for (int ix = 0; ix < nx; ++ix)
-                    if (iz != 0 || ix != 0) window_rows_checked<R>(S.gpatch, S.w8, pz[iz] - z0, px[ix] - x0, col, acc);
+                    if (iz != 0 || ix != 0) window_checked2<R>(S.gpatch, S.w2, pz[iz] - z0, px[ix] - x0, col, acc);
             float *dst = S.H + r * BY + col;
 #pragma unroll
             for (int j = 0; j < WIN; ++j) dst[j] += acc[j];
@@ -903,11 +911,11 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                                 const int sz = cz - ez, sx = cx - ex;
                                 if (sz < 0 || sz >= G::PZ || sx < 0 || sx >= G::PX) continue;
                                 // unflipped tap w[ez][ex][ey] sits at flipped pair (R-ez, R-ex), slot R-ey
-                                const float *wrow = S.w8 + ((R - ez) * G::K + (R - ex)) * 8 + R;
+                                const float *wrow = S.w2 + ((R - ez) * G::K + (R - ex)) * WS + 2 * R;
                                 const float *grow = S.gpatch + (sz * G::PX + sx) * G::PYS + cy;
                                 for (int ey = ey0; ey <= ey1; ++ey) {
-                                    if ((ey & 1) == 0) h0 = fmaf(wrow[-ey], grow[-ey], h0);
-                                    else h1 = fmaf(wrow[-ey], grow[-ey], h1);
+                                    if ((ey & 1) == 0) h0 = fmaf(wrow[-2 * ey], grow[-ey], h0);
+                                    else h1 = fmaf(wrow[-2 * ey], grow[-ey], h1);
                                 }
                             }
                     }
@@ -915,34 +923,50 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         }
         block_sync();
     }
-    // routing: the sources of the interior cells, plan entries n1 .. n1 + n2 (routing index q)
-    const RouteYLoader rl{L.y, L.ty, S.smeta + n1};
-    for_each_element(S.seg_lo + n1, S.pre + n1, n2, S.segid, rl, [&](int seg, int i, SlotYV &s) {
-        const int q = S.smeta[n1 + seg];
-        if (q < NIR) {
-            const float h = S.H[q * BY + (s.y - y0)];
-            if (h != 0.f) atomicAdd(&gp[i], h);
-        } else if (q < 2 * NIR) {
-            const float h = S.H[(q - NIR) * BY + (s.y - y0)];
-            if (h != 0.f) gt[i] = h;
-        } else {
-            const int r = q - 2 * NIR;
-            const int j0 = 2 * s.y - y0;  // first level-l cell column of the coarser particle
-            if (j0 < 0 || j0 >= BY) return;
-            const int pa = r / (TX / 2), pb = r % (TX / 2);
-            float sum = 0.f;
+    // routing: the sources of the interior cells, plan segments n1 .. n1 + n2 (routing index q)
+    const auto is_tree = [&](int seg) {
+        const int q = int(S.seg_nm[seg] >> 8);
+        return q >= NIR && q < 2 * NIR;
+    };
+    for_each_packet(S.seg_lo, S.seg_nm, S.pre, n1, n2, S.pseg, L.y, L.ty, is_tree, nullptr, 0,
+                    [&](int seg, int i0, const uint4 &yq, const float4 &, const float4 &, unsigned m) {
+                        const int q = int(S.seg_nm[seg] >> 8);
+                        int yv[8];
+                        unpack_y(yq, yv);
+                        if (q < NIR) {
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+                            for (int j = 0; j < 8; ++j)
+                                if ((m >> j) & 1u) {
+                                    const float h = S.H[q * BY + (yv[j] - y0)];
+                                    if (h != 0.f) atomicAdd(&gp[i0 + j], h);
+                                }
+                        } else if (q < 2 * NIR) {
 #pragma unroll
-                for (int b = 0; b < 2; ++b)
+                            for (int j = 0; j < 8; ++j)
+                                if ((m >> j) & 1u) gt[i0 + j] = S.H[(q - NIR) * BY + (yv[j] - y0)];
+                        } else {
+                            const int r = q - 2 * NIR;
+                            const int pa = r / (TX / 2), pb = r % (TX / 2);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int ia = 2 * pa + a, ib = 2 * pb + b;
-                        if (z0 + ia < g.dz && x0 + ib < g.dx && y0 + j0 + e < g.dy) sum += S.H[(ia * TX + ib) * BY + j0 + e];
-                    }
-            if (sum != 0.f) atomicAdd(&gp[i], sum);
-        }
-    });
+                            for (int j = 0; j < 8; ++j) {
+                                if (!((m >> j) & 1u)) continue;
+                                const int j0 = 2 * yv[j] - y0;  // first level-l cell column of the coarser particle
+                                if (j0 < 0 || j0 >= BY) continue;
+                                float sum = 0.f;
+#pragma unroll
+                                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                    for (int b = 0; b < 2; ++b)
+#pragma unroll
+                                        for (int e = 0; e < 2; ++e) {
+                                            const int ia = 2 * pa + a, ib = 2 * pb + b;
+                                            if (z0 + ia < g.dz && x0 + ib < g.dx && y0 + j0 + e < g.dy)
+                                                sum += S.H[(ia * TX + ib) * BY + j0 + e];
+                                        }
+                                if (sum != 0.f) atomicAdd(&gp[i0 + j], sum);
+                            }
+                        }
+                    });
 }
 
 template <int R>

@@ -32,29 +32,11 @@ namespace {
 
 using namespace dev;
 
-// Appends one item's entries: pre holds the running element count; the slot after the last entry
-// holds the item's total. Totals above 65535 (not reachable with 8x8-row tiles and 64-cell y-blocks:
-// at most 3 (8 + 2R)^2 rows of at most 2 BY + 2R elements) set `overflow`.
-struct Appender {
-    HostPlan &P;
-    int first = 0, total = 0;
-    bool overflow = false;
-    void begin() {
-        first = int(P.ent.size());
-        total = 0;
-    }
-    void add(int lo, int hi, int meta) {
-        if (hi <= lo) return;
-        P.ent.push_back(PlanEnt{lo, uint16_t(meta), uint16_t(total)});
-        total += hi - lo;
-        if (total > 65535) overflow = true;
-    }
-    int end() {
-        const int n = int(P.ent.size()) - first;
-        P.ent.push_back(PlanEnt{0, 0, uint16_t(total)});
-        return n;
-    }
-};
+// Narrows [lo, hi) of a sorted y range to the elements with y in [ya, yb).
+void trim_y(const uint16_t *ys, int &lo, int &hi, int ya, int yb) {
+    while (lo < hi && int(ys[lo]) < ya) ++lo;
+    while (hi > lo && int(ys[hi - 1]) >= yb) --hi;
+}
 
 // Forward items: the non-empty segments with their packet prefixes; the entry after an item's
 // segments holds its packet total. Totals above 65535 (not reachable: at most 3 (8 + 2R)^2
@@ -70,9 +52,16 @@ bool fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostFPlan &P) 
         const bool bnd = fwd_tile_at_boundary<R>(L, it);
         const int first = int(P.ent.size());
         int total = 0;
+        const LevelGeo &g = L.geo[it.l];
+        const int yw = it.yb * BY - R, ylo = imax(yw, 0), yhi = imin(yw + G::PY, g.dy);
         for (int s = 0; s < G::NSEG; ++s) {
             int lo, hi, meta;
             fwd_segment<R>(L, it, bnd, s, lo, hi, meta);
+            // exactly the elements whose cells lie in the patch window
+            const int kind = meta_kind(meta);
+            if (kind == 0) trim_y(L.y, lo, hi, ylo, yhi);
+            else if (kind == 1) trim_y(L.ty, lo, hi, ylo, yhi);
+            else trim_y(L.y, lo, hi, ylo >> 1, ((yhi - 1) >> 1) + 1);
             if (hi <= lo) continue;
             if (hi - lo > 255) overflow = true;
             const FPlanEnt e = fplan_encode(lo, hi - lo, meta, total);
@@ -87,28 +76,45 @@ bool fwd_plan(const DevLayout &L, const std::vector<Item> &items, HostFPlan &P) 
     return !overflow;
 }
 
-// Adjoint items: count = n1 | n2 << 16 (gradient rows, then routing segments); meta = the segment's
-// index within its group (patch row, routing index q).
+// Adjoint items (bwd_segment): count = n1 | n2 << 16 (gradient rows, then routing segments); meta =
+// the segment's index within its group (patch row, routing index q). Gradient rows are trimmed to
+// the patch window and coarser-particle routing segments to the interior's parent cells, so every
+// listed element lands in the tile.
 template <int R>
-bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostPlan &P) {
+bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostFPlan &P) {
     using G = Geo<R>;
     P.hdr.assign(items.size(), PlanHdr{0, 0});
-    Appender ap{P};
+    P.ent.clear();
+    bool overflow = false;
     for (size_t t = 0; t < items.size(); ++t) {
         const Item &it = items[t];
-        ap.begin();
-        int n1 = 0;
+        const LevelGeo &g = L.geo[it.l];
+        const int yw = it.yb * BY - R, y0 = it.yb * BY;
+        const int first = int(P.ent.size());
+        int total = 0, n1 = 0;
         for (int s = 0; s < G::NROW + G::NRSEG; ++s) {
             int lo, hi;
             bwd_segment<R>(L, it, s, lo, hi);
-            const int before = int(P.ent.size());
-            ap.add(lo, hi, s < G::NROW ? s : s - G::NROW);
-            if (s < G::NROW && int(P.ent.size()) > before) ++n1;
+            const int q = s - G::NROW;
+            if (s < G::NROW) {
+                trim_y(L.y, lo, hi, imax(yw, 0), imin(yw + G::PY, g.dy));
+            } else if (q >= 2 * NIR && it.l > L.l_min) {
+                trim_y(L.y, lo, hi, y0 / 2, y0 / 2 + BY / 2);
+            }
+            if (hi <= lo) continue;
+            if (hi - lo > 255) overflow = true;
+            const FPlanEnt e = fplan_encode(lo, hi - lo, s < G::NROW ? s : q, total);
+            P.ent.push_back(uint2{e.w0, e.w1});
+            total += packets_of(lo, hi - lo);
+            if (total > 65535) overflow = true;
+            if (s < G::NROW) ++n1;
         }
-        const int n = ap.end();
-        P.hdr[t] = PlanHdr{ap.first, n1 | ((n - n1) << 16)};
+        const FPlanEnt e = fplan_encode(0, 0, 0, total);
+        P.ent.push_back(uint2{e.w0, e.w1});
+        const int n = int(P.ent.size()) - 1 - first;
+        P.hdr[t] = PlanHdr{first, n1 | ((n - n1) << 16)};
     }
-    return !ap.overflow;
+    return !overflow;
 }
 
 }  // namespace
