@@ -242,7 +242,7 @@ def apr_from_levels(lreq: np.ndarray, l_min: int, l_max: int, lam_sum_fn, rng, d
     exists = {l_min: np.ones(need[l_min].shape, bool)}
     for l in range(l_min + 1, l_max + 1):
         exists[l] = _upsample2(split[l - 1], need[l].shape)
-    rows, ys, vals = [], [], []
+    rows, ys, vals, means = [], [], [], []
     for l in range(l_min, l_max + 1):
         leaf = exists[l] & ~split[l]
         dz, dx, _ = leaf.shape
@@ -252,11 +252,14 @@ def apr_from_levels(lreq: np.ndarray, l_min: int, l_max: int, lam_sum_fn, rng, d
         ssum, cnt = lam_sum_fn(l, z, x, y)
         v = rng.poisson(ssum).astype(np.float64) / cnt
         vals.append(v.astype(np.float32))
+        means.append((np.asarray(ssum, np.float64) / cnt).astype(np.float32))
         del leaf
     counts = np.concatenate(rows)
     row_ptr = np.zeros(counts.size + 1, np.int64)
     np.cumsum(counts, out=row_ptr[1:])
-    return AprInput(dims, l_min, l_max, row_ptr, np.concatenate(ys), np.concatenate(vals), name)
+    apr = AprInput(dims, l_min, l_max, row_ptr, np.concatenate(ys), np.concatenate(vals), name)
+    apr.values_clean = np.concatenate(means)  # the noise-free particle means (same particles)
+    return apr
 
 
 def _sum_pyramid(lam: np.ndarray, l_min, l_max):
@@ -293,8 +296,11 @@ def apr_from_blobs(img: BlobImage, E=0.1, sigma_floor=10.0, l_min=2, seed_noise=
             return sums[l][z, x, y].astype(np.float64), 1.0
         return sums[l][z, x, y], cnts[l][z, x, y].astype(np.float64)
 
-    rng = _Mean() if clean else np.random.default_rng(seed_noise if seed_noise is not None else 12345)
-    return apr_from_levels(lreq, l_min, l_max, lam_sum, rng, img.dims, name)
+    rng = np.random.default_rng(seed_noise if seed_noise is not None else 12345)
+    apr = apr_from_levels(lreq, l_min, l_max, lam_sum, rng, img.dims, name)
+    if clean:
+        apr.values = apr.values_clean
+    return apr
 
 
 # --------------------------------------------------------------------------------------------
@@ -422,26 +428,33 @@ def make_config(name: str, use_cache=True, clean=False, **overrides) -> AprInput
     particles with noise-free values (the mean intensity over each particle's pixels)."""
     cfg = dict(CONFIGS[name])
     cfg.update(overrides)
-    key = hashlib.sha1((repr(sorted(cfg.items())) + ("clean" if clean else "")).encode()).hexdigest()[:12]
+    key = hashlib.sha1((repr(sorted(cfg.items())) + "+clean").encode()).hexdigest()[:12]
     path = _cache_dir() / f"{name}_{key}.npz"
+
+    def pick(a, noisy, means):
+        a.values_clean = means
+        a.values = means if clean else noisy
+        return a
+
     if use_cache and path.exists():
         z = np.load(path)
-        return AprInput(tuple(int(v) for v in z["dims"]), int(z["l_min"]), int(z["l_max"]),
-                        z["row_ptr"], z["y_idx"], z["values"], name)
+        a = AprInput(tuple(int(v) for v in z["dims"]), int(z["l_min"]), int(z["l_max"]),
+                     z["row_ptr"], z["y_idx"], z["values"], name)
+        return pick(a, z["values"], z["values_clean"])
     img = blob_image(cfg["dims"], cfg["n_blobs"], cfg["sigma_range"], seed=cfg["seed"])
     apr = apr_from_blobs(img, E=cfg["E"], sigma_floor=cfg["sigma_floor"], l_min=cfg["l_min"],
                          seed_noise=cfg["seed"] + 1000, name=name,
-                         sigma_scale=cfg.get("sigma_scale", 1.0), clean=clean)
+                         sigma_scale=cfg.get("sigma_scale", 1.0))
     if use_cache:
         try:
             path.parent.mkdir(parents=True, exist_ok=True)
             tmp = path.with_suffix(".tmp.npz")
             np.savez(tmp, dims=np.array(apr.dims), l_min=apr.l_min, l_max=apr.l_max,
-                     row_ptr=apr.row_ptr, y_idx=apr.y_idx, values=apr.values)
+                     row_ptr=apr.row_ptr, y_idx=apr.y_idx, values=apr.values, values_clean=apr.values_clean)
             os.replace(tmp, path)
         except OSError:
             pass
-    return apr
+    return pick(apr, apr.values, apr.values_clean)
 
 
 def apr_from_particles(dims, l_min, particles, name="") -> AprInput:
