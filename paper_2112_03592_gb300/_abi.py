@@ -10,6 +10,8 @@ _lib = None
 APR_OK = 0
 STATUS = {0: "APR_OK", 1: "APR_ERR_INVALID_ARG", 2: "APR_ERR_INVALID_LAYOUT", 3: "APR_ERR_UNSUPPORTED",
           4: "APR_ERR_OOM", 5: "APR_ERR_CUDA", 6: "APR_ERR_TIMEOUT", 7: "APR_ERR_DEVICE"}
+(APR_ERR_INVALID_ARG, APR_ERR_INVALID_LAYOUT, APR_ERR_UNSUPPORTED, APR_ERR_OOM, APR_ERR_CUDA, APR_ERR_TIMEOUT,
+ APR_ERR_DEVICE) = range(1, 8)
 APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY, APR_SUBDOMAIN = 1, 2, 4, 8
 APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
@@ -25,8 +27,20 @@ class AprHostLayout(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("y_idx", ctypes.c_void_p), ("n_particles", ctypes.c_int64)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class AprAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "apr_build_device": (_I32, [ctypes.POINTER(AprHostLayout), _U32, _P, ctypes.POINTER(_P)]),
+    "apr_build_device_ex": (_I32, [ctypes.POINTER(AprHostLayout), _U32, _P, ctypes.POINTER(AprAllocator),
+                                   ctypes.POINTER(_P)]),
+    "apr_sobel_stencils": (_I32, [_I32, _P]),
+    "apr_dense_convolve": (_I32, [_P, _I64, _I64, _I64, _P, _I32, _I32, _P, _P]),
     "apr_destroy": (_I32, [_P]),
     "apr_num_particles": (_I64, [_P]),
     "apr_num_tree": (_I64, [_P]),
