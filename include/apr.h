@@ -91,15 +91,33 @@ typedef struct {
  * APR tree structure, and the list of non-empty tiles the kernels are launched on, Sec. 5.2 last
  * paragraph). The tree structure (which nodes exist) is derived from the particle cells; its
  * values are computed later by apr_tree_restrict. y indices are stored as uint16. For every tile
- * the host also lists the non-empty source segments of its staged patch (tile plans, for stencil
- * radius 1 and 2 and for the multi-channel sub-tiles), so the convolution kernels never evaluate
- * row offsets per call; on a 1024x1024x512 image with 8 M particles the plans take about 195 MB of
- * the handle's memory.
- * Allocates device memory (cudaMalloc) owned by *out; returns APR_ERR_INVALID_LAYOUT when the
- * arrays are inconsistent (row sizes, y order and range, and with the flags the partition and the
- * balance), APR_ERR_OOM on allocation failure. *out is NULL on error. */
+ * the host also lists the non-empty source segments of its staged patch with the prefix of their
+ * 8-element packets (tile plans, for stencil radius 1 and 2 and for the multi-channel sub-tiles),
+ * so the convolution kernels never evaluate row offsets per call; on a 1024x1024x512 image with
+ * 8 M particles the handle holds about 206 MB, plans included (the image itself would be 2.1 GB).
+ * The index is allocated stream-ordered (cudaMallocAsync on `stream`) and uploaded on `stream`;
+ * it is ready for work enqueued on `stream` (other streams synchronise with it first). Returns
+ * APR_ERR_INVALID_LAYOUT when the arrays are inconsistent (row sizes, y order and range, and with
+ * the flags the partition and the balance), APR_ERR_UNSUPPORTED for more than 2^28 particles or
+ * tree nodes, APR_ERR_OOM on allocation failure. *out is NULL on error. */
 apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream,
                               apr_handle_t *out);
+
+/* A caller allocator for the handle's device memory (e.g. a framework's caching allocator).
+ * alloc(bytes, stream, ctx) returns device memory usable in stream order on `stream` (NULL on
+ * failure: the build returns APR_ERR_OOM); free(ptr, bytes, stream, ctx) releases it, called by
+ * apr_destroy after the device has been synchronised. `stream` is the build stream; it must stay
+ * valid until apr_destroy. */
+typedef struct {
+    void *(*alloc)(size_t bytes, apr_stream_t stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, apr_stream_t stream, void *ctx);
+    void *ctx;
+} apr_allocator;
+
+/* apr_build_device with the handle's device memory taken from `allocator` (NULL: stream-ordered
+ * cudaMallocAsync, as apr_build_device). */
+apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream,
+                                 const apr_allocator *allocator, apr_handle_t *out);
 
 /* Release the handle and its device memory (synchronises the device first). NULL is accepted. */
 apr_status_t apr_destroy(apr_handle_t h);
@@ -114,7 +132,7 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which);
 /* Copy structure array `which` to host memory `dst` of `bytes` (>= apr_structure_bytes). */
 apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes);
 
-/* APR tree restriction (Sec. 3.4, two-step fill; P:407 step 2): for l = l_max-1 down to l_min, every
+/* APR tree restriction (Sec. 3.4, two-step fill, step 2; Sec. 5.2, GPU pipeline): for l = l_max-1 down to l_min, every
  * tree node gets the average of its children inside the level grid, each child being a particle of
  * level l+1 or a tree node of level l+1 (average downsampling, Sec. 2.3).
  *   particles: device [N_p][channels] float32 (channels-last), read only.
@@ -205,7 +223,10 @@ apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, c
  * apr_convolve_backward, and gets the same results.
  *   - Returns APR_ERR_UNSUPPORTED when apr_backward_workspace_bytes(h, k) exceeds 16 MiB.
  *   - The first call on each device looks up the array's device address with that device current
- *     (cudaGetSymbolAddress); make that first call before any stream capture on that device.
+ *     (cudaGetSymbolAddress). With CUDA's lazy module loading (the default) that first call is also
+ *     when the device reserves the 16 MiB, so it can fail with APR_ERR_OOM if other allocators have
+ *     taken the memory by then: make the first call at set-up, before other allocators reserve
+ *     memory and before any stream capture on that device.
  *   - Every call shares the one array, which keeps the previous call's contents (the call clears what
  *     must start at zero itself). Calls that overlap on the GPU, from any handle or stream, race on it. */
 apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particles, const float *tree,
@@ -308,6 +329,23 @@ apr_status_t apr_restrict_stencil(const float *w, int32_t k, int32_t l_max, int3
 
 /* Level-rescaled stencils (Eq. adapt_grad): out[l - l_min] = 2^-(l_max - l) * w. Host memory. */
 apr_status_t apr_rescale_stencil(const float *w, int32_t k, int32_t l_max, int32_t l_min, float *out);
+
+/* Dense pixel-grid correlation (the dense comparison of the paper's results, Sec. 6.1: a pixel
+ * image convolved with a stencil of the same size as the APR one; not part of the APR path):
+ * out[z][x][y] = sum_e w[e] img[refl(z + ez)][refl(x + ex)][refl(y + ey)] (or zero outside the
+ * image with APR_BC_ZERO), FP32.
+ *   image, out: device [dz][dx][dy] float32 (y contiguous); stencil: device [k^3] float32; k: 3 or 5.
+ * Returns APR_ERR_UNSUPPORTED for other k or grids of more than 65535 x 8 x columns or 65535 x 32
+ * z planes. */
+apr_status_t apr_dense_convolve(const float *image, int64_t dz, int64_t dx, int64_t dy, const float *stencil,
+                                int32_t k, int32_t bc, float *out, apr_stream_t stream);
+
+/* Host helper (no device): the Sobel derivative stencils of the gradient estimate (Sec. 4.3), out =
+ * host [3][k^3] float32 along z, x, y: the central difference (-1/2, 0, 1/2) along the axis times
+ * the smoothing (1/4, 1/2, 1/4) across it in both other axes, so a linear ramp of slope 1 gives 1.
+ * Pass each through apr_rescale_stencil (Eq. adapt_grad) for apr_gradient_magnitude. k = 3 only
+ * (APR_ERR_UNSUPPORTED otherwise). */
+apr_status_t apr_sobel_stencils(int32_t k, float *out);
 
 /* Self-test of the device error path (no paper counterpart): launches one block that waits on a
  * barrier nothing will complete, gives up after limit_us microseconds (1 .. 2 000 000) with the

@@ -37,7 +37,7 @@ __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
            "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_relu_bf16", "apr_convolve_mc_backward",
            "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
-           "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "AprError",
+           "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "apr_dense_convolve", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
            "APR_SUBDOMAIN"]
 
@@ -61,11 +61,36 @@ def _dev_ptr(t, name, numel=None, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _torch_allocator():
+    """apr_allocator callbacks backed by torch's CUDA caching allocator (stream-ordered on the
+    build stream). Returns (struct, keep-alive objects)."""
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          stream if stream else 0))
+        except Exception:  # out of memory: the library reports APR_ERR_OOM
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    fa, ff = _abi.ALLOC_FN(alloc), _abi.FREE_FN(free)
+    return _abi.AprAllocator(fa, ff, None), (fa, ff)
+
+
 class AprLayout:
-    """Owns an apr_handle_t: the device-resident index of one APR (particles + APR tree)."""
+    """Owns an apr_handle_t: the device-resident index of one APR (particles + APR tree).
+
+    allocator: None (the library allocates stream-ordered with cudaMallocAsync) or "torch" (the
+    index lives in torch's caching allocator, through apr_build_device_ex's callbacks)."""
 
     def __init__(self, dims, l_min, l_max, row_ptr, y_idx,
-                 flags=APR_VALIDATE | APR_REQUIRE_BALANCE):
+                 flags=APR_VALIDATE | APR_REQUIRE_BALANCE, allocator=None):
         lib = _abi.load()
         self._row_ptr = np.ascontiguousarray(np.asarray(row_ptr, np.int64))
         self._y_idx = np.ascontiguousarray(np.asarray(y_idx, np.int32))
@@ -80,7 +105,16 @@ class AprLayout:
         stream = ctypes.c_void_p(0)
         if not (flags & APR_HOST_ONLY):
             stream = _stream_ptr()
-        _abi.check("apr_build_device", lib.apr_build_device(ctypes.byref(L), flags, stream, ctypes.byref(h)))
+        self._alloc_keep = None
+        if allocator is None:
+            _abi.check("apr_build_device", lib.apr_build_device(ctypes.byref(L), flags, stream, ctypes.byref(h)))
+        elif allocator == "torch":
+            al, self._alloc_keep = _torch_allocator()
+            self._alloc_struct = al
+            _abi.check("apr_build_device_ex",
+                       lib.apr_build_device_ex(ctypes.byref(L), flags, stream, ctypes.byref(al), ctypes.byref(h)))
+        else:
+            raise ValueError("allocator must be None or 'torch'")
         self._h = h
         self._lib = lib
         self.dims = tuple(int(d) for d in dims)
@@ -91,9 +125,9 @@ class AprLayout:
         self._ws = {}
 
     @classmethod
-    def from_apr(cls, apr, flags=APR_VALIDATE | APR_REQUIRE_BALANCE):
+    def from_apr(cls, apr, flags=APR_VALIDATE | APR_REQUIRE_BALANCE, allocator=None):
         """From any object with dims, l_min, l_max, row_ptr, y_idx (e.g. aprsynth.AprInput)."""
-        return cls(apr.dims, apr.l_min, apr.l_max, apr.row_ptr, apr.y_idx, flags)
+        return cls(apr.dims, apr.l_min, apr.l_max, apr.row_ptr, apr.y_idx, flags, allocator)
 
     @property
     def n_levels(self):
@@ -211,18 +245,31 @@ def apr_gradient_magnitude(layout: AprLayout, particles, tree, stencils3, k, bc=
     return out
 
 
+def apr_dense_convolve(image, stencil, k, bc=APR_BC_REFLECT, out=None, stream=None):
+    """Dense pixel-grid correlation of a [dz][dx][dy] float32 image with one k^3 stencil (the
+    dense comparison; not part of the APR path)."""
+    import torch
+    if image.dim() != 3:
+        raise ValueError("image must be [dz][dx][dy]")
+    _dev_ptr(image, "image", dtype=torch.float32)
+    _dev_ptr(stencil, "stencil", k ** 3, torch.float32)
+    if out is None:
+        out = torch.empty_like(image)
+    _dev_ptr(out, "out", image.numel(), torch.float32)
+    dz, dx, dy = (int(d) for d in image.shape)
+    _abi.check("apr_dense_convolve", _abi.load().apr_dense_convolve(
+        _dev_ptr(image, "image"), dz, dx, dy, _dev_ptr(stencil, "stencil"), int(k), int(bc),
+        _dev_ptr(out, "out"), _stream_ptr(stream)))
+    return out
+
+
 def sobel_stencils(k=3):
-    """Sobel derivative stencils [3][k][k][k] along z, x, y (central difference along the axis,
-    [1, 2, 1] smoothing across it, normalised so a linear ramp of slope 1 gives 1). Host, float32."""
-    if k != 3:
-        raise ValueError("Sobel stencils are 3x3x3")
-    d = np.array([-0.5, 0.0, 0.5])
-    sm = np.array([0.25, 0.5, 0.25])
-    out = np.zeros((3, 3, 3, 3))
-    out[0] = np.einsum("i,j,k->ijk", d, sm, sm)
-    out[1] = np.einsum("i,j,k->ijk", sm, d, sm)
-    out[2] = np.einsum("i,j,k->ijk", sm, sm, d)
-    return out.astype(np.float32)
+    """Sobel derivative stencils [3][k][k][k] along z, x, y (apr_sobel_stencils: central difference
+    along the axis, [1, 2, 1] / 4 smoothing across it, so a linear ramp of slope 1 gives 1)."""
+    lib = _abi.load()
+    out = np.zeros((3, k, k, k), np.float32)
+    _abi.check("apr_sobel_stencils", lib.apr_sobel_stencils(int(k), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def apr_convolve_backward(layout: AprLayout, particles, tree, stencils, k, grad_out, bc=APR_BC_REFLECT,

@@ -32,18 +32,36 @@ namespace {
 
 thread_local char g_last_msg[256] = "";
 
-// Device copy of n elements, the allocation rounded up to a multiple of `pad` elements (zeroed
-// tail): the y arrays are read in aligned 8-element packets.
+// One device block of the handle: from the caller's allocator when one was given, else
+// stream-ordered (cudaMallocAsync on the build stream). Every block is recorded for apr_destroy.
+cudaError_t dev_alloc(apr_handle_s *h, void **p, size_t bytes) {
+    *p = nullptr;
+    if (h->has_alloc) {
+        *p = h->alloc.alloc(bytes, h->stream, h->alloc.ctx);
+        if (!*p) return cudaErrorMemoryAllocation;
+    } else {
+        const cudaError_t e = cudaMallocAsync(p, bytes, reinterpret_cast<cudaStream_t>(h->stream));
+        if (e != cudaSuccess) return e;
+    }
+    h->blocks.emplace_back(*p, bytes);
+    h->dev_bytes += bytes;
+    return cudaSuccess;
+}
+
+// Device copy of n elements on the build stream, the allocation rounded up to a multiple of `pad`
+// elements (zeroed tail): the y arrays are read in aligned 8-element packets. The host arrays are
+// pageable, so cudaMemcpyAsync has staged them when it returns; the caller may free them.
 template <typename T>
-cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes, size_t pad = 1) {
+cudaError_t upload(apr_handle_s *h, T **dst, const T *src, size_t n, size_t pad = 1) {
     *dst = nullptr;
     const size_t na = ((n ? n : 1) + pad - 1) / pad * pad;
-    const size_t b = na * sizeof(T);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), b);
+    void *p = nullptr;
+    cudaError_t e = dev_alloc(h, &p, na * sizeof(T));
     if (e != cudaSuccess) return e;
-    bytes += b;
-    if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && na > n) e = cudaMemset(*dst + n, 0, (na - n) * sizeof(T));
+    *dst = static_cast<T *>(p);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(h->stream);
+    if (n) e = cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && na > n) e = cudaMemsetAsync(*dst + n, 0, (na - n) * sizeof(T), s);
     return e;
 }
 
@@ -51,19 +69,13 @@ cudaError_t upload(T **dst, const T *src, size_t n, size_t &bytes, size_t pad = 
 // vectors: their base addresses must be 16-byte aligned.
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Releases every device block of the handle (the caller has synchronised the device).
 void free_device(apr_handle_s *h) {
-    void *ptrs[] = {h->d_fwd, h->d_bwd, h->d_tree, h->d_fwd_level_begin, h->d_row_ptr, h->d_trow_ptr,
-                    h->d_y, h->d_ty, h->d_off, h->d_toff, h->d_err, h->d_mcw};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    for (int i = 0; i < 2; ++i) {
-        if (h->d_plan_hdr[i]) cudaFree(h->d_plan_hdr[i]);
-        if (h->d_plan_ent[i]) cudaFree(h->d_plan_ent[i]);
+    for (const auto &b : h->blocks) {
+        if (h->has_alloc) h->alloc.free(b.first, b.second, h->stream, h->alloc.ctx);
+        else cudaFree(b.first);
     }
-    for (int i = 0; i < 4; ++i) {
-        if (h->d_fplan_hdr[i]) cudaFree(h->d_fplan_hdr[i]);
-        if (h->d_fplan_ent[i]) cudaFree(h->d_fplan_ent[i]);
-    }
+    h->blocks.clear();
 }
 
 bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
@@ -120,11 +132,22 @@ const char *apr_status_string(apr_status_t s) {
 const char *apr_last_error_message(void) { return g_last_msg; }
 
 apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream, apr_handle_t *out) {
+    return apr_build_device_ex(layout, flags, stream, nullptr, out);
+}
+
+apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, apr_stream_t stream,
+                                 const apr_allocator *allocator, apr_handle_t *out) {
     if (!out) return APR_ERR_INVALID_ARG;
     *out = nullptr;
     if (!layout || (flags & ~(APR_VALIDATE | APR_REQUIRE_BALANCE | APR_HOST_ONLY | APR_SUBDOMAIN))) return APR_ERR_INVALID_ARG;
+    if (allocator && (!allocator->alloc || !allocator->free)) return APR_ERR_INVALID_ARG;
     apr_handle_s *h = new (std::nothrow) apr_handle_s();
     if (!h) return APR_ERR_OOM;
+    h->stream = stream;
+    if (allocator) {
+        h->alloc = *allocator;
+        h->has_alloc = true;
+    }
     const char *msg = "";
     apr_status_t st;
     try {
@@ -140,7 +163,6 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
     }
     h->host_only = (flags & APR_HOST_ONLY) != 0;
     if (!h->host_only) {
-        (void)stream;  // uploads are synchronous: the index is built once
         const apr_status_t pst = build_plans(h->X);
         if (pst != APR_OK) {
             snprintf(g_last_msg, sizeof(g_last_msg), "%s", pst == APR_ERR_OOM ? "host allocation failed (tile plans)"
@@ -150,42 +172,42 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
         }
         const HostIndex &X = h->X;
         cudaError_t e = cudaSuccess;
-        size_t &b = h->dev_bytes;
-        if (e == cudaSuccess) e = upload(&h->d_row_ptr, X.row_ptr.data(), X.row_ptr.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_y, X.y.data(), X.y.size(), b, 8);
-        if (e == cudaSuccess) e = upload(&h->d_off, X.off.data(), X.off.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_trow_ptr, X.trow_ptr.data(), X.trow_ptr.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_ty, X.ty.data(), X.ty.size(), b, 8);
-        if (e == cudaSuccess) e = upload(&h->d_toff, X.toff.data(), X.toff.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_fwd, X.fwd_items.data(), X.fwd_items.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_bwd, X.bwd_items.data(), X.bwd_items.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_tree, X.tree_items.data(), X.tree_items.size(), b);
-        if (e == cudaSuccess) e = upload(&h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1), b);
+        if (e == cudaSuccess) e = upload(h, &h->d_row_ptr, X.row_ptr.data(), X.row_ptr.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_y, X.y.data(), X.y.size(), 8);
+        if (e == cudaSuccess) e = upload(h, &h->d_off, X.off.data(), X.off.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_trow_ptr, X.trow_ptr.data(), X.trow_ptr.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_ty, X.ty.data(), X.ty.size(), 8);
+        if (e == cudaSuccess) e = upload(h, &h->d_toff, X.toff.data(), X.toff.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_fwd, X.fwd_items.data(), X.fwd_items.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_bwd, X.bwd_items.data(), X.bwd_items.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_tree, X.tree_items.data(), X.tree_items.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1));
         for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
             const HostFPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
-            e = upload(&h->d_fplan_hdr[i], P.hdr.data(), P.hdr.size(), b);
-            if (e == cudaSuccess) e = upload(&h->d_fplan_ent[i], P.ent.data(), P.ent.size(), b);
+            e = upload(h, &h->d_fplan_hdr[i], P.hdr.data(), P.hdr.size());
+            if (e == cudaSuccess) e = upload(h, &h->d_fplan_ent[i], P.ent.data(), P.ent.size());
         }
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
             const HostPlan &P = i == 0 ? X.mcfplan : X.mcbplan;
-            e = upload(&h->d_plan_hdr[i], P.hdr.data(), P.hdr.size(), b);
-            if (e == cudaSuccess) e = upload(&h->d_plan_ent[i], P.ent.data(), P.ent.size(), b);
+            e = upload(h, &h->d_plan_hdr[i], P.hdr.data(), P.hdr.size());
+            if (e == cudaSuccess) e = upload(h, &h->d_plan_ent[i], P.ent.data(), P.ent.size());
         }
         if (e == cudaSuccess) {
-            e = cudaMalloc(reinterpret_cast<void **>(&h->d_err), sizeof(unsigned));
-            if (e == cudaSuccess) {
-                b += sizeof(unsigned);
-                e = cudaMemset(h->d_err, 0, sizeof(unsigned));
-            }
+            void *p = nullptr;
+            e = dev_alloc(h, &p, sizeof(unsigned));
+            h->d_err = static_cast<unsigned *>(p);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), reinterpret_cast<cudaStream_t>(stream));
         }
         if (e == cudaSuccess) {
             // operand-layout copy of multi-channel weights: [2 (plain, transposed)][levels][27 * 16 * 16]
             const size_t nb = size_t(2) * size_t(X.l_max - X.l_min + 1) * 27 * 16 * 16 * sizeof(uint16_t);
-            e = cudaMalloc(reinterpret_cast<void **>(&h->d_mcw), nb);
-            if (e == cudaSuccess) b += nb;
+            void *p = nullptr;
+            e = dev_alloc(h, &p, nb);
+            h->d_mcw = static_cast<uint16_t *>(p);
         }
         if (e != cudaSuccess) {
             st = cuda_status(e);
+            cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
             free_device(h);
             delete h;
             return st;
@@ -278,8 +300,10 @@ apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size
         memcpy(dst, host_src, need);
         return APR_OK;
     }
-    // the device copy is the one the kernels read
-    return cuda_status(cudaMemcpy(dst, dev_src, need, cudaMemcpyDeviceToHost));
+    // the device copy is the one the kernels read (uploaded on the build stream)
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(h->stream));
+    if (e == cudaSuccess) e = cudaMemcpy(dst, dev_src, need, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
 }
 
 apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tree, int32_t channels,

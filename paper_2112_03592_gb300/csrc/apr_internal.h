@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -147,6 +148,10 @@ struct apr_handle_s {
     uint16_t *d_y = nullptr, *d_ty = nullptr, *d_off = nullptr, *d_toff = nullptr;
     unsigned *d_err = nullptr;
     uint16_t *d_mcw = nullptr;   // multi-channel weights in the tensor-core operand layout, per level
+    apr_stream_t stream = nullptr;                      // the build stream (uploads, stream-ordered allocation)
+    apr_allocator alloc{};                              // the caller's allocator, if has_alloc
+    bool has_alloc = false;
+    std::vector<std::pair<void *, size_t>> blocks;      // every device block of the handle
     // tile plans: multi-channel feature, adjoint
     aprk::PlanHdr *d_plan_hdr[2] = {};
     aprk::PlanEnt *d_plan_ent[2] = {};

@@ -69,4 +69,18 @@ apr_status_t apr_rescale_stencil(const float *w, int32_t k, int32_t l_max, int32
     return APR_OK;
 }
 
+apr_status_t apr_sobel_stencils(int32_t k, float *out) {
+    if (!out) return APR_ERR_INVALID_ARG;
+    if (k != 3) return APR_ERR_UNSUPPORTED;
+    const double d[3] = {-0.5, 0.0, 0.5}, sm[3] = {0.25, 0.5, 0.25};
+    for (int a = 0; a < 3; ++a)           // derivative axis: z, x, y
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int m = 0; m < 3; ++m) {
+                    const double fz = a == 0 ? d[i] : sm[i], fx = a == 1 ? d[j] : sm[j], fy = a == 2 ? d[m] : sm[m];
+                    out[((a * 3 + i) * 3 + j) * 3 + m] = float(fz * fx * fy);
+                }
+    return APR_OK;
+}
+
 }  // extern "C"

@@ -193,3 +193,38 @@ def test_compute_calls_reject_bad_arguments_without_a_device():
     bad = _abi.AprHostLayout()
     out = P()
     assert lib.apr_build_device(ctypes.byref(bad), 1 << 7, P(0), ctypes.byref(out)) == inv  # unknown flag
+
+
+def test_sobel_stencils_helper():
+    """apr_sobel_stencils: derivative (-1/2, 0, 1/2) along one axis, smoothing (1/4, 1/2, 1/4) across
+    (Sec. 4.3); a linear ramp of slope 1 along the axis correlates to 1, the other axes to 0."""
+    import numpy as np
+    sob = G.sobel_stencils(3)
+    d, sm = np.array([-0.5, 0.0, 0.5]), np.array([0.25, 0.5, 0.25])
+    ref = np.stack([np.einsum("i,j,k->ijk", d, sm, sm), np.einsum("i,j,k->ijk", sm, d, sm),
+                    np.einsum("i,j,k->ijk", sm, sm, d)]).astype(np.float32)
+    np.testing.assert_array_equal(sob, ref)
+    g = np.meshgrid(np.arange(3.0), np.arange(3.0), np.arange(3.0), indexing="ij")
+    for a in range(3):
+        for b in range(3):
+            assert abs(float(np.sum(sob[a] * g[b])) - (1.0 if a == b else 0.0)) < 1e-6
+    lib = _abi.load()
+    assert lib.apr_sobel_stencils(3, None) == 1   # APR_ERR_INVALID_ARG
+    out = np.zeros(3 * 125, np.float32)
+    assert lib.apr_sobel_stencils(5, out.ctypes.data_as(ctypes.c_void_p)) == 3   # APR_ERR_UNSUPPORTED
+
+
+def test_build_device_ex_rejects_incomplete_allocator():
+    apr = S.random_balanced_apr((8, 8, 8), 1, seed=1)
+    lib = _abi.load()
+    L = _abi.AprHostLayout()
+    rp = np.ascontiguousarray(apr.row_ptr.astype(np.int64))
+    yi = np.ascontiguousarray(apr.y_idx.astype(np.int32))
+    L.l_min, L.l_max = apr.l_min, apr.l_max
+    for a in range(3):
+        L.dims[a] = apr.dims[a]
+    L.row_ptr, L.y_idx, L.n_particles = rp.ctypes.data_as(ctypes.c_void_p), yi.ctypes.data_as(ctypes.c_void_p), apr.n_particles
+    al = _abi.AprAllocator()  # both callbacks NULL
+    h = ctypes.c_void_p()
+    assert lib.apr_build_device_ex(ctypes.byref(L), 0, None, ctypes.byref(al), ctypes.byref(h)) == 1  # INVALID_ARG
+    assert not h.value

@@ -250,3 +250,34 @@ def test_convolve_auto_equals_restrict_then_convolve(bc):
     if lay.n_tree > 0:
         with pytest.raises(RuntimeError):
             G.apr_convolve_auto(lay, v, st, 5, bc, workspace=small)
+
+
+def test_index_in_torch_caching_allocator_gives_identical_results():
+    """apr_build_device_ex with callbacks into torch's caching allocator: the handle's index lives in
+    torch memory (torch counts it), results are bit-identical to the library's stream-ordered
+    allocation, and apr_destroy gives the memory back."""
+    apr = S.make_config("blob64", use_cache=False)
+    st = dev(stencil_stack(apr, 5, "restricted"))
+    v = dev(apr.values.astype(np.float32))
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    lay_t = G.AprLayout.from_apr(apr, FLAGS, allocator="torch")
+    torch.cuda.synchronize()
+    grown = torch.cuda.memory_allocated() - before
+    assert grown >= lay_t.layout_bytes() > 0
+    lay_c = G.AprLayout.from_apr(apr, FLAGS)
+    outs = []
+    for lay in (lay_t, lay_c):
+        tree = G.apr_tree_restrict(lay, v)
+        out = G.apr_convolve(lay, v, tree, st, 5)
+        gp, gw = G.apr_convolve_backward(lay, v, tree, st, 5, out)
+        torch.cuda.synchronize()
+        lay.sync_status()
+        outs.append((tree, out, gp, gw))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    nbytes = lay_t.layout_bytes()
+    held = torch.cuda.memory_allocated()
+    lay_t.close()
+    torch.cuda.synchronize()
+    assert held - torch.cuda.memory_allocated() >= nbytes
