@@ -19,7 +19,7 @@ OUT = PKG / "_build"
 LIB = OUT / "libaprconv.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["apr_index.cpp", "apr_stencil.cpp", "apr_plan.cu", "apr_api.cu", "apr_kernels.cu", "apr_noalloc.cu", "apr_mc.cu",
-           "apr_cnn.cu"]
+           "apr_cnn.cu", "apr_dense.cu"]
 
 
 def _nvcc() -> str:
