@@ -94,6 +94,20 @@ __host__ __device__ constexpr int w2_stride() {
     return ((2 * R + 1) + 1) / 2 * 4;
 }
 
+// Lanes per window: radius-1 windows (9 stencil rows) take one lane each, radius-2 windows (25 rows)
+// two lanes over alternate rows.
+template <int R>
+__host__ __device__ constexpr int lanes_per_window() {
+    return R == 1 ? 1 : 2;
+}
+
+// Offsets of the stencil rows (dz, dx) = pair in a staged patch: roff[pair] = (dz PX + dx) PYS.
+template <int R>
+__device__ __forceinline__ void fill_row_offsets(int *roff) {
+    using G = Geo<R>;
+    for (int i = threadIdx.x; i < G::NPAIR; i += NT) roff[i] = ((i / G::K) * G::PX + i % G::K) * G::PYS;
+}
+
 template <int R, int NS>
 struct FwdSmem {
     using G = Geo<R>;
@@ -107,6 +121,7 @@ struct FwdSmem {
     int rfirst[NIR];                            // first target (particle index) of interior row r
     unsigned short act[NIW];                    // windows holding targets, in window order
     unsigned short pseg[PCAP];                  // segment of every packet of the current chunk
+    int roff[G::NPAIR];                         // stencil-row offsets in the patch (fill_row_offsets)
     int nact;
 };
 
@@ -181,6 +196,13 @@ __device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0,
                     const int rz = rz0 + a, rx = rx0 + b;
                     if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
                     float *q = S.patch + (rz * G::PX + rx) * G::PYS;
+                    if constexpr (R % 2 == 0) {
+                        // yw = y0 - R is even, so pos is even: both cells are one aligned float2
+                        if (c0 && c1) {
+                            *reinterpret_cast<float2 *>(q + pos) = make_float2(vv[j], vv[j]);
+                            continue;
+                        }
+                    }
                     if (c0) q[pos] = vv[j];
                     if (c1) q[pos + 1] = vv[j];
                 }
@@ -203,6 +225,7 @@ __device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const fl
     const bool boundary = fwd_tile_at_boundary<R>(L, it);
     const bool reflect = bc == APR_BC_REFLECT;
 
+    fill_row_offsets<R>(S.roff);
     for (int i = tid; i < G::NROW * G::PYS / 4; i += NT)
         reinterpret_cast<float4 *>(S.patch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < NIR) {
@@ -333,15 +356,43 @@ __device__ void load_taps2(const float *__restrict__ stencils, int l_idx, bool f
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Partial window sums over the stencil rows pair = sub, sub + 2, ... (the two lanes of a window take
-// alternate rows): acc[j] = sum_rows sum_t w[row][t] * P[row][col + j + t], j < WIN. Paired FP32
-// FMAs: even taps update (acc_{2i}, acc_{2i+1}) from the aligned value pairs (v_{2i+t}, v_{2i+t+1}),
-// odd taps update separate pairs (o_{2m-1}, o_{2m}) from (v_{2m-1+t}, v_{2m+t}), also aligned; the
-// two are added at the end (o_{-1} and o_8 are unused).
+// One stencil row of a window: (acc_{2i}, acc_{2i+1}) += even taps x the aligned value pairs
+// (v_{2i+t}, v_{2i+t+1}) in E, (o_{2m-1}, o_{2m}) += odd taps x (v_{2m-1+t}, v_{2m+t}) in O (also
+// aligned pairs); paired FP32 FMAs.
 template <int R>
-__device__ __forceinline__ void window_part2(const float *patch, const float *w2, int w, int sub, float acc[WIN]) {
+__device__ __forceinline__ void window_row2(const float *src_row, const float *wrow, float2 E[4], float2 O[5]) {
+    const float4 *src = reinterpret_cast<const float4 *>(src_row);
+    const float4 q0 = src[0], q1 = src[1], q2 = src[2];
+    const float2 V[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                         make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float4 *wq = reinterpret_cast<const float4 *>(wrow);
+    const float4 wa = wq[0], wb = wq[1];
+    const float2 W0 = make_float2(wa.x, wa.y), W1 = make_float2(wa.z, wa.w), W2 = make_float2(wb.x, wb.y);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[i] = ffma2(W0, V[i], E[i]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[i] = ffma2(W2, V[i + 1], E[i]);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) O[m] = ffma2(W1, V[m], O[m]);
+    if constexpr (R == 2) {
+        const float4 wc = wq[2];
+        const float2 W3 = make_float2(wb.z, wb.w), W4 = make_float2(wc.x, wc.y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) E[i] = ffma2(W4, V[i + 2], E[i]);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) O[m] = ffma2(W3, V[m + 1], O[m]);
+    }
+}
+
+// Window sums over the stencil rows pair = sub, sub + LPW, ...: acc[j] = sum_rows sum_t
+// w[row][t] * P[row][col + j + t], j < WIN (window_row2; o_{-1} and o_8 are unused). Radius 1:
+// the 9 rows unrolled; radius 2: a loop over the row-offset table (not unrolled: it keeps the
+// instruction cache warm).
+template <int R>
+__device__ __forceinline__ void window_part2(const float *patch, const float *w2, const int *roff, int w, int sub,
+                                             float acc[WIN]) {
     using G = Geo<R>;
-    constexpr int WS = w2_stride<R>();
+    constexpr int WS = w2_stride<R>(), LPW = lanes_per_window<R>();
     const int r = w / NWIN;
     const float *base = patch + ((r / TX) * G::PX + (r % TX)) * G::PYS + (w % NWIN) * WIN;
     float2 E[4], O[5];
@@ -349,30 +400,13 @@ __device__ __forceinline__ void window_part2(const float *patch, const float *w2
     for (int i = 0; i < 4; ++i) E[i] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < 5; ++i) O[i] = make_float2(0.f, 0.f);
+    if constexpr (LPW == 1) {
+#pragma unroll
+        for (int pair = 0; pair < G::NPAIR; ++pair)
+            window_row2<R>(base + ((pair / G::K) * G::PX + pair % G::K) * G::PYS, w2 + pair * WS, E, O);
+    } else {
 #pragma unroll 1
-    for (int pair = sub; pair < G::NPAIR; pair += 2) {  // not unrolled: keeps the instruction cache warm
-        const int dz = pair / G::K, dx = pair - dz * G::K;
-        const float4 *src = reinterpret_cast<const float4 *>(base + (dz * G::PX + dx) * G::PYS);
-        const float4 q0 = src[0], q1 = src[1], q2 = src[2];
-        const float2 V[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                             make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
-        const float4 *wq = reinterpret_cast<const float4 *>(w2 + pair * WS);
-        const float4 wa = wq[0], wb = wq[1];
-        const float2 W0 = make_float2(wa.x, wa.y), W1 = make_float2(wa.z, wa.w), W2 = make_float2(wb.x, wb.y);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) E[i] = ffma2(W0, V[i], E[i]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) E[i] = ffma2(W2, V[i + 1], E[i]);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) O[m] = ffma2(W1, V[m], O[m]);
-        if constexpr (R == 2) {
-            const float4 wc = wq[2];
-            const float2 W3 = make_float2(wb.z, wb.w), W4 = make_float2(wc.x, wc.y);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) E[i] = ffma2(W4, V[i + 2], E[i]);
-#pragma unroll
-            for (int m = 0; m < 5; ++m) O[m] = ffma2(W3, V[m + 1], O[m]);
-        }
+        for (int pair = sub; pair < G::NPAIR; pair += LPW) window_row2<R>(base + roff[pair], w2 + pair * WS, E, O);
     }
     acc[0] = E[0].x + O[0].y;
     acc[1] = E[0].y + O[1].x;
@@ -384,33 +418,38 @@ __device__ __forceinline__ void window_part2(const float *patch, const float *w2
     acc[7] = E[3].y + O[4].x;
 }
 
-// Window sums of the active windows act[0..nact): two adjacent lanes per window over alternate
-// stencil rows, then a reduce-scatter between them (lane 0 of the pair keeps outputs 0..3, lane 1
-// outputs 4..7; the sum of the two halves is commutative, so the result is deterministic).
-// emit(w, j0, own[4]) receives outputs j0 .. j0+3 of window w.
+// Window sums of the active windows act[0..nact). One lane per window (radius 1), or two adjacent
+// lanes over alternate stencil rows followed by a reduce-scatter between them (lane 0 of the pair
+// keeps outputs 0..3, lane 1 outputs 4..7; the sum of the two halves is commutative, so the result
+// is deterministic). emit(w, j0, v, n) receives outputs j0 .. j0+n-1 of window w.
 template <int R, typename Emit>
-__device__ __forceinline__ void fwd_windows(const float *patch, const float *w2, const unsigned short *act, int nact,
-                                            Emit emit) {
-    const int sub = threadIdx.x & 1;
-    for (int base = 0; base < nact; base += NT / 2) {
-        const int a = base + (threadIdx.x >> 1);
+__device__ __forceinline__ void fwd_windows(const float *patch, const float *w2, const int *roff,
+                                            const unsigned short *act, int nact, Emit emit) {
+    constexpr int LPW = lanes_per_window<R>();
+    const int sub = threadIdx.x % LPW;
+    for (int base = 0; base < nact; base += NT / LPW) {
+        const int a = base + threadIdx.x / LPW;
         const bool valid = a < nact;
         const int w = valid ? act[a] : 0;
         float acc[WIN];
         if (valid) {
-            window_part2<R>(patch, w2, w, sub, acc);
+            window_part2<R>(patch, w2, roff, w, sub, acc);
         } else {
 #pragma unroll
             for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
         }
-        float own[4];
+        if constexpr (LPW == 1) {
+            if (valid) emit(w, 0, acc, WIN);
+        } else {
+            float own[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float send = sub ? acc[k] : acc[4 + k];
-            const float keep = sub ? acc[4 + k] : acc[k];
-            own[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+            for (int k = 0; k < 4; ++k) {
+                const float send = sub ? acc[k] : acc[4 + k];
+                const float keep = sub ? acc[4 + k] : acc[k];
+                own[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+            }
+            if (valid) emit(w, 4 * sub, own, 4);
         }
-        if (valid) emit(w, 4 * sub, own);
     }
 }
 
@@ -426,13 +465,13 @@ __device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it
     FwdSmem<R, 1> &S = *reinterpret_cast<FwdSmem<R, 1> *>(smem_raw);
     load_taps2<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w2[0]);
     stage_fwd<R, 1>(L, it, tile, vals, tree, bc, S);
-    fwd_windows<R>(S.patch, S.w2[0], S.act, S.nact, [&](int w, int j0, const float *own) {
+    fwd_windows<R>(S.patch, S.w2[0], S.roff, S.act, S.nact, [&](int w, int j0, const float *v, int n) {
         const unsigned m = win_mask(S, w);
         int p = win_first(S, w) + __popc(m & ((1u << j0) - 1u));
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < n; ++k)
             if ((m >> (j0 + k)) & 1u) {
-                out[p] = epi.apply(p, own[k]);
+                out[p] = epi.apply(p, v[k]);
                 ++p;
             }
     });
@@ -472,35 +511,43 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
 #pragma unroll 1
     for (int a = 0; a < 3; ++a) load_taps2<R>(stencils + size_t(a) * n_levels * G::K3, it.l - L.l_min, false, S.w2[a]);
     stage_fwd<R, 3>(L, it, blockIdx.x, vals, tree, bc, S);
-    const int sub = threadIdx.x & 1;
-    for (int base = 0; base < S.nact; base += NT / 2) {
-        const int ai = base + (threadIdx.x >> 1);
+    constexpr int LPW = lanes_per_window<R>(), NO = WIN / LPW;  // outputs kept per lane
+    const int sub = threadIdx.x % LPW;
+    for (int base = 0; base < S.nact; base += NT / LPW) {
+        const int ai = base + threadIdx.x / LPW;
         const bool valid = ai < S.nact;
         const int w = valid ? S.act[ai] : 0;
-        float sq[4] = {0.f, 0.f, 0.f, 0.f};
+        float sq[NO];
+#pragma unroll
+        for (int k = 0; k < NO; ++k) sq[k] = 0.f;
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             float acc[WIN];
             if (valid) {
-                window_part2<R>(S.patch, S.w2[a], w, sub, acc);
+                window_part2<R>(S.patch, S.w2[a], S.roff, w, sub, acc);
             } else {
 #pragma unroll
                 for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
             }
+            if constexpr (LPW == 1) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float send = sub ? acc[k] : acc[4 + k];
-                const float keep = sub ? acc[4 + k] : acc[k];
-                const float v = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-                sq[k] = fmaf(v, v, sq[k]);
+                for (int k = 0; k < NO; ++k) sq[k] = fmaf(acc[k], acc[k], sq[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float send = sub ? acc[k] : acc[4 + k];
+                    const float keep = sub ? acc[4 + k] : acc[k];
+                    const float v = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+                    sq[k] = fmaf(v, v, sq[k]);
+                }
             }
         }
         if (valid) {
             const unsigned m = win_mask(S, w);
-            const int j0 = 4 * sub;
+            const int j0 = NO * sub;
             int p = win_first(S, w) + __popc(m & ((1u << j0) - 1u));
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < NO; ++k)
                 if ((m >> (j0 + k)) & 1u) {
                     out[p] = sqrtf(sq[k]);
                     ++p;
@@ -604,6 +651,7 @@ struct BwdSmem {
     __align__(16) float w2[G::NPAIR * w2_stride<R>()];  // flipped taps, paired layout
     unsigned occ[G::NROW * 3];                 // nonzero-gradient columns of every patch row (68 bits)
     unsigned long long dil[G::NROW];           // interior columns within R (in y) of a gradient column
+    unsigned long long dilx[G::PZ * TX];       // dil OR-ed over patch rows x .. x + 2R of each z row
     unsigned long long need[NIR];
     int seg_lo[NS];
     unsigned seg_nm[NS];                       // element count | routing / patch-row index << 8
@@ -612,6 +660,7 @@ struct BwdSmem {
     unsigned char wmir[NIW];                   // window has cells with mirrored preimages
     unsigned short act[NIW];
     unsigned short pseg[PCAP];
+    int roff[G::NPAIR];                        // stencil-row offsets in the patch (fill_row_offsets)
     int nact;
 };
 
@@ -723,6 +772,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     const bool reflect = bc == APR_BC_REFLECT;
 
     load_taps2<R, RS>(stencils, l - L.l_min, true, S.w2);
+    fill_row_offsets<R>(S.roff);
     for (int i = tid; i < G::NROW * G::PYS / 4; i += NT) reinterpret_cast<float4 *>(S.gpatch)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < NIR * BY / 4; i += NT) reinterpret_cast<float4 *>(S.H)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < G::NROW * 3; i += NT) S.occ[i] = 0u;
@@ -766,14 +816,23 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                             if (o[wd]) atomicOr(&S.occ[row * 3 + wd], o[wd]);
                     });
     // y-dilation of every patch row: interior column j <-> patch column j + R, needed if any of the
-    // patch columns j .. j + 2R holds a gradient
-    for (int row = tid; row < G::NROW; row += NT) {
+    // patch columns j .. j + 2R holds a gradient; dilx: the same OR-ed over the 2R + 1 patch rows
+    // x .. x + 2R of one patch z row, for the TX interior x columns (the dilation is separable)
+    const auto ydil = [&](int row) {
         const unsigned long long lo64 = (unsigned long long)S.occ[row * 3] | ((unsigned long long)S.occ[row * 3 + 1] << 32);
         const unsigned long long hi64 = S.occ[row * 3 + 2];
         unsigned long long m = lo64;
 #pragma unroll
         for (int d = 1; d <= 2 * R; ++d) m |= (lo64 >> d) | (hi64 << (64 - d));
-        S.dil[row] = m;
+        return m;
+    };
+    for (int row = tid; row < G::NROW; row += NT) S.dil[row] = ydil(row);
+    for (int i = tid; i < G::PZ * TX; i += NT) {
+        const int pz = i / TX, ib = i % TX;
+        unsigned long long m = 0ull;
+#pragma unroll
+        for (int dx = 0; dx <= 2 * R; ++dx) m |= ydil(pz * G::PX + ib + dx);
+        S.dilx[i] = m;
     }
     block_sync();
 
@@ -797,13 +856,18 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                 nx += mirror_preimages<R>(x, g.dx, px + 1);
             }
             edge_zx = nz > 1 || nx > 1;
-            for (int iz = 0; iz < nz; ++iz)
-                for (int ix = 0; ix < nx; ++ix)
-                    for (int pr = q; pr < G::NPAIR; pr += 4) {
-                        const int rz = pz[iz] - z0 + pr / G::K, rx = px[ix] - x0 + pr % G::K;  // patch row
-                        if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
-                        m |= S.dil[rz * G::PX + rx];
-                    }
+            if (!edge_zx) {
+                // no mirrored rows: the patch rows (ia + dz, ib + dx), dz, dx in [0, 2R]
+                for (int dz = q; dz <= 2 * R; dz += 4) m |= S.dilx[((r / TX) + dz) * TX + (r % TX)];
+            } else {
+                for (int iz = 0; iz < nz; ++iz)
+                    for (int ix = 0; ix < nx; ++ix)
+                        for (int pr = q; pr < G::NPAIR; pr += 4) {
+                            const int rz = pz[iz] - z0 + pr / G::K, rx = px[ix] - x0 + pr % G::K;  // patch row
+                            if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
+                            m |= S.dil[rz * G::PX + rx];
+                        }
+            }
         }
         const unsigned mlo = unsigned(m), mhi = unsigned(m >> 32);
         const unsigned olo = mlo | __shfl_xor_sync(0xffffffffu, mlo, 1), ohi = mhi | __shfl_xor_sync(0xffffffffu, mhi, 1);
@@ -852,8 +916,10 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     block_sync();
 
     // H = (flipped stencil) correlated with the gradient patch, at the active windows (c' = c term)
-    fwd_windows<R>(S.gpatch, S.w2, S.act, S.nact, [&](int w, int j0, const float *own) {
-        *reinterpret_cast<float4 *>(S.H + (w / NWIN) * BY + (w % NWIN) * WIN + j0) = make_float4(own[0], own[1], own[2], own[3]);
+    fwd_windows<R>(S.gpatch, S.w2, S.roff, S.act, S.nact, [&](int w, int j0, const float *v, int n) {
+        float4 *dst = reinterpret_cast<float4 *>(S.H + (w / NWIN) * BY + (w % NWIN) * WIN + j0);
+#pragma unroll
+        for (int k = 0; k < n; k += 4) dst[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
     });
     block_sync();
     // mirrored preimages (reflect only). Rows with mirrored z / x rows: one thread per active window
@@ -945,24 +1011,28 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                             for (int j = 0; j < 8; ++j)
                                 if ((m >> j) & 1u) gt[i0 + j] = S.H[(q - NIR) * BY + (yv[j] - y0)];
                         } else {
+                            // a level-(l-1) particle: the sum of H over its (up to) 2 x 2 x 2 level-l cells,
+                            // in (a, b, e) order; the two cells along y are one aligned float2 (y0, j0 even)
                             const int r = q - 2 * NIR;
-                            const int pa = r / (TX / 2), pb = r % (TX / 2);
+                            const int ia = 2 * (r / (TX / 2)), ib = 2 * (r % (TX / 2));
+                            const bool za = z0 + ia + 1 < g.dz, xb = x0 + ib + 1 < g.dx;  // second rows in the grid
+                            const float *h0 = S.H + (ia * TX + ib) * BY;
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
                                 if (!((m >> j) & 1u)) continue;
                                 const int j0 = 2 * yv[j] - y0;  // first level-l cell column of the coarser particle
                                 if (j0 < 0 || j0 >= BY) continue;
+                                const bool ye = y0 + j0 + 1 < g.dy;
                                 float sum = 0.f;
 #pragma unroll
                                 for (int a = 0; a < 2; ++a)
 #pragma unroll
-                                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                                        for (int e = 0; e < 2; ++e) {
-                                            const int ia = 2 * pa + a, ib = 2 * pb + b;
-                                            if (z0 + ia < g.dz && x0 + ib < g.dx && y0 + j0 + e < g.dy)
-                                                sum += S.H[(ia * TX + ib) * BY + j0 + e];
-                                        }
+                                    for (int b = 0; b < 2; ++b) {
+                                        if ((a && !za) || (b && !xb)) continue;
+                                        const float2 h = *reinterpret_cast<const float2 *>(h0 + (a * TX + b) * BY + j0);
+                                        sum += h.x;
+                                        if (ye) sum += h.y;
+                                    }
                                 if (sum != 0.f) atomicAdd(&gp[i0 + j], sum);
                             }
                         }
