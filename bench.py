@@ -203,10 +203,29 @@ def dense_pixel_conv(dims, w, steps, flush, stream):
             ts.append(a.elapsed_time(b))
         ms = statistics.median(ts[1:])
         nbytes = float(img.numel()) * 4
-        del img, out
+        del out
+        # the hand-written dense stencil (2.5-D blocked, apr_dense_convolve), same image, reflect
+        import paper_2112_03592_gb300 as G
+        img3 = img.reshape(img.shape[2:])
+        ker1 = ker.reshape(-1).contiguous()
+        out3 = G.apr_dense_convolve(img3, ker1, w.shape[0])
+        th = []
+        for _ in range(max(3, steps)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.apr_dense_convolve(img3, ker1, w.shape[0], out=out3)
+            b.record(stream)
+            b.synchronize()
+            th.append(a.elapsed_time(b))
+        ms_h = statistics.median(th[1:])
+        del img, img3, out3
         torch.cuda.empty_cache()
         return {"ms": round(ms, 4), "pixel_GBps": round(nbytes / (ms * 1e-3) / 1e9, 2),
                 "library": "cuDNN via torch.nn.functional.conv3d, FP32 (TF32 off), zero padding",
+                "hand_written": {"ms": round(ms_h, 4), "pixel_GBps": round(nbytes / (ms_h * 1e-3) / 1e9, 2),
+                                 "kernel": "dense_conv_kernel (apr_dense_convolve), FP32, 2.5-D blocked, reflect",
+                                 "hbm_frac_read_write": round(2 * nbytes / (ms_h * 1e-3) / 1e9 / float(_peaks()[0]["hbm_gbs"]), 4)},
                 "note": "context for the pixel-equivalent metric; not part of the APR path"}
     except RuntimeError as e:
         return {"unavailable": str(e).splitlines()[0][:200]}
@@ -214,35 +233,15 @@ def dense_pixel_conv(dims, w, steps, flush, stream):
         torch.backends.cudnn.allow_tf32 = prev
 
 
-def run_ours(args, rank, world):
-    import numpy as np
+def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
+    """Times the layer step (tree restriction | convolution | convolution adjoint | tree adjoint |
+    stencil gradient) with stencil stack st on the buffers b: device-resident (CUDA events per part,
+    L2 flushed before every step) and end to end from pinned host buffers. Returns the per-part
+    times, the step and e2e means (max over ranks), the copy sizes and the clock record."""
     import torch
 
-    import aprsynth as S
     import paper_2112_03592_gb300 as G
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    apr = S.make_config(WORKLOAD)
-    t_build = time.perf_counter()
-    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
-    t_build = time.perf_counter() - t_build
-    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
-    st_h = G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
-    Np = apr.n_particles
-    st = torch.as_tensor(st_h, device=dev)
-    vals = torch.as_tensor(apr.values, device=dev)
-    gout = torch.as_tensor(np.random.default_rng(0).normal(size=Np).astype(np.float32), device=dev)
-    tree = torch.empty(lay.n_tree, device=dev)
-    out = torch.empty(Np, device=dev)
-    gp = torch.empty(Np, device=dev)
-    gw = torch.empty((apr.n_levels, K ** 3), device=dev)
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
-    stream = torch.cuda.current_stream()
-
-    gtree = torch.empty(lay.n_tree, device=dev)
-
-    # tree restriction | convolution | convolution adjoint | tree adjoint | stencil gradient
+    vals, gout, tree, out, gp, gw, gtree = (b[k] for k in ("vals", "gout", "tree", "out", "gp", "gw", "gtree"))
     parts_fns = [lambda: G.apr_tree_restrict(lay, vals, tree),
                  lambda: G.apr_convolve(lay, vals, tree, st, K, G.APR_BC_REFLECT, out),
                  lambda: G.apr_convolve_adjoint(lay, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_tree=gtree),
@@ -261,7 +260,7 @@ def run_ours(args, rank, world):
                 e[j + 1].record(stream)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
-    clk = ClockSampler(dev.index).__enter__()
+    clk = ClockSampler(dev.index).__enter__() if clocks else None
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -275,29 +274,27 @@ def run_ours(args, rank, world):
         step(ev[i])
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    wall = t1 - t0
-    time.sleep(0.12)
-    clk.__exit__()
+    clock_rec = None
+    if clk is not None:
+        time.sleep(0.12)
+        clk.__exit__()
+        clock_rec = clk.summary(t0, t1)
     if world > 1:
         torch.distributed.barrier()
     lay.sync_status()
     parts = [[ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)] for j in range(5)]
-    t_restrict, t_conv, t_adj, t_tadj, t_sgrad = parts
-    step_ms = sum(sum(p) for p in parts) / args.steps
-    step_ms = max_over_ranks(step_ms, dev)
+    step_ms = max_over_ranks(sum(sum(p) for p in parts) / args.steps, dev)
 
     # end to end through the public API with host buffers: H2D of the step's inputs (values,
-    # upstream gradient), the step, D2H of its results (outputs, both gradients)
-    h_vals = torch.as_tensor(apr.values).pin_memory()
+    # upstream gradient), the step, D2H of its results (outputs, both gradients). Copies that the
+    # kernels do not wait for run on a second stream: dL/dout goes in while the tree restriction
+    # and the convolution run, the outputs come back while the backward runs, and the particle
+    # gradient while the stencil gradient runs
+    h_vals = vals.cpu().pin_memory()
     h_gout = gout.cpu().pin_memory()
-    h_out = torch.empty(Np).pin_memory()
-    h_gp = torch.empty(Np).pin_memory()
+    h_out = torch.empty(out.numel()).pin_memory()
+    h_gp = torch.empty(gp.numel()).pin_memory()
     h_gw = torch.empty_like(gw, device="cpu").pin_memory()
-
-    # copies that the kernels do not wait for run on a second stream: dL/dout goes in while the tree
-    # restriction and the convolution run, the outputs come back while the backward runs, and the
-    # particle gradient while the stencil gradient runs (run_part order: restrict, convolve, adjoint,
-    # tree adjoint, stencil gradient)
     cs = torch.cuda.Stream(device=dev)
     ev_g, ev_out, ev_gp = (torch.cuda.Event() for _ in range(3))
 
@@ -330,14 +327,49 @@ def run_ours(args, rank, world):
     e2e_ms = []
     for _ in range(args.steps):
         flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e = sum(e2e_ms) / len(e2e_ms)
-    e2e = max_over_ranks(e2e, dev)
+        bb.record(stream)
+        bb.synchronize()
+        e2e_ms.append(a.elapsed_time(bb))
+    e2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dev)
+    return {"parts": parts, "step_ms": step_ms, "e2e_ms": e2e, "wall": t1 - t0, "clocks": clock_rec,
+            "h2d": int(h_vals.numel() * 4 + h_gout.numel() * 4),
+            "d2h": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4)}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    apr = S.make_config(WORKLOAD)
+    t_build = time.perf_counter()
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    t_build = time.perf_counter() - t_build
+    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
+    st_h = G.apr_restrict_stencil(w, apr.l_max, apr.l_min)
+    Np = apr.n_particles
+    st = torch.as_tensor(st_h, device=dev)
+    vals = torch.as_tensor(apr.values, device=dev)
+    gout = torch.as_tensor(np.random.default_rng(0).normal(size=Np).astype(np.float32), device=dev)
+    tree = torch.empty(lay.n_tree, device=dev)
+    out = torch.empty(Np, device=dev)
+    gp = torch.empty(Np, device=dev)
+    gw = torch.empty((apr.n_levels, K ** 3), device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    gtree = torch.empty(lay.n_tree, device=dev)
+    bufs = dict(vals=vals, gout=gout, tree=tree, out=out, gp=gp, gw=gw, gtree=gtree)
+    T = layer_step(args, lay, st, bufs, dev, stream, flush, world, clocks=True)
+    parts, step_ms, e2e, wall, clocks = T["parts"], T["step_ms"], T["e2e_ms"], T["wall"], T["clocks"]
+    t_restrict, t_conv, t_adj, t_tadj, t_sgrad = parts
 
     # gradient magnitude with level-rescaled Sobel filters (Sec. 4.3): three 3^3 convolutions on one
     # staged patch, timed alone (L2 flushed before each launch)
@@ -381,7 +413,6 @@ def run_ours(args, rank, world):
     dom_ms, dom_kernel = (adj_ms, "conv_bwd_data_kernel<2>") if adj_ms >= conv_ms else (conv_ms, "conv_fwd_kernel<2>")
     dom_name = dom_kernel + (" (apr_convolve_adjoint)" if dom_kernel.startswith("conv_bwd") else " (apr_convolve)")
     traffic = recorded_traffic(dom_kernel)
-    clocks = clk.summary(t0, t1)
     rec = {
         "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
         "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4),
@@ -422,8 +453,7 @@ def run_ours(args, rank, world):
                      "algorithmic_bytes_per_launch": conv_bytes,
                      "convolve_frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4)},
         "e2e": {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
-                "h2d_bytes_per_step": int(h_vals.numel() * 4 + h_gout.numel() * 4),
-                "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),
+                "h2d_bytes_per_step": T["h2d"], "d2h_bytes_per_step": T["d2h"],
                 "ms_per_step": round(e2e, 4),
                 "copies": "pinned host buffers; dL/dout in and outputs out on a second stream, overlapped with "
                           "the step's kernels"},
@@ -433,9 +463,69 @@ def run_ours(args, rank, world):
         "layout_bytes": lay.layout_bytes(),
         "layout_build_s": round(t_build, 3),   # once per APR: validation, index, work lists, tile plans, upload
     }
+    # the plain method on the same APR (Sec. 4.1): the 5^3 Gaussian itself at every level (radius 2
+    # everywhere), the same step, buffers and timing
+    if not args.no_plain:
+        st_plain = torch.as_tensor(np.repeat(w.reshape(1, -1), apr.n_levels, 0), device=dev).contiguous()
+        P = layer_step(args, lay, st_plain, bufs, dev, stream, flush, world)
+        pp = [mean(v) for v in P["parts"]]
+        p_dom_ms, p_dom = (pp[2], "conv_bwd_data_kernel<2>") if pp[2] >= pp[1] else (pp[1], "conv_fwd_kernel<2>")
+        rec["plain5"] = {
+            "value": round(world * Np / (P["step_ms"] * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
+            "ms_per_step": round(P["step_ms"], 5),
+            "config": "same APR and step, 5^3 Gaussian sigma=1.5 at every level (no per-level restriction)",
+            "step_ms_parts": dict(zip(("tree_restrict", "convolve", "convolve_adjoint", "tree_restrict_adjoint",
+                                       "stencil_grad"), (round(v, 5) for v in pp))),
+            "forward_pipeline": {"ms": round(pp[0] + pp[1], 5),
+                                 "pixel_equiv_GBps": round(pix_bytes / ((pp[0] + pp[1]) * 1e-3) / 1e9, 2)},
+            "roofline": {"kernel": p_dom, "bound": "hbm", "achieved": round(conv_bytes / (p_dom_ms * 1e-3) / 1e9, 2),
+                         "peak": hbm, "unit": "GB/s", "frac": round(conv_bytes / (p_dom_ms * 1e-3) / 1e9 / hbm, 4),
+                         "convolve_frac": round(conv_bytes / (pp[1] * 1e-3) / 1e9 / hbm, 4),
+                         "algorithmic_bytes_per_launch": conv_bytes, "peak_source": src + " (hbm_gbs)"},
+            "e2e": {"value": round(world * Np / (P["e2e_ms"] * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
+                    "h2d_bytes_per_step": P["h2d"], "d2h_bytes_per_step": P["d2h"], "ms_per_step": round(P["e2e_ms"], 4)},
+            "gpu_launches": launches_per_step * args.steps,
+        }
     if rank == 0 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(apr, st_h, gout.cpu().numpy(), budget_s=args.cpu_budget)
+        rec["cpu_multicore"] = cpu_multicore(apr, st_h, gout.cpu().numpy())
     return rec
+
+
+def cpu_multicore(apr, st, gout, reps=2):
+    """The multi-core FP32 CPU implementation (cpubase/: rows of a level in parallel, dynamic
+    scheduling) timed on the whole step (tree restriction, convolution, backward) on all host
+    threads; one untimed run first."""
+    import numpy as np
+
+    import cpubase
+    c = cpubase.CpuApr(apr)
+    stf = np.ascontiguousarray(st, np.float32).reshape(apr.n_levels, -1)
+
+    def step():
+        t = c.tree_restrict(apr.values)
+        t1 = time.perf_counter()
+        c.convolve(apr.values, t, stf, K)
+        t2 = time.perf_counter()
+        c.backward(apr.values, t, stf, K, gout)
+        return t1, t2
+
+    step()
+    ts, parts = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        t1, t2 = step()
+        t3 = time.perf_counter()
+        ts.append(t3 - t0)
+        parts.append((t1 - t0, t2 - t1, t3 - t2))
+    sec = statistics.mean(ts)
+    pm = [statistics.mean(p[i] for p in parts) for i in range(3)]
+    return {"value": round(apr.n_particles / sec / 1e9, 6), "unit": "Gparticles/s", "cores": c.threads,
+            "kind": "FP32 multi-threaded CPU implementation (cpubase/; rows of a level in parallel, dynamic scheduling)",
+            "ms_per_step": round(1e3 * sec, 2),
+            "step_ms_parts": {"tree_restrict": round(1e3 * pm[0], 2), "convolve": round(1e3 * pm[1], 2),
+                              "backward": round(1e3 * pm[2], 2)},
+            "sample": f"the whole step on all {apr.n_particles} particles, mean of {reps} runs after one untimed run"}
 
 
 MC_WORKLOAD = "blob256"
@@ -790,9 +880,13 @@ def pixels_per_particle(apr):
     return (ext[0] * ext[1] * ext[2]).astype(np.float64)
 
 
-def run_surrogate(args, rank, world):
-    """APR CNN surrogate of 20 Richardson-Lucy iterations: trained on seeded 256^3 blob APRs, evaluated
-    on the 1024x1024x512 blob APR against the plain 20-iteration filter (time and PSNR)."""
+SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2112_03592_gb300", "surrogate_weights", "rl20_blob256.npz")
+
+
+def run_surrogate(args, rank, world, pretrained=None):
+    """APR CNN surrogate of 20 Richardson-Lucy iterations: trained on seeded 256^3 blob APRs (here,
+    or the committed weights written by surrogate_weights/train.py when `pretrained` names them),
+    evaluated on the 1024x1024x512 blob APR against the plain 20-iteration filter (time and PSNR)."""
     import numpy as np
     import torch
 
@@ -804,21 +898,30 @@ def run_surrogate(args, rank, world):
     torch.cuda.set_device(dev)
     w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
     flags = G.APR_VALIDATE | G.APR_REQUIRE_BALANCE
-    t0 = time.perf_counter()
-    samples = []
-    for i in range(args.sur_train):
-        a = S.make_config("blob256", seed=100 + i)
-        lay = G.AprLayout.from_apr(a, flags)
-        x = torch.as_tensor(a.values, device=dev)
-        st = torch.as_tensor(G.apr_restrict_stencil(w, a.l_max, a.l_min), device=dev)
-        t = G.apr_richardson_lucy(lay, x, st, K, RL_ITERS)
-        samples.append((lay, x, t, float(1.0 / float(x.mean()))))
-    t_data = time.perf_counter() - t0
     model = AprCnn(4, n_dist=8, seed=0)
-    t0 = time.perf_counter()
-    hist = train(model, samples, args.sur_steps, lr=args.sur_lr)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    if pretrained:
+        z = np.load(pretrained)
+        model.W = [torch.as_tensor(z[f"layer{i}"], device=dev).contiguous() for i in range(4)]
+        hist = [float(z["loss_first"])] * 10 + [float(z["loss_last"])] * 10
+        t_data = t_train = 0.0
+        train_desc = (f"{int(z['n_train'])} seeded 256^3 blob APRs (seeds {int(z['seed0'])}..), {int(z['steps'])} Adam "
+                      f"steps, lr {float(z['lr'])}; committed weights (surrogate_weights/train.py)")
+    else:
+        t0 = time.perf_counter()
+        samples = []
+        for i in range(args.sur_train):
+            a = S.make_config("blob256", seed=100 + i)
+            lay = G.AprLayout.from_apr(a, flags)
+            x = torch.as_tensor(a.values, device=dev)
+            st = torch.as_tensor(G.apr_restrict_stencil(w, a.l_max, a.l_min), device=dev)
+            t = G.apr_richardson_lucy(lay, x, st, K, RL_ITERS)
+            samples.append((lay, x, t, float(1.0 / float(x.mean()))))
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hist = train(model, samples, args.sur_steps, lr=args.sur_lr)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        train_desc = f"{args.sur_train} seeded 256^3 blob APRs, {args.sur_steps} Adam steps, lr {args.sur_lr}"
 
     apr = S.make_config(WORKLOAD)
     clean = S.make_config(WORKLOAD, clean=True)
@@ -871,8 +974,7 @@ def run_surrogate(args, rank, world):
         "data": "synthetic (seeded blob images with Poisson noise -> APR); noise-free particle means as ground truth",
         "config": {"workload": "4-layer APR CNN (16 ch bf16, 3^3 per-level weights, ReLU, residual) vs 20 Richardson-Lucy "
                                "iterations (restricted 5^3 Gaussian PSF sigma=1.5), on the 1024x1024x512 blob APR",
-                   "n_particles": Np, "train": f"{args.sur_train} seeded 256^3 blob APRs, {args.sur_steps} Adam steps, "
-                                               f"lr {args.sur_lr}", "launch": "CUDA graphs" if not args.no_graph else "eager"},
+                   "n_particles": Np, "train": train_desc, "launch": "CUDA graphs" if not args.no_graph else "eager"},
         "rl20_ms": round(rl_ms, 4), "cnn_ms": round(cnn_ms, 4),
         "cnn_Gparticles_per_s": round(Np / (cnn_ms * 1e-3) / 1e9, 4),
         "psnr_db": {"cnn_vs_rl20": round(psnr(y, est, wts), 3), "input_vs_rl20": round(psnr(x, est, wts), 3),
@@ -1077,12 +1179,17 @@ def main():
     ap.add_argument("--sur-train", type=int, default=8, help="surrogate: training APRs")
     ap.add_argument("--sur-steps", type=int, default=1500, help="surrogate: Adam steps")
     ap.add_argument("--sur-lr", type=float, default=2e-3, help="surrogate: learning rate")
+    ap.add_argument("--sur-pretrained", action="store_true",
+                    help="surrogate workload: evaluate the committed weights instead of training")
     ap.add_argument("--workload", default="blob1024", choices=["blob1024", "blob256_mc", "blob512_rl", "surrogate"],
                     help="blob1024: single-channel FP32 step (default); blob256_mc: 16-channel bf16 step; "
                          "blob512_rl: 20 Richardson-Lucy iterations")
     ap.add_argument("--no-mc", action="store_true", help="skip the multi-channel summary of the default line")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense pixel convolution context timing")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain 5^3 (unrestricted) arm of the default line")
+    ap.add_argument("--no-rl", action="store_true", help="skip the Richardson-Lucy summary of the default line")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1103,13 +1210,23 @@ def main():
     elif args.workload == "blob512_rl":
         rec = run_rl(args, rank, world, full=True)
     elif args.workload == "surrogate":
-        rec = run_surrogate(args, rank, world)
+        rec = run_surrogate(args, rank, world, pretrained=SURROGATE_WEIGHTS if args.sur_pretrained else None)
     else:
         rec = run_ours(args, rank, world)
         if not args.no_mc:
             mc = run_mc(args, rank, world, full=False)
             rec["multichannel"] = {k: mc[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "step_ms_parts",
                                                       "roofline", "gpu_launches")}
+        if not args.no_rl:
+            rl = run_rl(args, rank, world, full=False)
+            rec["rl"] = {k: rl[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "gpu_launches")}
+        if not args.no_surrogate:
+            if os.path.exists(SURROGATE_WEIGHTS):
+                sr = run_surrogate(args, rank, world, pretrained=SURROGATE_WEIGHTS)
+                rec["surrogate"] = {k: sr[k] for k in ("value", "unit", "config", "rl20_ms", "cnn_ms", "psnr_db",
+                                                       "training", "gpu_launches")}
+            else:
+                rec["surrogate"] = {"unavailable": "no trained weights (run surrogate_weights/train.py)"}
     if rank == 0:
         print(json.dumps(rec))
     if world > 1:
