@@ -63,6 +63,11 @@ def _load():
         lib.ora_conv.argtypes = [P, D, I32, I32, I32, P, I64, D]
         lib.ora_conv_backward.restype = I32
         lib.ora_conv_backward.argtypes = [P, D, I32, I32, I32, D, P, I64, D, D]
+        lib.ora_conv_backward_direct.restype = I32
+        lib.ora_conv_backward_direct.argtypes = [P, D, I32, I32, I32, D, P, I64, D, D, D]
+        lib.ora_tree_transpose.restype = I32
+        lib.ora_tree_transpose.argtypes = [P, D, D]
+        lib.ora_set_tree.argtypes = [P, D]
         lib.ora_check_coarse_fill.restype = I64
         lib.ora_check_coarse_fill.argtypes = [P, I32]
         lib.ora_tree_fill_bf16.restype = I32
@@ -203,6 +208,40 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle: invalid APR in backward (code {rc})")
         return gp[:self.apr.n_particles], gw
+
+    def set_tree(self, tree):
+        """Use the given tree values [N_t][C] (instead of filling them from the particles)."""
+        t = np.ascontiguousarray(np.asarray(tree, np.float64).reshape(self.n_tree, self.C))
+        if self.n_tree:
+            _load().ora_set_tree(self.h, _ptr(t))
+        self._filled = True
+
+    def conv_backward_parts(self, stencils, k, grad_out, bc=BC_REFLECT, C_out=1, sample=None):
+        """The backward's two linear parts: (dL/d particles through particle sources [N][C], dL/d tree
+        nodes through tree sources [N_t][C], dL/d stencils). conv_backward adds
+        tree_transpose(the second) to the first."""
+        self.tree()
+        W = self._stencils(stencils, k, C_out)
+        G = np.ascontiguousarray(np.asarray(grad_out, np.float64).reshape(self.apr.n_particles, C_out))
+        gp = np.zeros((max(self.apr.n_particles, 1), self.C), np.float64)
+        gt = np.zeros((max(self.n_tree, 1), self.C), np.float64)
+        gw = np.zeros(W.shape, np.float64)
+        sp = None if sample is None else np.ascontiguousarray(np.asarray(sample, np.int64))
+        rc = _load().ora_conv_backward_direct(self.h, _ptr(W), k, C_out, bc, _ptr(G),
+                                              _ptr(sp) if sp is not None else None, 0 if sp is None else sp.size,
+                                              _ptr(gp), _ptr(gt), _ptr(gw))
+        if rc:
+            raise ValueError(f"oracle: invalid APR in backward (code {rc})")
+        return gp[:self.apr.n_particles], gt[:self.n_tree], gw
+
+    def tree_transpose(self, grad_tree):
+        """Particle shares [N][C] of a tree gradient [N_t][C] (transpose of the tree averages)."""
+        gt = np.ascontiguousarray(np.asarray(grad_tree, np.float64).reshape(max(self.n_tree, 1), self.C))
+        gp = np.zeros((max(self.apr.n_particles, 1), self.C), np.float64)
+        rc = _load().ora_tree_transpose(self.h, _ptr(gt), _ptr(gp))
+        if rc:
+            raise ValueError(f"oracle: invalid APR in tree transpose (code {rc})")
+        return gp[:self.apr.n_particles]
 
     def check_coarse_fill(self, r: int) -> int:
         return int(_load().ora_check_coarse_fill(self.h, r))

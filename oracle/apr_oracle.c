@@ -393,11 +393,14 @@ int ora_conv(const ora_t *o, const double *W, int k, int C_out, int bc, const in
  * (only the outputs listed in `sample` contribute when it is not NULL), as the explicit transpose of ora_tree_fill + ora_conv: every tap scatters G*w to the source of
  * its cell; tree gradients are then pushed from coarse to fine, each child receiving its parent's
  * gradient divided by the parent's number of children. Returns 0 or 3 (tap without source). */
-int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc, const double *G,
-                      const int64_t *sample, int64_t ns, double *grad_p, double *grad_w) {
+/* The backward in its two linear parts. Part 1 (transpose of the convolution through the patch
+ * sources): grad_p receives the terms whose source is a particle, gt those whose source is a tree
+ * node, grad_w the stencil gradient. Part 2 (transpose of the tree averages): ora_tree_transpose. */
+static int conv_backward_direct(const ora_t *o, const double *W, int k, int C_out, int bc, const double *G,
+                                const int64_t *sample, int64_t ns, double *grad_p, double *gt, double *grad_w) {
     const int r = k / 2, C = o->C, k3 = k * k * k, L = o->l_max - o->l_min + 1;
-    double *gt = (double *)calloc((size_t)(o->nt ? o->nt : 1) * C, sizeof(double));
     memset(grad_p, 0, sizeof(double) * (size_t)o->np * C);
+    memset(gt, 0, sizeof(double) * (size_t)(o->nt ? o->nt : 1) * C);
     if (grad_w) memset(grad_w, 0, sizeof(double) * (size_t)L * C_out * C * k3);
     if (!sample) ns = o->np;
     for (int64_t s = 0; s < ns; ++s) {
@@ -411,7 +414,7 @@ int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc,
                     int64_t c[3], idx;
                     if (!tap_cell(o, l, bc, o->pz[p] + dz, o->px[p] + dx, o->py[p] + dy, c)) continue;
                     int src = resolve(o, l, c[0], c[1], c[2], &idx);
-                    if (src == SRC_NONE) { free(gt); return 3; }
+                    if (src == SRC_NONE) return 3;
                     double *g = src == SRC_PARTICLE ? &grad_p[idx * C] : &gt[idx * C];
                     const double *u = src == SRC_PARTICLE ? &o->pval[idx * C] : &o->tval[idx * C];
                     int e = ((dz + r) * k + (dx + r)) * k + (dy + r);
@@ -424,7 +427,15 @@ int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc,
                     }
                 }
     }
-    /* transpose of the tree averages, coarse to fine */
+    return 0;
+}
+
+/* Transpose of the tree averages (Sec. 3.4), coarse to fine: every child of a tree node (a particle
+ * or a tree node of the next finer level) receives the node's gradient / (its in-grid children).
+ * gt [N_t][C] is updated in place (tree nodes pass on what they received); the particle shares are
+ * added to grad_p. */
+static int tree_transpose(const ora_t *o, double *gt, double *grad_p) {
+    const int C = o->C;
     for (int l = o->l_min; l < o->l_max; ++l)
         for (int64_t j = 0; j < o->T[l].n; ++j) {
             int64_t t = o->t_off[l] + j;
@@ -441,14 +452,45 @@ int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc,
                         if (i >= 0) dst = &grad_p[i * C];
                         else {
                             int64_t ti = find(&o->T[l + 1], kk);
-                            if (ti < 0) { free(gt); return 2; }
+                            if (ti < 0) return 2;
                             dst = &gt[ti * C];
                         }
                         for (int c = 0; c < C; ++c) dst[c] += gt[t * C + c] / (double)n;
                     }
         }
-    free(gt);
     return 0;
+}
+
+int ora_conv_backward(const ora_t *o, const double *W, int k, int C_out, int bc, const double *G,
+                      const int64_t *sample, int64_t ns, double *grad_p, double *grad_w) {
+    double *gt = (double *)calloc((size_t)(o->nt ? o->nt : 1) * o->C, sizeof(double));
+    if (!gt) return 4;
+    int rc = conv_backward_direct(o, W, k, C_out, bc, G, sample, ns, grad_p, gt, grad_w);
+    if (rc == 0) rc = tree_transpose(o, gt, grad_p);
+    free(gt);
+    return rc;
+}
+
+/* Part 1 alone: grad_p (particle sources), grad_tree (tree-node sources), grad_w (nullable). */
+int ora_conv_backward_direct(const ora_t *o, const double *W, int k, int C_out, int bc, const double *G,
+                             const int64_t *sample, int64_t ns, double *grad_p, double *grad_tree, double *grad_w) {
+    return conv_backward_direct(o, W, k, C_out, bc, G, sample, ns, grad_p, grad_tree, grad_w);
+}
+
+/* Part 2 alone: grad_p = the particle shares of the tree gradient grad_tree (copied, not changed). */
+int ora_tree_transpose(const ora_t *o, const double *grad_tree, double *grad_p) {
+    double *gt = (double *)malloc(sizeof(double) * (size_t)(o->nt ? o->nt : 1) * o->C);
+    if (!gt) return 4;
+    memcpy(gt, grad_tree, sizeof(double) * (size_t)o->nt * o->C);
+    memset(grad_p, 0, sizeof(double) * (size_t)o->np * o->C);
+    const int rc = tree_transpose(o, gt, grad_p);
+    free(gt);
+    return rc;
+}
+
+/* Replace the tree values (e.g. tree values assembled elsewhere); later convolutions use them. */
+void ora_set_tree(ora_t *o, const double *tval) {
+    memcpy(o->tval, tval, sizeof(double) * (size_t)o->nt * (size_t)o->C);
 }
 
 /* ---------------------------------------------------------------- balance check */
