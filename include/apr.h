@@ -86,6 +86,7 @@ typedef struct {
 #define APR_STRUCT_TREE_Y_IDX 3    /* uint16 [N_t]    tree node y */
 #define APR_STRUCT_FWD_ITEMS 4     /* int32 [n][4]    convolution work items (l, tz, tx, yb) */
 #define APR_STRUCT_TREE_ITEMS 5    /* int32 [n][4]    tree work items (l, z, x, yb) */
+#define APR_STRUCT_BWD_ITEMS 6     /* int32 [n][4]    data-adjoint work items (l, tz, tx, yb) */
 
 /* Build the device-resident index of an APR (Sec. 3.1 LinearAccess for the particles, Sec. 3.4
  * APR tree structure, and the list of non-empty tiles the kernels are launched on, Sec. 5.2 last
@@ -156,6 +157,21 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
  * (the paper's pipeline: restriction, then convolution). workspace: caller-owned device memory of at
  * least apr_convolve_auto_workspace_bytes(h) bytes, 4-byte aligned; it holds the tree values [N_t]
  * afterwards. APR_ERR_INVALID_ARG if it is missing or too small; otherwise as the two calls. */
+/* apr_convolve restricted to the forward work items [first_tile, first_tile + n_tiles) of
+ * APR_STRUCT_FWD_ITEMS (ordered by level, then tile z, tile x, y-block): only the outputs of the
+ * targets of those tiles are written. For a rank of a z-sharded APR (Sec. 5.1 parallelisation over
+ * rows), one range per level covers the tiles that hold its particles. */
+apr_status_t apr_convolve_tiles(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                int32_t k, int32_t bc, float *out, int64_t first_tile, int64_t n_tiles,
+                                apr_stream_t stream);
+
+/* apr_convolve_adjoint restricted to the data-adjoint work items [first_tile, first_tile + n_tiles)
+ * of APR_STRUCT_BWD_ITEMS. Nothing is cleared: particle gradients are ADDED, the tree-node
+ * gradients of the launched tiles' interior cells are written (each node belongs to one tile). */
+apr_status_t apr_convolve_adjoint_tiles(apr_handle_t h, const float *stencils, int32_t k, int32_t bc,
+                                        const float *grad_out, float *grad_particles, float *grad_tree,
+                                        int64_t first_tile, int64_t n_tiles, apr_stream_t stream);
+
 size_t apr_convolve_auto_workspace_bytes(apr_handle_t h);
 apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const float *stencils, int32_t k, int32_t bc,
                                float *out, void *workspace, size_t workspace_bytes, apr_stream_t stream);

@@ -37,7 +37,8 @@ __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
            "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_relu_bf16", "apr_convolve_mc_backward",
            "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
-           "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "apr_dense_convolve", "AprError",
+           "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "apr_dense_convolve", "apr_convolve_tiles",
+           "apr_convolve_adjoint_tiles", "AprError",
            "APR_BC_REFLECT", "APR_BC_ZERO", "APR_VALIDATE", "APR_REQUIRE_BALANCE", "APR_HOST_ONLY",
            "APR_SUBDOMAIN"]
 
@@ -152,7 +153,7 @@ class AprLayout:
             pass
 
     # ---- structure export (bit-exact checks)
-    _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32}
+    _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32, 6: np.int32}
 
     def export(self, which: int) -> np.ndarray:
         nbytes = int(self._lib.apr_structure_bytes(self._h, which))
@@ -161,7 +162,7 @@ class AprLayout:
         _abi.check("apr_export_structure",
                    self._lib.apr_export_structure(self._h, which, out.ctypes.data_as(ctypes.c_void_p), nbytes))
         out = out[:nbytes // np.dtype(dt).itemsize]
-        return out.reshape(-1, 4) if which in (4, 5) else out
+        return out.reshape(-1, 4) if which in (4, 5, 6) else out
 
     def workspace(self, k):
         import torch
@@ -243,6 +244,39 @@ def apr_gradient_magnitude(layout: AprLayout, particles, tree, stencils3, k, bc=
         layout.handle, ctypes.c_void_p(particles.data_ptr()), ctypes.c_void_p(tree.data_ptr()),
         ctypes.c_void_p(stencils3.data_ptr()), int(k), int(bc), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def apr_convolve_tiles(layout: AprLayout, particles, tree, stencils, k, first_tile, n_tiles, bc=APR_BC_REFLECT,
+                       out=None, stream=None):
+    """apr_convolve over the forward work items [first_tile, first_tile + n_tiles) only (the other
+    entries of out are left as they are)."""
+    import torch
+    _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
+    _dev_ptr(tree, "tree", layout.n_tree, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    if out is None:
+        out = torch.zeros_like(particles)
+    _dev_ptr(out, "out", layout.n_particles, torch.float32)
+    _abi.check("apr_convolve_tiles", layout._lib.apr_convolve_tiles(
+        layout.handle, _dev_ptr(particles, "particles"), _dev_ptr(tree, "tree"), _dev_ptr(stencils, "stencils"),
+        int(k), int(bc), _dev_ptr(out, "out"), int(first_tile), int(n_tiles), _stream_ptr(stream)))
+    return out
+
+
+def apr_convolve_adjoint_tiles(layout: AprLayout, stencils, k, grad_out, grad_particles, grad_tree, first_tile,
+                               n_tiles, bc=APR_BC_REFLECT, stream=None):
+    """apr_convolve_adjoint over the data-adjoint work items [first_tile, first_tile + n_tiles): adds
+    into grad_particles, writes the tiles' tree-node gradients into grad_tree (nothing is cleared)."""
+    import torch
+    _dev_ptr(grad_out, "grad_out", layout.n_particles, torch.float32)
+    _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)
+    _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32)
+    _dev_ptr(grad_tree, "grad_tree", layout.n_tree, torch.float32)
+    _abi.check("apr_convolve_adjoint_tiles", layout._lib.apr_convolve_adjoint_tiles(
+        layout.handle, _dev_ptr(stencils, "stencils"), int(k), int(bc), _dev_ptr(grad_out, "grad_out"),
+        _dev_ptr(grad_particles, "grad_particles"), _dev_ptr(grad_tree, "grad_tree"), int(first_tile), int(n_tiles),
+        _stream_ptr(stream)))
+    return grad_particles, grad_tree
 
 
 def apr_dense_convolve(image, stencil, k, bc=APR_BC_REFLECT, out=None, stream=None):

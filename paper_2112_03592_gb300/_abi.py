@@ -15,7 +15,7 @@ STATUS = {0: "APR_OK", 1: "APR_ERR_INVALID_ARG", 2: "APR_ERR_INVALID_LAYOUT", 3:
 APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY, APR_SUBDOMAIN = 1, 2, 4, 8
 APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
-APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS = 4, 5
+APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS, APR_STRUCT_BWD_ITEMS = 4, 5, 6
 APR_TILE_ZX, APR_BLOCK_Y = 8, 64  # work-item geometry, as in include/apr.h
 
 # every function include/apr.h declares, with (restype, argtypes)
@@ -40,6 +40,8 @@ SIGNATURES = {
     "apr_build_device_ex": (_I32, [ctypes.POINTER(AprHostLayout), _U32, _P, ctypes.POINTER(AprAllocator),
                                    ctypes.POINTER(_P)]),
     "apr_sobel_stencils": (_I32, [_I32, _P]),
+    "apr_convolve_tiles": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _I64, _I64, _P]),
+    "apr_convolve_adjoint_tiles": (_I32, [_P, _P, _I32, _I32, _P, _P, _P, _I64, _I64, _P]),
     "apr_dense_convolve": (_I32, [_P, _I64, _I64, _I64, _P, _I32, _I32, _P, _P]),
     "apr_destroy": (_I32, [_P]),
     "apr_num_particles": (_I64, [_P]),

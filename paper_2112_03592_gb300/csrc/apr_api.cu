@@ -12,13 +12,13 @@
 namespace aprk {
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s,
-                            int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr);
+                            int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr, int tile0 = 0);
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
                                  cudaStream_t s, int C = 1, int ch = 0);
 cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                            const float *st, int bc, float *out, cudaStream_t s);
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
-                            const float *gout, float *gp, float *gt, cudaStream_t s);
+                            const float *gout, float *gp, float *gt, cudaStream_t s, int tile0 = 0);
 cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int n, const float *vals,
                                const float *tree, int bc, const float *gout, float *partial, cudaStream_t s);
 cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64_t *level_begin, int l_min,
@@ -275,6 +275,7 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
         case APR_STRUCT_TREE_Y_IDX: return X.ty.size() * sizeof(uint16_t);
         case APR_STRUCT_FWD_ITEMS: return X.fwd_items.size() * sizeof(Item);
         case APR_STRUCT_TREE_ITEMS: return X.tree_items.size() * sizeof(Item);
+        case APR_STRUCT_BWD_ITEMS: return X.bwd_items.size() * sizeof(Item);
     }
     return 0;
 }
@@ -282,7 +283,7 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
 apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes) {
     if (!h || (!dst && bytes)) return APR_ERR_INVALID_ARG;
     const size_t need = apr_structure_bytes(h, which);
-    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_TREE_ITEMS) return APR_ERR_INVALID_ARG;
+    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_BWD_ITEMS) return APR_ERR_INVALID_ARG;
     if (bytes < need) return APR_ERR_INVALID_ARG;
     if (need == 0) return APR_OK;
     const HostIndex &X = h->X;
@@ -295,6 +296,7 @@ apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size
         case APR_STRUCT_TREE_Y_IDX: host_src = X.ty.data(); dev_src = h->d_ty; break;
         case APR_STRUCT_FWD_ITEMS: host_src = X.fwd_items.data(); dev_src = h->d_fwd; break;
         case APR_STRUCT_TREE_ITEMS: host_src = X.tree_items.data(); dev_src = h->d_tree; break;
+        case APR_STRUCT_BWD_ITEMS: host_src = X.bwd_items.data(); dev_src = h->d_bwd; break;
     }
     if (h->host_only) {
         memcpy(dst, host_src, need);
@@ -331,6 +333,34 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
     if (!aligned16(particles) || !aligned16(tree)) return misaligned();
     const int n = int(h->X.fwd_items.size());
     return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
+}
+
+apr_status_t apr_convolve_tiles(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                int32_t k, int32_t bc, float *out, int64_t first_tile, int64_t n_tiles,
+                                apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const int64_t nt = int64_t(h->X.fwd_items.size());
+    if (first_tile < 0 || n_tiles < 0 || first_tile + n_tiles > nt) return APR_ERR_INVALID_ARG;
+    if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles) || !aligned16(tree)) return misaligned();
+    return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, int(n_tiles), particles, tree, stencils, bc, out, stream,
+                                       EPI_PLAIN, false, nullptr, int(first_tile)));
+}
+
+apr_status_t apr_convolve_adjoint_tiles(apr_handle_t h, const float *stencils, int32_t k, int32_t bc,
+                                        const float *grad_out, float *grad_particles, float *grad_tree,
+                                        int64_t first_tile, int64_t n_tiles, apr_stream_t stream) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    const int64_t nt = int64_t(X.bwd_items.size());
+    if (first_tile < 0 || n_tiles < 0 || first_tile + n_tiles > nt) return APR_ERR_INVALID_ARG;
+    if (!stencils || (X.np && (!grad_out || !grad_particles)) || (X.nt && !grad_tree)) return APR_ERR_INVALID_ARG;
+    return cuda_status(launch_bwd_data(k, h->L, h->d_bwd, int(n_tiles), stencils, bc, grad_out, grad_particles,
+                                       grad_tree, stream, int(first_tile)));
 }
 
 size_t apr_convolve_auto_workspace_bytes(apr_handle_t h) {

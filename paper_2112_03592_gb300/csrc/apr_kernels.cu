@@ -479,19 +479,20 @@ __device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it
 
 template <int R>
 __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                         const float *__restrict__ vals,
+                                                         int tile0, const float *__restrict__ vals,
                                                          const float *__restrict__ tree,
                                                          const float *__restrict__ stencils, int bc,
                                                          float *out, const Epilogue epi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Item it = items[blockIdx.x];
+    const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
+    const Item it = items[tile];
     if constexpr (R == 2) {
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_fwd_tile<1, 2>(L, it, blockIdx.x, vals, tree, stencils, bc, out, epi, smem_raw);
+            conv_fwd_tile<1, 2>(L, it, tile, vals, tree, stencils, bc, out, epi, smem_raw);
             return;
         }
     }
-    conv_fwd_tile<R, R>(L, it, blockIdx.x, vals, tree, stencils, bc, out, epi, smem_raw);
+    conv_fwd_tile<R, R>(L, it, tile, vals, tree, stencils, bc, out, epi, smem_raw);
 }
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
@@ -1041,18 +1042,19 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
 
 template <int R>
 __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                              const float *__restrict__ stencils, int bc,
+                                                              int tile0, const float *__restrict__ stencils, int bc,
                                                               const float *__restrict__ gout,
                                                               float *__restrict__ gp, float *__restrict__ gt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Item it = items[blockIdx.x];
+    const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
+    const Item it = items[tile];
     if constexpr (R == 2) {
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_bwd_data_tile<1, 2>(L, it, blockIdx.x, stencils, bc, gout, gp, gt, smem_raw);
+            conv_bwd_data_tile<1, 2>(L, it, tile, stencils, bc, gout, gp, gt, smem_raw);
             return;
         }
     }
-    conv_bwd_data_tile<R, R>(L, it, blockIdx.x, stencils, bc, gout, gp, gt, smem_raw);
+    conv_bwd_data_tile<R, R>(L, it, tile, stencils, bc, gout, gp, gt, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1208,22 +1210,23 @@ static_assert(sizeof(FwdSmem<1, 1>) <= sizeof(FwdSmem<2, 1>) && sizeof(BwdSmem<1
 cudaError_t set_smem(const void *fn, size_t bytes) { return set_max_dynamic_smem(fn, bytes); }
 
 template <int R>
-cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
-                              const float *st, int bc, float *out, const Epilogue &epi, cudaStream_t s) {
+cudaError_t launch_conv_fwd_t(const DevLayout &L, const Item *items, int tile0, int n, const float *vals,
+                              const float *tree, const float *st, int bc, float *out, const Epilogue &epi,
+                              cudaStream_t s) {
     const size_t sm = sizeof(FwdSmem<R, 1>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_fwd_kernel<R>), sm);
     if (e != cudaSuccess) return e;
-    if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, vals, tree, st, bc, out, epi);
+    if (n > 0) conv_fwd_kernel<R><<<n, NT, sm, s>>>(L, items, tile0, vals, tree, st, bc, out, epi);
     return cudaGetLastError();
 }
 
 template <int R>
-cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int n, const float *st, int bc,
+cudaError_t launch_bwd_data_t(const DevLayout &L, const Item *items, int tile0, int n, const float *st, int bc,
                               const float *gout, float *gp, float *gt, cudaStream_t s) {
     const size_t sm = sizeof(BwdSmem<R>);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_data_kernel<R>), sm);
     if (e != cudaSuccess) return e;
-    if (n > 0) conv_bwd_data_kernel<R><<<n, NT, sm, s>>>(L, items, st, bc, gout, gp, gt);
+    if (n > 0) conv_bwd_data_kernel<R><<<n, NT, sm, s>>>(L, items, tile0, st, bc, gout, gp, gt);
     return cudaGetLastError();
 }
 
@@ -1242,10 +1245,10 @@ cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, c
 // ---- launch entry points used by the C ABI (apr_api.cu)
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s, int epi_mode,
-                            bool flip, const float *aux) {
+                            bool flip, const float *aux, int tile0) {
     const Epilogue epi{epi_mode, flip, aux};
-    return k == 3 ? launch_conv_fwd_t<1>(L, items, n, vals, tree, st, bc, out, epi, s)
-                  : launch_conv_fwd_t<2>(L, items, n, vals, tree, st, bc, out, epi, s);
+    return k == 3 ? launch_conv_fwd_t<1>(L, items, tile0, n, vals, tree, st, bc, out, epi, s)
+                  : launch_conv_fwd_t<2>(L, items, tile0, n, vals, tree, st, bc, out, epi, s);
 }
 
 template <int R>
@@ -1271,9 +1274,9 @@ cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, c
 }
 
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
-                            const float *gout, float *gp, float *gt, cudaStream_t s) {
-    return k == 3 ? launch_bwd_data_t<1>(L, items, n, st, bc, gout, gp, gt, s)
-                  : launch_bwd_data_t<2>(L, items, n, st, bc, gout, gp, gt, s);
+                            const float *gout, float *gp, float *gt, cudaStream_t s, int tile0) {
+    return k == 3 ? launch_bwd_data_t<1>(L, items, tile0, n, st, bc, gout, gp, gt, s)
+                  : launch_bwd_data_t<2>(L, items, tile0, n, st, bc, gout, gp, gt, s);
 }
 
 cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int n, const float *vals,

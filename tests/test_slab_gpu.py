@@ -1,20 +1,27 @@
-"""The local work of a z-slab shard on the GPU: each rank's sub-APR (built with APR_SUBDOMAIN) fed
-with the whole image's values of its region gives the whole-volume oracle's outputs and gradients
-for the particles it owns."""
+"""The local work of z-slab shards on the GPU (CudaLocal: tile-range convolution and adjoint on the
+whole-APR layout), the exchange and all-reduces emulated on one GPU: the stitched outputs and
+gradients of all ranks equal the whole-volume oracle (the collectives themselves run as gloo ranks
+in test_slab_gloo.py)."""
 import numpy as np
 import pytest
 import torch
 
 import aprsynth as S
 import oracle
-from paper_2112_03592_gb300.slab import SlabConv
+from paper_2112_03592_gb300.slab import CudaLocal, SlabPlan
 
 pytestmark = pytest.mark.gpu
 
+CASES = {
+    "rand": lambda: S.random_balanced_apr((40, 24, 30), 3, seed=21, p_fine=0.02),
+    "c2_shaped": lambda: S.random_balanced_apr((512, 8, 1024), 3, seed=23, p_fine=0.0005),
+}
 
+
+@pytest.mark.parametrize("case,world", [("rand", 3), ("c2_shaped", 8)])
 @pytest.mark.parametrize("k,bc", [(3, 0), (5, 0), (5, 1)])
-def test_slab_local_gpu_matches_whole_volume(k, bc):
-    apr = S.random_balanced_apr((40, 24, 30), 3, seed=21, p_fine=0.02)
+def test_slab_local_gpu_matches_whole_volume(case, world, k, bc):
+    apr = CASES[case]()
     rng = np.random.default_rng(5)
     vals = rng.normal(size=apr.n_particles) + 3.0
     gout = rng.normal(size=apr.n_particles)
@@ -22,22 +29,40 @@ def test_slab_local_gpu_matches_whole_volume(k, bc):
     o = oracle.Oracle(apr, vals)
     ref = o.conv(W, k, bc)[:, 0]
     ref_gp, ref_gw = o.conv_backward(W, k, gout, bc)
-    world = 3
-    gw_sum = np.zeros((apr.n_levels, k ** 3))
+    plan = SlabPlan(apr, world, k // 2)
+    st = torch.as_tensor(W.astype(np.float32), device="cuda")
+    v_all = torch.as_tensor(vals.astype(np.float32), device="cuda")
+    g_all = torch.as_tensor(gout.astype(np.float32), device="cuda")
+    locs = [CudaLocal(apr, plan, r, st, k, bc) for r in range(world)]
+    # the tree: the sum over ranks of each rank's restriction of its own particles (the all-reduce)
+    tree = None
+    for r, loc in enumerate(locs):
+        mine = torch.zeros_like(v_all)
+        ix = torch.as_tensor(plan.owned[r], device="cuda")
+        mine[ix] = v_all[ix]
+        t = loc.restrict(mine)
+        tree = t if tree is None else tree + t
+    out = np.full(apr.n_particles, np.nan)
     gp = np.zeros(apr.n_particles)
-    for rank in range(world):
-        sc = SlabConv(apr, rank, world, k, stencils=torch.as_tensor(W.astype(np.float32), device="cuda"), bc=bc)
-        loc = np.concatenate([np.arange(a, b) for a, b in sc.plan.local[rank]])
-        own = sc.plan.owned_positions_global(rank)
-        lv = torch.as_tensor(vals[loc].astype(np.float32), device="cuda")
-        out = sc._local_forward(lv).cpu().numpy()[sc.own_loc]
-        np.testing.assert_allclose(out, ref[own], rtol=1e-5, atol=1e-5 * np.abs(ref).max())
-        # backward of the owned outputs only; halo shares added back by global position
-        g = np.zeros(sc.sub.n_particles, np.float32)
-        g[sc.own_loc] = gout[own]
-        gl, gw = sc._local_backward(lv, torch.as_tensor(g, device="cuda"))
-        np.add.at(gp, loc, gl.cpu().numpy().astype(np.float64))
-        gw_sum += gw.cpu().numpy().reshape(apr.n_levels, -1)
-    scale = np.abs(ref_gp).max()
-    np.testing.assert_allclose(gp, ref_gp[:, 0], rtol=0, atol=1e-5 * scale)
+    gt_sum = torch.zeros(tree.numel(), device="cuda")
+    gw_sum = np.zeros((apr.n_levels, k ** 3))
+    for r, loc in enumerate(locs):
+        need = torch.as_tensor(plan.needed[r], device="cuda")
+        v = torch.zeros_like(v_all)
+        v[need] = v_all[need]                          # the rank's values after the exchange
+        own = plan.owned[r]
+        out[own] = loc.convolve(v, tree, own).cpu().numpy()[own]
+        g = torch.zeros_like(g_all)
+        ixo = torch.as_tensor(own, device="cuda")
+        g[ixo] = g_all[ixo]
+        p, t, w = loc.adjoint(v, tree, g, own)
+        gp += p.double().cpu().numpy()                 # direct shares, added back to their owners
+        gt_sum += t
+        gw_sum += w.double().cpu().numpy().reshape(apr.n_levels, -1)
+    torch.cuda.synchronize()
+    for r, loc in enumerate(locs):
+        own = plan.owned[r]
+        gp[own] += loc.tree_transpose(gt_sum).double().cpu().numpy()[own]
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    np.testing.assert_allclose(gp, ref_gp[:, 0], rtol=0, atol=1e-5 * np.abs(ref_gp).max())
     np.testing.assert_allclose(gw_sum, ref_gw.reshape(apr.n_levels, -1), rtol=0, atol=1e-5 * np.abs(ref_gw).max())
