@@ -1167,6 +1167,33 @@ def run_reference_rl(args, rank, world):
             "e2e": {"value": round(val, 9), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def ncu_launches(part, reps=3):
+    """Runs one part of the default step `reps` times on the 1024x1024x512 APR, for an ncu capture
+    of that kernel (no timing); prints a one-line JSON note."""
+    import numpy as np
+    import torch
+
+    import aprsynth as S
+    import paper_2112_03592_gb300 as G
+    apr = S.make_config(WORKLOAD)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
+    st = torch.as_tensor(G.apr_restrict_stencil(w, apr.l_max, apr.l_min), device="cuda")
+    v = torch.as_tensor(apr.values, device="cuda")
+    g = torch.as_tensor(np.random.default_rng(0).normal(size=apr.n_particles).astype(np.float32), device="cuda")
+    tree = G.apr_tree_restrict(lay, v)
+    gp, gt = torch.empty_like(v), torch.empty(lay.n_tree, device="cuda")
+    run = {"restrict": lambda: G.apr_tree_restrict(lay, v, tree),
+           "convolve": lambda: G.apr_convolve(lay, v, tree, st, K),
+           "adjoint": lambda: G.apr_convolve_adjoint(lay, st, K, g, grad_particles=gp, grad_tree=gt),
+           "stencil_grad": lambda: G.apr_convolve_stencil_grad(lay, v, tree, K, g)}[part]
+    for _ in range(reps):
+        run()
+    torch.cuda.synchronize()
+    lay.sync_status()
+    print(json.dumps({"ncu_launches": part, "reps": reps, "workload": WORKLOAD}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1190,7 +1217,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain 5^3 (unrestricted) arm of the default line")
     ap.add_argument("--no-rl", action="store_true", help="skip the Richardson-Lucy summary of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
+    ap.add_argument("--ncu-launches", choices=["restrict", "convolve", "adjoint", "stencil_grad"],
+                    help="run one part of the step 3 times for an ncu capture, no timing")
     args = ap.parse_args()
+    if args.ncu_launches:
+        ncu_launches(args.ncu_launches)
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

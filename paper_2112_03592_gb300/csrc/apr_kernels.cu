@@ -113,14 +113,21 @@ struct FwdSmem {
     using G = Geo<R>;
     float patch[G::NROW * G::PYS];             // first member: 16-byte aligned
     __align__(16) float w2[NS][G::NPAIR * w2_stride<R>()];  // paired taps of NS stencil stacks
-    int seg_lo[G::NSEG];                        // first element of segment s
-    unsigned seg_nm[G::NSEG];                   // element count | segment meta << 8 (with_trow)
-    int pre[G::NSEG + 1];                       // packet prefix over the segments
+    struct Staging {
+        int seg_lo[G::NSEG];                    // first element of segment s
+        unsigned seg_nm[G::NSEG];               // element count | segment meta << 8 (with_trow)
+        int pre[G::NSEG + 1];                   // packet prefix over the segments
+        unsigned short pseg[PCAP];              // segment of every packet of the current chunk
+    };
+    static constexpr int GWIN = int(sizeof(Staging) / 32);  // windows of dL/dout that fit in its place
+    union {
+        Staging st;                             // during staging
+        float4 gwin[GWIN * 2];                  // after staging (stencil gradient): 8 dL/dout per window
+    };
     int warp_tot[NWARP + 1];
     unsigned long long rmask[NIR];              // targets of interior row r: bit j = cell y0 + j
     int rfirst[NIR];                            // first target (particle index) of interior row r
     unsigned short act[NIW];                    // windows holding targets, in window order
-    unsigned short pseg[PCAP];                  // segment of every packet of the current chunk
     int roff[G::NPAIR];                         // stencil-row offsets in the patch (fill_row_offsets)
     int nact;
 };
@@ -144,8 +151,8 @@ template <int R, int NS>
 __device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0, const uint4 &yq, const float4 &va,
                                              const float4 &vb, int dy, int yw, int y0) {
     using G = Geo<R>;
-    const int lo = S.seg_lo[seg];
-    const unsigned nm = S.seg_nm[seg];
+    const int lo = S.st.seg_lo[seg];
+    const unsigned nm = S.st.seg_nm[seg];
     const int n = int(nm & 255u), meta = int(nm >> 8);
     const int kind = meta_kind(meta);
     const int yv[8] = {int(yq.x & 0xffffu), int(yq.x >> 16), int(yq.y & 0xffffu), int(yq.y >> 16),
@@ -245,19 +252,19 @@ __device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const fl
         if (k < nseg) {
             const int meta = fplan_meta(e);
             const bool drop = !reflect && (meta & META_REFL);
-            S.seg_lo[k] = fplan_lo(e);
-            S.seg_nm[k] = unsigned(drop ? 0 : fplan_n(e)) | (unsigned(with_trow<R>(g, it, meta)) << 8);
+            S.st.seg_lo[k] = fplan_lo(e);
+            S.st.seg_nm[k] = unsigned(drop ? 0 : fplan_n(e)) | (unsigned(with_trow<R>(g, it, meta)) << 8);
         }
-        S.pre[k] = fplan_pre(e);
+        S.st.pre[k] = fplan_pre(e);
     }
     block_sync();
 
-    const int P = S.pre[nseg];
+    const int P = S.st.pre[nseg];
     for (int c0 = 0; c0 < P; c0 += PCAP) {
         const int c1 = min(P, c0 + PCAP);
         for (int s = tid; s < nseg; s += NT) {
-            const int a = max(S.pre[s], c0), b = min(S.pre[s + 1], c1);
-            for (int p = a; p < b; ++p) S.pseg[p - c0] = (unsigned short)s;
+            const int a = max(S.st.pre[s], c0), b = min(S.st.pre[s + 1], c1);
+            for (int p = a; p < b; ++p) S.st.pseg[p - c0] = (unsigned short)s;
         }
         block_sync();
         // two packets per thread and step: the loads of both are issued before either is placed
@@ -271,9 +278,9 @@ __device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const fl
                 sg[u] = -1;
                 i0[u] = 0;
                 if (p < c1) {
-                    const int s = S.pseg[p - c0];
-                    const bool t = meta_kind(int(S.seg_nm[s] >> 8)) == 1;
-                    const int g8 = (S.seg_lo[s] >> 3) + (p - S.pre[s]);
+                    const int s = S.st.pseg[p - c0];
+                    const bool t = meta_kind(int(S.st.seg_nm[s] >> 8)) == 1;
+                    const int g8 = (S.st.seg_lo[s] >> 3) + (p - S.st.pre[s]);
                     const uint4 *yt = reinterpret_cast<const uint4 *>(t ? L.ty : L.y);
                     const float *vs = t ? tree : vals;
                     yq[u] = __ldg(yt + g8);
@@ -568,46 +575,64 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
                                                                  const float *__restrict__ gout,
                                                                  float *__restrict__ partial) {
     using G = Geo<R>;
+    using Smem = FwdSmem<R, 1>;
     constexpr int NGRP = NT / G::NPAIR;
     static_assert(NGRP * G::NPAIR * G::K <= G::NROW * G::PYS, "partials fit in the patch");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FwdSmem<R, 1> &S = *reinterpret_cast<FwdSmem<R, 1> *>(smem_raw);
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     const Item it = items[blockIdx.x];
     stage_fwd<R, 1>(L, it, blockIdx.x, vals, tree, bc, S);
     const int tid = threadIdx.x;
     const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
-    float acc[G::K];
+    // acc2[t] = (sum over even j, sum over odd j) of g_j * P[row][col + j + t]: taps t even pair
+    // (g_{2i}, g_{2i+1}) with the aligned values (v_{2i+t}, v_{2i+1+t}), taps t odd pair
+    // (g_{2i-1}, g_{2i}) with (v_{2i-1+t}, v_{2i+t}), also aligned (g_{-1} = g_8 = 0)
+    float2 acc2[G::K];
 #pragma unroll
-    for (int t = 0; t < G::K; ++t) acc[t] = 0.f;
-    if (grp < NGRP) {
-        const int dz = pair / G::K, dx = pair % G::K;
-        for (int a = grp; a < S.nact; a += NGRP) {
-            const int w = S.act[a], r = w / NWIN, col = (w % NWIN) * WIN;
-            const int ia = r / TX, ib = r % TX;
-            const float4 *src = reinterpret_cast<const float4 *>(S.patch + ((ia + dz) * G::PX + (ib + dx)) * G::PYS + col);
-            const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-            const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-            // dL/dout of the window's targets: consecutive particles from its first target (0 at other cells)
+    for (int t = 0; t < G::K; ++t) acc2[t] = make_float2(0.f, 0.f);
+    const int roff = grp < NGRP ? S.roff[pair] : 0;
+    // the windows in chunks: dL/dout of a chunk's windows (0 at cells without a target) are read
+    // from global memory once into the place of the staging tables, then every stencil row uses them
+    for (int c0 = 0; c0 < S.nact; c0 += Smem::GWIN) {
+        const int nc = min(Smem::GWIN, S.nact - c0);
+        float *gw = reinterpret_cast<float *>(S.gwin);
+        for (int i = tid; i < nc * WIN; i += NT) {
+            const int w = S.act[c0 + i / WIN], j = i % WIN;
             const unsigned m = win_mask(S, w);
-            const float *gs = gout + win_first(S, w);
-            float gg[WIN];
-            int c = 0;
-#pragma unroll
-            for (int j = 0; j < WIN; ++j) {
-                gg[j] = 0.f;
-                if ((m >> j) & 1u) gg[j] = gs[c++];
-            }
-#pragma unroll
-            for (int t = 0; t < G::K; ++t)
-#pragma unroll
-                for (int j = 0; j < WIN; ++j) acc[t] = fmaf(gg[j], v[j + t], acc[t]);
+            gw[i] = ((m >> j) & 1u) ? gout[win_first(S, w) + __popc(m & ((1u << j) - 1u))] : 0.f;
         }
+        block_sync();
+        if (grp < NGRP) {
+            for (int a = grp; a < nc; a += NGRP) {
+                const int w = S.act[c0 + a], r = w / NWIN;
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    S.patch + ((r / TX) * G::PX + (r % TX)) * G::PYS + roff + (w % NWIN) * WIN);
+                const float4 q0 = src[0], q1 = src[1], q2 = src[2];
+                const float2 V[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                     make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+                const float4 ga = S.gwin[2 * a], gb = S.gwin[2 * a + 1];
+                const float2 Ge[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                                      make_float2(gb.z, gb.w)};
+                const float2 Go[5] = {make_float2(0.f, ga.x), make_float2(ga.y, ga.z), make_float2(ga.w, gb.x),
+                                      make_float2(gb.y, gb.z), make_float2(gb.w, 0.f)};
+#pragma unroll
+                for (int t = 0; t < G::K; ++t) {
+                    if (t % 2 == 0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc2[t] = ffma2(Ge[i], V[i + t / 2], acc2[t]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) acc2[t] = ffma2(Go[i], V[i + (t - 1) / 2], acc2[t]);
+                    }
+                }
+            }
+        }
+        block_sync();   // the next chunk (or the partials) reuse shared memory
     }
-    block_sync();   // the partials reuse the patch
     float *red = S.patch;
     if (grp < NGRP)
 #pragma unroll
-        for (int t = 0; t < G::K; ++t) red[(grp * G::NPAIR + pair) * G::K + t] = acc[t];
+        for (int t = 0; t < G::K; ++t) red[(grp * G::NPAIR + pair) * G::K + t] = acc2[t].x + acc2[t].y;
     block_sync();
     if (tid < G::K3) {
         const int pr = tid / G::K, t = tid % G::K;
@@ -616,6 +641,7 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
         partial[size_t(tid) * n_items + blockIdx.x] = s;
     }
 }
+
 // grad_w[l][e] = sum over the level's items of partial[e][item], fixed-order block reduction.
 __global__ void __launch_bounds__(NT) stencil_grad_reduce_kernel(const float *__restrict__ partial, int n_items,
                                                                  const int64_t *__restrict__ level_begin,
@@ -662,17 +688,20 @@ struct BwdSmem {
     unsigned short act[NIW];
     unsigned short pseg[PCAP];
     int roff[G::NPAIR];                        // stencil-row offsets in the patch (fill_row_offsets)
+    static constexpr int RCAP = 320;           // routing packets whose y values are kept from the staging pass
+    uint4 rstash[RCAP];
     int nact;
 };
 
 // The packets of segments [s0, s0 + ns) (packet prefixes in pre[s0 .. s0 + ns]): loads y (from ty for
-// segments with tree(seg), else from py) and, with vals, the values of 8 elements per packet, then
-// calls use(seg, i0, yq, va, vb, mask) with the packet's valid-element mask. Chunks of PCAP packets;
-// ends with a block barrier.
-template <typename Tree, typename Use>
+// segments with tree(seg), else from py) and, for segments with has_vals(seg), the values of 8
+// elements per packet, then calls use(seg, p, i0, yq, va, vb, mask) with the packet index p and the
+// packet's valid-element mask. Chunks of PCAP packets; ends with a block barrier (with a single
+// chunk, pseg still maps every packet to its segment afterwards).
+template <typename Tree, typename HasVals, typename Use>
 __device__ __forceinline__ void for_each_packet(const int *seg_lo, const unsigned *seg_nm, const int *pre, int s0,
                                                 int ns, unsigned short *pseg, const uint16_t *py, const uint16_t *ty,
-                                                Tree tree, const float *vals, int nvals, Use use) {
+                                                Tree tree, const float *vals, int nvals, HasVals has_vals, Use use) {
     const int tid = threadIdx.x;
     const int P0 = pre[s0], P1 = pre[s0 + ns];
     for (int c0 = P0; c0 < P1; c0 += PCAP) {
@@ -696,7 +725,7 @@ __device__ __forceinline__ void for_each_packet(const int *seg_lo, const unsigne
                     const int s = pseg[p - c0];
                     const int g8 = (seg_lo[s] >> 3) + (p - pre[s]);
                     yq[u] = __ldg(reinterpret_cast<const uint4 *>(tree(s) ? ty : py) + g8);
-                    if (vals) {
+                    if (has_vals(s)) {
                         if (8 * g8 + 8 <= nvals) {
                             va[u] = __ldg(reinterpret_cast<const float4 *>(vals) + 2 * g8);
                             vb[u] = __ldg(reinterpret_cast<const float4 *>(vals) + 2 * g8 + 1);
@@ -720,7 +749,7 @@ __device__ __forceinline__ void for_each_packet(const int *seg_lo, const unsigne
                 unsigned m = 0u;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) m |= (unsigned(i0[u] + j - lo) < unsigned(n) ? 1u : 0u) << j;
-                use(sg[u], i0[u], yq[u], va[u], vb[u], m);
+                use(sg[u], p0 + u * NT, i0[u], yq[u], va[u], vb[u], m);
             }
         }
         block_sync();
@@ -796,9 +825,20 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     }
     block_sync();
 
-    // gradient patch and its occupancy (the first n1 segments; one patch row per segment)
-    for_each_packet(S.seg_lo, S.seg_nm, S.pre, 0, n1, S.pseg, L.y, L.ty, [](int) { return false; }, gout, L.np,
-                    [&](int seg, int, const uint4 &yq, const float4 &va, const float4 &vb, unsigned m) {
+    // gradient patch and its occupancy (the first n1 segments; one patch row per segment), in one pass
+    // with the y values of the routing segments, which are kept in rstash for the routing at the end
+    const auto is_tree = [&](int seg) {
+        const int q = int(S.seg_nm[seg] >> 8);
+        return seg >= n1 && q >= NIR && q < 2 * NIR;
+    };
+    const int P1 = S.pre[n1], P2 = S.pre[n1 + n2];
+    for_each_packet(S.seg_lo, S.seg_nm, S.pre, 0, n1 + n2, S.pseg, L.y, L.ty, is_tree, gout, L.np,
+                    [&](int seg) { return seg < n1; },
+                    [&](int seg, int p, int, const uint4 &yq, const float4 &va, const float4 &vb, unsigned m) {
+                        if (seg >= n1) {
+                            if (p - P1 < BwdSmem<R>::RCAP) S.rstash[p - P1] = yq;
+                            return;
+                        }
                         const int row = int(S.seg_nm[seg] >> 8);
                         float *prow = S.gpatch + row * G::PYS;
                         int yv[8];
@@ -991,12 +1031,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         block_sync();
     }
     // routing: the sources of the interior cells, plan segments n1 .. n1 + n2 (routing index q)
-    const auto is_tree = [&](int seg) {
-        const int q = int(S.seg_nm[seg] >> 8);
-        return q >= NIR && q < 2 * NIR;
-    };
-    for_each_packet(S.seg_lo, S.seg_nm, S.pre, n1, n2, S.pseg, L.y, L.ty, is_tree, nullptr, 0,
-                    [&](int seg, int i0, const uint4 &yq, const float4 &, const float4 &, unsigned m) {
+    const auto route = [&](int seg, int i0, const uint4 &yq, unsigned m) {
                         const int q = int(S.seg_nm[seg] >> 8);
                         int yv[8];
                         unpack_y(yq, yv);
@@ -1037,7 +1072,28 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                                 if (sum != 0.f) atomicAdd(&gp[i0 + j], sum);
                             }
                         }
-                    });
+    };
+    if (P2 <= PCAP) {
+        // one staging chunk: pseg still maps the routing packets to their segments, and their y
+        // values are in rstash (the packets beyond its capacity are read again)
+        for (int p = P1 + tid; p < P2; p += NT) {
+            const int seg = S.pseg[p];
+            const int lo = S.seg_lo[seg], n = int(S.seg_nm[seg] & 255u);
+            const int g8 = (lo >> 3) + (p - S.pre[seg]);
+            const uint4 yq = p - P1 < BwdSmem<R>::RCAP ? S.rstash[p - P1]
+                                                       : __ldg(reinterpret_cast<const uint4 *>(is_tree(seg) ? L.ty : L.y) + g8);
+            unsigned m = 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) m |= (unsigned(8 * g8 + j - lo) < unsigned(n) ? 1u : 0u) << j;
+            route(seg, 8 * g8, yq, m);
+        }
+    } else {
+        for_each_packet(S.seg_lo, S.seg_nm, S.pre, n1, n2, S.pseg, L.y, L.ty, is_tree, nullptr, 0,
+                        [](int) { return false; },
+                        [&](int seg, int, int i0, const uint4 &yq, const float4 &, const float4 &, unsigned m) {
+                            route(seg, i0, yq, m);
+                        });
+    }
 }
 
 template <int R>
