@@ -28,13 +28,15 @@ namespace {
 using namespace dev;
 
 constexpr int MC = 16;                      // channels (c_in = c_out)
-constexpr int SZ = 4, SX = 4;               // sub-tile rows (z, x)
-constexpr int PZ = SZ + 2, PX = SX + 2, PY = BY + 2;
+constexpr int SZ = 4, SX = 4, SY = BY;      // sub-tile rows (z, x) and cells (y)
+constexpr int PZ = SZ + 2, PX = SX + 2, PY = SY + 2;
 constexpr int NPROW = PZ * PX;              // patch rows
 constexpr int NPC = NPROW * PY;             // patch cells
 constexpr int NIROW = SZ * SX;              // interior rows
-constexpr int MAXT = NIROW * BY;            // interior cells
-constexpr int NSUB = (TZ / SZ) * (TX / SX); // sub-tiles per work item
+constexpr int MAXT = NIROW * SY;            // interior cells
+constexpr int NSUB_ZX = (TZ / SZ) * (TX / SX);
+constexpr int NSUB = NSUB_ZX * (BY / SY);   // sub-tiles per work item: (z, x) quarters, then y halves
+constexpr int NWY = (PY + 31) / 32;         // 32-bit words of a patch row's cell mask
 constexpr int NTAP = 27;
 constexpr int WTAP = 512;                   // bytes of one tap's 16 x 16 bf16 weight block
 constexpr uint32_t TMEM_COLS = 256;
@@ -45,7 +47,8 @@ constexpr int NCZM = ((SZ + 1) >> 1) + 2;   // level-(l-1) rows per axis under a
 constexpr int WG_T = 16;                    // targets per weight-gradient GEMM step (one K step)
 constexpr int WG_MG = 64;                   // M groups of 8 rows allocated (54 used: 27 taps x 2)
 constexpr int WG_ROWS = NTAP * MC;          // 432 rows (e, ci) of the weight gradient
-static_assert(TZ % SZ == 0 && TX % SX == 0, "sub-tiles must divide the work-item tile");
+static_assert(TZ % SZ == 0 && TX % SX == 0 && BY % SY == 0, "sub-tiles must divide the work-item tile");
+static_assert(MAXT % NT == 0, "whole interior cells per thread");
 static_assert(SZ % 2 == 0 && SX % 2 == 0, "sub-tiles must be even-aligned (coarse cells)");
 static_assert(TM_A + 8 * NTAP <= TM_D && TM_D + 16 <= TMEM_COLS, "tensor-memory columns");
 static_assert(NPC < 65536 && MAXT <= 1024, "16-bit cell ids");
@@ -160,6 +163,14 @@ __device__ __forceinline__ bool block_timed_out(bool ok, uint64_t *bar, uint32_t
     return bad;
 }
 
+// Completion of the MMAs committed to `bar`: thread 0 (the issuing thread) waits on the mbarrier,
+// the others at the block barrier that shares the outcome (so they spend no issue slots polling);
+// tcgen05.fence::after_thread_sync after it orders their tensor-memory reads. True on a timeout.
+__device__ __forceinline__ bool block_wait_mma(uint64_t *bar, uint32_t parity, unsigned *err) {
+    const bool ok = threadIdx.x == 0 ? mbar_wait(bar, parity) : true;
+    return block_timed_out(ok, bar, parity, err);
+}
+
 // Self-test of the bounded-wait path: one block waits on an mbarrier that nothing arrives at, gives up
 // after limit_ns and records ERR_TIMEOUT, exactly as the tensor-core kernels do when their MMAs do
 // not complete. Nothing faults; the context stays usable.
@@ -185,11 +196,12 @@ __host__ __device__ __forceinline__ bool sub_of(const DevLayout &L, const Item &
     s.l = it.l;
     s.g = L.geo[it.l];
     s.gc = it.l > L.l_min ? L.geo[it.l - 1] : s.g;
-    s.z0 = it.a * TZ + (sub / (TX / SX)) * SZ;
-    s.x0 = it.b * TX + (sub % (TX / SX)) * SX;
+    const int zx = sub % NSUB_ZX;
+    s.z0 = it.a * TZ + (zx / (TX / SX)) * SZ;
+    s.x0 = it.b * TX + (zx % (TX / SX)) * SX;
     s.yb = it.yb;
-    s.y0 = it.yb * BY;
-    return s.z0 < s.g.dz && s.x0 < s.g.dx;
+    s.y0 = it.yb * BY + (sub / NSUB_ZX) * SY;
+    return s.z0 < s.g.dz && s.x0 < s.g.dx && s.y0 < s.g.dy;
 }
 
 // Patch row pr = (iz, ix) covers level cells (z0-1+iz, x0-1+ix). 0: never read, 1: staged from the
@@ -252,7 +264,7 @@ __host__ __device__ __forceinline__ bool sub_inner(const Sub &s) {
 // elements; refl: the patch row lies outside the grid (with zero boundary the segment is empty).
 __host__ __device__ inline void feat_segment(const DevLayout &L, const Sub &s, int sg, int &lo, int &hi, bool &refl) {
     const int ylo = s.y0 - 1;
-    const int ya = imax(ylo, 0), yb = imin(s.y0 + BY + 1, s.g.dy);
+    const int ya = imax(ylo, 0), yb = imin(s.y0 + SY + 1, s.g.dy);
     const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
     const int kind = sg / NPROW, pr = sg - kind * NPROW;
     lo = 0;
@@ -323,7 +335,7 @@ __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *
                                  int nseg, FeatStage &S) {
     const int tid = threadIdx.x;
     const int ylo = s.y0 - 1;
-    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);
+    const int ya = max(ylo, 0), yb = min(s.y0 + SY + 1, s.g.dy);
     const bool inner = sub_inner(s);
     const FeatLoader loader{L.y, L.ty, vals, tree, S.smeta};
     for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int sg, int, const McSlot &sl) {
@@ -365,26 +377,33 @@ __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *
             }
         }
     });
-    // cells outside the grid: y mirrors of staged rows, whole rows for the zero boundary
+    // cells outside the grid (none when the patch lies inside it): the cells y = -1 and y = dy of each
+    // staged row mirror y = 0 and y = dy - 1 (zero with the zero boundary), and with the zero boundary
+    // the rows outside the grid are zero
     const uint4 z4 = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < NPROW * PY; i += NT) {
-        const int pr = i / PY, py = i - pr * PY;
-        int rz, rx;
-        const int m = row_mode(s, pr, bc, rz, rx);
-        const int y = ylo + py;
-        if (m == 2) {
-            S.p0[i] = z4;
-            S.p1[i] = z4;
-        } else if (m == 1 && (y == -1 || y == s.g.dy)) {
+    if (!inner || ylo < 0 || s.y0 + SY >= s.g.dy) {
+        for (int t = tid; t < 2 * NPROW; t += NT) {
+            const int pr = t >> 1, y = (t & 1) ? s.g.dy : -1, py = y - ylo;
+            int rz, rx;
+            if (py < 0 || py >= PY || row_mode(s, pr, bc, rz, rx) != 1) continue;
+            const int i = pr * PY + py;
             if (bc == APR_BC_ZERO) {
                 S.p0[i] = z4;
                 S.p1[i] = z4;
             } else {
-                const int src = pr * PY + reflect_idx(y, s.g.dy) - ylo;  // in the patch: y = -1 -> 0, y = dy -> dy-1
+                const int src = pr * PY + reflect_idx(y, s.g.dy) - ylo;  // y = -1 -> 0, y = dy -> dy-1
                 S.p0[i] = S.p0[src];
                 S.p1[i] = S.p1[src];
             }
         }
+        if (bc == APR_BC_ZERO && !inner)
+            for (int i = tid; i < NPROW * PY; i += NT) {
+                int rz, rx;
+                if (row_mode(s, i / PY, bc, rz, rx) == 2) {
+                    S.p0[i] = z4;
+                    S.p1[i] = z4;
+                }
+            }
     }
     block_sync();
 }
@@ -404,8 +423,10 @@ struct Targets {
     int row_lo[NIROW], row_base[NIROW + 1];
 };
 
-// Row offsets of the targets (warp 0; no barrier).
+// Row offsets of the targets (warp 0; no barrier): the sub-tile spans whole y-blocks, so the block
+// offsets give each interior row's level-l particles exactly.
 __device__ __forceinline__ void target_rows(const DevLayout &L, const Sub &s, Targets &T) {
+    static_assert(SY == BY, "sub-tiles span one y-block");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         int lo = 0, cnt = 0;
@@ -659,15 +680,17 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     for (int b0 = 0; b0 < nt; b0 += 128) {
         const int t = b0 + 32 * q + lane;
         const int cell = t < nt ? int(S.tg.cell[t]) : -1;
-        for (int e = e0; e < e1; ++e) {
-            uint4 a = make_uint4(0, 0, 0, 0), b = a;
-            if (cell >= 0) {
-                const int c = cell + tap_off(e);
-                a = S.st.p0[c];
-                b = S.st.p1[c];
+        // rows past the last target are never read back: a warp holding only such rows skips them
+        if (b0 + 32 * q < nt)
+            for (int e = e0; e < e1; ++e) {
+                uint4 a = make_uint4(0, 0, 0, 0), b = a;
+                if (cell >= 0) {
+                    const int c = cell + tap_off(e);
+                    a = S.st.p0[c];
+                    b = S.st.p1[c];
+                }
+                tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
             }
-            tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
-        }
         tmem_wait_st();
         tc_fence_before();
         block_sync();
@@ -677,8 +700,7 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
                 mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc, e > 0);
             mma_commit(&S.bar);
         }
-        const bool ok = mbar_wait(&S.bar, phase);
-        if (block_timed_out(ok, &S.bar, phase, L.err)) break;
+        if (block_wait_mma(&S.bar, phase, L.err)) break;
         phase ^= 1;
         tc_fence_after();
         if (warp < 4) {
@@ -710,6 +732,13 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
 
 // ---------------------------------------------------------------- data adjoint
 constexpr int NSEG_B = NPROW + 3 * NIROW;  // gradient rows, then interior particle / tree / coarse rows
+// Row groups of the data adjoint: a destination with q pre-images that a gradient reaches takes an
+// aligned group of rows, one pre-image per row: class 0 (33..64 pre-images, 32 rows, two passes),
+// class c = 1..6 (2^(6-c) rows for up to that many pre-images). Classes are laid out in order, so
+// every group starts at a multiple of its size and stays inside one warp's 32 rows.
+constexpr int NCLS = 7;
+__device__ __forceinline__ int group_rows(int c) { return min(32, 64 >> c); }
+__device__ __forceinline__ int group_class(int q) { return q > 32 ? 0 : 6 - (q > 1 ? 32 - __clz(q - 1) : 0); }
 constexpr unsigned char SRC_NONE = 0xFF, SRC_P = 0, SRC_T = 1, SRC_C = 2;  // source kinds of a patch cell
 static_assert(SRC_P == 0 && SRC_T == 1, "interior particle / tree segments store their kind index");
 
@@ -719,15 +748,17 @@ struct BwdSmem {
     alignas(16) unsigned char w[NTAP * WTAP];
     int srci[MAXT];                 // source of each interior cell: index ...
     unsigned char srck[MAXT];       // ... and kind (particle, tree, coarse particle)
-    unsigned short dlist[MAXT];     // destinations: one-pre-image ones from the front, others from the back
-    unsigned tmask[NPROW][3];       // cells holding a target, per patch row (bits along y)
-    unsigned hot[NPROW][3];         // cells within distance 1 of a target
+    unsigned short dorder[MAXT];    // destinations grouped by row-group class, in slot order
+    unsigned tmask[NPROW][NWY];     // cells holding a target, per patch row (bits along y)
+    unsigned hot[NPROW][NWY];       // cells within distance 1 of a target
     int seg_lo[NSEG_B];
     int pre[NSEG_B + 1];
     unsigned short smeta[NSEG_B];  // plan meta (segment index) of every entry
     int warp_tot[NWARP + 1];
     unsigned short segid[SEGID_CAP];
-    int n1, nn;
+    int ccnt[NCLS];                 // destinations per row-group class
+    int coff[NCLS + 1];             // first destination (in dorder) of each class
+    int rbase[NCLS + 1];            // first row of each class
     uint64_t bar;
     uint32_t tmem;
 };
@@ -737,8 +768,8 @@ struct BwdSmem {
 // nodes and the level-(l-1) particles over the interior y range.
 __host__ __device__ inline void adj_segment(const DevLayout &L, const Sub &s, int sg, int &lo, int &hi) {
     const int ylo = s.y0 - 1;
-    const int ya = imax(ylo, 0), yb = imin(s.y0 + BY + 1, s.g.dy);
-    const int yia = s.y0, yib = imin(s.y0 + BY, s.g.dy);
+    const int ya = imax(ylo, 0), yb = imin(s.y0 + SY + 1, s.g.dy);
+    const int yia = s.y0, yib = imin(s.y0 + SY, s.g.dy);
     const bool has_tree = s.l < L.l_max, has_coarse = s.l > L.l_min;
     lo = 0;
     hi = 0;
@@ -765,17 +796,21 @@ __device__ __forceinline__ bool hot_at(const BwdSmem &S, int pz, int px, int py)
 }
 
 // Pre-images along one axis of a destination whose first fine coordinate is u: its in-grid fine
-// cells (one, or two for a coarse particle) and the out-of-grid cells that reflect onto them.
-__device__ __forceinline__ int axis_pre(int u, bool coarse, int d, bool reflect, int *o) {
-    int n = 0;
-    o[n++] = u;
-    if (coarse && u + 1 < d) o[n++] = u + 1;
+// cells (one, or two for a coarse particle) and the out-of-grid cells that reflect onto them, as
+// patch coordinates (position - base, base = the patch's first position) packed 8 bits each into
+// *w (registers, no local array). Returns the count (at most 4).
+__device__ __forceinline__ int axis_pre(int u, bool coarse, int d, bool reflect, int base, uint32_t *w) {
+    uint32_t v = uint32_t(u - base);
+    int n = 1;
+    if (coarse && u + 1 < d) v |= uint32_t(u + 1 - base) << (8 * n++);
     if (reflect) {
-        if (u == 0) o[n++] = -1;
-        if ((coarse ? min(u + 1, d - 1) : u) == d - 1) o[n++] = d;
+        if (u == 0) v |= uint32_t(-1 - base) << (8 * n++);
+        if ((coarse ? min(u + 1, d - 1) : u) == d - 1) v |= uint32_t(d - base) << (8 * n++);
     }
+    *w = v;
     return n;
 }
+__device__ __forceinline__ int pre_at(uint32_t w, int a) { return int((w >> (8 * a)) & 255u); }
 
 __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
                                                             const uint16_t *__restrict__ W, int bc,
@@ -792,19 +827,15 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     preload_weights(W, s.l - L.l_min, wreg);
     const bool reflect = bc == APR_BC_REFLECT;
     const int ylo = s.y0 - 1;
-    const int ya = max(ylo, 0), yb = min(s.y0 + BY + 1, s.g.dy);  // gradient rows: y range of the patch
-    const int yia = s.y0, yib = min(s.y0 + BY, s.g.dy);            // interior y range
+    const int ya = max(ylo, 0), yb = min(s.y0 + SY + 1, s.g.dy);  // gradient rows: y range of the patch
+    const int yia = s.y0, yib = min(s.y0 + SY, s.g.dy);            // interior y range
     const uint4 z4 = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < NPC; i += NT) {
         S.g0[i] = z4;
         S.g1[i] = z4;
     }
     for (int i = tid; i < MAXT; i += NT) S.srck[i] = SRC_NONE;
-    for (int i = tid; i < NPROW * 3; i += NT) (&S.tmask[0][0])[i] = 0;
-    if (tid == 0) {
-        S.n1 = 0;
-        S.nn = 0;
-    }
+    for (int i = tid; i < NPROW * NWY; i += NT) (&S.tmask[0][0])[i] = 0;
     const int nseg = load_mc_plan(L.mcbplan, blockIdx.x * NSUB + blockIdx.y, 0, false, S.seg_lo, S.smeta, S.pre,
                                   S.warp_tot);
 
@@ -837,16 +868,16 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
         const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
         if (k < 2) {
             if (sl.y >= yia && sl.y < yib) {
-                S.srck[r * BY + sl.y - s.y0] = (unsigned char)k;
-                S.srci[r * BY + sl.y - s.y0] = i;
+                S.srck[r * SY + sl.y - s.y0] = (unsigned char)k;
+                S.srci[r * SY + sl.y - s.y0] = i;
             }
         } else {
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const int y = 2 * sl.y + f;
                 if (y >= yia && y < yib) {
-                    S.srck[r * BY + y - s.y0] = SRC_C;
-                    S.srci[r * BY + y - s.y0] = i;
+                    S.srck[r * SY + y - s.y0] = SRC_C;
+                    S.srci[r * SY + y - s.y0] = i;
                 }
             }
         }
@@ -854,52 +885,74 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     // cells within distance 1 of a target: y dilation of each row, OR over the 3 x 3 neighbour rows
     if (tid < NPROW) {
         const int pz = tid / PX, px = tid % PX;
-        unsigned h[3] = {0, 0, 0};
+        unsigned h[NWY] = {};
         for (int dz = -1; dz <= 1; ++dz)
             for (int dx = -1; dx <= 1; ++dx) {
                 const int qz = pz + dz, qx = px + dx;
                 if (qz < 0 || qz >= PZ || qx < 0 || qx >= PX) continue;
                 const unsigned *m = S.tmask[qz * PX + qx];
-                h[0] |= m[0] | (m[0] << 1) | (m[0] >> 1) | (m[1] << 31);
-                h[1] |= m[1] | (m[1] << 1) | (m[1] >> 1) | (m[0] >> 31) | (m[2] << 31);
-                h[2] |= m[2] | (m[2] << 1) | (m[2] >> 1) | (m[1] >> 31);
+#pragma unroll
+                for (int w = 0; w < NWY; ++w)
+                    h[w] |= m[w] | (m[w] << 1) | (m[w] >> 1) | (w + 1 < NWY ? m[w + 1] << 31 : 0u) |
+                            (w > 0 ? m[w - 1] >> 31 : 0u);
             }
-        S.hot[tid][0] = h[0];
-        S.hot[tid][1] = h[1];
-        S.hot[tid][2] = h[2];
+#pragma unroll
+        for (int w = 0; w < NWY; ++w) S.hot[tid][w] = h[w];
     }
     block_sync();
     // destinations: every particle / tree node of the interior, and every coarse particle (anchored
-    // at its first fine cell), that has a pre-image within distance 1 of a target
-    for (int ic = tid; ic < MAXT; ic += NT) {
-        const int r = ic / BY, iy = ic % BY;
+    // at its first fine cell), with q > 0 pre-images within distance 1 of a target (the others add
+    // exact zeros). Each takes a slot in its row-group class.
+    constexpr int CPT = MAXT / NT;  // interior cells per thread
+    if (tid < NCLS) S.ccnt[tid] = 0;
+    block_sync();
+    // class of interior cell ic as a destination (-1: none)
+    auto dest_class = [&](int ic) -> int {
+        const int r = ic / SY, iy = ic % SY;
         const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
-        if (z >= s.g.dz || x >= s.g.dx || y >= s.g.dy) continue;
+        if (z >= s.g.dz || x >= s.g.dx || y >= s.g.dy) return -1;
         const int k = S.srck[ic];
         if (k == SRC_NONE) {
             if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
-            continue;
+            return -1;
         }
         const bool coarse = k == SRC_C;
-        if (coarse && ((z | x | y) & 1)) continue;
-        int oz[4], ox[4], oy[4];
-        const int nz = axis_pre(z, coarse, s.g.dz, reflect, oz);
-        const int nx = axis_pre(x, coarse, s.g.dx, reflect, ox);
-        const int ny = axis_pre(y, coarse, s.g.dy, reflect, oy);
-        bool any = false;
-        for (int a = 0; a < nz && !any; ++a)
-            for (int b = 0; b < nx && !any; ++b)
-                for (int c = 0; c < ny && !any; ++c)
-                    any = hot_at(S, oz[a] - s.z0 + 1, ox[b] - s.x0 + 1, oy[c] - ylo);
-        if (!any) continue;
-        if (nz * nx * ny == 1)
-            S.dlist[atomicAdd(&S.n1, 1)] = (unsigned short)ic;
-        else
-            S.dlist[MAXT - 1 - atomicAdd(&S.nn, 1)] = (unsigned short)ic;
+        if (coarse && ((z | x | y) & 1)) return -1;
+        uint32_t wz, wx, wy;
+        const int nz = axis_pre(z, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
+        const int nx = axis_pre(x, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
+        const int ny = axis_pre(y, coarse, s.g.dy, reflect, ylo, &wy);
+        int q = 0;
+        for (int a = 0; a < nz; ++a)
+            for (int b = 0; b < nx; ++b)
+                for (int c = 0; c < ny; ++c) q += hot_at(S, pre_at(wz, a), pre_at(wx, b), pre_at(wy, c));
+        return q == 0 ? -1 : group_class(q);
+    };
+    int my_c[CPT], my_slot[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        my_c[u] = dest_class(tid + u * NT);
+        my_slot[u] = 0;
+        if (my_c[u] >= 0) my_slot[u] = atomicAdd(&S.ccnt[my_c[u]], 1);
     }
     block_sync();
-    const int n1 = S.n1, nn = S.nn;
-    if (n1 + nn == 0) return;
+    if (tid == 0) {
+        int d = 0, rw = 0;
+        for (int c = 0; c < NCLS; ++c) {
+            S.coff[c] = d;
+            S.rbase[c] = rw;
+            d += S.ccnt[c];
+            rw += S.ccnt[c] * group_rows(c);
+        }
+        S.coff[NCLS] = d;
+        S.rbase[NCLS] = rw;
+    }
+    block_sync();
+#pragma unroll
+    for (int u = 0; u < CPT; ++u)
+        if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)(tid + u * NT);
+    const int nrows = S.rbase[NCLS], rows2 = S.rbase[1];  // rows2: the two-pass rows come first
+    if (nrows == 0) return;
     store_weights(wreg, S.w);
     if (tid == 0) mbar_init(&S.bar);
     if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
@@ -912,45 +965,57 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     const uint32_t lane_base = uint32_t(32 * q) << 16;
     const int e0 = warp < 4 ? 0 : 14, e1 = warp < 4 ? 14 : NTAP;
     constexpr uint32_t idesc = idesc_bf16(128, 16, false);
-    const int nb1 = (n1 + 127) / 128, nbn = (nn + 127) / 128;
     uint32_t phase = 0;
-    for (int bk = 0; bk < nb1 + nbn; ++bk) {
-        // this thread's destination row
-        const int row = 32 * q + lane;
-        int ic = -1;
-        if (bk < nb1) {
-            if (bk * 128 + row < n1) ic = S.dlist[bk * 128 + row];
-        } else {
-            const int j = (bk - nb1) * 128 + row;
-            if (j < nn) ic = S.dlist[MAXT - 1 - j];
+    for (int b0 = 0; b0 < nrows; b0 += 128) {
+        // this thread's row: destination ic, its j-th pre-image (j + 32 in the second pass)
+        const int row = b0 + 32 * q + lane;
+        int ic = -1, j = 0, gr = 0;
+        if (row < nrows) {
+            int c = 0;
+            while (row >= S.rbase[c + 1]) ++c;
+            gr = group_rows(c);
+            const int off = row - S.rbase[c];
+            ic = S.dorder[S.coff[c] + off / gr];
+            j = off % gr;
         }
-        int oz[4], ox[4], oy[4], nz = 0, nx = 0, ny = 0;
+        uint32_t wz = 0, wx = 0, wy = 0;
+        int nz = 0, nx = 0, ny = 0;
         if (ic >= 0) {
-            const int r = ic / BY;
+            const int r = ic / SY;
             const bool coarse = S.srck[ic] == SRC_C;
-            nz = axis_pre(s.z0 + r / SX, coarse, s.g.dz, reflect, oz);
-            nx = axis_pre(s.x0 + r % SX, coarse, s.g.dx, reflect, ox);
-            ny = axis_pre(s.y0 + ic % BY, coarse, s.g.dy, reflect, oy);
+            nz = axis_pre(s.z0 + r / SX, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
+            nx = axis_pre(s.x0 + r % SX, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
+            ny = axis_pre(s.y0 + ic % SY, coarse, s.g.dy, reflect, ylo, &wy);
         }
-        const int nq = nz * nx * ny;
+        const int npass = b0 < rows2 ? 2 : 1;
         bool failed = false;
-        for (int j = 0; __syncthreads_or(j < nq); ++j) {
-            int pz = -100, px = 0, py = 0;
-            if (j < nq) {
-                pz = oz[j / (nx * ny)] - s.z0 + 1;
-                px = ox[(j / ny) % nx] - s.x0 + 1;
-                py = oy[j % ny] - ylo;
-            }
-            for (int e = e0; e < e1; ++e) {
-                const int cz = pz - (e / 9 - 1), cx = px - ((e / 3) % 3 - 1), cy = py - (e % 3 - 1);
-                uint4 a = make_uint4(0, 0, 0, 0), b = a;
-                if (cz >= 0 && cz < PZ && cx >= 0 && cx < PX && cy >= 0 && cy < PY) {
-                    const int c = (cz * PX + cx) * PY + cy;
-                    a = S.g0[c];
-                    b = S.g1[c];
+        for (int pass = 0; pass < npass; ++pass) {
+            // the (j + 32 pass)-th pre-image within distance 1 of a target, in (z, x, y) order
+            int pz = -100, px = 0, py = 0, want = j + 32 * pass;
+            for (int a = 0; a < nz && pz < -1; ++a)
+                for (int bb = 0; bb < nx && pz < -1; ++bb)
+                    for (int c = 0; c < ny; ++c) {
+                        const int tz = pre_at(wz, a), tx = pre_at(wx, bb), ty = pre_at(wy, c);
+                        if (!hot_at(S, tz, tx, ty)) continue;
+                        if (want-- == 0) {
+                            pz = tz;
+                            px = tx;
+                            py = ty;
+                            break;
+                        }
+                    }
+            // rows past the last one are never read back: a warp holding only such rows skips them
+            if (b0 + 32 * q < nrows)
+                for (int e = e0; e < e1; ++e) {
+                    const int cz = pz - (e / 9 - 1), cx = px - ((e / 3) % 3 - 1), cy = py - (e % 3 - 1);
+                    uint4 a = make_uint4(0, 0, 0, 0), b = a;
+                    if (cz >= 0 && cz < PZ && cx >= 0 && cx < PX && cy >= 0 && cy < PY) {
+                        const int c = (cz * PX + cx) * PY + cy;
+                        a = S.g0[c];
+                        b = S.g1[c];
+                    }
+                    tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
                 }
-                tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
-            }
             tmem_wait_st();
             tc_fence_before();
             block_sync();
@@ -958,11 +1023,10 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
             if (tid == 0) {
                 for (int e = 0; e < NTAP; ++e)
                     mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc,
-                           (j > 0 || e > 0) ? 1u : 0u);
+                           (pass > 0 || e > 0) ? 1u : 0u);
                 mma_commit(&S.bar);
             }
-            const bool ok = mbar_wait(&S.bar, phase);
-            if (block_timed_out(ok, &S.bar, phase, L.err)) {
+            if (block_wait_mma(&S.bar, phase, L.err)) {
                 failed = true;
                 break;
             }
@@ -973,7 +1037,16 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
         if (warp < 4) {
             float v[16];
             tmem_ld16(tb + lane_base + TM_D, v);
-            if (ic >= 0) {
+            // sum over the row group in a fixed butterfly order (every lane of a group gets the same sum)
+            const int gmax = __reduce_max_sync(0xffffffffu, gr);
+            for (int w = 1; w < gmax; w <<= 1) {
+#pragma unroll
+                for (int c = 0; c < MC; ++c) {
+                    const float o = __shfl_xor_sync(0xffffffffu, v[c], w);
+                    if (w < gr) v[c] += o;
+                }
+            }
+            if (ic >= 0 && j == 0) {
                 const int k = S.srck[ic];
                 const size_t idx = size_t(S.srci[ic]);
                 if (k == SRC_T) {
@@ -1101,8 +1174,7 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
                 }
                 mma_commit(&S.bar);
             }
-            const bool ok = mbar_wait(&S.bar, phase);
-            if (block_timed_out(ok, &S.bar, phase, L.err)) {
+            if (block_wait_mma(&S.bar, phase, L.err)) {
                 failed = true;
                 break;
             }
