@@ -13,7 +13,7 @@ namespace aprk {
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s,
                             int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr, int tile0 = 0);
-cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
+cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals, float *tree,
                                  cudaStream_t s, int C = 1, int ch = 0);
 cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                            const float *st, int bc, float *out, cudaStream_t s);
@@ -23,7 +23,8 @@ cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int
                                const float *tree, int bc, const float *gout, float *partial, cudaStream_t s);
 cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64_t *level_begin, int l_min,
                                   int n_levels, int K3, float *gw, cudaStream_t s);
-cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, int n, float *gp, float *gt, cudaStream_t s);
+cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
+                                 cudaStream_t s);
 }  // namespace aprk
 
 using namespace aprk;
@@ -181,6 +182,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         if (e == cudaSuccess) e = upload(h, &h->d_fwd, X.fwd_items.data(), X.fwd_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_bwd, X.bwd_items.data(), X.bwd_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_tree, X.tree_items.data(), X.tree_items.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_tplan, X.tplan.data(), X.tplan.size());
         if (e == cudaSuccess) e = upload(h, &h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1));
         for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
             const HostFPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
@@ -229,6 +231,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
             L.fplan[i] = FPlanView{h->d_fplan_hdr[i], h->d_fplan_ent[i]};
             L.bplan[i] = FPlanView{h->d_fplan_hdr[2 + i], h->d_fplan_ent[2 + i]};
         }
+        L.tplan = h->d_tplan;
         L.mcfplan = PlanView{h->d_plan_hdr[0], h->d_plan_ent[0]};
         L.mcbplan = PlanView{h->d_plan_hdr[1], h->d_plan_ent[1]};
         // the plans live on the device now; the host copies are not needed again
@@ -238,6 +241,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         }
         h->X.mcfplan = HostPlan{};
         h->X.mcbplan = HostPlan{};
+        h->X.tplan = std::vector<TreePlan>{};
     }
     *out = h;
     return APR_OK;
@@ -317,7 +321,7 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
     for (int l = X.l_max - 1; l >= X.l_min; --l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
         for (int c = 0; c < channels; ++c) {  // channels-last values: one strided pass per channel
-            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, int(n), particles, tree, stream, channels, c);
+            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, h->d_tplan + b, int(n), particles, tree, stream, channels, c);
             if (e != cudaSuccess) return cuda_status(e);
         }
     }
@@ -418,7 +422,7 @@ apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *
     cudaError_t e = cudaSuccess;
     for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-        e = launch_tree_pushdown(h->L, h->d_tree + b, int(n), grad_particles, grad_tree, stream);
+        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, stream);
     }
     return cuda_status(e);
 }

@@ -43,6 +43,17 @@ struct PlanEnt {
     uint16_t meta, pre;
 };
 static_assert(sizeof(PlanEnt) == 8, "plan entries are 8-byte words");
+// Tree brick plan, one per tree work item (built once per APR): the brick's child segments (k = 0..3:
+// the level-(l+1) particle rows (a, b) = (k >> 1, k & 1); k = 4..7: the tree rows), each over the
+// child y-blocks 2 yb, 2 yb + 1, starting at clo[k] with byte k % 4 of cn[k / 4] elements; and the
+// brick's own tree nodes [tlo, tlo + tn).
+struct TreePlan {
+    int32_t clo[8];
+    uint32_t cn[2];
+    int32_t tlo;
+    uint32_t tn;
+};
+static_assert(sizeof(TreePlan) == 48, "tree plans are three 16-byte words");
 struct PlanView {
     const PlanHdr *hdr;
     const PlanEnt *ent;
@@ -74,6 +85,7 @@ struct DevLayout {
     LevelGeo geo[MAXL];
     FPlanView fplan[2];  // forward tiles (fwd_items), stencil radius 1 and 2
     FPlanView bplan[2];  // data-adjoint tiles (bwd_items), stencil radius 1 and 2
+    const TreePlan *tplan;  // tree bricks (tree_items)
     PlanView mcfplan;    // multi-channel feature patches of the sub-tiles of fwd_items
     PlanView mcbplan;    // multi-channel data-adjoint sub-tiles of bwd_items
 };
@@ -98,6 +110,7 @@ struct HostIndex {
     HostFPlan fplan[2];                       // forward tile plans (build_plans), radius 1 and 2
     HostFPlan bplan[2];                       // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
+    std::vector<TreePlan> tplan;              // tree bricks (tree_plan)
 };
 
 // Builds and validates the index from the host layout. Returns APR_OK or an error code; `msg`
@@ -110,6 +123,7 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &ou
 apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
 bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
+bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P);
 // DevLayout over the host copy of X's index (for host code that walks it like a kernel).
 DevLayout host_layout_view(const HostIndex &X);
 
@@ -155,6 +169,7 @@ struct apr_handle_s {
     // tile plans: multi-channel feature, adjoint
     aprk::PlanHdr *d_plan_hdr[2] = {};
     aprk::PlanEnt *d_plan_ent[2] = {};
+    aprk::TreePlan *d_tplan = nullptr;
     aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
     uint2 *d_fplan_ent[4] = {};
     size_t dev_bytes = 0;

@@ -1118,45 +1118,14 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
 // brick's nodes live in the 2x2 child rows of level l+1, y-blocks 2yb and 2yb+1 (lanes 0..3:
 // particle rows (a, b), lanes 4..7: tree rows).
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void child_segment(const DevLayout &L, const Item &it, int lane, int &lo, int &n) {
-    const int l = it.l;
-    const LevelGeo gc = L.geo[l + 1];
-    lo = 0;
-    n = 0;
-    if (lane < 8) {
-        const int kind = lane >> 2, a = (lane >> 1) & 1, b = lane & 1;
-        const int cz = 2 * it.a + a, cx = 2 * it.b + b;
-        if (cz < gc.dz && cx < gc.dx && (kind == 0 || l + 1 < L.l_max)) {
-            const int crr = cz * gc.dx + cx;
-            const int j0 = 2 * it.yb, j1 = min(2 * it.yb + 2, gc.nb);
-            const uint32_t a0 = kind == 0 ? pblock(L, gc, crr, j0) : tblock(L, gc, crr, j0);
-            const uint32_t a1 = kind == 0 ? pblock(L, gc, crr, j1) : tblock(L, gc, crr, j1);
-            lo = int(a0);
-            n = int(a1 - a0);
-        }
-    }
-}
-
 // Warp-level flattened loop over the children: f(segment, index, y, value), values read from vp
 // (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use.
 template <typename F>
 __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f,
                                               int C = 1, int c = 0) {
     const int lane = threadIdx.x & 31;
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    int ex[8], sl[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        ex[k] = __shfl_sync(0xffffffffu, incl - n, k);
-        sl[k] = __shfl_sync(0xffffffffu, lo, k);
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 7);
-    for (int e0 = 0; e0 < total; e0 += 32 * UNROLL) {
+    const ChildSegs cs(lo, n);
+    for (int e0 = 0; e0 < cs.total; e0 += 32 * UNROLL) {
         int sg[UNROLL], ix[UNROLL], yv[UNROLL];
         float vv[UNROLL];
 #pragma unroll
@@ -1166,19 +1135,9 @@ __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n,
             ix[u] = 0;
             yv[u] = 0;
             vv[u] = 0.f;
-            if (e < total) {
-                int s = 0;
-#pragma unroll
-                for (int k = 1; k < 8; ++k) s = ex[k] <= e ? k : s;
-                int slo = sl[0], sex = ex[0];
-#pragma unroll
-                for (int k = 1; k < 8; ++k)
-                    if (k == s) {
-                        slo = sl[k];
-                        sex = ex[k];
-                    }
+            if (e < cs.total) {
+                const int s = cs.seg(e, ix[u]);
                 sg[u] = s;
-                ix[u] = slo + (e - sex);
                 yv[u] = s >= 4 ? int(L.ty[ix[u]]) : int(L.y[ix[u]]);
                 vv[u] = s >= 4 ? vt[size_t(ix[u]) * C + c] : vp[size_t(ix[u]) * C + c];
             }
@@ -1191,7 +1150,8 @@ __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n,
 
 // APR tree restriction for one level l (Sec. 3.4): each child value goes to a slot (a, b, y&1) of its
 // parent, then every node averages its in-grid slots in a fixed order.
-__global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+__global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                           const TreePlan *__restrict__ tplan, int n,
                                                            const float *__restrict__ vals,
                                                            float *__restrict__ tree, int C, int ch) {
     __shared__ float slot[NWARP][8][BY];
@@ -1199,20 +1159,24 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
     const int bi = blockIdx.x * NWARP + warp;
     if (bi >= n) return;
     const Item it = items[bi];
-    const int l = it.l;
-    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+    int lo, cn, tlo, tn;
+    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    const LevelGeo gc = L.geo[it.l + 1];
     const int y0 = it.yb * BY;
-    int lo, cn;
-    child_segment(L, it, lane, lo, cn);
-    const int rr = it.a * g.dx + it.b;
-    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
+    // the brick's node y values (at most BY: two per lane) are loaded together with the children
+    const int ty0 = lane < tn ? int(L.ty[tlo + lane]) : 0;
+    const int ty1 = lane + 32 < tn ? int(L.ty[tlo + lane + 32]) : 0;
     float(*sl)[BY] = slot[warp];
     warp_children(L, lo, cn, vals, tree, [&](int s, int, int yv, float v) {
         sl[(s & 3) * 2 + (yv & 1)][(yv >> 1) - y0] = v;
     }, C, ch);
     __syncwarp();
-    for (int t = tlo + lane; t < thi; t += 32) {
-        const int yv = L.ty[t];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j >= tn) break;
+        const int yv = h ? ty1 : ty0;
+        const size_t t = size_t(tlo + j);
         float s = 0.f;
         int cnt = 0;
 #pragma unroll
@@ -1223,31 +1187,33 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
                 ++cnt;
             }
         }
-        tree[size_t(t) * C + ch] = s / float(cnt);
+        tree[t * C + ch] = s / float(cnt);
     }
 }
 
 // Backward through the tree averages, one level l (coarse to fine): each child (particle or tree
 // node of level l+1) of a tree node t receives gt[t] / n_children(t).
-__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                           const TreePlan *__restrict__ tplan, int n,
                                                            float *__restrict__ gp, float *__restrict__ gt) {
     __shared__ float share[NWARP][BY];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * NWARP + warp;
     if (bi >= n) return;
     const Item it = items[bi];
-    const int l = it.l;
-    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+    int lo, cn, tlo, tn;
+    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    const LevelGeo gc = L.geo[it.l + 1];
     const int y0 = it.yb * BY;
-    const int rr = it.a * g.dx + it.b;
-    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
-    for (int t = tlo + lane; t < thi; t += 32) {
-        const int yv = L.ty[t];
-        const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
-        share[warp][yv - y0] = gt[t] / float(cnt);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j < tn) {
+            const int yv = L.ty[tlo + j];
+            const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
+            share[warp][yv - y0] = gt[tlo + j] / float(cnt);
+        }
     }
-    int lo, cn;
-    child_segment(L, it, lane, lo, cn);
     __syncwarp();
     warp_children(L, lo, cn, gp, gt, [&](int s, int i, int yv, float v) {
         float *dst = s >= 4 ? gt : gp;
@@ -1323,9 +1289,9 @@ cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, 
                   : launch_gradmag_t<2>(L, items, n, vals, tree, st, bc, out, s);
 }
 
-cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, int n, const float *vals, float *tree,
-                                 cudaStream_t s, int C, int ch) {
-    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, vals, tree, C, ch);
+cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals,
+                                 float *tree, cudaStream_t s, int C, int ch) {
+    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, tp, n, vals, tree, C, ch);
     return cudaGetLastError();
 }
 
@@ -1347,8 +1313,9 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, int n, float *gp, float *gt, cudaStream_t s) {
-    if (n > 0) tree_pushdown_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, n, gp, gt);
+cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
+                                 cudaStream_t s) {
+    if (n > 0) tree_pushdown_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, tp, n, gp, gt);
     return cudaGetLastError();
 }
 

@@ -521,7 +521,8 @@ struct TreeMcSmem {
 };
 
 __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                                           int n, const uint4 *__restrict__ vals,
+                                                                           const TreePlan *__restrict__ tplan, int n,
+                                                                           const uint4 *__restrict__ vals,
                                                                            uint4 *__restrict__ tree) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TreeMcSmem &S = *reinterpret_cast<TreeMcSmem *>(smraw);
@@ -529,35 +530,43 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
     const int bi = blockIdx.x * TREE_WARPS + warp;
     if (bi >= n) return;
     const Item it = items[bi];
-    const int l = it.l;
-    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
-    const bool child_tree = l + 1 < L.l_max;
+    int lo, cn, tlo, tn;
+    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    const LevelGeo gc = L.geo[it.l + 1];
     S.pres[warp][lane] = 0;
     S.pres[warp][lane + 32] = 0;
     __syncwarp();
     const int cy0 = 2 * it.yb * BY;
-    for (int ab = 0; ab < 4; ++ab) {
-        const int cz = 2 * it.a + (ab >> 1), cx = 2 * it.b + (ab & 1);
-        if (cz >= gc.dz || cx >= gc.dx) continue;
-        const int rr = cz * gc.dx + cx;
-        for (int src = 0; src < (child_tree ? 2 : 1); ++src) {
-            const int lo = int(src ? tblock(L, gc, rr, 2 * it.yb) : pblock(L, gc, rr, 2 * it.yb));
-            const int hi = int(src ? tblock(L, gc, rr, 2 * it.yb + 2) : pblock(L, gc, rr, 2 * it.yb + 2));
-            const uint16_t *yv = src ? L.ty : L.y;
-            const uint4 *v = src ? tree : vals;
-            for (int i = lo + lane; i < hi; i += 32) {
-                const int cy = int(yv[i]) - cy0;  // in [0, 2 BY): exact block range
-                const int slot = ab * 2 + (cy & 1);
-                S.child[warp][cy >> 1][slot][0] = v[2 * size_t(i)];
-                S.child[warp][cy >> 1][slot][1] = v[2 * size_t(i) + 1];
-                atomicOr(&S.pres[warp][cy >> 1], 1u << slot);
+    // the children of the 2 x 2 child rows (segments 0..3 particles, 4..7 tree nodes), flattened;
+    // two elements per lane in flight
+    const ChildSegs cs(lo, cn);
+    for (int e0 = lane; e0 < cs.total; e0 += 64) {
+        int sg[2], ix[2], cy[2];
+        uint4 va[2], vb[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = e0 + 32 * u;
+            sg[u] = -1;
+            if (e < cs.total) {
+                sg[u] = cs.seg(e, ix[u]);
+                const bool src = sg[u] >= 4;
+                cy[u] = int(src ? L.ty[ix[u]] : L.y[ix[u]]) - cy0;  // in [0, 2 BY): exact block range
+                const uint4 *v = src ? tree : vals;
+                va[u] = v[2 * size_t(ix[u])];
+                vb[u] = v[2 * size_t(ix[u]) + 1];
             }
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (sg[u] >= 0) {
+                const int slot = (sg[u] & 3) * 2 + (cy[u] & 1);
+                S.child[warp][cy[u] >> 1][slot][0] = va[u];
+                S.child[warp][cy[u] >> 1][slot][1] = vb[u];
+                atomicOr(&S.pres[warp][cy[u] >> 1], 1u << slot);
+            }
     }
     __syncwarp();
-    const int rr = it.a * g.dx + it.b;
-    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
-    for (int t = tlo + lane; t < thi; t += 32) {
+    for (int t = tlo + lane; t < tlo + tn; t += 32) {
         const int sl = int(L.ty[t]) - it.yb * BY;
         const unsigned m = S.pres[warp][sl];
         float acc[MC];
@@ -591,18 +600,18 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
 
 // Transpose of the tree restriction for 16 FP32 gradient channels, one level (coarse to fine):
 // every child (particle or tree node of level l+1) gets its parent's gradient / #children added.
-__global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items, int n,
+__global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                              const TreePlan *__restrict__ tplan, int n,
                                                               float4 *__restrict__ gp, float4 *__restrict__ gt) {
     __shared__ float4 share[NWARP][BY][MC / 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * NWARP + warp;
     if (bi >= n) return;
     const Item it = items[bi];
-    const int l = it.l;
-    const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
-    const int rr = it.a * g.dx + it.b;
-    const int tlo = int(tblock(L, g, rr, it.yb)), thi = int(tblock(L, g, rr, it.yb + 1));
-    for (int k = lane; k < (thi - tlo) * (MC / 4); k += 32) {
+    int lo, cn, tlo, tn;
+    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    const LevelGeo gc = L.geo[it.l + 1];
+    for (int k = lane; k < tn * (MC / 4); k += 32) {
         const int t = tlo + k / (MC / 4), c = k % (MC / 4);
         const int yv = L.ty[t];
         const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
@@ -611,24 +620,19 @@ __global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L,
         share[warp][yv - it.yb * BY][c] = make_float4(v.x / f, v.y / f, v.z / f, v.w / f);
     }
     __syncwarp();
-    const bool child_tree = l + 1 < L.l_max;
-    for (int ab = 0; ab < 4; ++ab) {
-        const int cz = 2 * it.a + (ab >> 1), cx = 2 * it.b + (ab & 1);
-        if (cz >= gc.dz || cx >= gc.dx) continue;
-        const int crr = cz * gc.dx + cx;
-        for (int src = 0; src < (child_tree ? 2 : 1); ++src) {
-            const int lo = int(src ? tblock(L, gc, crr, 2 * it.yb) : pblock(L, gc, crr, 2 * it.yb));
-            const int hi = int(src ? tblock(L, gc, crr, 2 * it.yb + 2) : pblock(L, gc, crr, 2 * it.yb + 2));
-            const uint16_t *yv = src ? L.ty : L.y;
-            float4 *dst = src ? gt : gp;
-            for (int k = lane; k < (hi - lo) * (MC / 4); k += 32) {
-                const int i = lo + k / (MC / 4), c = k % (MC / 4);
-                const float4 s = share[warp][(int(yv[i]) >> 1) - it.yb * BY][c];
-                float4 &d = dst[size_t(i) * (MC / 4) + c];
-                const float4 v = d;
-                d = make_float4(v.x + s.x, v.y + s.y, v.z + s.z, v.w + s.w);
-            }
-        }
+    // every child (segments 0..3 particles, 4..7 tree nodes) gets its parent's share, 16 channels as
+    // four float4 per element
+    const ChildSegs cs(lo, cn);
+    for (int k = lane; k < cs.total * (MC / 4); k += 32) {
+        const int c = k % (MC / 4);
+        int i;
+        const bool src = cs.seg(k / (MC / 4), i) >= 4;
+        const int yv = src ? L.ty[i] : L.y[i];
+        float4 *dst = src ? gt : gp;
+        const float4 s = share[warp][(yv >> 1) - it.yb * BY][c];
+        float4 &d = dst[size_t(i) * (MC / 4) + c];
+        const float4 v = d;
+        d = make_float4(v.x + s.x, v.y + s.y, v.z + s.z, v.w + s.w);
     }
 }
 
@@ -1296,7 +1300,8 @@ apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, u
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
         if (n > 0)
             mc_tree_restrict_kernel<<<int((n + TREE_WARPS - 1) / TREE_WARPS), TREE_WARPS * 32, sm, stream>>>(
-                h->L, h->d_tree + b, int(n), reinterpret_cast<const uint4 *>(particles), reinterpret_cast<uint4 *>(tree));
+                h->L, h->d_tree + b, h->d_tplan + b, int(n), reinterpret_cast<const uint4 *>(particles),
+                reinterpret_cast<uint4 *>(tree));
         e = cudaGetLastError();
     }
     return cuda_status(e);
@@ -1383,7 +1388,8 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
             const int64_t b = X.tree_level_begin[l], nt = X.tree_level_begin[l + 1] - b;
             if (nt > 0)
                 mc_tree_pushdown_kernel<<<int((nt + NWARP - 1) / NWARP), NT, 0, stream>>>(
-                    h->L, h->d_tree + b, int(nt), reinterpret_cast<float4 *>(grad_particles), reinterpret_cast<float4 *>(gt));
+                    h->L, h->d_tree + b, h->d_tplan + b, int(nt), reinterpret_cast<float4 *>(grad_particles),
+                    reinterpret_cast<float4 *>(gt));
             e = cudaGetLastError();
         }
     }
