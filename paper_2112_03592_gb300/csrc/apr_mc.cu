@@ -187,6 +187,29 @@ __device__ __forceinline__ int tap_off(int e) {  // patch-cell offset of tap e =
     return (e / 9 - 1) * (PX * PY) + ((e / 3) % 3 - 1) * PY + (e % 3 - 1);
 }
 
+// A operand rows of taps E0 .. E1-1 (columns TM_A + 8e) for one row: the patch cells at
+// (pz, px, py) + S_ * (tap offset), both 16-byte halves, zero outside the patch or for an invalid row
+// (a warp-collective store, so every lane calls it). The tap offsets are compile-time constants;
+// only rows on the patch edge test them against the patch.
+template <int E0, int E1, int S_>
+__device__ __forceinline__ void store_taps(const uint4 *p0, const uint4 *p1, int pz, int px, int py, bool valid,
+                                           uint32_t taddr) {
+    const bool inner = valid && pz >= 1 && pz <= PZ - 2 && px >= 1 && px <= PX - 2 && py >= 1 && py <= PY - 2;
+    const int cell = (pz * PX + px) * PY + py;
+#pragma unroll
+    for (int e = E0; e < E1; ++e) {
+        const int dz = S_ * (e / 9 - 1), dx = S_ * ((e / 3) % 3 - 1), dy = S_ * (e % 3 - 1);
+        uint4 a = make_uint4(0, 0, 0, 0), b = a;
+        if (inner || (valid && unsigned(pz + dz) < unsigned(PZ) && unsigned(px + dx) < unsigned(PX) &&
+                      unsigned(py + dy) < unsigned(PY))) {
+            const int c = cell + (dz * PX + dx) * PY + dy;
+            a = p0[c];
+            b = p1[c];
+        }
+        tmem_st8(taddr + TM_A + 8 * e, a, b);
+    }
+}
+
 struct Sub {         // a sub-tile: level, interior origin, level grids
     int l, z0, x0, y0, yb;
     LevelGeo g, gc;  // level l and level l-1 (gc valid if l > l_min)
@@ -678,23 +701,17 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     const uint32_t tb = S.tmem;
     const int q = warp & 3;
     const uint32_t lane_base = uint32_t(32 * q) << 16;
-    const int e0 = warp < 4 ? 0 : 14, e1 = warp < 4 ? 14 : NTAP;
     constexpr uint32_t idesc = idesc_bf16(128, 16, false);
     uint32_t phase = 0;
     for (int b0 = 0; b0 < nt; b0 += 128) {
         const int t = b0 + 32 * q + lane;
-        const int cell = t < nt ? int(S.tg.cell[t]) : -1;
+        const int cell = t < nt ? int(S.tg.cell[t]) : 0;
+        const int cz = cell / (PX * PY), cx = (cell / PY) % PX, cy = cell % PY;
         // rows past the last target are never read back: a warp holding only such rows skips them
-        if (b0 + 32 * q < nt)
-            for (int e = e0; e < e1; ++e) {
-                uint4 a = make_uint4(0, 0, 0, 0), b = a;
-                if (cell >= 0) {
-                    const int c = cell + tap_off(e);
-                    a = S.st.p0[c];
-                    b = S.st.p1[c];
-                }
-                tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
-            }
+        if (b0 + 32 * q < nt) {
+            if (warp < 4) store_taps<0, 14, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
+            else store_taps<14, NTAP, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
+        }
         tmem_wait_st();
         tc_fence_before();
         block_sync();
@@ -752,7 +769,7 @@ struct BwdSmem {
     alignas(16) unsigned char w[NTAP * WTAP];
     int srci[MAXT];                 // source of each interior cell: index ...
     unsigned char srck[MAXT];       // ... and kind (particle, tree, coarse particle)
-    unsigned short dorder[MAXT];    // destinations grouped by row-group class, in slot order
+    unsigned short dorder[MAXT];    // candidate cells, then the destinations grouped by row-group class in slot order
     unsigned tmask[NPROW][NWY];     // cells holding a target, per patch row (bits along y)
     unsigned hot[NPROW][NWY];       // cells within distance 1 of a target
     int seg_lo[NSEG_B];
@@ -906,22 +923,51 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     block_sync();
     // destinations: every particle / tree node of the interior, and every coarse particle (anchored
     // at its first fine cell), with q > 0 pre-images within distance 1 of a target (the others add
-    // exact zeros). Each takes a slot in its row-group class.
+    // exact zeros). Each takes a slot in its row-group class. First the candidates (interior cells
+    // holding a particle, a tree node or a coarse particle's first cell) are listed in cell order
+    // (warp w: cells [w CPT 32, (w + 1) CPT 32)), in dorder's space; an uncovered cell next to a
+    // target means an invalid layout.
     constexpr int CPT = MAXT / NT;  // interior cells per thread
     if (tid < NCLS) S.ccnt[tid] = 0;
+    unsigned bal[CPT];
+    int wcnt = 0;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const int ic = (warp * CPT + u) * 32 + lane;
+        const int r = ic / SY, iy = ic % SY;
+        const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
+        bool cand = false;
+        if (z < s.g.dz && x < s.g.dx && y < s.g.dy) {
+            const int k = S.srck[ic];
+            if (k == SRC_NONE) {
+                if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
+            } else {
+                cand = k != SRC_C || !((z | x | y) & 1);
+            }
+        }
+        bal[u] = __ballot_sync(0xffffffffu, cand);
+        wcnt += __popc(bal[u]);
+    }
+    if (lane == 0) S.warp_tot[warp] = wcnt;
     block_sync();
-    // class of interior cell ic as a destination (-1: none)
+    int ncand = 0, cbase = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+        cbase += w < warp ? S.warp_tot[w] : 0;
+        ncand += S.warp_tot[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        if ((bal[u] >> lane) & 1u) S.dorder[cbase + __popc(bal[u] & below)] = (unsigned short)((warp * CPT + u) * 32 + lane);
+        cbase += __popc(bal[u]);
+    }
+    block_sync();
+    // class of candidate cell ic as a destination (-1: no pre-image within reach of a target)
     auto dest_class = [&](int ic) -> int {
         const int r = ic / SY, iy = ic % SY;
         const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
-        if (z >= s.g.dz || x >= s.g.dx || y >= s.g.dy) return -1;
-        const int k = S.srck[ic];
-        if (k == SRC_NONE) {
-            if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
-            return -1;
-        }
-        const bool coarse = k == SRC_C;
-        if (coarse && ((z | x | y) & 1)) return -1;
+        const bool coarse = S.srck[ic] == SRC_C;
         uint32_t wz, wx, wy;
         const int nz = axis_pre(z, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
         const int nx = axis_pre(x, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
@@ -932,12 +978,18 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                 for (int c = 0; c < ny; ++c) q += hot_at(S, pre_at(wz, a), pre_at(wx, b), pre_at(wy, c));
         return q == 0 ? -1 : group_class(q);
     };
-    int my_c[CPT], my_slot[CPT];
+    int my_ic[CPT], my_c[CPT], my_slot[CPT];
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
-        my_c[u] = dest_class(tid + u * NT);
+        const int jc = tid + u * NT;
+        my_ic[u] = 0;
+        my_c[u] = -1;
         my_slot[u] = 0;
-        if (my_c[u] >= 0) my_slot[u] = atomicAdd(&S.ccnt[my_c[u]], 1);
+        if (jc < ncand) {
+            my_ic[u] = S.dorder[jc];
+            my_c[u] = dest_class(my_ic[u]);
+            if (my_c[u] >= 0) my_slot[u] = atomicAdd(&S.ccnt[my_c[u]], 1);
+        }
     }
     block_sync();
     if (tid == 0) {
@@ -954,7 +1006,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     block_sync();
 #pragma unroll
     for (int u = 0; u < CPT; ++u)
-        if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)(tid + u * NT);
+        if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)my_ic[u];
     const int nrows = S.rbase[NCLS], rows2 = S.rbase[1];  // rows2: the two-pass rows come first
     if (nrows == 0) return;
     store_weights(wreg, S.w);
@@ -967,7 +1019,6 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     const uint32_t tb = S.tmem;
     const int q = warp & 3;
     const uint32_t lane_base = uint32_t(32 * q) << 16;
-    const int e0 = warp < 4 ? 0 : 14, e1 = warp < 4 ? 14 : NTAP;
     constexpr uint32_t idesc = idesc_bf16(128, 16, false);
     uint32_t phase = 0;
     for (int b0 = 0; b0 < nrows; b0 += 128) {
@@ -1008,26 +1059,20 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                             break;
                         }
                     }
-            // rows past the last one are never read back: a warp holding only such rows skips them
-            if (b0 + 32 * q < nrows)
-                for (int e = e0; e < e1; ++e) {
-                    const int cz = pz - (e / 9 - 1), cx = px - ((e / 3) % 3 - 1), cy = py - (e % 3 - 1);
-                    uint4 a = make_uint4(0, 0, 0, 0), b = a;
-                    if (cz >= 0 && cz < PZ && cx >= 0 && cx < PX && cy >= 0 && cy < PY) {
-                        const int c = (cz * PX + cx) * PY + cy;
-                        a = S.g0[c];
-                        b = S.g1[c];
-                    }
-                    tmem_st8(tb + lane_base + TM_A + 8 * e, a, b);
-                }
+            // rows past the last one are never read back: a warp holding only such rows skips them;
+            // the adjoint reads G at q - e (the flipped stencil)
+            if (b0 + 32 * q < nrows) {
+                if (warp < 4) store_taps<0, 14, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
+                else store_taps<14, NTAP, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
+            }
             tmem_wait_st();
             tc_fence_before();
             block_sync();
             tc_fence_after();
             if (tid == 0) {
                 for (int e = 0; e < NTAP; ++e)
-                    mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc,
-                           (pass > 0 || e > 0) ? 1u : 0u);
+                    mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256),
+                           idesc, (pass > 0 || e > 0) ? 1u : 0u);
                 mma_commit(&S.bar);
             }
             if (block_wait_mma(&S.bar, phase, L.err)) {
