@@ -234,9 +234,12 @@ def dense_pixel_conv(dims, w, steps, flush, stream):
 
 
 def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
-    """Times the layer step (tree restriction | convolution | convolution adjoint | tree adjoint |
-    stencil gradient) with stencil stack st on the buffers b: device-resident (CUDA events per part,
-    L2 flushed before every step) and end to end from pinned host buffers. Returns the per-part
+    """Times the layer step with stencil stack st on the buffers b: tree restriction, convolution and
+    the backward (apr_convolve_backward: data adjoint and tree adjoint on this stream, the stencil
+    gradient concurrently on the library's second stream), device-resident (CUDA events around the
+    step, L2 flushed before every step) and end to end from pinned host buffers; and, in a separate
+    pass, each of the five parts alone (tree restriction | convolution | convolution adjoint | tree
+    adjoint | stencil gradient, one after the other, CUDA events per part). Returns the per-part
     times, the step and e2e means (max over ranks), the copy sizes and the clock record."""
     import torch
 
@@ -247,11 +250,15 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
                  lambda: G.apr_convolve_adjoint(lay, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp, grad_tree=gtree),
                  lambda: G.apr_tree_restrict_adjoint(lay, gtree, gp),
                  lambda: G.apr_convolve_stencil_grad(lay, vals, tree, K, gout, G.APR_BC_REFLECT, grad_stencils=gw)]
-    for f in parts_fns:
+    step_fns = [parts_fns[0], parts_fns[1],
+                lambda: G.apr_convolve_backward(lay, vals, tree, st, K, gout, G.APR_BC_REFLECT, grad_particles=gp,
+                                                grad_stencils=gw)]
+    for f in parts_fns + step_fns[2:]:
         f()
     run_part = make_replayers(parts_fns, not args.no_graph)
+    run_step = make_replayers(step_fns, not args.no_graph)
 
-    def step(e=None):
+    def parts_pass(e=None):
         if e is not None:
             e[0].record(stream)
         for j, f in enumerate(run_part):
@@ -259,11 +266,25 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
             if e is not None:
                 e[j + 1].record(stream)
 
+    # each part alone, one after the other
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        parts_pass()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        parts_pass(ev[i])
+    torch.cuda.synchronize()
+    parts = [[ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)] for j in range(5)]
+
+    # the step
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     clk = ClockSampler(dev.index).__enter__() if clocks else None
     for _ in range(args.warmup):
         flush.zero_()
-        step()
+        for f in run_step:
+            f()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -271,7 +292,10 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()
-        step(ev[i])
+        evs[i][0].record(stream)
+        for f in run_step:
+            f()
+        evs[i][1].record(stream)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     clock_rec = None
@@ -282,14 +306,15 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
     if world > 1:
         torch.distributed.barrier()
     lay.sync_status()
-    parts = [[ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)] for j in range(5)]
-    step_ms = max_over_ranks(sum(sum(p) for p in parts) / args.steps, dev)
+    step_ms = max_over_ranks(sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps, dev)
 
     # end to end through the public API with host buffers: H2D of the step's inputs (values,
     # upstream gradient), the step, D2H of its results (outputs, both gradients). Copies that the
     # kernels do not wait for run on a second stream: dL/dout goes in while the tree restriction
     # and the convolution run, the outputs come back while the backward runs, and the particle
-    # gradient while the stencil gradient runs
+    # gradient while the stencil gradient runs (so here the backward's three parts are called one
+    # after the other: overlapping that copy saves more than running the stencil gradient beside
+    # the adjoints)
     h_vals = vals.cpu().pin_memory()
     h_gout = gout.cpu().pin_memory()
     h_out = torch.empty(out.numel()).pin_memory()
@@ -430,6 +455,8 @@ def run_ours(args, rank, world):
                    "n_particles": Np, "n_tree": lay.n_tree, "levels": [apr.l_min, apr.l_max],
                    "computational_ratio": round(float(np.prod(apr.dims)) / Np, 2),
                    "step": "tree restrict + convolve + convolve_backward (data + stencil grads)",
+                   "backward": "apr_convolve_backward: data adjoint and tree adjoint on the step's stream, stencil "
+                               "gradient concurrently on the library's second stream (fork / join events)",
                    "l2": "flushed before every step (512 MB write, outside the step events)",
                    "launch": "CUDA graphs (one per part)" if not args.no_graph else "eager",
                    "parallelism": f"replicas x{world}"},
@@ -444,7 +471,9 @@ def run_ours(args, rank, world):
                                "hbm_frac_conv_bytes": round(algorithmic_bytes(apr, lay, 3)[0] / (gm_ms * 1e-3) / 1e9 / hbm, 4)},
         "step_ms_parts": {"tree_restrict": round(mean(t_restrict), 5), "convolve": round(conv_ms, 5),
                           "convolve_adjoint": round(adj_ms, 5), "tree_restrict_adjoint": round(mean(t_tadj), 5),
-                          "stencil_grad": round(mean(t_sgrad), 5)},
+                          "stencil_grad": round(mean(t_sgrad), 5),
+                          "timing": "each part alone, one after the other (a separate pass; the step overlaps "
+                                    "the stencil gradient with the data and tree adjoints)"},
         "roofline": {"kernel": dom_name, "bound": "hbm",
                      "achieved": round(conv_bytes / (dom_ms * 1e-3) / 1e9, 2), "peak": hbm,
                      "unit": "GB/s", "frac": round(conv_bytes / (dom_ms * 1e-3) / 1e9 / hbm, 4),
@@ -456,7 +485,8 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": T["h2d"], "d2h_bytes_per_step": T["d2h"],
                 "ms_per_step": round(e2e, 4),
                 "copies": "pinned host buffers; dL/dout in and outputs out on a second stream, overlapped with "
-                          "the step's kernels"},
+                          "the step's kernels (the backward's parts called one after the other, so the particle "
+                          "gradient goes out while the stencil gradient runs)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": round(wall, 4),

@@ -252,6 +252,9 @@ apr_status_t apr_destroy(apr_handle_t h) {
     if (!h->host_only) {
         cudaDeviceSynchronize();
         free_device(h);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
+        if (h->side) cudaStreamDestroy(h->side);
     }
     delete h;
     return APR_OK;
@@ -451,10 +454,13 @@ apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, c
     return cuda_status(e);
 }
 
-apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
-                                   int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
-                                   float *grad_stencils, void *workspace, size_t workspace_bytes,
-                                   apr_stream_t stream) {
+}  // extern "C"
+
+namespace aprk {
+apr_status_t convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                               int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
+                               float *grad_stencils, void *workspace, size_t workspace_bytes, apr_stream_t stream,
+                               bool concurrent) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;
     if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
@@ -467,6 +473,30 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
     float *gt = static_cast<float *>(workspace);
     void *partial = static_cast<char *>(workspace) + gt_bytes;
     apr_status_t st = APR_OK;
+    if (concurrent && grad_particles && grad_stencils) {
+        // the stencil gradient reads only the values, the tree and dL/dout: it runs on the handle's
+        // second stream while the data adjoint and the tree adjoint run on the caller's (their
+        // workspace regions are disjoint); the caller's stream then waits for it
+        std::lock_guard<std::mutex> lock(h->side_mu);
+        cudaError_t e = cudaSuccess;
+        if (!h->side) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !h->ev_fork) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_join) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        const apr_status_t sg = apr_convolve_stencil_grad(h, particles, tree, k, bc, grad_out, grad_stencils, partial,
+                                                          workspace_bytes - gt_bytes, reinterpret_cast<apr_stream_t>(h->side));
+        st = apr_convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream);
+        if (st == APR_OK) st = apr_tree_restrict_adjoint(h, gt, grad_particles, stream);
+        // always joined, so that a stream capture of the caller's stream ends joined
+        e = cudaEventRecord(h->ev_join, h->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
+        if (st == APR_OK) st = sg;
+        if (st == APR_OK && e != cudaSuccess) st = cuda_status(e);
+        return st;
+    }
     if (grad_particles) {
         st = apr_convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream);
         if (st == APR_OK) st = apr_tree_restrict_adjoint(h, gt, grad_particles, stream);
@@ -475,6 +505,17 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
         st = apr_convolve_stencil_grad(h, particles, tree, k, bc, grad_out, grad_stencils, partial,
                                        workspace_bytes - gt_bytes, stream);
     return st;
+}
+}  // namespace aprk
+
+extern "C" {
+
+apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                                   int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
+                                   float *grad_stencils, void *workspace, size_t workspace_bytes,
+                                   apr_stream_t stream) {
+    return aprk::convolve_backward(h, particles, tree, stencils, k, bc, grad_out, grad_particles, grad_stencils,
+                                   workspace, workspace_bytes, stream, true);
 }
 
 size_t apr_rl_workspace_bytes(apr_handle_t h) {

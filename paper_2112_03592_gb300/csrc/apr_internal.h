@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -124,6 +125,11 @@ apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
 bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
 bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P);
+// apr_convolve_backward; concurrent: the stencil gradient on the handle's second stream
+apr_status_t convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
+                               int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
+                               float *grad_stencils, void *workspace, size_t workspace_bytes, apr_stream_t stream,
+                               bool concurrent);
 // DevLayout over the host copy of X's index (for host code that walks it like a kernel).
 DevLayout host_layout_view(const HostIndex &X);
 
@@ -173,4 +179,9 @@ struct apr_handle_s {
     aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
     uint2 *d_fplan_ent[4] = {};
     size_t dev_bytes = 0;
+    // apr_convolve_backward runs the stencil gradient on a second stream, forked from and joined back
+    // to the caller's stream with these events (created on first use; side_mu orders the enqueues)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::mutex side_mu;
 };

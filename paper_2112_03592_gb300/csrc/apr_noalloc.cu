@@ -57,8 +57,9 @@ apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particle
     void *scratch = nullptr;
     const apr_status_t st = scratch_for_current_device(&scratch);
     if (st != APR_OK) return st;
-    return apr_convolve_backward(h, particles, tree, stencils, k, bc, grad_out, grad_particles, grad_stencils,
-                                 scratch, kNoAllocScratchBytes, stream);
+    // the three parts in order on the caller's stream (the concurrent form would create a stream)
+    return aprk::convolve_backward(h, particles, tree, stencils, k, bc, grad_out, grad_particles, grad_stencils,
+                                   scratch, kNoAllocScratchBytes, stream, false);
 }
 
 }  // extern "C"
