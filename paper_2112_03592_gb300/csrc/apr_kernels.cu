@@ -45,21 +45,31 @@ __device__ __forceinline__ bool outer_taps_zero5(const float *__restrict__ stenc
     return __syncthreads_or(nz) == 0;
 }
 
-// Positions v in [-R, d + R) outside [0, d) that reflect onto c (at most 2R). Returns the count.
+// c itself (self) and, with reflection, the positions v in [-R, d + R) outside [0, d) that reflect
+// onto it, each as (position - base) in 8 bits of one register word (base <= every position < base + 256);
+// returns the count (at most 2R + 1). Registers only, no local array.
 template <int R>
-__device__ __forceinline__ int mirror_preimages(int c, int d, int *out) {
+__device__ __forceinline__ int with_mirrors(int c, int d, int base, bool self, bool reflect, uint64_t &w) {
+    uint64_t v = 0;
     int n = 0;
-    if (d >= 2 * R) {  // at most one mirror per side: -c-1 (c < R) and 2d-1-c (c >= d-R)
-        if (c < R) out[n++] = -c - 1;
-        if (c >= d - R) out[n++] = 2 * d - 1 - c;
-        return n;
+    if (self) v |= uint64_t(c - base) << (8 * n++);
+    if (reflect) {
+        if (d >= 2 * R) {
+            if (c < R) v |= uint64_t(-c - 1 - base) << (8 * n++);
+            if (c >= d - R) v |= uint64_t(2 * d - 1 - c - base) << (8 * n++);
+        } else {
+#pragma unroll
+            for (int t = -R; t < 0; ++t)
+                if (reflect_idx(t, d) == c) v |= uint64_t(t - base) << (8 * n++);
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (reflect_idx(d + t, d) == c) v |= uint64_t(d + t - base) << (8 * n++);
+        }
     }
-    for (int v = -R; v < 0; ++v)
-        if (reflect_idx(v, d) == c) out[n++] = v;
-    for (int v = d; v < d + R; ++v)
-        if (reflect_idx(v, d) == c) out[n++] = v;
+    w = v;
     return n;
 }
+__device__ __forceinline__ int at8(uint64_t w, int i) { return int((w >> (8 * i)) & 255u); }
 
 // Per-particle epilogue of the convolution: the plain output, or the element-wise division and
 // multiplication of a Richardson-Lucy update (Sec. 6.2) fused into the write. aux may alias the
@@ -222,8 +232,21 @@ __device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0,
 // in y the reflected cells (or zeros); cells no source covers (possible only in layouts not checked
 // for 2:1 balance) hold 0. Also records the target rows (rmask, rfirst) and lists the windows that
 // hold targets (act, nact). Ends with a block barrier.
+// A tile's plan header and this thread's first entry (entry threadIdx.x, when the plan has it),
+// loaded at kernel start so that they overlap the work item and stencil loads instead of following
+// them. count: the entries listed (the entry after them holds the packet total).
+struct PlanPre {
+    PlanHdr hd;
+    uint2 e0;
+};
+__device__ __forceinline__ PlanHdr plan_hdr(const FPlanView &P, int tile) { return P.hdr[tile]; }
+__device__ __forceinline__ PlanPre plan_pre(const FPlanView &P, const PlanHdr &hd, int count) {
+    return PlanPre{hd, int(threadIdx.x) <= count ? P.ent[hd.first + threadIdx.x] : make_uint2(0u, 0u)};
+}
+__device__ __forceinline__ int bplan_count(const PlanHdr &hd) { return (hd.count & 0xffff) + (hd.count >> 16); }
+
 template <int R, int NS>
-__device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
+__device__ void stage_fwd(const DevLayout &L, const Item &it, const PlanPre &pp, const float *__restrict__ vals,
                           const float *__restrict__ tree, int bc, FwdSmem<R, NS> &S) {
     using G = Geo<R>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -244,10 +267,10 @@ __device__ void stage_fwd(const DevLayout &L, const Item &it, int tile, const fl
     // the tile plan); with zero boundary the segments of rows outside the grid are skipped (their
     // cells stay 0)
     const FPlanView FP = L.fplan[R - 1];
-    const PlanHdr hd = FP.hdr[tile];
+    const PlanHdr hd = pp.hd;
     const int nseg = hd.count;
     for (int k = tid; k <= nseg; k += NT) {
-        const uint2 raw = FP.ent[hd.first + k];
+        const uint2 raw = k == tid ? pp.e0 : FP.ent[hd.first + k];
         const FPlanEnt e{raw.x, raw.y};
         if (k < nseg) {
             const int meta = fplan_meta(e);
@@ -466,12 +489,12 @@ __device__ __forceinline__ void fwd_windows(const float *patch, const float *w2,
 // ------------------------------------------------------------------------------------------------
 // One forward tile with stencil radius R from a stack of radius RS >= R.
 template <int R, int RS>
-__device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, int tile, const float *__restrict__ vals,
+__device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it, const PlanPre &pp, const float *__restrict__ vals,
                                               const float *__restrict__ tree, const float *__restrict__ stencils,
                                               int bc, float *out, const Epilogue &epi, unsigned char *smem_raw) {
     FwdSmem<R, 1> &S = *reinterpret_cast<FwdSmem<R, 1> *>(smem_raw);
     load_taps2<R, RS>(stencils, it.l - L.l_min, epi.flip, S.w2[0]);
-    stage_fwd<R, 1>(L, it, tile, vals, tree, bc, S);
+    stage_fwd<R, 1>(L, it, pp, vals, tree, bc, S);
     fwd_windows<R>(S.patch, S.w2[0], S.roff, S.act, S.nact, [&](int w, int j0, const float *v, int n) {
         const unsigned m = win_mask(S, w);
         int p = win_first(S, w) + __popc(m & ((1u << j0) - 1u));
@@ -493,13 +516,20 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
     const Item it = items[tile];
+    // the plan of each radius the tile may take, loaded with the item (the radius follows from the
+    // level's stencil)
+    const PlanHdr h1 = plan_hdr(L.fplan[0], tile);
     if constexpr (R == 2) {
+        const PlanHdr h2 = plan_hdr(L.fplan[1], tile);
+        const PlanPre p1 = plan_pre(L.fplan[0], h1, h1.count), p2 = plan_pre(L.fplan[1], h2, h2.count);
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_fwd_tile<1, 2>(L, it, tile, vals, tree, stencils, bc, out, epi, smem_raw);
+            conv_fwd_tile<1, 2>(L, it, p1, vals, tree, stencils, bc, out, epi, smem_raw);
             return;
         }
+        conv_fwd_tile<2, 2>(L, it, p2, vals, tree, stencils, bc, out, epi, smem_raw);
+    } else {
+        conv_fwd_tile<R, R>(L, it, plan_pre(L.fplan[0], h1, h1.count), vals, tree, stencils, bc, out, epi, smem_raw);
     }
-    conv_fwd_tile<R, R>(L, it, tile, vals, tree, stencils, bc, out, epi, smem_raw);
 }
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
@@ -515,10 +545,12 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdSmem<R, 3> &S = *reinterpret_cast<FwdSmem<R, 3> *>(smem_raw);
     const Item it = items[blockIdx.x];
+    const PlanHdr hd = plan_hdr(L.fplan[R - 1], blockIdx.x);
+    const PlanPre pp = plan_pre(L.fplan[R - 1], hd, hd.count);
     const int n_levels = L.l_max - L.l_min + 1;
 #pragma unroll 1
     for (int a = 0; a < 3; ++a) load_taps2<R>(stencils + size_t(a) * n_levels * G::K3, it.l - L.l_min, false, S.w2[a]);
-    stage_fwd<R, 3>(L, it, blockIdx.x, vals, tree, bc, S);
+    stage_fwd<R, 3>(L, it, pp, vals, tree, bc, S);
     constexpr int LPW = lanes_per_window<R>(), NO = WIN / LPW;  // outputs kept per lane
     const int sub = threadIdx.x % LPW;
     for (int base = 0; base < S.nact; base += NT / LPW) {
@@ -581,7 +613,8 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     const Item it = items[blockIdx.x];
-    stage_fwd<R, 1>(L, it, blockIdx.x, vals, tree, bc, S);
+    const PlanHdr hd = plan_hdr(L.fplan[R - 1], blockIdx.x);
+    stage_fwd<R, 1>(L, it, plan_pre(L.fplan[R - 1], hd, hd.count), vals, tree, bc, S);
     const int tid = threadIdx.x;
     const int pair = tid % G::NPAIR, grp = tid / G::NPAIR;
     // acc2[t] = (sum over even j, sum over odd j) of g_j * P[row][col + j + t]: taps t even pair
@@ -788,7 +821,7 @@ __device__ __forceinline__ void window_checked2(const float *patch, const float 
 
 // One data-adjoint tile with stencil radius R from a stack of radius RS >= R.
 template <int R, int RS>
-__device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Item &it, int tile,
+__device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Item &it, const PlanPre &pp,
                                                    const float *__restrict__ stencils, int bc,
                                                    const float *__restrict__ gout, float *__restrict__ gp,
                                                    float *__restrict__ gt, unsigned char *smem_raw) {
@@ -812,10 +845,10 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
     // grid), then n2 sources of the interior cells (particles and tree nodes of the interior rows in
     // y-block yb, level-(l-1) particles over the interior)
     const FPlanView P = L.bplan[R - 1];
-    const PlanHdr hd = P.hdr[tile];
+    const PlanHdr hd = pp.hd;
     const int n1 = hd.count & 0xffff, n2 = hd.count >> 16;
     for (int k = tid; k <= n1 + n2; k += NT) {
-        const uint2 raw = P.ent[hd.first + k];
+        const uint2 raw = k == tid ? pp.e0 : P.ent[hd.first + k];
         const FPlanEnt e{raw.x, raw.y};
         if (k < n1 + n2) {
             S.seg_lo[k] = fplan_lo(e);
@@ -888,14 +921,9 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
         unsigned long long m = 0ull;
         bool edge_zx = false;
         if (valid) {
-            int pz[2 * R + 1], px[2 * R + 1];
-            int nz = 1, nx = 1;
-            pz[0] = z;
-            px[0] = x;
-            if (reflect) {
-                nz += mirror_preimages<R>(z, g.dz, pz + 1);
-                nx += mirror_preimages<R>(x, g.dx, px + 1);
-            }
+            uint64_t wz, wx;  // rows and their mirrors, relative to the patch's first row (z0 - R)
+            const int nz = with_mirrors<R>(z, g.dz, z0 - R, true, reflect, wz);
+            const int nx = with_mirrors<R>(x, g.dx, x0 - R, true, reflect, wx);
             edge_zx = nz > 1 || nx > 1;
             if (!edge_zx) {
                 // no mirrored rows: the patch rows (ia + dz, ib + dx), dz, dx in [0, 2R]
@@ -904,7 +932,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
                 for (int iz = 0; iz < nz; ++iz)
                     for (int ix = 0; ix < nx; ++ix)
                         for (int pr = q; pr < G::NPAIR; pr += 4) {
-                            const int rz = pz[iz] - z0 + pr / G::K, rx = px[ix] - x0 + pr % G::K;  // patch row
+                            const int rz = at8(wz, iz) - R + pr / G::K, rx = at8(wx, ix) - R + pr % G::K;  // patch row
                             if (rz < 0 || rz >= G::PZ || rx < 0 || rx >= G::PX) continue;
                             m |= S.dil[rz * G::PX + rx];
                         }
@@ -973,16 +1001,15 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
             if (!(S.wmir[w] & 1)) continue;
             const int r = w / NWIN, col = (w % NWIN) * WIN;
             const int z = z0 + r / TX, x = x0 + r % TX;
-            int pz[2 * R + 1], px[2 * R + 1];
-            pz[0] = z;
-            px[0] = x;
-            const int nz = 1 + mirror_preimages<R>(z, g.dz, pz + 1), nx = 1 + mirror_preimages<R>(x, g.dx, px + 1);
+            uint64_t wz, wx;
+            const int nz = with_mirrors<R>(z, g.dz, z0 - R, true, true, wz);
+            const int nx = with_mirrors<R>(x, g.dx, x0 - R, true, true, wx);
             float acc[WIN];
 #pragma unroll
             for (int j = 0; j < WIN; ++j) acc[j] = 0.f;
             for (int iz = 0; iz < nz; ++iz)
                 for (int ix = 0; ix < nx; ++ix)
-                    if (iz != 0 || ix != 0) window_checked2<R>(S.gpatch, S.w2, pz[iz] - z0, px[ix] - x0, col, acc);
+                    if (iz != 0 || ix != 0) window_checked2<R>(S.gpatch, S.w2, at8(wz, iz) - R, at8(wx, ix) - R, col, acc);
             float *dst = S.H + r * BY + col;
 #pragma unroll
             for (int j = 0; j < WIN; ++j) dst[j] += acc[j];
@@ -999,17 +1026,16 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
             const int z = z0 + r / TX, x = x0 + r % TX, yy = y0 + j;
             if (z >= g.dz || x >= g.dx) continue;
             if (!((S.need[r] >> j) & 1ull)) continue;
-            int pz[2 * R + 1], px[2 * R + 1], py[2 * R];
-            pz[0] = z;
-            px[0] = x;
-            const int nz = 1 + mirror_preimages<R>(z, g.dz, pz + 1), nx = 1 + mirror_preimages<R>(x, g.dx, px + 1);
-            const int ny = mirror_preimages<R>(yy, g.dy, py);
+            uint64_t wz, wx, wy;
+            const int nz = with_mirrors<R>(z, g.dz, z0 - R, true, true, wz);
+            const int nx = with_mirrors<R>(x, g.dx, x0 - R, true, true, wx);
+            const int ny = with_mirrors<R>(yy, g.dy, yw, false, true, wy);
             float h0 = 0.f, h1 = 0.f;
             for (int iz = 0; iz < nz; ++iz)
                 for (int ix = 0; ix < nx; ++ix)
                     for (int iy = 0; iy < ny; ++iy) {
                         // taps e with c' - e inside the staged window (the rest reads zero gradient)
-                        const int cz = pz[iz] - (z0 - R), cx = px[ix] - (x0 - R), cy = py[iy] - yw;
+                        const int cz = at8(wz, iz), cx = at8(wx, ix), cy = at8(wy, iy);
                         const int ey0 = max(-R, cy - G::PY + 1), ey1 = min(R, cy);
 #pragma unroll 1
                         for (int ez = -R; ez <= R; ++ez)
@@ -1104,13 +1130,19 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
     const Item it = items[tile];
+    // the plan of each radius the tile may take, loaded with the item
+    const PlanHdr h1 = plan_hdr(L.bplan[0], tile);
     if constexpr (R == 2) {
+        const PlanHdr h2 = plan_hdr(L.bplan[1], tile);
+        const PlanPre p1 = plan_pre(L.bplan[0], h1, bplan_count(h1)), p2 = plan_pre(L.bplan[1], h2, bplan_count(h2));
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_bwd_data_tile<1, 2>(L, it, tile, stencils, bc, gout, gp, gt, smem_raw);
+            conv_bwd_data_tile<1, 2>(L, it, p1, stencils, bc, gout, gp, gt, smem_raw);
             return;
         }
+        conv_bwd_data_tile<2, 2>(L, it, p2, stencils, bc, gout, gp, gt, smem_raw);
+    } else {
+        conv_bwd_data_tile<R, R>(L, it, plan_pre(L.bplan[0], h1, bplan_count(h1)), stencils, bc, gout, gp, gt, smem_raw);
     }
-    conv_bwd_data_tile<R, R>(L, it, tile, stencils, bc, gout, gp, gt, smem_raw);
 }
 
 // ------------------------------------------------------------------------------------------------
