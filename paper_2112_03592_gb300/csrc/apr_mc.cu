@@ -37,6 +37,7 @@ constexpr int MAXT = NIROW * SY;            // interior cells
 constexpr int NSUB_ZX = (TZ / SZ) * (TX / SX);
 constexpr int NSUB = NSUB_ZX * (BY / SY);   // sub-tiles per work item: (z, x) quarters, then y halves
 constexpr int NWY = (PY + 31) / 32;         // 32-bit words of a patch row's cell mask
+constexpr int SPC_F = 4, SPC_B = 2;         // sub-tiles per CTA: forward, data adjoint (measured best)
 constexpr int NTAP = 27;
 constexpr int WTAP = 512;                   // bytes of one tap's 16 x 16 bf16 weight block
 constexpr uint32_t TMEM_COLS = 256;
@@ -49,6 +50,7 @@ constexpr int WG_MG = 64;                   // M groups of 8 rows allocated (54 
 constexpr int WG_ROWS = NTAP * MC;          // 432 rows (e, ci) of the weight gradient
 static_assert(TZ % SZ == 0 && TX % SX == 0 && BY % SY == 0, "sub-tiles must divide the work-item tile");
 static_assert(MAXT % NT == 0, "whole interior cells per thread");
+static_assert(NSUB % SPC_F == 0 && NSUB % SPC_B == 0, "whole sub-tile groups per work item");
 static_assert(SZ % 2 == 0 && SX % 2 == 0, "sub-tiles must be even-aligned (coarse cells)");
 static_assert(TM_A + 8 * NTAP <= TM_D && TM_D + 16 <= TMEM_COLS, "tensor-memory columns");
 static_assert(NPC < 65536 && MAXT <= 1024, "16-bit cell ids");
@@ -670,6 +672,8 @@ struct FwdSmem {
 
 // out (float32 [N][16]) receives the convolution; if out_bf16 is given instead, it receives
 // bf16(max(conv, 0)), the next layer's input in an APR CNN (the ReLU fused into the write).
+// A CTA takes SPC_F consecutive sub-tiles of one work item (one level): the weights, the mbarrier and
+// the tensor memory are set up once, at its first sub-tile with targets.
 __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
                                                        const uint4 *__restrict__ vals, const uint4 *__restrict__ tree,
                                                        const uint16_t *__restrict__ W, int bc, float *__restrict__ out,
@@ -677,78 +681,91 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
     extern __shared__ __align__(16) unsigned char smraw[];
     FwdSmem &S = *reinterpret_cast<FwdSmem *>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    Sub s;
-    if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
-    // the level's weights, the feature segments' and the targets' row offsets are loaded in the same
-    // round (the weights are held in registers until the patch is staged)
+    const Item it = items[blockIdx.x];
+    // the level's weights are held in registers until the first patch is staged
     uint4 wreg[4];
-    preload_weights(W, s.l - L.l_min, wreg);
-    target_rows(L, s, S.tg);   // warp 0, while the other warps read the plan
-    const int nseg = load_mc_plan(L.mcfplan, blockIdx.x * NSUB + blockIdx.y, 32,
-                                  bc != APR_BC_REFLECT && !sub_inner(s), S.st.seg_lo, S.st.smeta, S.st.pre,
-                                  S.st.warp_tot);
-    const int nt = S.tg.row_base[NIROW];
-    if (nt == 0) return;
-    target_fill(L, s, S.tg);
-    feature_elements(L, s, vals, tree, bc, nseg, S.st);
-    store_weights(wreg, S.w);
-    if (tid == 0) mbar_init(&S.bar);
-    if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
-    fence_async_smem();
-    tc_fence_before();
-    block_sync();
-    tc_fence_after();
-    const uint32_t tb = S.tmem;
+    preload_weights(W, it.l - L.l_min, wreg);
     const int q = warp & 3;
     const uint32_t lane_base = uint32_t(32 * q) << 16;
     constexpr uint32_t idesc = idesc_bf16(128, 16, false);
-    uint32_t phase = 0;
-    for (int b0 = 0; b0 < nt; b0 += 128) {
-        const int t = b0 + 32 * q + lane;
-        const int cell = t < nt ? int(S.tg.cell[t]) : 0;
-        const int cz = cell / (PX * PY), cx = (cell / PY) % PX, cy = cell % PY;
-        // rows past the last target are never read back: a warp holding only such rows skips them
-        if (b0 + 32 * q < nt) {
-            if (warp < 4) store_taps<0, 14, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
-            else store_taps<14, NTAP, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
+    uint32_t phase = 0, tb = 0;
+    bool ready = false, failed = false;  // block-uniform
+    for (int k = 0; k < SPC_F && !failed; ++k) {
+        const int sub = blockIdx.y * SPC_F + k;
+        Sub s;
+        if (!sub_of(L, it, sub, s)) continue;
+        if (k > 0) block_sync();  // the previous sub-tile's readers of S.tg and S.st are done
+        target_rows(L, s, S.tg);  // warp 0, while the other warps read the plan
+        const int nseg = load_mc_plan(L.mcfplan, blockIdx.x * NSUB + sub, 32,
+                                      bc != APR_BC_REFLECT && !sub_inner(s), S.st.seg_lo, S.st.smeta, S.st.pre,
+                                      S.st.warp_tot);
+        const int nt = S.tg.row_base[NIROW];
+        if (nt == 0) continue;
+        target_fill(L, s, S.tg);
+        feature_elements(L, s, vals, tree, bc, nseg, S.st);
+        if (!ready) {
+            store_weights(wreg, S.w);
+            if (tid == 0) mbar_init(&S.bar);
+            if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
+            ready = true;
         }
-        tmem_wait_st();
+        fence_async_smem();
         tc_fence_before();
         block_sync();
         tc_fence_after();
-        if (tid == 0) {
-            for (int e = 0; e < NTAP; ++e)
-                mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc, e > 0);
-            mma_commit(&S.bar);
-        }
-        if (block_wait_mma(&S.bar, phase, L.err)) break;
-        phase ^= 1;
-        tc_fence_after();
-        if (warp < 4) {
-            float v[16];
-            tmem_ld16(tb + lane_base + TM_D, v);
-            if (t < nt) {
-                if (out_bf16) {
-                    uint4 r[2];
-                    __nv_bfloat162 *b2 = reinterpret_cast<__nv_bfloat162 *>(r);
+        tb = S.tmem;
+        for (int b0 = 0; b0 < nt; b0 += 128) {
+            const int t = b0 + 32 * q + lane;
+            const int cell = t < nt ? int(S.tg.cell[t]) : 0;
+            const int cz = cell / (PX * PY), cx = (cell / PY) % PX, cy = cell % PY;
+            // rows past the last target are never read back: a warp holding only such rows skips them
+            if (b0 + 32 * q < nt) {
+                if (warp < 4) store_taps<0, 14, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
+                else store_taps<14, NTAP, 1>(S.st.p0, S.st.p1, cz, cx, cy, t < nt, tb + lane_base);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            block_sync();
+            tc_fence_after();
+            if (tid == 0) {
+                for (int e = 0; e < NTAP; ++e)
+                    mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256), idesc, e > 0);
+                mma_commit(&S.bar);
+            }
+            if (block_wait_mma(&S.bar, phase, L.err)) {
+                failed = true;
+                break;
+            }
+            phase ^= 1;
+            tc_fence_after();
+            if (warp < 4) {
+                float v[16];
+                tmem_ld16(tb + lane_base + TM_D, v);
+                if (t < nt) {
+                    if (out_bf16) {
+                        uint4 r[2];
+                        __nv_bfloat162 *b2 = reinterpret_cast<__nv_bfloat162 *>(r);
 #pragma unroll
-                    for (int k = 0; k < MC / 2; ++k) b2[k] = __floats2bfloat162_rn(fmaxf(v[2 * k], 0.f), fmaxf(v[2 * k + 1], 0.f));
-                    out_bf16[2 * size_t(S.tg.idx[t])] = r[0];
-                    out_bf16[2 * size_t(S.tg.idx[t]) + 1] = r[1];
-                } else {
-                    float4 *o = reinterpret_cast<float4 *>(out + size_t(S.tg.idx[t]) * MC);
+                        for (int c = 0; c < MC / 2; ++c) b2[c] = __floats2bfloat162_rn(fmaxf(v[2 * c], 0.f), fmaxf(v[2 * c + 1], 0.f));
+                        out_bf16[2 * size_t(S.tg.idx[t])] = r[0];
+                        out_bf16[2 * size_t(S.tg.idx[t]) + 1] = r[1];
+                    } else {
+                        float4 *o = reinterpret_cast<float4 *>(out + size_t(S.tg.idx[t]) * MC);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                        for (int c = 0; c < 4; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    }
                 }
             }
+            tc_fence_before();
+            block_sync();
+            tc_fence_after();
         }
+    }
+    if (ready) {
         tc_fence_before();
         block_sync();
-        tc_fence_after();
+        if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
     }
-    tc_fence_before();
-    block_sync();
-    if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
 }
 
 // ---------------------------------------------------------------- data adjoint
@@ -840,281 +857,297 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
     extern __shared__ __align__(16) unsigned char smraw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    Sub s;
-    if (!sub_of(L, items[blockIdx.x], blockIdx.y, s)) return;
-    // the level's (transposed) weights are loaded now and held in registers until the destination
-    // list is known, so their latency overlaps the staging
+    const Item it = items[blockIdx.x];
+    // the level's (transposed) weights are loaded now and held in registers until the first
+    // destination list is known, so their latency overlaps the staging
     uint4 wreg[4];
-    preload_weights(W, s.l - L.l_min, wreg);
+    preload_weights(W, it.l - L.l_min, wreg);
     const bool reflect = bc == APR_BC_REFLECT;
-    const int ylo = s.y0 - 1;
-    const int ya = max(ylo, 0), yb = min(s.y0 + SY + 1, s.g.dy);  // gradient rows: y range of the patch
-    const int yia = s.y0, yib = min(s.y0 + SY, s.g.dy);            // interior y range
-    const uint4 z4 = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < NPC; i += NT) {
-        S.g0[i] = z4;
-        S.g1[i] = z4;
-    }
-    for (int i = tid; i < MAXT; i += NT) S.srck[i] = SRC_NONE;
-    for (int i = tid; i < NPROW * NWY; i += NT) (&S.tmask[0][0])[i] = 0;
-    const int nseg = load_mc_plan(L.mcbplan, blockIdx.x * NSUB + blockIdx.y, 0, false, S.seg_lo, S.smeta, S.pre,
-                                  S.warp_tot);
-
-    struct Loader {
-        using Slot = McSlot;
-        const DevLayout *L;
-        const uint4 *gout;
-        const unsigned short *meta;
-        __device__ void operator()(int k, int i, Slot &sl) const {
-            const int sg = meta[k];
-            const bool t = sg >= NPROW + NIROW && sg < NPROW + 2 * NIROW;
-            sl.y = t ? int(L->ty[i]) : int(L->y[i]);
-            if (sg < NPROW) {
-                sl.a = gout[2 * size_t(i)];
-                sl.b = gout[2 * size_t(i) + 1];
-            }
-        }
-    } loader{&L, gout, S.smeta};
-    for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int ent, int i, const McSlot &sl) {
-        const int sg = S.smeta[ent];
-        if (sg < NPROW) {
-            if (sl.y >= ya && sl.y < yb) {
-                const int py = sl.y - ylo;
-                S.g0[sg * PY + py] = sl.a;
-                S.g1[sg * PY + py] = sl.b;
-                atomicOr(&S.tmask[sg][py >> 5], 1u << (py & 31));
-            }
-            return;
-        }
-        const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
-        if (k < 2) {
-            if (sl.y >= yia && sl.y < yib) {
-                S.srck[r * SY + sl.y - s.y0] = (unsigned char)k;
-                S.srci[r * SY + sl.y - s.y0] = i;
-            }
-        } else {
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                const int y = 2 * sl.y + f;
-                if (y >= yia && y < yib) {
-                    S.srck[r * SY + y - s.y0] = SRC_C;
-                    S.srci[r * SY + y - s.y0] = i;
-                }
-            }
-        }
-    });
-    // cells within distance 1 of a target: y dilation of each row, OR over the 3 x 3 neighbour rows
-    if (tid < NPROW) {
-        const int pz = tid / PX, px = tid % PX;
-        unsigned h[NWY] = {};
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qz = pz + dz, qx = px + dx;
-                if (qz < 0 || qz >= PZ || qx < 0 || qx >= PX) continue;
-                const unsigned *m = S.tmask[qz * PX + qx];
-#pragma unroll
-                for (int w = 0; w < NWY; ++w)
-                    h[w] |= m[w] | (m[w] << 1) | (m[w] >> 1) | (w + 1 < NWY ? m[w + 1] << 31 : 0u) |
-                            (w > 0 ? m[w - 1] >> 31 : 0u);
-            }
-#pragma unroll
-        for (int w = 0; w < NWY; ++w) S.hot[tid][w] = h[w];
-    }
-    block_sync();
-    // destinations: every particle / tree node of the interior, and every coarse particle (anchored
-    // at its first fine cell), with q > 0 pre-images within distance 1 of a target (the others add
-    // exact zeros). Each takes a slot in its row-group class. First the candidates (interior cells
-    // holding a particle, a tree node or a coarse particle's first cell) are listed in cell order
-    // (warp w: cells [w CPT 32, (w + 1) CPT 32)), in dorder's space; an uncovered cell next to a
-    // target means an invalid layout.
-    constexpr int CPT = MAXT / NT;  // interior cells per thread
-    if (tid < NCLS) S.ccnt[tid] = 0;
-    unsigned bal[CPT];
-    int wcnt = 0;
-#pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-        const int ic = (warp * CPT + u) * 32 + lane;
-        const int r = ic / SY, iy = ic % SY;
-        const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
-        bool cand = false;
-        if (z < s.g.dz && x < s.g.dx && y < s.g.dy) {
-            const int k = S.srck[ic];
-            if (k == SRC_NONE) {
-                if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
-            } else {
-                cand = k != SRC_C || !((z | x | y) & 1);
-            }
-        }
-        bal[u] = __ballot_sync(0xffffffffu, cand);
-        wcnt += __popc(bal[u]);
-    }
-    if (lane == 0) S.warp_tot[warp] = wcnt;
-    block_sync();
-    int ncand = 0, cbase = 0;
-#pragma unroll
-    for (int w = 0; w < NWARP; ++w) {
-        cbase += w < warp ? S.warp_tot[w] : 0;
-        ncand += S.warp_tot[w];
-    }
-    const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-        if ((bal[u] >> lane) & 1u) S.dorder[cbase + __popc(bal[u] & below)] = (unsigned short)((warp * CPT + u) * 32 + lane);
-        cbase += __popc(bal[u]);
-    }
-    block_sync();
-    // class of candidate cell ic as a destination (-1: no pre-image within reach of a target)
-    auto dest_class = [&](int ic) -> int {
-        const int r = ic / SY, iy = ic % SY;
-        const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
-        const bool coarse = S.srck[ic] == SRC_C;
-        uint32_t wz, wx, wy;
-        const int nz = axis_pre(z, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
-        const int nx = axis_pre(x, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
-        const int ny = axis_pre(y, coarse, s.g.dy, reflect, ylo, &wy);
-        int q = 0;
-        for (int a = 0; a < nz; ++a)
-            for (int b = 0; b < nx; ++b)
-                for (int c = 0; c < ny; ++c) q += hot_at(S, pre_at(wz, a), pre_at(wx, b), pre_at(wy, c));
-        return q == 0 ? -1 : group_class(q);
-    };
-    int my_ic[CPT], my_c[CPT], my_slot[CPT];
-#pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-        const int jc = tid + u * NT;
-        my_ic[u] = 0;
-        my_c[u] = -1;
-        my_slot[u] = 0;
-        if (jc < ncand) {
-            my_ic[u] = S.dorder[jc];
-            my_c[u] = dest_class(my_ic[u]);
-            if (my_c[u] >= 0) my_slot[u] = atomicAdd(&S.ccnt[my_c[u]], 1);
-        }
-    }
-    block_sync();
-    if (tid == 0) {
-        int d = 0, rw = 0;
-        for (int c = 0; c < NCLS; ++c) {
-            S.coff[c] = d;
-            S.rbase[c] = rw;
-            d += S.ccnt[c];
-            rw += S.ccnt[c] * group_rows(c);
-        }
-        S.coff[NCLS] = d;
-        S.rbase[NCLS] = rw;
-    }
-    block_sync();
-#pragma unroll
-    for (int u = 0; u < CPT; ++u)
-        if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)my_ic[u];
-    const int nrows = S.rbase[NCLS], rows2 = S.rbase[1];  // rows2: the two-pass rows come first
-    if (nrows == 0) return;
-    store_weights(wreg, S.w);
-    if (tid == 0) mbar_init(&S.bar);
-    if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
-    fence_async_smem();
-    tc_fence_before();
-    block_sync();
-    tc_fence_after();
-    const uint32_t tb = S.tmem;
     const int q = warp & 3;
     const uint32_t lane_base = uint32_t(32 * q) << 16;
     constexpr uint32_t idesc = idesc_bf16(128, 16, false);
-    uint32_t phase = 0;
-    for (int b0 = 0; b0 < nrows; b0 += 128) {
-        // this thread's row: destination ic, its j-th pre-image (j + 32 in the second pass)
-        const int row = b0 + 32 * q + lane;
-        int ic = -1, j = 0, gr = 0;
-        if (row < nrows) {
-            int c = 0;
-            while (row >= S.rbase[c + 1]) ++c;
-            gr = group_rows(c);
-            const int off = row - S.rbase[c];
-            ic = S.dorder[S.coff[c] + off / gr];
-            j = off % gr;
+    uint32_t phase = 0, tb = 0;
+    bool ready = false, stop = false;  // block-uniform
+    // SPC_B consecutive sub-tiles of the work item; the weights, the mbarrier and the tensor memory
+    // are set up once, at the first sub-tile with destinations
+    for (int kk = 0; kk < SPC_B && !stop; ++kk) {
+        const int sub = blockIdx.y * SPC_B + kk;
+        Sub s;
+        if (!sub_of(L, it, sub, s)) continue;
+        if (kk > 0) block_sync();  // the previous sub-tile's readers of the shared tables are done
+        const int ylo = s.y0 - 1;
+        const int ya = max(ylo, 0), yb = min(s.y0 + SY + 1, s.g.dy);  // gradient rows: y range of the patch
+        const int yia = s.y0, yib = min(s.y0 + SY, s.g.dy);            // interior y range
+        const uint4 z4 = make_uint4(0, 0, 0, 0);
+        for (int i = tid; i < NPC; i += NT) {
+            S.g0[i] = z4;
+            S.g1[i] = z4;
         }
-        uint32_t wz = 0, wx = 0, wy = 0;
-        int nz = 0, nx = 0, ny = 0;
-        if (ic >= 0) {
-            const int r = ic / SY;
-            const bool coarse = S.srck[ic] == SRC_C;
-            nz = axis_pre(s.z0 + r / SX, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
-            nx = axis_pre(s.x0 + r % SX, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
-            ny = axis_pre(s.y0 + ic % SY, coarse, s.g.dy, reflect, ylo, &wy);
-        }
-        const int npass = b0 < rows2 ? 2 : 1;
-        bool failed = false;
-        for (int pass = 0; pass < npass; ++pass) {
-            // the (j + 32 pass)-th pre-image within distance 1 of a target, in (z, x, y) order
-            int pz = -100, px = 0, py = 0, want = j + 32 * pass;
-            for (int a = 0; a < nz && pz < -1; ++a)
-                for (int bb = 0; bb < nx && pz < -1; ++bb)
-                    for (int c = 0; c < ny; ++c) {
-                        const int tz = pre_at(wz, a), tx = pre_at(wx, bb), ty = pre_at(wy, c);
-                        if (!hot_at(S, tz, tx, ty)) continue;
-                        if (want-- == 0) {
-                            pz = tz;
-                            px = tx;
-                            py = ty;
-                            break;
-                        }
+        for (int i = tid; i < MAXT; i += NT) S.srck[i] = SRC_NONE;
+        for (int i = tid; i < NPROW * NWY; i += NT) (&S.tmask[0][0])[i] = 0;
+        const int nseg = load_mc_plan(L.mcbplan, blockIdx.x * NSUB + sub, 0, false, S.seg_lo, S.smeta, S.pre,
+                                      S.warp_tot);
+
+        struct Loader {
+            using Slot = McSlot;
+            const DevLayout *L;
+            const uint4 *gout;
+            const unsigned short *meta;
+            __device__ void operator()(int k, int i, Slot &sl) const {
+                const int sg = meta[k];
+                const bool t = sg >= NPROW + NIROW && sg < NPROW + 2 * NIROW;
+                sl.y = t ? int(L->ty[i]) : int(L->y[i]);
+                if (sg < NPROW) {
+                    sl.a = gout[2 * size_t(i)];
+                    sl.b = gout[2 * size_t(i) + 1];
+                }
+            }
+        } loader{&L, gout, S.smeta};
+        for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int ent, int i, const McSlot &sl) {
+            const int sg = S.smeta[ent];
+            if (sg < NPROW) {
+                if (sl.y >= ya && sl.y < yb) {
+                    const int py = sl.y - ylo;
+                    S.g0[sg * PY + py] = sl.a;
+                    S.g1[sg * PY + py] = sl.b;
+                    atomicOr(&S.tmask[sg][py >> 5], 1u << (py & 31));
+                }
+                return;
+            }
+            const int k = (sg - NPROW) / NIROW, r = (sg - NPROW) % NIROW;
+            if (k < 2) {
+                if (sl.y >= yia && sl.y < yib) {
+                    S.srck[r * SY + sl.y - s.y0] = (unsigned char)k;
+                    S.srci[r * SY + sl.y - s.y0] = i;
+                }
+            } else {
+    #pragma unroll
+                for (int f = 0; f < 2; ++f) {
+                    const int y = 2 * sl.y + f;
+                    if (y >= yia && y < yib) {
+                        S.srck[r * SY + y - s.y0] = SRC_C;
+                        S.srci[r * SY + y - s.y0] = i;
                     }
-            // rows past the last one are never read back: a warp holding only such rows skips them;
-            // the adjoint reads G at q - e (the flipped stencil)
-            if (b0 + 32 * q < nrows) {
-                if (warp < 4) store_taps<0, 14, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
-                else store_taps<14, NTAP, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
-            }
-            tmem_wait_st();
-            tc_fence_before();
-            block_sync();
-            tc_fence_after();
-            if (tid == 0) {
-                for (int e = 0; e < NTAP; ++e)
-                    mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256),
-                           idesc, (pass > 0 || e > 0) ? 1u : 0u);
-                mma_commit(&S.bar);
-            }
-            if (block_wait_mma(&S.bar, phase, L.err)) {
-                failed = true;
-                break;
-            }
-            phase ^= 1;
-            tc_fence_after();
-        }
-        if (failed) break;
-        if (warp < 4) {
-            float v[16];
-            tmem_ld16(tb + lane_base + TM_D, v);
-            // sum over the row group in a fixed butterfly order (every lane of a group gets the same sum)
-            const int gmax = __reduce_max_sync(0xffffffffu, gr);
-            for (int w = 1; w < gmax; w <<= 1) {
-#pragma unroll
-                for (int c = 0; c < MC; ++c) {
-                    const float o = __shfl_xor_sync(0xffffffffu, v[c], w);
-                    if (w < gr) v[c] += o;
                 }
             }
-            if (ic >= 0 && j == 0) {
+        });
+        // cells within distance 1 of a target: y dilation of each row, OR over the 3 x 3 neighbour rows
+        if (tid < NPROW) {
+            const int pz = tid / PX, px = tid % PX;
+            unsigned h[NWY] = {};
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qz = pz + dz, qx = px + dx;
+                    if (qz < 0 || qz >= PZ || qx < 0 || qx >= PX) continue;
+                    const unsigned *m = S.tmask[qz * PX + qx];
+    #pragma unroll
+                    for (int w = 0; w < NWY; ++w)
+                        h[w] |= m[w] | (m[w] << 1) | (m[w] >> 1) | (w + 1 < NWY ? m[w + 1] << 31 : 0u) |
+                                (w > 0 ? m[w - 1] >> 31 : 0u);
+                }
+    #pragma unroll
+            for (int w = 0; w < NWY; ++w) S.hot[tid][w] = h[w];
+        }
+        block_sync();
+        // destinations: every particle / tree node of the interior, and every coarse particle (anchored
+        // at its first fine cell), with q > 0 pre-images within distance 1 of a target (the others add
+        // exact zeros). Each takes a slot in its row-group class. First the candidates (interior cells
+        // holding a particle, a tree node or a coarse particle's first cell) are listed in cell order
+        // (warp w: cells [w CPT 32, (w + 1) CPT 32)), in dorder's space; an uncovered cell next to a
+        // target means an invalid layout.
+        constexpr int CPT = MAXT / NT;  // interior cells per thread
+        if (tid < NCLS) S.ccnt[tid] = 0;
+        unsigned bal[CPT];
+        int wcnt = 0;
+    #pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            const int ic = (warp * CPT + u) * 32 + lane;
+            const int r = ic / SY, iy = ic % SY;
+            const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
+            bool cand = false;
+            if (z < s.g.dz && x < s.g.dx && y < s.g.dy) {
                 const int k = S.srck[ic];
-                const size_t idx = size_t(S.srci[ic]);
-                if (k == SRC_T) {
-                    float4 *o = reinterpret_cast<float4 *>(gt + idx * MC);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                if (k == SRC_NONE) {
+                    if (hot_at(S, r / SX + 1, r % SX + 1, iy + 1)) atomicOr(L.err, ERR_DEVICE_CHECK);
                 } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) red_add_v4(gp + idx * MC + 4 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    cand = k != SRC_C || !((z | x | y) & 1);
                 }
             }
+            bal[u] = __ballot_sync(0xffffffffu, cand);
+            wcnt += __popc(bal[u]);
         }
+        if (lane == 0) S.warp_tot[warp] = wcnt;
+        block_sync();
+        int ncand = 0, cbase = 0;
+    #pragma unroll
+        for (int w = 0; w < NWARP; ++w) {
+            cbase += w < warp ? S.warp_tot[w] : 0;
+            ncand += S.warp_tot[w];
+        }
+        const unsigned below = (1u << lane) - 1u;
+    #pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            if ((bal[u] >> lane) & 1u) S.dorder[cbase + __popc(bal[u] & below)] = (unsigned short)((warp * CPT + u) * 32 + lane);
+            cbase += __popc(bal[u]);
+        }
+        block_sync();
+        // class of candidate cell ic as a destination (-1: no pre-image within reach of a target)
+        auto dest_class = [&](int ic) -> int {
+            const int r = ic / SY, iy = ic % SY;
+            const int z = s.z0 + r / SX, x = s.x0 + r % SX, y = s.y0 + iy;
+            const bool coarse = S.srck[ic] == SRC_C;
+            uint32_t wz, wx, wy;
+            const int nz = axis_pre(z, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
+            const int nx = axis_pre(x, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
+            const int ny = axis_pre(y, coarse, s.g.dy, reflect, ylo, &wy);
+            int q = 0;
+            for (int a = 0; a < nz; ++a)
+                for (int b = 0; b < nx; ++b)
+                    for (int c = 0; c < ny; ++c) q += hot_at(S, pre_at(wz, a), pre_at(wx, b), pre_at(wy, c));
+            return q == 0 ? -1 : group_class(q);
+        };
+        int my_ic[CPT], my_c[CPT], my_slot[CPT];
+    #pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            const int jc = tid + u * NT;
+            my_ic[u] = 0;
+            my_c[u] = -1;
+            my_slot[u] = 0;
+            if (jc < ncand) {
+                my_ic[u] = S.dorder[jc];
+                my_c[u] = dest_class(my_ic[u]);
+                if (my_c[u] >= 0) my_slot[u] = atomicAdd(&S.ccnt[my_c[u]], 1);
+            }
+        }
+        block_sync();
+        if (tid == 0) {
+            int d = 0, rw = 0;
+            for (int c = 0; c < NCLS; ++c) {
+                S.coff[c] = d;
+                S.rbase[c] = rw;
+                d += S.ccnt[c];
+                rw += S.ccnt[c] * group_rows(c);
+            }
+            S.coff[NCLS] = d;
+            S.rbase[NCLS] = rw;
+        }
+        block_sync();
+    #pragma unroll
+        for (int u = 0; u < CPT; ++u)
+            if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)my_ic[u];
+        const int nrows = S.rbase[NCLS], rows2 = S.rbase[1];  // rows2: the two-pass rows come first
+        if (nrows == 0) continue;
+        if (!ready) {
+            store_weights(wreg, S.w);
+            if (tid == 0) mbar_init(&S.bar);
+            if (warp == 0) tmem_alloc(smem_u32(&S.tmem), TMEM_COLS);
+            ready = true;
+        }
+        fence_async_smem();
         tc_fence_before();
         block_sync();
         tc_fence_after();
+        tb = S.tmem;
+        for (int b0 = 0; b0 < nrows; b0 += 128) {
+            // this thread's row: destination ic, its j-th pre-image (j + 32 in the second pass)
+            const int row = b0 + 32 * q + lane;
+            int ic = -1, j = 0, gr = 0;
+            if (row < nrows) {
+                int c = 0;
+                while (row >= S.rbase[c + 1]) ++c;
+                gr = group_rows(c);
+                const int off = row - S.rbase[c];
+                ic = S.dorder[S.coff[c] + off / gr];
+                j = off % gr;
+            }
+            uint32_t wz = 0, wx = 0, wy = 0;
+            int nz = 0, nx = 0, ny = 0;
+            if (ic >= 0) {
+                const int r = ic / SY;
+                const bool coarse = S.srck[ic] == SRC_C;
+                nz = axis_pre(s.z0 + r / SX, coarse, s.g.dz, reflect, s.z0 - 1, &wz);
+                nx = axis_pre(s.x0 + r % SX, coarse, s.g.dx, reflect, s.x0 - 1, &wx);
+                ny = axis_pre(s.y0 + ic % SY, coarse, s.g.dy, reflect, ylo, &wy);
+            }
+            const int npass = b0 < rows2 ? 2 : 1;
+            bool failed = false;
+            for (int pass = 0; pass < npass; ++pass) {
+                // the (j + 32 pass)-th pre-image within distance 1 of a target, in (z, x, y) order
+                int pz = -100, px = 0, py = 0, want = j + 32 * pass;
+                for (int a = 0; a < nz && pz < -1; ++a)
+                    for (int bb = 0; bb < nx && pz < -1; ++bb)
+                        for (int c = 0; c < ny; ++c) {
+                            const int tz = pre_at(wz, a), tx = pre_at(wx, bb), ty = pre_at(wy, c);
+                            if (!hot_at(S, tz, tx, ty)) continue;
+                            if (want-- == 0) {
+                                pz = tz;
+                                px = tx;
+                                py = ty;
+                                break;
+                            }
+                        }
+                // rows past the last one are never read back: a warp holding only such rows skips them;
+                // the adjoint reads G at q - e (the flipped stencil)
+                if (b0 + 32 * q < nrows) {
+                    if (warp < 4) store_taps<0, 14, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
+                    else store_taps<14, NTAP, -1>(S.g0, S.g1, pz, px, py, pz >= 0, tb + lane_base);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                block_sync();
+                tc_fence_after();
+                if (tid == 0) {
+                    for (int e = 0; e < NTAP; ++e)
+                        mma_ts(tb + TM_D, tb + TM_A + 8 * e, sdesc(smem_u32(S.w + e * WTAP), 128, 256),
+                               idesc, (pass > 0 || e > 0) ? 1u : 0u);
+                    mma_commit(&S.bar);
+                }
+                if (block_wait_mma(&S.bar, phase, L.err)) {
+                    failed = true;
+                    break;
+                }
+                phase ^= 1;
+                tc_fence_after();
+            }
+            if (failed) {
+                stop = true;
+                break;
+            }
+            if (warp < 4) {
+                float v[16];
+                tmem_ld16(tb + lane_base + TM_D, v);
+                // sum over the row group in a fixed butterfly order (every lane of a group gets the same sum)
+                const int gmax = __reduce_max_sync(0xffffffffu, gr);
+                for (int w = 1; w < gmax; w <<= 1) {
+    #pragma unroll
+                    for (int c = 0; c < MC; ++c) {
+                        const float o = __shfl_xor_sync(0xffffffffu, v[c], w);
+                        if (w < gr) v[c] += o;
+                    }
+                }
+                if (ic >= 0 && j == 0) {
+                    const int k = S.srck[ic];
+                    const size_t idx = size_t(S.srci[ic]);
+                    if (k == SRC_T) {
+                        float4 *o = reinterpret_cast<float4 *>(gt + idx * MC);
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    } else {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) red_add_v4(gp + idx * MC + 4 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    }
+                }
+            }
+            tc_fence_before();
+            block_sync();
+            tc_fence_after();
+        }
     }
-    tc_fence_before();
-    block_sync();
-    if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
+    if (ready) {
+        tc_fence_before();
+        block_sync();
+        if (warp == 0) tmem_dealloc(tb, TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -1367,7 +1400,7 @@ static apr_status_t convolve_mc(apr_handle_t h, const uint16_t *particles, const
     const int nl = X.l_max - X.l_min + 1;
     if (e == cudaSuccess && n > 0) {
         mc_weight_layout_kernel<<<(nl * MC * MC * NTAP + 255) / 256, 256, 0, stream>>>(weights, nl, 0, h->d_mcw);
-        mc_fwd_kernel<<<dim3(n, NSUB), NT, sm, stream>>>(h->L, h->d_fwd, reinterpret_cast<const uint4 *>(particles),
+        mc_fwd_kernel<<<dim3(n, NSUB / SPC_F), NT, sm, stream>>>(h->L, h->d_fwd, reinterpret_cast<const uint4 *>(particles),
                                                           reinterpret_cast<const uint4 *>(tree), h->d_mcw, bc, out,
                                                           reinterpret_cast<uint4 *>(out_bf16));
         e = cudaGetLastError();
@@ -1425,7 +1458,7 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
         if (e == cudaSuccess && n > 0) {
             mc_weight_layout_kernel<<<(n_levels * MC * MC * NTAP + 255) / 256, 256, 0, stream>>>(
                 weights, n_levels, 1, h->d_mcw + size_t(n_levels) * MC * MC * NTAP);
-            mc_bwd_data_kernel<<<dim3(n, NSUB), NT, sizeof(BwdSmem), stream>>>(
+            mc_bwd_data_kernel<<<dim3(n, NSUB / SPC_B), NT, sizeof(BwdSmem), stream>>>(
                 h->L, h->d_bwd, wt, bc, reinterpret_cast<const uint4 *>(grad_out), grad_particles, gt);
             e = cudaGetLastError();
         }
