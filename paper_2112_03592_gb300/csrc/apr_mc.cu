@@ -563,13 +563,14 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
     __syncwarp();
     const int cy0 = 2 * it.yb * BY;
     // the children of the 2 x 2 child rows (segments 0..3 particles, 4..7 tree nodes), flattened;
-    // two elements per lane in flight
+    // four elements per lane in flight
+    constexpr int U = 4;
     const ChildSegs cs(lo, cn);
-    for (int e0 = lane; e0 < cs.total; e0 += 64) {
-        int sg[2], ix[2], cy[2];
-        uint4 va[2], vb[2];
+    for (int e0 = lane; e0 < cs.total; e0 += 32 * U) {
+        int sg[U], ix[U], cy[U];
+        uint4 va[U], vb[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int e = e0 + 32 * u;
             sg[u] = -1;
             if (e < cs.total) {
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < U; ++u)
             if (sg[u] >= 0) {
                 const int slot = (sg[u] & 3) * 2 + (cy[u] & 1);
                 S.child[warp][cy[u] >> 1][slot][0] = va[u];
@@ -636,28 +637,61 @@ __global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L,
     int lo, cn, tlo, tn;
     tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
     const LevelGeo gc = L.geo[it.l + 1];
-    for (int k = lane; k < tn * (MC / 4); k += 32) {
-        const int t = tlo + k / (MC / 4), c = k % (MC / 4);
-        const int yv = L.ty[t];
-        const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
-        const float4 v = gt[size_t(t) * (MC / 4) + c];
-        const float f = float(cnt);
-        share[warp][yv - it.yb * BY][c] = make_float4(v.x / f, v.y / f, v.z / f, v.w / f);
+    // the nodes' shares (at most BY nodes x 4 channel groups: eight items per lane, loads first)
+    {
+        int yv[8];
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = lane + 32 * u;
+            if (k < tn * (MC / 4)) {
+                const int t = tlo + k / (MC / 4);
+                yv[u] = L.ty[t];
+                v[u] = gt[size_t(t) * (MC / 4) + k % (MC / 4)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = lane + 32 * u;
+            if (k < tn * (MC / 4)) {
+                const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv[u] + 1 < gc.dy ? 2 : 1);
+                const float f = float(cnt);
+                share[warp][yv[u] - it.yb * BY][k % (MC / 4)] = make_float4(v[u].x / f, v[u].y / f, v[u].z / f, v[u].w / f);
+            }
+        }
     }
     __syncwarp();
     // every child (segments 0..3 particles, 4..7 tree nodes) gets its parent's share, 16 channels as
     // four float4 per element
+    // four (element, channel group) items per lane in flight: their y and gradient loads are issued
+    // before any of them is updated
+    constexpr int U = 4;
     const ChildSegs cs(lo, cn);
-    for (int k = lane; k < cs.total * (MC / 4); k += 32) {
-        const int c = k % (MC / 4);
-        int i;
-        const bool src = cs.seg(k / (MC / 4), i) >= 4;
-        const int yv = src ? L.ty[i] : L.y[i];
-        float4 *dst = src ? gt : gp;
-        const float4 s = share[warp][(yv >> 1) - it.yb * BY][c];
-        float4 &d = dst[size_t(i) * (MC / 4) + c];
-        const float4 v = d;
-        d = make_float4(v.x + s.x, v.y + s.y, v.z + s.z, v.w + s.w);
+    for (int k0 = lane; k0 < cs.total * (MC / 4); k0 += 32 * U) {
+        float4 *d[U];
+        float4 v[U];
+        int yv[U], c[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + 32 * u;
+            ok[u] = k < cs.total * (MC / 4);
+            d[u] = nullptr;
+            if (ok[u]) {
+                c[u] = k % (MC / 4);
+                int i;
+                const bool src = cs.seg(k / (MC / 4), i) >= 4;
+                yv[u] = src ? L.ty[i] : L.y[i];
+                d[u] = (src ? gt : gp) + size_t(i) * (MC / 4) + c[u];
+                v[u] = *d[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (ok[u]) {
+                const float4 s = share[warp][(yv[u] >> 1) - it.yb * BY][c[u]];
+                *d[u] = make_float4(v[u].x + s.x, v[u].y + s.y, v[u].z + s.z, v[u].w + s.w);
+            }
     }
 }
 
