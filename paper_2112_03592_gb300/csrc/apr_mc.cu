@@ -1256,6 +1256,10 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
         if (!sub_of(L, it, u % NSUB, s)) continue;
         const int nt = list_targets(L, s, S.tg);
         if (nt == 0) continue;
+        // dL/dout of the first step's targets, loaded while the patch is staged; each step then loads
+        // the next step's while its MMAs run (threads 0 .. 2 WG_T - 1: target tid / 2, half tid % 2)
+        uint4 gnext = make_uint4(0, 0, 0, 0);
+        if (tid < 2 * WG_T && (tid >> 1) < nt) gnext = gout[2 * size_t(S.tg.idx[tid >> 1]) + (tid & 1)];
         stage_features(L, s, u, vals, tree, bc, S.st);
         for (int t0 = 0; t0 < nt; t0 += WG_T) {
             // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t
@@ -1270,9 +1274,9 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
             }
             // g^T (N = co rows, K = targets), K-major core matrices
             if (tid < 2 * WG_T) {
-                const int tt = tid >> 1, h = tid & 1, tg = t0 + tt;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (tg < nt) v = gout[2 * size_t(S.tg.idx[tg]) + h];
+                const int tt = tid >> 1, h = tid & 1, tn = t0 + WG_T + tt;
+                const uint4 v = gnext;
+                gnext = tn < nt ? gout[2 * size_t(S.tg.idx[tn]) + h] : make_uint4(0, 0, 0, 0);
                 const uint16_t *p = reinterpret_cast<const uint16_t *>(&v);
 #pragma unroll
                 for (int j = 0; j < 8; ++j)  // co = 8h + j
