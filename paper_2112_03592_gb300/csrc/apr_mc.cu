@@ -1221,6 +1221,10 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
     const uint32_t lane_base = uint32_t(32 * q) << 16;
     constexpr uint32_t idesc = idesc_bf16(128, 16, true);
     uint32_t phase = 0;
+    // this thread's im2col share, the same in every K step: target it_t, taps ie0 and ie1 (both halves)
+    static_assert(NT == WG_T * 16 && NTAP <= 32, "one target and two taps per thread");
+    const int it_t = tid % WG_T, ie0 = tid / WG_T, ie1 = ie0 + 16;
+    const int off0 = tap_off(ie0), off1 = ie1 < NTAP ? tap_off(ie1) : 0;
     int cur_l = items[u0 / NSUB].l;
     bool dirty = false, failed = false;
     // writes the level's accumulator (zeros if nothing was accumulated) to partial[cta + level index];
@@ -1262,15 +1266,25 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
         if (tid < 2 * WG_T && (tid >> 1) < nt) gnext = gout[2 * size_t(S.tg.idx[tid >> 1]) + (tid & 1)];
         stage_features(L, s, u, vals, tree, bc, S.st);
         for (int t0 = 0; t0 < nt; t0 += WG_T) {
-            // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t
-            for (int i = tid; i < 2 * NTAP * WG_T; i += NT) {
-                const int mg = i / WG_T, t = i % WG_T, e = mg >> 1;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (t0 + t < nt) {
-                    const int c = int(S.tg.cell[t0 + t]) + tap_off(e);
-                    v = (mg & 1) ? S.st.p1[c] : S.st.p0[c];
+            // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t; this
+            // thread copies both halves of taps ie0 and ie1 for target it_t
+            {
+                const bool live = t0 + it_t < nt;
+                const int cell = live ? int(S.tg.cell[t0 + it_t]) : 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = h ? ie1 : ie0;
+                    if (e < NTAP) {
+                        uint4 a = make_uint4(0, 0, 0, 0), b = a;
+                        if (live) {
+                            const int c = cell + (h ? off1 : off0);
+                            a = S.st.p0[c];
+                            b = S.st.p1[c];
+                        }
+                        *reinterpret_cast<uint4 *>(S.u + (2 * e) * (WG_T * 16) + it_t * 16) = a;
+                        *reinterpret_cast<uint4 *>(S.u + (2 * e + 1) * (WG_T * 16) + it_t * 16) = b;
+                    }
                 }
-                *reinterpret_cast<uint4 *>(S.u + mg * (WG_T * 16) + t * 16) = v;
             }
             // g^T (N = co rows, K = targets), K-major core matrices
             if (tid < 2 * WG_T) {
