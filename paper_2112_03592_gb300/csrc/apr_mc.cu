@@ -354,16 +354,25 @@ __device__ __forceinline__ int load_mc_plan(const PlanView &P, int tile, int t0,
     return n;
 }
 
+// Target list of the sub-tile: the level-l particles of its interior, in particle order.
+struct Targets {
+    int idx[MAXT];
+    unsigned short cell[MAXT];
+    int row_lo[NIROW], row_base[NIROW + 1];
+};
+
 // Element loads and patch writes for the nseg plan entries in S (after load_mc_plan); ends with a
-// block barrier.
+// block barrier. T (optional, its row offsets set): the targets (level-l particles of the in-grid
+// interior rows with y in [y0, y0 + SY), all among the staged elements) are listed as they pass,
+// target j of row r at T->row_base[r] + j.
 __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *vals, const uint4 *tree, int bc,
-                                 int nseg, FeatStage &S) {
+                                 int nseg, FeatStage &S, Targets *T = nullptr) {
     const int tid = threadIdx.x;
     const int ylo = s.y0 - 1;
     const int ya = max(ylo, 0), yb = min(s.y0 + SY + 1, s.g.dy);
     const bool inner = sub_inner(s);
     const FeatLoader loader{L.y, L.ty, vals, tree, S.smeta};
-    for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int sg, int, const McSlot &sl) {
+    for_each_element(S.seg_lo, S.pre, nseg, S.segid, loader, [&](int sg, int i, const McSlot &sl) {
         const int og = S.smeta[sg] & MC_SEG;
         const int kind = og / NPROW, pr = og - kind * NPROW;
         if (kind < 2) {
@@ -371,6 +380,15 @@ __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *
                 const int c = pr * PY + sl.y - ylo;
                 S.p0[c] = sl.a;
                 S.p1[c] = sl.b;
+                if (T && kind == 0 && sl.y >= s.y0 && sl.y < s.y0 + SY) {
+                    const int iz = pr / PX - 1, ix = pr % PX - 1;
+                    if (unsigned(iz) < unsigned(SZ) && unsigned(ix) < unsigned(SX) && s.z0 + iz < s.g.dz &&
+                        s.x0 + ix < s.g.dx) {
+                        const int r = iz * SX + ix, slot = T->row_base[r] + (i - T->row_lo[r]);
+                        T->idx[slot] = i;
+                        T->cell[slot] = (unsigned short)c;
+                    }
+                }
             }
         } else if (!inner) {
 #pragma unroll
@@ -435,18 +453,11 @@ __device__ void feature_elements(const DevLayout &L, const Sub &s, const uint4 *
 
 // The whole staging of sub-tile `tile` (index into the feature plan: item * NSUB + sub).
 __device__ void stage_features(const DevLayout &L, const Sub &s, int tile, const uint4 *vals, const uint4 *tree,
-                               int bc, FeatStage &S) {
+                               int bc, FeatStage &S, Targets *T = nullptr) {
     const int n = load_mc_plan(L.mcfplan, tile, 0, bc != APR_BC_REFLECT && !sub_inner(s), S.seg_lo, S.smeta, S.pre,
                                S.warp_tot);
-    feature_elements(L, s, vals, tree, bc, n, S);
+    feature_elements(L, s, vals, tree, bc, n, S, T);
 }
-
-// Target list of the sub-tile: the level-l particles of its interior, in particle order.
-struct Targets {
-    int idx[MAXT];
-    unsigned short cell[MAXT];
-    int row_lo[NIROW], row_base[NIROW + 1];
-};
 
 // Row offsets of the targets (warp 0; no barrier): the sub-tile spans whole y-blocks, so the block
 // offsets give each interior row's level-l particles exactly.
@@ -477,27 +488,19 @@ __device__ __forceinline__ void target_rows(const DevLayout &L, const Sub &s, Ta
     }
 }
 
-// Target indices and patch cells from the row offsets (after a barrier); ends with a barrier.
-__device__ __forceinline__ void target_fill(const DevLayout &L, const Sub &s, Targets &T) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < NIROW; r += NWARP) {
-        const int iz = r / SX, ix = r % SX;
-        const int b = T.row_base[r], n = T.row_base[r + 1] - b;
-        for (int j = lane; j < n; j += 32) {
-            const int i = T.row_lo[r] + j;
-            T.idx[b + j] = i;
-            T.cell[b + j] = (unsigned short)(((iz + 1) * PX + ix + 1) * PY + int(L.y[i]) - s.y0 + 1);
-        }
-    }
-    block_sync();
+// Particle index of target j from the row offsets alone (before the list is filled).
+__device__ __forceinline__ int target_index(const Targets &T, int j) {
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < NIROW; ++k) r = T.row_base[k] <= j ? k : r;
+    return T.row_lo[r] + (j - T.row_base[r]);
 }
 
-__device__ int list_targets(const DevLayout &L, const Sub &s, Targets &T) {
+// Row offsets of the targets; returns their count (ends with a barrier).
+__device__ int count_targets(const DevLayout &L, const Sub &s, Targets &T) {
     target_rows(L, s, T);
     block_sync();
-    const int n = T.row_base[NIROW];
-    target_fill(L, s, T);
-    return n;
+    return T.row_base[NIROW];
 }
 
 // Weights of every level in the B-operand layout of each tap e: K-major core matrices of 8 rows x 16
@@ -735,8 +738,7 @@ __global__ void __launch_bounds__(NT, 2) mc_fwd_kernel(const DevLayout L, const 
                                       S.st.warp_tot);
         const int nt = S.tg.row_base[NIROW];
         if (nt == 0) continue;
-        target_fill(L, s, S.tg);
-        feature_elements(L, s, vals, tree, bc, nseg, S.st);
+        feature_elements(L, s, vals, tree, bc, nseg, S.st, &S.tg);
         if (!ready) {
             store_weights(wreg, S.w);
             if (tid == 0) mbar_init(&S.bar);
@@ -1258,13 +1260,13 @@ __global__ void __launch_bounds__(NT, 2) mc_wgrad_kernel(const DevLayout L, cons
             dirty = false;
         }
         if (!sub_of(L, it, u % NSUB, s)) continue;
-        const int nt = list_targets(L, s, S.tg);
+        const int nt = count_targets(L, s, S.tg);
         if (nt == 0) continue;
         // dL/dout of the first step's targets, loaded while the patch is staged; each step then loads
         // the next step's while its MMAs run (threads 0 .. 2 WG_T - 1: target tid / 2, half tid % 2)
         uint4 gnext = make_uint4(0, 0, 0, 0);
-        if (tid < 2 * WG_T && (tid >> 1) < nt) gnext = gout[2 * size_t(S.tg.idx[tid >> 1]) + (tid & 1)];
-        stage_features(L, s, u, vals, tree, bc, S.st);
+        if (tid < 2 * WG_T && (tid >> 1) < nt) gnext = gout[2 * size_t(target_index(S.tg, tid >> 1)) + (tid & 1)];
+        stage_features(L, s, u, vals, tree, bc, S.st, &S.tg);
         for (int t0 = 0; t0 < nt; t0 += WG_T) {
             // im2col: entry (mg, t) = channels 8h .. 8h+7 of tap e = mg / 2 at target t0 + t; this
             // thread copies both halves of taps ie0 and ie1 for target it_t
