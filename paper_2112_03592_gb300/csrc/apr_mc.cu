@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                     S.srci[r * SY + sl.y - s.y0] = i;
                 }
             } else {
-    #pragma unroll
+#pragma unroll
                 for (int f = 0; f < 2; ++f) {
                     const int y = 2 * sl.y + f;
                     if (y >= yia && y < yib) {
@@ -976,12 +976,12 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                     const int qz = pz + dz, qx = px + dx;
                     if (qz < 0 || qz >= PZ || qx < 0 || qx >= PX) continue;
                     const unsigned *m = S.tmask[qz * PX + qx];
-    #pragma unroll
+#pragma unroll
                     for (int w = 0; w < NWY; ++w)
                         h[w] |= m[w] | (m[w] << 1) | (m[w] >> 1) | (w + 1 < NWY ? m[w + 1] << 31 : 0u) |
                                 (w > 0 ? m[w - 1] >> 31 : 0u);
                 }
-    #pragma unroll
+#pragma unroll
             for (int w = 0; w < NWY; ++w) S.hot[tid][w] = h[w];
         }
         block_sync();
@@ -995,7 +995,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
         if (tid < NCLS) S.ccnt[tid] = 0;
         unsigned bal[CPT];
         int wcnt = 0;
-    #pragma unroll
+#pragma unroll
         for (int u = 0; u < CPT; ++u) {
             const int ic = (warp * CPT + u) * 32 + lane;
             const int r = ic / SY, iy = ic % SY;
@@ -1015,13 +1015,13 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
         if (lane == 0) S.warp_tot[warp] = wcnt;
         block_sync();
         int ncand = 0, cbase = 0;
-    #pragma unroll
+#pragma unroll
         for (int w = 0; w < NWARP; ++w) {
             cbase += w < warp ? S.warp_tot[w] : 0;
             ncand += S.warp_tot[w];
         }
         const unsigned below = (1u << lane) - 1u;
-    #pragma unroll
+#pragma unroll
         for (int u = 0; u < CPT; ++u) {
             if ((bal[u] >> lane) & 1u) S.dorder[cbase + __popc(bal[u] & below)] = (unsigned short)((warp * CPT + u) * 32 + lane);
             cbase += __popc(bal[u]);
@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
             return q == 0 ? -1 : group_class(q);
         };
         int my_ic[CPT], my_c[CPT], my_slot[CPT];
-    #pragma unroll
+#pragma unroll
         for (int u = 0; u < CPT; ++u) {
             const int jc = tid + u * NT;
             my_ic[u] = 0;
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
             S.rbase[NCLS] = rw;
         }
         block_sync();
-    #pragma unroll
+#pragma unroll
         for (int u = 0; u < CPT; ++u)
             if (my_c[u] >= 0) S.dorder[S.coff[my_c[u]] + my_slot[u]] = (unsigned short)my_ic[u];
         const int nrows = S.rbase[NCLS], rows2 = S.rbase[1];  // rows2: the two-pass rows come first
@@ -1155,7 +1155,7 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                 // sum over the row group in a fixed butterfly order (every lane of a group gets the same sum)
                 const int gmax = __reduce_max_sync(0xffffffffu, gr);
                 for (int w = 1; w < gmax; w <<= 1) {
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < MC; ++c) {
                         const float o = __shfl_xor_sync(0xffffffffu, v[c], w);
                         if (w < gr) v[c] += o;
@@ -1166,10 +1166,10 @@ __global__ void __launch_bounds__(NT, 2) mc_bwd_data_kernel(const DevLayout L, c
                     const size_t idx = size_t(S.srci[ic]);
                     if (k == SRC_T) {
                         float4 *o = reinterpret_cast<float4 *>(gt + idx * MC);
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 4; ++c) o[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
                     } else {
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 4; ++c) red_add_v4(gp + idx * MC + 4 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
                     }
                 }
