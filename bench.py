@@ -310,8 +310,9 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
 
     # end to end through the public API with host buffers: H2D of the step's inputs (values,
     # upstream gradient), the step, D2H of its results (outputs, both gradients). Copies that the
-    # kernels do not wait for run on a second stream: dL/dout goes in while the tree restriction
-    # and the convolution run, the outputs come back while the backward runs, and the particle
+    # kernels do not wait for run on a second stream: dL/dout goes in (after the values, so that they
+    # have the host link to themselves) while the tree restriction and the convolution run, the
+    # outputs come back while the backward runs, and the particle
     # gradient while the stencil gradient runs (so here the backward's three parts are called one
     # after the other: overlapping that copy saves more than running the stencil gradient beside
     # the adjoints)
@@ -321,12 +322,14 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
     h_gp = torch.empty(gp.numel()).pin_memory()
     h_gw = torch.empty_like(gw, device="cpu").pin_memory()
     cs = torch.cuda.Stream(device=dev)
-    ev_g, ev_out, ev_gp = (torch.cuda.Event() for _ in range(3))
+    ev_v, ev_g, ev_out, ev_gp = (torch.cuda.Event() for _ in range(4))
 
     def e2e_step():
         cs.wait_stream(stream)                  # the previous step has finished with gout
         vals.copy_(h_vals, non_blocking=True)
+        ev_v.record(stream)
         with torch.cuda.stream(cs):
+            cs.wait_event(ev_v)                 # the values, which the first kernel waits for, go first
             gout.copy_(h_gout, non_blocking=True)
             ev_g.record(cs)
         run_part[0]()
