@@ -232,9 +232,9 @@ __device__ __forceinline__ void place_packet(FwdSmem<R, NS> &S, int seg, int i0,
 // in y the reflected cells (or zeros); cells no source covers (possible only in layouts not checked
 // for 2:1 balance) hold 0. Also records the target rows (rmask, rfirst) and lists the windows that
 // hold targets (act, nact). Ends with a block barrier.
-// A tile's plan header and this thread's first entry (entry threadIdx.x, when the plan has it),
-// loaded at kernel start so that they overlap the work item and stencil loads instead of following
-// them. count: the entries listed (the entry after them holds the packet total).
+// A tile's plan header (loaded at kernel start, with the work item) and this thread's first entry
+// (entry threadIdx.x, when the plan has it). count: the entries listed (the entry after them holds
+// the packet total).
 struct PlanPre {
     PlanHdr hd;
     uint2 e0;
@@ -516,17 +516,16 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
     const Item it = items[tile];
-    // the plan of each radius the tile may take, loaded with the item (the radius follows from the
-    // level's stencil)
+    // the plan headers of both radii the tile may take, loaded with the item (the radius follows
+    // from the level's stencil; the entries are read only for the radius taken)
     const PlanHdr h1 = plan_hdr(L.fplan[0], tile);
     if constexpr (R == 2) {
         const PlanHdr h2 = plan_hdr(L.fplan[1], tile);
-        const PlanPre p1 = plan_pre(L.fplan[0], h1, h1.count), p2 = plan_pre(L.fplan[1], h2, h2.count);
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_fwd_tile<1, 2>(L, it, p1, vals, tree, stencils, bc, out, epi, smem_raw);
+            conv_fwd_tile<1, 2>(L, it, plan_pre(L.fplan[0], h1, h1.count), vals, tree, stencils, bc, out, epi, smem_raw);
             return;
         }
-        conv_fwd_tile<2, 2>(L, it, p2, vals, tree, stencils, bc, out, epi, smem_raw);
+        conv_fwd_tile<2, 2>(L, it, plan_pre(L.fplan[1], h2, h2.count), vals, tree, stencils, bc, out, epi, smem_raw);
     } else {
         conv_fwd_tile<R, R>(L, it, plan_pre(L.fplan[0], h1, h1.count), vals, tree, stencils, bc, out, epi, smem_raw);
     }
@@ -1130,16 +1129,16 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = tile0 + int(blockIdx.x);   // work items [tile0, tile0 + gridDim.x)
     const Item it = items[tile];
-    // the plan of each radius the tile may take, loaded with the item
+    // the plan headers of both radii the tile may take, loaded with the item (the entries are read
+    // only for the radius taken)
     const PlanHdr h1 = plan_hdr(L.bplan[0], tile);
     if constexpr (R == 2) {
         const PlanHdr h2 = plan_hdr(L.bplan[1], tile);
-        const PlanPre p1 = plan_pre(L.bplan[0], h1, bplan_count(h1)), p2 = plan_pre(L.bplan[1], h2, bplan_count(h2));
         if (outer_taps_zero5(stencils, it.l - L.l_min)) {
-            conv_bwd_data_tile<1, 2>(L, it, p1, stencils, bc, gout, gp, gt, smem_raw);
+            conv_bwd_data_tile<1, 2>(L, it, plan_pre(L.bplan[0], h1, bplan_count(h1)), stencils, bc, gout, gp, gt, smem_raw);
             return;
         }
-        conv_bwd_data_tile<2, 2>(L, it, p2, stencils, bc, gout, gp, gt, smem_raw);
+        conv_bwd_data_tile<2, 2>(L, it, plan_pre(L.bplan[1], h2, bplan_count(h2)), stencils, bc, gout, gp, gt, smem_raw);
     } else {
         conv_bwd_data_tile<R, R>(L, it, plan_pre(L.bplan[0], h1, bplan_count(h1)), stencils, bc, gout, gp, gt, smem_raw);
     }
