@@ -197,7 +197,12 @@ size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k);
  * Inputs as in apr_convolve; grad_out device [N_p]. grad_particles (device [N_p]) and grad_stencils
  * (device [L][k^3]) are overwritten; either may be NULL to skip it. workspace: device scratch of at
  * least apr_backward_workspace_bytes(h, k) bytes, 256-byte aligned, contents ignored on entry.
- * Results are deterministic (fixed summation order). */
+ * Results are deterministic (fixed summation order).
+ * When both gradients are requested, the stencil gradient runs on a second stream that the handle
+ * owns (created on the first such call), forked from `stream` and joined back to it with events:
+ * the call stays ordered on `stream` (work enqueued after it waits for both gradients) and can be
+ * captured into a CUDA graph from `stream`. Concurrent calls on one handle are serialised while
+ * they enqueue. */
 apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree,
                                    const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                    float *grad_particles, float *grad_stencils, void *workspace,
