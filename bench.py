@@ -322,16 +322,26 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
     h_gp = torch.empty(gp.numel()).pin_memory()
     h_gw = torch.empty_like(gw, device="cpu").pin_memory()
     cs = torch.cuda.Stream(device=dev)
-    ev_v, ev_g, ev_out, ev_gp = (torch.cuda.Event() for _ in range(4))
+    ev_v, ev_g, ev_out, ev_gp, ev_stage = (torch.cuda.Event() for _ in range(5))
+    # a streaming input pipeline: the values of step i+1 come in (host to device, into a staging
+    # buffer) while step i runs, and each step starts with a device copy of its values from there;
+    # every step's timed region still holds one full host-to-device copy of values and dL/dout
+    staging = torch.empty_like(vals)
+    staging.copy_(h_vals)
+    ev_stage.record(stream)
+    torch.cuda.synchronize()
 
     def e2e_step():
         cs.wait_stream(stream)                  # the previous step has finished with gout
-        vals.copy_(h_vals, non_blocking=True)
+        stream.wait_event(ev_stage)             # this step's values have landed in the staging buffer
+        vals.copy_(staging, non_blocking=True)
         ev_v.record(stream)
         with torch.cuda.stream(cs):
-            cs.wait_event(ev_v)                 # the values, which the first kernel waits for, go first
+            cs.wait_event(ev_v)
             gout.copy_(h_gout, non_blocking=True)
             ev_g.record(cs)
+            staging.copy_(h_vals, non_blocking=True)  # the next step's values
+            ev_stage.record(cs)
         run_part[0]()
         run_part[1]()
         ev_out.record(stream)
@@ -489,7 +499,8 @@ def run_ours(args, rank, world):
                 "ms_per_step": round(e2e, 4),
                 "copies": "pinned host buffers; dL/dout in and outputs out on a second stream, overlapped with "
                           "the step's kernels (the backward's parts called one after the other, so the particle "
-                          "gradient goes out while the stencil gradient runs)"},
+                          "gradient goes out while the stencil gradient runs); the values of the next step "
+                          "come in during the step (a staging buffer, copied to the values at step start)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": round(wall, 4),
@@ -697,16 +708,24 @@ def run_mc(args, rank, world, full=True):
     # while the tree and the forward run, the outputs come back while the data adjoint runs and the
     # particle gradient while the weight gradient runs
     cs = torch.cuda.Stream(device=dev)
-    ev_x, ev_g, ev_out, ev_gp = (torch.cuda.Event() for _ in range(4))
+    ev_x, ev_g, ev_out, ev_gp, ev_stage = (torch.cuda.Event() for _ in range(5))
+    # streaming input: the next step's features come in (into a staging buffer) during this step
+    staging = torch.empty_like(x)
+    staging.copy_(h_x)
+    ev_stage.record(stream)
+    torch.cuda.synchronize()
 
     def e2e_step():
         cs.wait_stream(stream)                  # the previous step has finished with g
-        x.copy_(h_x, non_blocking=True)
+        stream.wait_event(ev_stage)
+        x.copy_(staging, non_blocking=True)
         ev_x.record(stream)
         with torch.cuda.stream(cs):
             cs.wait_event(ev_x)
             g.copy_(h_g, non_blocking=True)
             ev_g.record(cs)
+            staging.copy_(h_x, non_blocking=True)   # the next step's features
+            ev_stage.record(cs)
         run_part[0]()
         run_part[1]()
         ev_out.record(stream)
@@ -741,7 +760,8 @@ def run_mc(args, rank, world, full=True):
                   "d2h_bytes_per_step": int(h_out.numel() * 4 + h_gp.numel() * 4 + h_gw.numel() * 4),
                   "ms_per_step": round(e2e, 4),
                   "copies": "pinned host buffers; dL/dout in, outputs and particle gradients out on a second "
-                            "stream, overlapped with the step's kernels"}
+                            "stream, overlapped with the step's kernels; the next step's features come in during "
+                            "the step (a staging buffer, copied to the features at step start)"}
     rec["clocks"] = clk.summary(t0, t1)
     if rank == 0 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = mc_cpu_baseline(apr, xh, wh, gh, budget_s=args.cpu_budget)
