@@ -3,11 +3,13 @@
 // isotropic patch of Sec. 3.5 and the per-level convolution of Sec. 4.1 applied per channel pair.
 //
 // Work decomposition: every convolution work item (an 8 x 8-row, 64-cell tile of one level) is cut
-// into four 4 x 4-row sub-tiles. A CTA stages the sub-tile's patch (radius 1) with 16 channels per
-// cell in shared memory from the segments its tile plan lists (built once per APR by
-// build_mc_plans), lists the target cells, and runs the channel mixing as GEMMs:
+// into four 4 x 4-row sub-tiles; a CTA takes several consecutive sub-tiles of one item. For each it
+// stages the patch (radius 1) with 16 channels per cell in shared memory from the segments its tile
+// plan lists (built once per APR by build_mc_plans), lists the target cells, and runs the channel
+// mixing as GEMMs:
 //   forward      D[target][co] += sum_e A_e[target][ci] W_e[ci][co]     (A_e gathered per tap)
-//   data adjoint D[dest][ci]   += sum_j sum_e G(q_j - e)[co] W_e[co][ci] (q_j: pre-images of dest)
+//   data adjoint D[row][ci]    += sum_e G(q_row - e)[co] W_e[co][ci]    (one row per pre-image q of a
+//                                  destination; each destination sums its rows afterwards)
 //   weights      D[(e,ci)][co] += sum_t U[t][(e,ci)] g_t[co]             (U: im2col of the targets)
 // The gathered A operand of the first two is written to tensor memory with tcgen05.st (one lane
 // per row, 8 columns per tap), B comes from shared memory, D lives in tensor memory. One thread
