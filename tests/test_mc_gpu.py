@@ -25,6 +25,9 @@ CASES = {
     "uniform_coarse": lambda: S.uniform_level_apr((32, 32, 32), 3, l_min=3),
     "tiny": lambda: S.random_balanced_apr((2, 3, 5), 0, seed=9, p_fine=0.3),
     "single": lambda: S.uniform_level_apr((1, 1, 1), 0, l_min=0),
+    # level grids 2 cells wide along z and x: with reflection a coarse particle has up to 4 x 4 x 3
+    # pre-images (two of them here reach more than 32), and the 5^3 mirror lists take the d < 2R path
+    "thin_2x2": lambda: S.random_balanced_apr((2, 2, 40), 0, seed=22, p_fine=0.3),
 }
 
 

@@ -78,6 +78,9 @@ CASES = {
     "single": lambda: S.uniform_level_apr((1, 1, 1), 0, l_min=0),
     "row": lambda: S.random_balanced_apr((1, 1, 200), 0, seed=13, p_fine=0.05),
     "plane": lambda: S.random_balanced_apr((1, 37, 90), 1, seed=14, p_fine=0.03),
+    # level grids 2 cells wide along z and x: with reflection a coarse particle has up to 4 x 4 x 3
+    # pre-images (two of them here reach more than 32), and the 5^3 mirror lists take the d < 2R path
+    "thin_2x2": lambda: S.random_balanced_apr((2, 2, 40), 0, seed=22, p_fine=0.3),
 }
 
 
