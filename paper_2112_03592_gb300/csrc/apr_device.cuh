@@ -52,10 +52,6 @@ __device__ __forceinline__ uint32_t pblock(const DevLayout &L, const LevelGeo &g
     return blk_start(L.row_ptr, L.off, g.row0, g.off0, g.nb, rr, j);
 }
 
-__device__ __forceinline__ uint32_t tblock(const DevLayout &L, const LevelGeo &g, int rr, int j) {
-    return blk_start(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, j);
-}
-
 // Index range [lo, hi) of a row containing every element with y in [ya, yb) (ya < yb), plus at
 // most BY/2 extra elements on each side (callers filter by y). Uses the per-block offsets only:
 // at most BY - ra elements of block ja lie at or after ya, at most rb elements of block jb before yb.
