@@ -25,6 +25,12 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
                                   int n_levels, int K3, float *gw, cudaStream_t s);
 cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
                                  cudaStream_t s);
+cudaError_t launch_conv_fwd_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
+                                  const float *vals, const float *tree, const float *st, int bc, float *out,
+                                  cudaStream_t s, int epi_mode, bool flip, const float *aux);
+cudaError_t launch_bwd_data_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
+                                  const float *st, int bc, const float *gout, float *gp, float *gt, cudaStream_t s);
+cudaError_t launch_radius_hint(const DevLayout &L, const LevelRanges &lo, const float *st, int *hint, cudaStream_t s);
 }  // namespace aprk
 
 using namespace aprk;
@@ -80,6 +86,88 @@ void free_device(apr_handle_s *h) {
 }
 
 bool stencil_k_ok(int32_t k) { return k == 3 || k == 5; }
+
+// Work-item ranges of the levels below l_max (begin: fwd_level_begin or bwd_level_begin).
+LevelRanges lower_levels(const HostIndex &X, const int64_t *begin) {
+    LevelRanges r;
+    r.l0 = X.l_min;
+    r.n = X.l_max - X.l_min;
+    for (int i = 0; i <= r.n; ++i) r.begin[i] = int32_t(begin[X.l_min + i]);
+    return r;
+}
+
+// `side` enqueues work on the handle's split stream, `main` on the caller's stream s: the split
+// stream is forked from s and joined back to it (also when a launch failed, so that a stream capture
+// of s ends joined).
+template <typename Side, typename Main>
+cudaError_t fork_join(apr_handle_t h, cudaStream_t s, Side side, Main main) {
+    std::lock_guard<std::mutex> lock(h->split_mu);
+    cudaError_t e = cudaSuccess;
+    if (!h->split) e = cudaStreamCreateWithFlags(&h->split, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->ev_split_fork) e = cudaEventCreateWithFlags(&h->ev_split_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !h->ev_split_join) e = cudaEventCreateWithFlags(&h->ev_split_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_split_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->split, h->ev_split_fork, 0);
+    if (e != cudaSuccess) return e;
+    const cudaError_t e_side = side(h->split);
+    const cudaError_t e_main = main(s);
+    e = cudaEventRecord(h->ev_split_join, h->split);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_split_join, 0);
+    return e_side != cudaSuccess ? e_side : e_main != cudaSuccess ? e_main : e;
+}
+
+// Whether the last radius-split or hinted call of kind `which` (0 convolution, 1 data adjoint) saw a
+// level below l_max with taps outside the central 3^3 (read without waiting: it may be older).
+bool outer_taps_seen(apr_handle_t h, int which) {
+    return static_cast<volatile const int *>(h->h_hint)[which] != 0;
+}
+
+// apr_convolve over the whole forward work list (with the Richardson-Lucy epilogues). For k = 5 the
+// levels below l_max run split by radius on the split stream (launch_conv_fwd_split) beside the l_max
+// tiles, unless the last call's stack had taps outside the central 3^3 below l_max: then one launch
+// over all items, with the hint refreshed beside it. Either way every tile is computed the same way.
+cudaError_t conv_fwd_all(apr_handle_t h, int k, const float *vals, const float *tree, const float *st, int bc,
+                         float *out, cudaStream_t s, int epi_mode = EPI_PLAIN, bool flip = false,
+                         const float *aux = nullptr) {
+    const HostIndex &X = h->X;
+    const int n = int(X.fwd_items.size()), n_lo = int(X.fwd_level_begin[X.l_max]);
+    if (k != 5 || n_lo == 0)
+        return launch_conv_fwd(k, h->L, h->d_fwd, n, vals, tree, st, bc, out, s, epi_mode, flip, aux);
+    const LevelRanges lo = lower_levels(X, X.fwd_level_begin);
+    if (outer_taps_seen(h, 0))
+        return fork_join(
+            h, s, [&](cudaStream_t side) { return launch_radius_hint(h->L, lo, st, h->d_hint, side); },
+            [&](cudaStream_t main) { return launch_conv_fwd(k, h->L, h->d_fwd, n, vals, tree, st, bc, out, main, epi_mode, flip, aux); });
+    return fork_join(
+        h, s,
+        [&](cudaStream_t side) {
+            return launch_conv_fwd_split(h->L, h->d_fwd, n_lo, lo, h->d_hint, vals, tree, st, bc, out, side, epi_mode,
+                                         flip, aux);
+        },
+        [&](cudaStream_t main) {
+            return launch_conv_fwd(k, h->L, h->d_fwd, n - n_lo, vals, tree, st, bc, out, main, epi_mode, flip, aux, n_lo);
+        });
+}
+
+// The data adjoint over the whole adjoint work list; with `split`, k = 5 chooses its launches like
+// conv_fwd_all.
+cudaError_t bwd_data_all(apr_handle_t h, int k, const float *st, int bc, const float *gout, float *gp, float *gt,
+                         cudaStream_t s, bool split) {
+    const HostIndex &X = h->X;
+    const int n = int(X.bwd_items.size()), n_lo = int(X.bwd_level_begin[X.l_max]);
+    if (!split || k != 5 || n_lo == 0) return launch_bwd_data(k, h->L, h->d_bwd, n, st, bc, gout, gp, gt, s);
+    const LevelRanges lo = lower_levels(X, X.bwd_level_begin);
+    if (outer_taps_seen(h, 1))
+        return fork_join(
+            h, s, [&](cudaStream_t side) { return launch_radius_hint(h->L, lo, st, h->d_hint + 1, side); },
+            [&](cudaStream_t main) { return launch_bwd_data(k, h->L, h->d_bwd, n, st, bc, gout, gp, gt, main); });
+    return fork_join(
+        h, s,
+        [&](cudaStream_t side) {
+            return launch_bwd_data_split(h->L, h->d_bwd, n_lo, lo, h->d_hint + 1, st, bc, gout, gp, gt, side);
+        },
+        [&](cudaStream_t main) { return launch_bwd_data(k, h->L, h->d_bwd, n - n_lo, st, bc, gout, gp, gt, main, n_lo); });
+}
 
 apr_status_t misaligned() {
     aprk::set_last_message("staged value arrays (particles, tree values) must be 16-byte aligned");
@@ -200,6 +288,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
             h->d_err = static_cast<unsigned *>(p);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), reinterpret_cast<cudaStream_t>(stream));
         }
+
         if (e == cudaSuccess) {
             // operand-layout copy of multi-channel weights: [2 (plain, transposed)][levels][27 * 16 * 16]
             const size_t nb = size_t(2) * size_t(X.l_max - X.l_min + 1) * 27 * 16 * 16 * sizeof(uint16_t);
@@ -242,6 +331,24 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         h->X.mcfplan = HostPlan{};
         h->X.mcbplan = HostPlan{};
         h->X.tplan = std::vector<TreePlan>{};
+        // the second streams of apr_convolve_backward and of the radius split, and their events, are
+        // made here, so that no later call creates them inside a stream capture
+        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->split, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_split_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_split_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&h->h_hint), 2 * sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            h->h_hint[0] = h->h_hint[1] = 0;
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->d_hint), h->h_hint, 0);
+        }
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            apr_destroy(h);
+            return st;
+        }
     }
     *out = h;
     return APR_OK;
@@ -255,6 +362,10 @@ apr_status_t apr_destroy(apr_handle_t h) {
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
         if (h->side) cudaStreamDestroy(h->side);
+        if (h->ev_split_fork) cudaEventDestroy(h->ev_split_fork);
+        if (h->ev_split_join) cudaEventDestroy(h->ev_split_join);
+        if (h->split) cudaStreamDestroy(h->split);
+        if (h->h_hint) cudaFreeHost(h->h_hint);
     }
     delete h;
     return APR_OK;
@@ -338,8 +449,7 @@ apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *t
     if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
     if (!stencils || (h->X.np && (!particles || !out)) || (h->X.nt && !tree)) return APR_ERR_INVALID_ARG;
     if (!aligned16(particles) || !aligned16(tree)) return misaligned();
-    const int n = int(h->X.fwd_items.size());
-    return cuda_status(launch_conv_fwd(k, h->L, h->d_fwd, n, particles, tree, stencils, bc, out, stream));
+    return cuda_status(conv_fwd_all(h, k, particles, tree, stencils, bc, out, stream));
 }
 
 apr_status_t apr_convolve_tiles(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
@@ -405,17 +515,7 @@ size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k) {
 
 apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                   float *grad_particles, float *grad_tree, apr_stream_t stream) {
-    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
-    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
-    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
-    const HostIndex &X = h->X;
-    if (!stencils || (X.np && (!grad_out || !grad_particles)) || (X.nt && !grad_tree)) return APR_ERR_INVALID_ARG;
-    cudaError_t e = cudaSuccess;
-    if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * sizeof(float), stream);
-    if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(grad_tree, 0, size_t(X.nt) * sizeof(float), stream);
-    if (e == cudaSuccess)
-        e = launch_bwd_data(k, h->L, h->d_bwd, int(X.bwd_items.size()), stencils, bc, grad_out, grad_particles, grad_tree, stream);
-    return cuda_status(e);
+    return aprk::convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, grad_tree, stream, true);
 }
 
 apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *grad_particles, apr_stream_t stream) {
@@ -457,6 +557,21 @@ apr_status_t apr_convolve_stencil_grad(apr_handle_t h, const float *particles, c
 }  // extern "C"
 
 namespace aprk {
+apr_status_t convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                              float *grad_particles, float *grad_tree, apr_stream_t stream, bool split) {
+    if (!h || h->host_only) return APR_ERR_INVALID_ARG;
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    const HostIndex &X = h->X;
+    if (!stencils || (X.np && (!grad_out || !grad_particles)) || (X.nt && !grad_tree)) return APR_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (X.np) e = cudaMemsetAsync(grad_particles, 0, size_t(X.np) * sizeof(float), stream);
+    if (e == cudaSuccess && X.nt) e = cudaMemsetAsync(grad_tree, 0, size_t(X.nt) * sizeof(float), stream);
+    if (e == cudaSuccess)
+        e = bwd_data_all(h, k, stencils, bc, grad_out, grad_particles, grad_tree, stream, split);
+    return cuda_status(e);
+}
+
 apr_status_t convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                                int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
                                float *grad_stencils, void *workspace, size_t workspace_bytes, apr_stream_t stream,
@@ -488,7 +603,7 @@ apr_status_t convolve_backward(apr_handle_t h, const float *particles, const flo
         if (e != cudaSuccess) return cuda_status(e);
         const apr_status_t sg = apr_convolve_stencil_grad(h, particles, tree, k, bc, grad_out, grad_stencils, partial,
                                                           workspace_bytes - gt_bytes, reinterpret_cast<apr_stream_t>(h->side));
-        st = apr_convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream);
+        st = convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream, true);
         if (st == APR_OK) st = apr_tree_restrict_adjoint(h, gt, grad_particles, stream);
         // always joined, so that a stream capture of the caller's stream ends joined
         e = cudaEventRecord(h->ev_join, h->side);
@@ -498,7 +613,7 @@ apr_status_t convolve_backward(apr_handle_t h, const float *particles, const flo
         return st;
     }
     if (grad_particles) {
-        st = apr_convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream);
+        st = convolve_adjoint(h, stencils, k, bc, grad_out, grad_particles, gt, stream, concurrent);
         if (st == APR_OK) st = apr_tree_restrict_adjoint(h, gt, grad_particles, stream);
     }
     if (st == APR_OK && grad_stencils)
@@ -538,18 +653,15 @@ apr_status_t apr_richardson_lucy(apr_handle_t h, const float *observed, const fl
         return APR_ERR_INVALID_ARG;
     float *tree = static_cast<float *>(workspace);
     float *ratio = reinterpret_cast<float *>(static_cast<char *>(workspace) + (size_t(X.nt) * sizeof(float) + 255) / 256 * 256);
-    const int n = int(X.fwd_items.size());
     for (int it = 0; it < n_iter; ++it) {
         // ratio = u / (i_k conv w); i_{k+1} = i_k * (ratio conv w_flipped)
         apr_status_t st = apr_tree_restrict(h, estimate, tree, 1, stream);
         if (st != APR_OK) return st;
-        cudaError_t e = launch_conv_fwd(k, h->L, h->d_fwd, n, estimate, tree, stencils, bc, ratio, stream, EPI_DIVIDE,
-                                        false, observed);
+        cudaError_t e = conv_fwd_all(h, k, estimate, tree, stencils, bc, ratio, stream, EPI_DIVIDE, false, observed);
         if (e != cudaSuccess) return cuda_status(e);
         st = apr_tree_restrict(h, ratio, tree, 1, stream);
         if (st != APR_OK) return st;
-        e = launch_conv_fwd(k, h->L, h->d_fwd, n, ratio, tree, stencils, bc, estimate, stream, EPI_MULTIPLY, true,
-                            estimate);
+        e = conv_fwd_all(h, k, ratio, tree, stencils, bc, estimate, stream, EPI_MULTIPLY, true, estimate);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return APR_OK;

@@ -222,6 +222,7 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &X,
     std::vector<uint8_t> occ, near;
     for (int l = L.l_min; l <= L.l_max; ++l) {
         X.fwd_level_begin[l] = int64_t(X.fwd_items.size());
+        X.bwd_level_begin[l] = int64_t(X.bwd_items.size());
         const LevelGeo &g = X.geo[l];
         const int32_t ntz = (g.dz + TZ - 1) / TZ, ntx = (g.dx + TX - 1) / TX;
         occ.assign(size_t(ntz) * ntx * g.nb, 0);
@@ -248,7 +249,11 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &X,
                 }
     }
     X.fwd_level_begin[L.l_max + 1] = int64_t(X.fwd_items.size());
-    for (int l = L.l_max + 2; l <= MAXL; ++l) X.fwd_level_begin[l] = X.fwd_level_begin[L.l_max + 1];
+    X.bwd_level_begin[L.l_max + 1] = int64_t(X.bwd_items.size());
+    for (int l = L.l_max + 2; l <= MAXL; ++l) {
+        X.fwd_level_begin[l] = X.fwd_level_begin[L.l_max + 1];
+        X.bwd_level_begin[l] = X.bwd_level_begin[L.l_max + 1];
+    }
 
     // tree bricks: (l, z, x, yb) holding at least one tree node
     X.tree_items.clear();

@@ -107,11 +107,19 @@ struct HostIndex {
     std::vector<Item> bwd_items;              // tiles whose interior cells receive gradient
     std::vector<Item> tree_items;             // non-empty (l, z, x, yb) tree bricks, by level
     int64_t fwd_level_begin[MAXL + 1] = {};   // fwd_items of level l: [begin[l], begin[l+1])
+    int64_t bwd_level_begin[MAXL + 1] = {};   // bwd_items of level l: [begin[l], begin[l+1])
     int64_t tree_level_begin[MAXL + 1] = {};
     HostFPlan fplan[2];                       // forward tile plans (build_plans), radius 1 and 2
     HostFPlan bplan[2];                       // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
     std::vector<TreePlan> tplan;              // tree bricks (tree_plan)
+};
+
+// Work items of the consecutive levels l0 .. l0 + n - 1: level l0 + i owns items [begin[i], begin[i + 1])
+// (passed to kernels by value).
+struct LevelRanges {
+    int32_t l0 = 0, n = 0;
+    int32_t begin[MAXL + 1] = {};
 };
 
 // Builds and validates the index from the host layout. Returns APR_OK or an error code; `msg`
@@ -125,7 +133,11 @@ apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
 bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
 bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P);
-// apr_convolve_backward; concurrent: the stencil gradient on the handle's second stream
+// apr_convolve_adjoint; split: a 5^3 stack's levels below l_max on the handle's split stream
+apr_status_t convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
+                              float *grad_particles, float *grad_tree, apr_stream_t stream, bool split);
+// apr_convolve_backward; concurrent: the stencil gradient on the handle's second stream and the
+// data adjoint split by radius
 apr_status_t convolve_backward(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                                int32_t k, int32_t bc, const float *grad_out, float *grad_particles,
                                float *grad_stencils, void *workspace, size_t workspace_bytes, apr_stream_t stream,
@@ -184,4 +196,14 @@ struct apr_handle_s {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::mutex side_mu;
+    // a 5^3 convolution or data adjoint over the whole work list runs its radius-1 tiles of the
+    // levels below l_max on this stream, beside the l_max tiles on the caller's stream (split_mu
+    // orders the enqueues; taken after side_mu where both are held)
+    cudaStream_t split = nullptr;
+    cudaEvent_t ev_split_fork = nullptr, ev_split_join = nullptr;
+    std::mutex split_mu;
+    // whether the last such call saw a level below l_max with taps outside the central 3^3 ([0]
+    // convolution, [1] data adjoint): mapped host memory that the kernels write and the host reads to
+    // choose the next call's launches (h_hint host view, d_hint device view)
+    int *h_hint = nullptr, *d_hint = nullptr;
 };

@@ -16,6 +16,7 @@
 // loads. A 5^3 stack whose level has zero taps outside the central 3^3 is applied with radius 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -43,6 +44,45 @@ __device__ __forceinline__ bool outer_taps_zero5(const float *__restrict__ stenc
         nz = outer && stencils[l_idx * 125 + t] != 0.f;
     }
     return __syncthreads_or(nz) == 0;
+}
+
+// Bit i set: level l_idx0 + i of a 5^3 stack has a nonzero tap outside the central 3^3 (block-wide;
+// uses the shared-memory word `word`, free again on return).
+__device__ __forceinline__ unsigned levels_with_outer_taps(const float *__restrict__ stencils, int l_idx0, int n,
+                                                           unsigned *word) {
+    const int t = threadIdx.x;
+    unsigned m = 0u;
+    if (t < 125) {
+        const int a = t / 25, b = (t / 5) % 5, c = t % 5;
+        if (a == 0 || a == 4 || b == 0 || b == 4 || c == 0 || c == 4)
+            for (int i = 0; i < n; ++i)
+                if (stencils[(l_idx0 + i) * 125 + t] != 0.f) m |= 1u << i;
+    }
+    if (t == 0) *word = 0u;
+    __syncthreads();
+    if (m) atomicOr(word, m);
+    __syncthreads();
+    m = *word;
+    __syncthreads();
+    return m;
+}
+
+// The levels of lr selected by `sel` (bit i: level lr.l0 + i): their work-item count, and their j-th
+// work item in level order.
+__device__ __forceinline__ int selected_count(const LevelRanges &lr, unsigned sel) {
+    int c = 0;
+    for (int i = 0; i < lr.n; ++i)
+        if ((sel >> i) & 1u) c += lr.begin[i + 1] - lr.begin[i];
+    return c;
+}
+__device__ __forceinline__ int selected_item(const LevelRanges &lr, unsigned sel, int j) {
+    for (int i = 0; i < lr.n; ++i) {
+        if (!((sel >> i) & 1u)) continue;
+        const int c = lr.begin[i + 1] - lr.begin[i];
+        if (j < c) return lr.begin[i] + j;
+        j -= c;
+    }
+    return -1;
 }
 
 // c itself (self) and, with reflection, the positions v in [-R, d + R) outside [0, d) that reflect
@@ -508,7 +548,7 @@ __device__ __forceinline__ void conv_fwd_tile(const DevLayout &L, const Item &it
 }
 
 template <int R>
-__global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, R == 1 ? 5 : 4) conv_fwd_kernel(const DevLayout L, const Item *__restrict__ items,
                                                          int tile0, const float *__restrict__ vals,
                                                          const float *__restrict__ tree,
                                                          const float *__restrict__ stencils, int bc,
@@ -531,11 +571,53 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_kernel(const DevLayout L, cons
     }
 }
 
+// A 5^3 convolution over the whole work list, split by radius. The levels below l_max of a
+// restricted stack have no taps outside the central 3^3 (Eq. restrict_stenc); their tiles run in a
+// launch of their own with radius-1 shared memory and registers, five blocks per SM instead of the
+// radius-2 launch's four, beside the launch over the l_max tiles.
+// First part: items [0, gridDim.x) (the levels below l_max) as radius-1 tiles. A tile of a level with
+// outer taps returns at once; conv_fwd_r2_pool_kernel takes it.
+__global__ void __launch_bounds__(NT, 5) conv_fwd_r1_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                            const float *__restrict__ vals,
+                                                            const float *__restrict__ tree,
+                                                            const float *__restrict__ stencils, int bc, float *out,
+                                                            const Epilogue epi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = int(blockIdx.x);
+    const Item it = items[tile];
+    if (!outer_taps_zero5(stencils, it.l - L.l_min)) return;
+    const PlanHdr h1 = plan_hdr(L.fplan[0], tile);
+    conv_fwd_tile<1, 2>(L, it, plan_pre(L.fplan[0], h1, h1.count), vals, tree, stencils, bc, out, epi, smem_raw);
+}
+
+// Second part: the tiles of the levels in lr (those below l_max) whose taps reach outside the
+// central 3^3 (none for a restricted stack), as radius-2 tiles in a persistent grid, each block
+// taking every gridDim.x-th of them. Block 0 records in *hint whether there were any.
+__global__ void __launch_bounds__(NT, 4) conv_fwd_r2_pool_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                                 const LevelRanges lr, int *hint,
+                                                                 const float *__restrict__ vals,
+                                                                 const float *__restrict__ tree,
+                                                                 const float *__restrict__ stencils, int bc,
+                                                                 float *out, const Epilogue epi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned sel = levels_with_outer_taps(stencils, lr.l0 - L.l_min, lr.n, reinterpret_cast<unsigned *>(smem_raw));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hint = sel != 0u;
+    const int total = selected_count(lr, sel);
+#pragma unroll 1
+    for (int j = int(blockIdx.x); j < total; j += int(gridDim.x)) {
+        const int tile = selected_item(lr, sel, j);
+        const Item it = items[tile];
+        const PlanHdr h2 = plan_hdr(L.fplan[1], tile);
+        conv_fwd_tile<2, 2>(L, it, plan_pre(L.fplan[1], h2, h2.count), vals, tree, stencils, bc, out, epi, smem_raw);
+        __syncthreads();   // the next tile reuses the shared memory
+    }
+}
+
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
 // out[p] = sqrt(sum_a (w_a (*) u)_p^2) for three stencil stacks w_a (a = z, x, y) on one staged
 // patch; each window's three sums are taken by the same two lanes in turn.
 template <int R>
-__global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, R == 1 ? 5 : 4) conv_gradmag_kernel(const DevLayout L, const Item *__restrict__ items,
                                                              const float *__restrict__ vals,
                                                              const float *__restrict__ tree,
                                                              const float *__restrict__ stencils, int bc,
@@ -600,7 +682,7 @@ __global__ void __launch_bounds__(NT, 4) conv_gradmag_kernel(const DevLayout L, 
 // u_l(p + e) (fixed order); stencil_grad_reduce_kernel then sums the items of every level.
 // ------------------------------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, 4) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, R == 1 ? 5 : 4) conv_bwd_stencil_kernel(const DevLayout L, const Item *__restrict__ items,
                                                                  int n_items, const float *__restrict__ vals,
                                                                  const float *__restrict__ tree, int bc,
                                                                  const float *__restrict__ gout,
@@ -720,7 +802,9 @@ struct BwdSmem {
     unsigned short act[NIW];
     unsigned short pseg[PCAP];
     int roff[G::NPAIR];                        // stencil-row offsets in the patch (fill_row_offsets)
-    static constexpr int RCAP = 320;           // routing packets whose y values are kept from the staging pass
+    // routing packets whose y values are kept from the staging pass (radius 1: fewer, so that four
+    // blocks share an SM)
+    static constexpr int RCAP = R == 1 ? 150 : 320;
     uint4 rstash[RCAP];
     int nact;
 };
@@ -1122,7 +1206,7 @@ __device__ __forceinline__ void conv_bwd_data_tile(const DevLayout &L, const Ite
 }
 
 template <int R>
-__global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
+__global__ void __launch_bounds__(NT, R == 1 ? 4 : 3) conv_bwd_data_kernel(const DevLayout L, const Item *__restrict__ items,
                                                               int tile0, const float *__restrict__ stencils, int bc,
                                                               const float *__restrict__ gout,
                                                               float *__restrict__ gp, float *__restrict__ gt) {
@@ -1142,6 +1226,50 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_kernel(const DevLayout L,
     } else {
         conv_bwd_data_tile<R, R>(L, it, plan_pre(L.bplan[0], h1, bplan_count(h1)), stencils, bc, gout, gp, gt, smem_raw);
     }
+}
+
+// The data adjoint of a 5^3 stack over the whole work list, split by radius like the convolution:
+// radius-1 tiles of the levels below l_max (items [0, gridDim.x)) with radius-1 shared memory, four
+// blocks per SM instead of three; tiles of a level with outer taps return at once.
+__global__ void __launch_bounds__(NT, 4) conv_bwd_data_r1_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                                 const float *__restrict__ stencils, int bc,
+                                                                 const float *__restrict__ gout,
+                                                                 float *__restrict__ gp, float *__restrict__ gt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = int(blockIdx.x);
+    const Item it = items[tile];
+    if (!outer_taps_zero5(stencils, it.l - L.l_min)) return;
+    const PlanHdr h1 = plan_hdr(L.bplan[0], tile);
+    conv_bwd_data_tile<1, 2>(L, it, plan_pre(L.bplan[0], h1, bplan_count(h1)), stencils, bc, gout, gp, gt, smem_raw);
+}
+
+// ... and the tiles of the levels in lr whose taps reach outside the central 3^3, as radius-2 tiles
+// in a persistent grid (block 0 records in *hint whether there were any).
+__global__ void __launch_bounds__(NT, 3) conv_bwd_data_r2_pool_kernel(const DevLayout L, const Item *__restrict__ items,
+                                                                      const LevelRanges lr, int *hint,
+                                                                      const float *__restrict__ stencils, int bc,
+                                                                      const float *__restrict__ gout,
+                                                                      float *__restrict__ gp, float *__restrict__ gt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned sel = levels_with_outer_taps(stencils, lr.l0 - L.l_min, lr.n, reinterpret_cast<unsigned *>(smem_raw));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hint = sel != 0u;
+    const int total = selected_count(lr, sel);
+#pragma unroll 1
+    for (int j = int(blockIdx.x); j < total; j += int(gridDim.x)) {
+        const int tile = selected_item(lr, sel, j);
+        const Item it = items[tile];
+        const PlanHdr h2 = plan_hdr(L.bplan[1], tile);
+        conv_bwd_data_tile<2, 2>(L, it, plan_pre(L.bplan[1], h2, bplan_count(h2)), stencils, bc, gout, gp, gt, smem_raw);
+        __syncthreads();   // the next tile reuses the shared memory
+    }
+}
+
+// Records in *hint whether a level in lr of a 5^3 stack has taps outside the central 3^3 (one block).
+__global__ void __launch_bounds__(NT) radius_hint_kernel(const float *__restrict__ stencils, int l_idx0, int n,
+                                                         int *hint) {
+    __shared__ unsigned word;
+    const unsigned sel = levels_with_outer_taps(stencils, l_idx0, n, &word);
+    if (threadIdx.x == 0) *hint = sel != 0u;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1257,6 +1385,9 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
 static_assert(4 * (sizeof(FwdSmem<2, 1>) + 1024) <= 228 * 1024, "forward: four blocks per SM");
 static_assert(4 * (sizeof(FwdSmem<2, 3>) + 1024) <= 228 * 1024, "gradient magnitude: four blocks per SM");
 static_assert(3 * (sizeof(BwdSmem<2>) + 1024) <= 228 * 1024, "data adjoint: three blocks per SM");
+static_assert(5 * (sizeof(FwdSmem<1, 1>) + 1024) <= 228 * 1024, "radius-1 forward: five blocks per SM");
+static_assert(5 * (sizeof(FwdSmem<1, 3>) + 1024) <= 228 * 1024, "radius-1 gradient magnitude: five blocks per SM");
+static_assert(4 * (sizeof(BwdSmem<1>) + 1024) <= 228 * 1024, "radius-1 data adjoint: four blocks per SM");
 static_assert(sizeof(FwdSmem<1, 1>) <= sizeof(FwdSmem<2, 1>) && sizeof(BwdSmem<1>) <= sizeof(BwdSmem<2>),
               "radius-1 tiles run inside the radius-2 launch");
 
@@ -1291,6 +1422,14 @@ cudaError_t launch_bwd_stencil_t(const DevLayout &L, const Item *items, int n, c
     if (e != cudaSuccess) return e;
     if (n > 0) conv_bwd_stencil_kernel<R><<<n, NT, sm, s>>>(L, items, n, vals, tree, bc, gout, partial);
     return cudaGetLastError();
+}
+
+// Streaming multiprocessors of the current device (the persistent grids take a multiple of it).
+cudaError_t sm_count(int *n) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev);
+    return e;
 }
 
 }  // namespace
@@ -1330,6 +1469,47 @@ cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n,
                             const float *gout, float *gp, float *gt, cudaStream_t s, int tile0) {
     return k == 3 ? launch_bwd_data_t<1>(L, items, tile0, n, st, bc, gout, gp, gt, s)
                   : launch_bwd_data_t<2>(L, items, tile0, n, st, bc, gout, gp, gt, s);
+}
+
+// The levels-below-l_max part of a 5^3 convolution (items [0, n_lo), level ranges lo), both launches
+// on stream s: radius-1 tiles, then the persistent radius-2 launch for levels with outer taps, which
+// writes *hint (see launch_radius_hint).
+cudaError_t launch_conv_fwd_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
+                                  const float *vals, const float *tree, const float *st, int bc, float *out,
+                                  cudaStream_t s, int epi_mode, bool flip, const float *aux) {
+    if (n_lo <= 0) return cudaSuccess;
+    const Epilogue epi{epi_mode, flip, aux};
+    const size_t sm1 = sizeof(FwdSmem<1, 1>), sm2 = sizeof(FwdSmem<2, 1>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_fwd_r1_kernel), sm1);
+    if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void *>(conv_fwd_r2_pool_kernel), sm2);
+    int nsm = 0;
+    if (e == cudaSuccess) e = sm_count(&nsm);
+    if (e != cudaSuccess) return e;
+    conv_fwd_r1_kernel<<<n_lo, NT, sm1, s>>>(L, items, vals, tree, st, bc, out, epi);
+    conv_fwd_r2_pool_kernel<<<std::min(n_lo, 4 * nsm), NT, sm2, s>>>(L, items, lo, hint, vals, tree, st, bc, out, epi);
+    return cudaGetLastError();
+}
+
+// The same for the data adjoint (items [0, n_lo) of the adjoint work list).
+cudaError_t launch_bwd_data_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
+                                  const float *st, int bc, const float *gout, float *gp, float *gt, cudaStream_t s) {
+    if (n_lo <= 0) return cudaSuccess;
+    const size_t sm1 = sizeof(BwdSmem<1>), sm2 = sizeof(BwdSmem<2>);
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(conv_bwd_data_r1_kernel), sm1);
+    if (e == cudaSuccess) e = set_smem(reinterpret_cast<const void *>(conv_bwd_data_r2_pool_kernel), sm2);
+    int nsm = 0;
+    if (e == cudaSuccess) e = sm_count(&nsm);
+    if (e != cudaSuccess) return e;
+    conv_bwd_data_r1_kernel<<<n_lo, NT, sm1, s>>>(L, items, st, bc, gout, gp, gt);
+    conv_bwd_data_r2_pool_kernel<<<std::min(n_lo, 3 * nsm), NT, sm2, s>>>(L, items, lo, hint, st, bc, gout, gp, gt);
+    return cudaGetLastError();
+}
+
+// *hint = whether a level of lo (a 5^3 stack) has taps outside the central 3^3: the radius split
+// pays off only when none has, and the next call reads the hint to choose.
+cudaError_t launch_radius_hint(const DevLayout &L, const LevelRanges &lo, const float *st, int *hint, cudaStream_t s) {
+    radius_hint_kernel<<<1, NT, 0, s>>>(st, lo.l0 - L.l_min, lo.n, hint);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int n, const float *vals,
