@@ -116,9 +116,9 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel sources are
-    unchanged since that capture (sha1 prefix match); else None."""
+def recorded_traffic(call):
+    """DRAM bytes of one call of `call` (the sum over its launches) from the committed ncu summary,
+    if the kernel sources are unchanged since that capture (sha1 prefix match); else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
@@ -127,7 +127,21 @@ def recorded_traffic(kernel):
         return None
     if sha != rec.get("sha1_prefix"):
         return None
-    return rec.get("dram_bytes_per_launch", {}).get(kernel)
+    return rec.get("dram_bytes_per_call", {}).get(call)
+
+
+def conv_launches(apr, st_h, k):
+    """Kernels of one apr_convolve (or apr_convolve_adjoint) call on the whole work list: for k = 5
+    with levels below l_max, three when no such level has taps outside the central 3^3 (radius-1
+    launch, persistent radius-2 launch, l_max launch), else two (one launch over all tiles and the
+    hint kernel beside it); otherwise one."""
+    import numpy as np
+    if k != 5 or apr.l_max == apr.l_min:
+        return 1
+    w = np.asarray(st_h, np.float32).reshape(apr.n_levels, 5, 5, 5)[:-1]
+    outer = w.copy()
+    outer[:, 1:4, 1:4, 1:4] = 0
+    return 2 if np.any(outer != 0) else 3
 
 
 def make_replayers(fns, use_graph):
@@ -444,13 +458,19 @@ def run_ours(args, rank, world):
     # our kernels per step: restriction (one per level holding tree nodes), convolution, convolution
     # adjoint, push-down (one per level holding tree nodes), stencil-gradient partials, reduction
     n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
-    launches_per_step = n_tree_levels + 1 + 1 + n_tree_levels + 2
-    # the dominant kernel of the step: the convolution adjoint (one kernel; its call also clears the
-    # two gradient outputs with cudaMemsetAsync). Its algorithmic bytes equal the forward's: dL/dout
-    # in, dL/dparticles and dL/dtree out, y indices and row pointers.
-    dom_ms, dom_kernel = (adj_ms, "conv_bwd_data_kernel<2>") if adj_ms >= conv_ms else (conv_ms, "conv_fwd_kernel<2>")
-    dom_name = dom_kernel + (" (apr_convolve_adjoint)" if dom_kernel.startswith("conv_bwd") else " (apr_convolve)")
-    traffic = recorded_traffic(dom_kernel)
+    nc = conv_launches(apr, st_h, K)
+    launches_per_step = n_tree_levels + nc + nc + n_tree_levels + 2
+    # the dominant call of the step: the convolution adjoint (its radius-1 tiles in one launch on the
+    # library's second stream beside the launch over the l_max tiles; the call also clears the two
+    # gradient outputs). Its algorithmic bytes equal the forward's: dL/dout in, dL/dparticles and
+    # dL/dtree out, y indices and row pointers.
+    dom_ms, dom_call = (adj_ms, "apr_convolve_adjoint") if adj_ms >= conv_ms else (conv_ms, "apr_convolve")
+    dom_name = dom_call + (": conv_bwd_data_r1_kernel (levels below l_max, radius 1) beside conv_bwd_data_kernel<2> "
+                           "(l_max), conv_bwd_data_r2_pool_kernel after the radius-1 launch"
+                           if dom_call == "apr_convolve_adjoint" else
+                           ": conv_fwd_r1_kernel (levels below l_max, radius 1) beside conv_fwd_kernel<2> (l_max), "
+                           "conv_fwd_r2_pool_kernel after the radius-1 launch")
+    traffic = recorded_traffic(dom_call)
     rec = {
         "metric": "APR conv Gparticles/s & pixel-equiv GB/s",
         "value": round(world * Np / (step_ms * 1e-3) / 1e9, 4),
@@ -490,9 +510,11 @@ def run_ours(args, rank, world):
         "roofline": {"kernel": dom_name, "bound": "hbm",
                      "achieved": round(conv_bytes / (dom_ms * 1e-3) / 1e9, 2), "peak": hbm,
                      "unit": "GB/s", "frac": round(conv_bytes / (dom_ms * 1e-3) / 1e9 / hbm, 4),
-                     "traffic": traffic, "traffic_source": "profiles/traffic.json (ncu dram bytes, same source)"
-                     if traffic else None, "peak_source": src + " (hbm_gbs, copy bandwidth)",
+                     "traffic": traffic, "traffic_source": "profiles/traffic.json (ncu dram bytes of the call's "
+                     "launches, same source)" if traffic else None, "peak_source": src + " (hbm_gbs, copy bandwidth)",
                      "algorithmic_bytes_per_launch": conv_bytes,
+                     "per_launch": "per call: algorithmic bytes of the whole call / the call's event time (its "
+                                   "launches on two streams, joined)",
                      "convolve_frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4)},
         "e2e": {"value": round(world * Np / (e2e * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
                 "h2d_bytes_per_step": T["h2d"], "d2h_bytes_per_step": T["d2h"],
@@ -513,7 +535,9 @@ def run_ours(args, rank, world):
         st_plain = torch.as_tensor(np.repeat(w.reshape(1, -1), apr.n_levels, 0), device=dev).contiguous()
         P = layer_step(args, lay, st_plain, bufs, dev, stream, flush, world)
         pp = [mean(v) for v in P["parts"]]
-        p_dom_ms, p_dom = (pp[2], "conv_bwd_data_kernel<2>") if pp[2] >= pp[1] else (pp[1], "conv_fwd_kernel<2>")
+        p_dom_ms, p_dom = ((pp[2], "conv_bwd_data_kernel<2> (apr_convolve_adjoint: one launch over all tiles)")
+                           if pp[2] >= pp[1] else (pp[1], "conv_fwd_kernel<2> (apr_convolve: one launch over all tiles)"))
+        npc = conv_launches(apr, st_plain.cpu().numpy(), K)
         rec["plain5"] = {
             "value": round(world * Np / (P["step_ms"] * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
             "ms_per_step": round(P["step_ms"], 5),
@@ -528,7 +552,7 @@ def run_ours(args, rank, world):
                          "algorithmic_bytes_per_launch": conv_bytes, "peak_source": src + " (hbm_gbs)"},
             "e2e": {"value": round(world * Np / (P["e2e_ms"] * 1e-3) / 1e9, 4), "unit": "Gparticles/s",
                     "h2d_bytes_per_step": P["h2d"], "d2h_bytes_per_step": P["d2h"], "ms_per_step": round(P["e2e_ms"], 4)},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": (2 * n_tree_levels + 2 * npc + 2) * args.steps,
         }
     if rank == 0 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(apr, st_h, gout.cpu().numpy(), budget_s=args.cpu_budget)
@@ -884,12 +908,13 @@ def run_rl(args, rank, world, full=True):
                    "l2": "flushed before every step (512 MB write, outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "pixel_equiv_GBps_per_conv": round(pix * 4 * 2 * RL_ITERS / (step_ms * 1e-3) / 1e9, 2),
-        "roofline": {"kernel": "conv_fwd_kernel<2> (apr_convolve, one launch timed alone)", "bound": "hbm",
+        "roofline": {"kernel": "apr_convolve (one call timed alone: conv_fwd_r1_kernel beside conv_fwd_kernel<2>, "
+                               "conv_fwd_r2_pool_kernel)", "bound": "hbm",
                      "achieved": round(conv_bytes / (conv_ms * 1e-3) / 1e9, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(conv_bytes / (conv_ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
                      "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": conv_bytes,
                      "conv_ms": round(conv_ms, 5)},
-        "gpu_launches": RL_ITERS * 2 * (n_tree_levels + 1) * args.steps,
+        "gpu_launches": RL_ITERS * 2 * (n_tree_levels + conv_launches(apr, st_h, K)) * args.steps,
     }
     if not full:
         return rec
@@ -1061,7 +1086,8 @@ def run_surrogate(args, rank, world, pretrained=None):
                      "data_s": round(t_data, 1), "train_s": round(t_train, 1)},
         # per CNN inference: embedding, 4 x (tree restriction per level, weight layout, convolution;
         # hidden ReLUs fused into the convolution), read-out; per RL run: 2 x (tree + convolution) per iteration
-        "gpu_launches": (2 + 4 * (n_tree_levels + 2) + RL_ITERS * 2 * (n_tree_levels + 1)) * args.steps,
+        "gpu_launches": (2 + 4 * (n_tree_levels + 2) +
+                         RL_ITERS * 2 * (n_tree_levels + conv_launches(apr, st.cpu().numpy(), 5))) * args.steps,
     }
     return rec
 

@@ -95,9 +95,11 @@ typedef struct {
  * the host also lists the non-empty source segments of its staged patch with the prefix of their
  * 8-element packets (tile plans, for stencil radius 1 and 2 and for the multi-channel sub-tiles),
  * so the convolution kernels never evaluate row offsets per call; on a 1024x1024x512 image with
- * 8 M particles the handle holds about 206 MB, plans included (the image itself would be 2.1 GB).
+ * 8 M particles the handle holds about 212 MB, plans included (the image itself would be 2.1 GB).
  * The index is allocated stream-ordered (cudaMallocAsync on `stream`) and uploaded on `stream`;
- * it is ready for work enqueued on `stream` (other streams synchronise with it first). Returns
+ * it is ready for work enqueued on `stream` (other streams synchronise with it first). The handle
+ * also creates two streams and four events for the concurrent parts of later calls, and 8 bytes of
+ * mapped pinned host memory (the radius hint of apr_convolve). Returns
  * APR_ERR_INVALID_LAYOUT when the arrays are inconsistent (row sizes, y order and range, and with
  * the flags the partition and the balance), APR_ERR_UNSUPPORTED for more than 2^28 particles or
  * tree nodes, APR_ERR_OOM on allocation failure. *out is NULL on error. */
@@ -149,7 +151,15 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
  *   particles: device [N_p] float32;  tree: device [N_t] float32 from apr_tree_restrict (required);
  *   stencils:  device [(l_max-l_min+1)][k][k][k] float32, level l_min first, [z][x][y] y fastest;
  *   k: 3 or 5;  bc: APR_BC_REFLECT or APR_BC_ZERO;  out: device [N_p] float32, overwritten.
- * Requires the 2:1 balance of the APR (checked by APR_REQUIRE_BALANCE at build). */
+ * Requires the 2:1 balance of the APR (checked by APR_REQUIRE_BALANCE at build).
+ * A level whose 5^3 stencil is zero outside the central 3^3 (every level below l_max of a restricted
+ * stack, Eq. restrict_stenc) is computed with radius 1. For k = 5 the tiles of the levels below l_max
+ * run on a second stream that the handle owns, in a launch sized for radius 1, beside the l_max tiles
+ * on `stream` (forked from and joined back to `stream` with events: the call stays ordered on
+ * `stream` and can be captured into a CUDA graph). When the previous call's stack had taps outside
+ * the central 3^3 below l_max (read from a hint that the kernels write, without waiting), one launch
+ * over all tiles is taken instead. Either way every output is computed by the same code, so results
+ * do not depend on the choice. */
 apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                           int32_t k, int32_t bc, float *out, apr_stream_t stream);
 
@@ -199,10 +209,10 @@ size_t apr_backward_workspace_bytes(apr_handle_t h, int32_t k);
  * least apr_backward_workspace_bytes(h, k) bytes, 256-byte aligned, contents ignored on entry.
  * Results are deterministic (fixed summation order).
  * When both gradients are requested, the stencil gradient runs on a second stream that the handle
- * owns (created on the first such call), forked from `stream` and joined back to it with events:
- * the call stays ordered on `stream` (work enqueued after it waits for both gradients) and can be
- * captured into a CUDA graph from `stream`. Concurrent calls on one handle are serialised while
- * they enqueue. */
+ * owns, forked from `stream` and joined back to it with events, and the data adjoint takes its
+ * launches as apr_convolve_adjoint does: the call stays ordered on `stream` (work enqueued after it
+ * waits for both gradients) and can be captured into a CUDA graph from `stream`. Concurrent calls on
+ * one handle are serialised while they enqueue. */
 apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const float *tree,
                                    const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                    float *grad_particles, float *grad_stencils, void *workspace,
@@ -214,7 +224,8 @@ apr_status_t apr_convolve_backward(apr_handle_t h, const float *particles, const
  * apr_convolve_adjoint: transpose of apr_convolve w.r.t. its value inputs (Sec. 4.1, 5.2): with
  * g = grad_out, grad_particles[q] = sum of g_p * w[e] over the taps that read particle q directly
  * (at q's level) or as the coarse fill of the next finer level; grad_tree[t] = the same for tree
- * node t. Both outputs are overwritten (device [N_p] and [N_t] float32). */
+ * node t. Both outputs are overwritten (device [N_p] and [N_t] float32). For k = 5 the launches are
+ * chosen as in apr_convolve (the same results either way). */
 apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                                   float *grad_particles, float *grad_tree, apr_stream_t stream);
 
@@ -260,7 +271,8 @@ apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particle
  * the PSF, apr_restrict_stencil, for the paper's scheme), w_flip is every level's stencil with its
  * taps reversed in each dimension, and division and multiplication are per particle (the division
  * gives 0 where the denominator is <= 0). Each iteration restricts the tree of i_k and of the ratio.
- * The division and the multiplication run inside the convolution kernel's output write.
+ * The division and the multiplication run inside the convolution kernel's output write; the
+ * convolutions take their launches as apr_convolve does.
  *   observed: device [N_p] float32 (u);  estimate: device [N_p] float32, in: i_0, out: i_n_iter;
  *   stencils: device [L][k^3] float32;  k: 3 or 5;  bc as apr_convolve;
  *   workspace: apr_rl_workspace_bytes(h) bytes, 256-byte aligned (a tree and a ratio buffer). */
