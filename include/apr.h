@@ -163,10 +163,6 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
 apr_status_t apr_convolve(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
                           int32_t k, int32_t bc, float *out, apr_stream_t stream);
 
-/* apr_tree_restrict into `workspace` followed by apr_convolve, for callers that do not keep the tree
- * (the paper's pipeline: restriction, then convolution). workspace: caller-owned device memory of at
- * least apr_convolve_auto_workspace_bytes(h) bytes, 4-byte aligned; it holds the tree values [N_t]
- * afterwards. APR_ERR_INVALID_ARG if it is missing or too small; otherwise as the two calls. */
 /* apr_convolve restricted to the forward work items [first_tile, first_tile + n_tiles) of
  * APR_STRUCT_FWD_ITEMS (ordered by level, then tile z, tile x, y-block): only the outputs of the
  * targets of those tiles are written. For a rank of a z-sharded APR (Sec. 5.1 parallelisation over
@@ -182,6 +178,12 @@ apr_status_t apr_convolve_adjoint_tiles(apr_handle_t h, const float *stencils, i
                                         const float *grad_out, float *grad_particles, float *grad_tree,
                                         int64_t first_tile, int64_t n_tiles, apr_stream_t stream);
 
+/* apr_tree_restrict into `workspace` followed by apr_convolve (the paper's pipeline: restriction,
+ * then convolution, Sec. 5.2). workspace: caller-owned device memory of at least
+ * apr_convolve_auto_workspace_bytes(h) bytes, 16-byte aligned; it holds the tree values [N_t]
+ * afterwards. APR_ERR_INVALID_ARG if it is missing or too small; otherwise as the two calls, with the
+ * same results. When the convolution is split by radius (see apr_convolve), its l_max tiles read no
+ * tree node, so their launch runs on the handle's second stream beside the restriction. */
 size_t apr_convolve_auto_workspace_bytes(apr_handle_t h);
 apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const float *stencils, int32_t k, int32_t bc,
                                float *out, void *workspace, size_t workspace_bytes, apr_stream_t stream);
@@ -271,8 +273,8 @@ apr_status_t apr_convolve_backward_noalloc(apr_handle_t h, const float *particle
  * the PSF, apr_restrict_stencil, for the paper's scheme), w_flip is every level's stencil with its
  * taps reversed in each dimension, and division and multiplication are per particle (the division
  * gives 0 where the denominator is <= 0). Each iteration restricts the tree of i_k and of the ratio.
- * The division and the multiplication run inside the convolution kernel's output write; the
- * convolutions take their launches as apr_convolve does.
+ * The division and the multiplication run inside the convolution kernel's output write; each
+ * restriction and the convolution after it take their launches as apr_convolve_auto does.
  *   observed: device [N_p] float32 (u);  estimate: device [N_p] float32, in: i_0, out: i_n_iter;
  *   stencils: device [L][k^3] float32;  k: 3 or 5;  bc as apr_convolve;
  *   workspace: apr_rl_workspace_bytes(h) bytes, 256-byte aligned (a tree and a ratio buffer). */

@@ -212,7 +212,8 @@ def apr_convolve(layout: AprLayout, particles, tree, stencils, k, bc=APR_BC_REFL
 
 def apr_convolve_auto(layout: AprLayout, particles, stencils, k, bc=APR_BC_REFLECT, out=None, workspace=None,
                       stream=None):
-    """Tree restriction into a workspace, then apr_convolve (one call; the tree is not kept)."""
+    """Tree restriction into a workspace, then apr_convolve, in one call (the paper's forward
+    pipeline); the workspace (at least N_t float32) holds the tree values afterwards."""
     import torch
     _dev_ptr(particles, "particles", layout.n_particles, torch.float32)
     _dev_ptr(stencils, "stencils", layout.n_levels * k ** 3, torch.float32)

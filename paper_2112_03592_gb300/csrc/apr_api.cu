@@ -149,6 +149,37 @@ cudaError_t conv_fwd_all(apr_handle_t h, int k, const float *vals, const float *
         });
 }
 
+// The paper's forward pipeline (Sec. 5.2): the tree restriction of `vals` into `tree`, then
+// conv_fwd_all. When a 5^3 call is split by radius, its l_max tiles read no tree node (the tree ends
+// at level l_max - 1): their launch starts on the split stream beside the restriction, and the
+// levels below l_max follow the restriction on s.
+apr_status_t restrict_then_conv(apr_handle_t h, int k, const float *vals, float *tree, const float *st, int bc,
+                                float *out, cudaStream_t s, int epi_mode = EPI_PLAIN, bool flip = false,
+                                const float *aux = nullptr) {
+    const HostIndex &X = h->X;
+    const int n = int(X.fwd_items.size()), n_lo = int(X.fwd_level_begin[X.l_max]);
+    if (k != 5 || n_lo == 0 || n_lo == n || outer_taps_seen(h, 0)) {
+        const apr_status_t r = apr_tree_restrict(h, vals, tree, 1, s);
+        if (r != APR_OK) return r;
+        return cuda_status(conv_fwd_all(h, k, vals, tree, st, bc, out, s, epi_mode, flip, aux));
+    }
+    const LevelRanges lo = lower_levels(X, X.fwd_level_begin);
+    apr_status_t r = APR_OK;
+    const cudaError_t e = fork_join(
+        h, s,
+        [&](cudaStream_t side) {
+            return launch_conv_fwd(k, h->L, h->d_fwd, n - n_lo, vals, tree, st, bc, out, side, epi_mode, flip, aux, n_lo);
+        },
+        [&](cudaStream_t main) {
+            r = apr_tree_restrict(h, vals, tree, 1, main);
+            if (r != APR_OK) return cudaSuccess;
+            return launch_conv_fwd_split(h->L, h->d_fwd, n_lo, lo, h->d_hint, vals, tree, st, bc, out, main, epi_mode,
+                                         flip, aux);
+        });
+    if (r != APR_OK) return r;
+    return cuda_status(e);
+}
+
 // The data adjoint over the whole adjoint work list; with `split`, k = 5 chooses its launches like
 // conv_fwd_all.
 cudaError_t bwd_data_all(apr_handle_t h, int k, const float *st, int bc, const float *gout, float *gp, float *gt,
@@ -490,10 +521,11 @@ apr_status_t apr_convolve_auto(apr_handle_t h, const float *particles, const flo
     if (!workspace || workspace_bytes < apr_convolve_auto_workspace_bytes(h) ||
         !aligned16(workspace))
         return APR_ERR_INVALID_ARG;
-    float *tree = static_cast<float *>(workspace);
-    const apr_status_t st = apr_tree_restrict(h, particles, tree, 1, stream);
-    if (st != APR_OK) return st;
-    return apr_convolve(h, particles, tree, stencils, k, bc, out, stream);
+    if (!stencil_k_ok(k)) return APR_ERR_UNSUPPORTED;
+    if (bc != APR_BC_REFLECT && bc != APR_BC_ZERO) return APR_ERR_INVALID_ARG;
+    if (!stencils || (h->X.np && (!particles || !out))) return APR_ERR_INVALID_ARG;
+    if (!aligned16(particles)) return misaligned();
+    return restrict_then_conv(h, k, particles, static_cast<float *>(workspace), stencils, bc, out, stream);
 }
 
 apr_status_t apr_gradient_magnitude(apr_handle_t h, const float *particles, const float *tree, const float *stencils,
@@ -654,15 +686,12 @@ apr_status_t apr_richardson_lucy(apr_handle_t h, const float *observed, const fl
     float *tree = static_cast<float *>(workspace);
     float *ratio = reinterpret_cast<float *>(static_cast<char *>(workspace) + (size_t(X.nt) * sizeof(float) + 255) / 256 * 256);
     for (int it = 0; it < n_iter; ++it) {
-        // ratio = u / (i_k conv w); i_{k+1} = i_k * (ratio conv w_flipped)
-        apr_status_t st = apr_tree_restrict(h, estimate, tree, 1, stream);
+        // ratio = u / (i_k conv w); i_{k+1} = i_k * (ratio conv w_flipped); each convolution with the
+        // tree restriction of its input before it
+        apr_status_t st = restrict_then_conv(h, k, estimate, tree, stencils, bc, ratio, stream, EPI_DIVIDE, false, observed);
         if (st != APR_OK) return st;
-        cudaError_t e = conv_fwd_all(h, k, estimate, tree, stencils, bc, ratio, stream, EPI_DIVIDE, false, observed);
-        if (e != cudaSuccess) return cuda_status(e);
-        st = apr_tree_restrict(h, ratio, tree, 1, stream);
+        st = restrict_then_conv(h, k, ratio, tree, stencils, bc, estimate, stream, EPI_MULTIPLY, true, estimate);
         if (st != APR_OK) return st;
-        e = conv_fwd_all(h, k, ratio, tree, stencils, bc, estimate, stream, EPI_MULTIPLY, true, estimate);
-        if (e != cudaSuccess) return cuda_status(e);
     }
     return APR_OK;
 }

@@ -1,8 +1,9 @@
 """A 5^3 convolution or data adjoint over the whole work list runs the levels below l_max split by
 radius (radius-1 tiles in their own launch on the library's second stream, beside the l_max tiles;
 the tiles of lower levels with outer taps in a persistent radius-2 launch), or as one launch when the
-last call's stack had outer taps below l_max. Whichever launches a call takes, every tile is computed
-by the same code: the results equal, bit for bit, the single launch over all work items
+last call's stack had outer taps below l_max; apr_convolve_auto starts the l_max launch beside the
+tree restriction (those tiles read no tree node). Whichever launches a call takes, every tile is
+computed by the same code: the results equal, bit for bit, the single launch over all work items
 (apr_convolve_tiles / apr_convolve_adjoint_tiles), also when consecutive calls switch between
 restricted, plain and mixed stacks without waiting (so the choice rests on an older call), and
 inside a captured CUDA graph."""
@@ -60,14 +61,18 @@ def test_split_equals_single_launch_across_stack_switches(bc):
         gp = torch.empty_like(vals)
         gt = torch.empty(lay.n_tree, device=dev)
         G.apr_convolve_adjoint(lay, sts[name], 5, gout, bc, grad_particles=gp, grad_tree=gt)
-        got.append((name, out, gp, gt))
+        tree2 = torch.full_like(tree, float("nan"))
+        auto = G.apr_convolve_auto(lay, vals, sts[name], 5, bc, workspace=tree2)
+        got.append((name, out, gp, gt, auto, tree2))
     torch.cuda.synchronize()
     lay.sync_status()
-    for name, out, gp, gt in got:
+    for name, out, gp, gt, auto, tree2 in got:
         r_out, r_gp, r_gt = refs[name]
         assert torch.equal(out, r_out), name
         assert torch.equal(gp, r_gp), name
         assert torch.equal(gt, r_gt), name
+        assert torch.equal(auto, r_out), name
+        assert torch.equal(tree2, tree), name
     # captured after each kind of stack, replayed with each stack's values copied in
     st_buf = torch.empty_like(sts["restricted"])
     for first in ["restricted", "plain"]:
@@ -78,16 +83,22 @@ def test_split_equals_single_launch_across_stack_switches(bc):
         gp = torch.empty_like(vals)
         gt = torch.empty(lay.n_tree, device=dev)
         g = torch.cuda.CUDAGraph()
+        out2 = torch.empty_like(vals)
+        tree2 = torch.empty_like(tree)
         with torch.cuda.graph(g):
             G.apr_convolve(lay, vals, tree, st_buf, 5, bc, out=out)
             G.apr_convolve_adjoint(lay, st_buf, 5, gout, bc, grad_particles=gp, grad_tree=gt)
+            G.apr_convolve_auto(lay, vals, st_buf, 5, bc, out=out2, workspace=tree2)
         for name in ["restricted", "mixed", "plain"]:
             st_buf.copy_(sts[name])
             out.fill_(float("nan"))
+            out2.fill_(float("nan"))
+            tree2.fill_(float("nan"))
             g.replay()
             torch.cuda.synchronize()
             r_out, r_gp, r_gt = refs[name]
             assert torch.equal(out, r_out) and torch.equal(gp, r_gp) and torch.equal(gt, r_gt), (first, name)
+            assert torch.equal(out2, r_out) and torch.equal(tree2, tree), (first, name)
     lay.sync_status()
 
 
