@@ -237,6 +237,14 @@ apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t
  * gradients; the particle shares are ADDED to grad_particles (device [N_p]). */
 apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *grad_particles, apr_stream_t stream);
 
+/* apr_tree_restrict_adjoint over the tree levels [level_first, level_last] only (clipped to
+ * [l_min, l_max - 1]), coarsest first. Calling it level by level from l_min up to l_max - 1 gives the
+ * whole apr_tree_restrict_adjoint; after the call for tree level t the particles of level t + 1 hold
+ * their final gradient (their parents are level-t tree nodes), so a caller can copy them out while
+ * the finer levels still run. APR_ERR_INVALID_ARG if level_first > level_last. */
+apr_status_t apr_tree_restrict_adjoint_levels(apr_handle_t h, float *grad_tree, float *grad_particles,
+                                              int32_t level_first, int32_t level_last, apr_stream_t stream);
+
 /* Scratch bytes of apr_convolve_stencil_grad for stencil size k (per-tile partial sums). */
 size_t apr_stencil_grad_workspace_bytes(apr_handle_t h, int32_t k);
 

@@ -35,6 +35,7 @@ from ._abi import (APR_BC_REFLECT, APR_BC_ZERO, APR_HOST_ONLY, APR_REQUIRE_BALAN
 
 __all__ = ["AprLayout", "AprConv", "apr_build_device", "apr_tree_restrict", "apr_convolve", "apr_convolve_auto",
            "apr_convolve_backward", "apr_convolve_adjoint", "apr_tree_restrict_adjoint",
+           "apr_tree_restrict_adjoint_levels",
            "apr_convolve_stencil_grad", "apr_gradient_magnitude", "sobel_stencils", "apr_richardson_lucy", "apr_tree_restrict_bf16", "apr_convolve_mc", "apr_convolve_mc_relu_bf16", "apr_convolve_mc_backward",
            "apr_mc_embed_bf16", "apr_mc_relu_bf16", "apr_mc_relu_backward_bf16", "apr_mc_readout",
            "apr_mc_readout_backward_bf16", "apr_restrict_stencil", "apr_rescale_stencil", "apr_dense_convolve", "apr_convolve_tiles",
@@ -356,6 +357,18 @@ def apr_tree_restrict_adjoint(layout: AprLayout, grad_tree, grad_particles, stre
     _abi.check("apr_tree_restrict_adjoint", layout._lib.apr_tree_restrict_adjoint(
         layout.handle, _dev_ptr(grad_tree, "grad_tree", layout.n_tree, torch.float32),
         _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32), _stream_ptr(stream)))
+    return grad_particles
+
+
+def apr_tree_restrict_adjoint_levels(layout: AprLayout, grad_tree, grad_particles, level_first, level_last,
+                                     stream=None):
+    """apr_tree_restrict_adjoint over the tree levels [level_first, level_last] only, coarsest first
+    (after tree level t the particles of level t + 1 hold their final gradient)."""
+    import torch
+    _abi.check("apr_tree_restrict_adjoint_levels", layout._lib.apr_tree_restrict_adjoint_levels(
+        layout.handle, _dev_ptr(grad_tree, "grad_tree", layout.n_tree, torch.float32),
+        _dev_ptr(grad_particles, "grad_particles", layout.n_particles, torch.float32), int(level_first),
+        int(level_last), _stream_ptr(stream)))
     return grad_particles
 
 

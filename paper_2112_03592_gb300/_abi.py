@@ -60,6 +60,7 @@ SIGNATURES = {
     "apr_convolve_backward_noalloc": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]),
     "apr_convolve_adjoint": (_I32, [_P, _P, _I32, _I32, _P, _P, _P, _P]),
     "apr_tree_restrict_adjoint": (_I32, [_P, _P, _P, _P]),
+    "apr_tree_restrict_adjoint_levels": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "apr_stencil_grad_workspace_bytes": (_SZ, [_P, _I32]),
     "apr_convolve_stencil_grad": (_I32, [_P, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "apr_rl_workspace_bytes": (_SZ, [_P]),

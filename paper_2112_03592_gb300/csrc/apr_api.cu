@@ -200,6 +200,22 @@ cudaError_t bwd_data_all(apr_handle_t h, int k, const float *st, int bc, const f
         [&](cudaStream_t main) { return launch_bwd_data(k, h->L, h->d_bwd, n - n_lo, st, bc, gout, gp, gt, main, n_lo); });
 }
 
+// The tree push-down (apr_tree_restrict_adjoint) of the tree levels [l0, l1] within [l_min, l_max - 1],
+// coarsest first, one launch per level.
+apr_status_t pushdown_levels(apr_handle_t h, float *grad_tree, float *grad_particles, int l0, int l1,
+                             cudaStream_t s) {
+    const HostIndex &X = h->X;
+    if ((X.nt && !grad_tree) || (X.np && !grad_particles)) return APR_ERR_INVALID_ARG;
+    if (l0 < X.l_min) l0 = X.l_min;
+    if (l1 > X.l_max - 1) l1 = X.l_max - 1;
+    cudaError_t e = cudaSuccess;
+    for (int l = l0; e == cudaSuccess && l <= l1; ++l) {
+        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, s);
+    }
+    return cuda_status(e);
+}
+
 apr_status_t misaligned() {
     aprk::set_last_message("staged value arrays (particles, tree values) must be 16-byte aligned");
     return APR_ERR_INVALID_ARG;
@@ -552,14 +568,13 @@ apr_status_t apr_convolve_adjoint(apr_handle_t h, const float *stencils, int32_t
 
 apr_status_t apr_tree_restrict_adjoint(apr_handle_t h, float *grad_tree, float *grad_particles, apr_stream_t stream) {
     if (!h || h->host_only) return APR_ERR_INVALID_ARG;
-    const HostIndex &X = h->X;
-    if ((X.nt && !grad_tree) || (X.np && !grad_particles)) return APR_ERR_INVALID_ARG;
-    cudaError_t e = cudaSuccess;
-    for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
-        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, stream);
-    }
-    return cuda_status(e);
+    return pushdown_levels(h, grad_tree, grad_particles, h->X.l_min, h->X.l_max - 1, stream);
+}
+
+apr_status_t apr_tree_restrict_adjoint_levels(apr_handle_t h, float *grad_tree, float *grad_particles,
+                                              int32_t level_first, int32_t level_last, apr_stream_t stream) {
+    if (!h || h->host_only || level_first > level_last) return APR_ERR_INVALID_ARG;
+    return pushdown_levels(h, grad_tree, grad_particles, level_first, level_last, stream);
 }
 
 size_t apr_stencil_grad_workspace_bytes(apr_handle_t h, int32_t k) {

@@ -50,3 +50,31 @@ def test_concurrent_backward_equals_sequential_parts(k):
         torch.cuda.synchronize()
         assert torch.equal(gp2, gp_ref) and torch.equal(gw2, gw_ref)
     lay.sync_status()
+
+
+def test_tree_adjoint_level_by_level():
+    """apr_tree_restrict_adjoint_levels called level by level, coarsest first, equals the whole tree
+    adjoint bit for bit; after tree level t the particles of level t + 1 already hold their final
+    gradient (what a caller copies out early)."""
+    apr = S.random_balanced_apr((40, 24, 130), 2, seed=33, p_fine=0.03)
+    lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+    assert apr.l_max - apr.l_min >= 3
+    rng = np.random.default_rng(9)
+    dev = torch.device("cuda")
+    gout = torch.as_tensor(rng.normal(size=apr.n_particles).astype(np.float32), device=dev)
+    st = torch.as_tensor(rng.normal(size=(apr.n_levels, 125)).astype(np.float32), device=dev)
+    gp0, gt0 = G.apr_convolve_adjoint(lay, st, 5, gout)
+    gp_ref, gt_ref = gp0.clone(), gt0.clone()
+    G.apr_tree_restrict_adjoint(lay, gt_ref, gp_ref)
+    gp, gt = gp0.clone(), gt0.clone()
+    first = [apr.level_row_offset(l) for l in range(apr.l_min, apr.l_max + 2)]
+    rp = apr.row_ptr
+    for t in range(apr.l_min, apr.l_max):
+        G.apr_tree_restrict_adjoint_levels(lay, gt, gp, t, t)
+        torch.cuda.synchronize()
+        lo, hi = int(rp[first[t + 1 - apr.l_min]]), int(rp[first[t + 2 - apr.l_min]])
+        assert torch.equal(gp[lo:hi], gp_ref[lo:hi]), t
+    assert torch.equal(gp, gp_ref) and torch.equal(gt, gt_ref)
+    with pytest.raises(RuntimeError):
+        G.apr_tree_restrict_adjoint_levels(lay, gt, gp, apr.l_max - 1, apr.l_min)
+    lay.sync_status()
