@@ -273,7 +273,8 @@ def layer_step(args, lay, st, b, dev, stream, flush, world, clocks=False):
     for f in parts_fns + step_fns[1:]:
         f()
     run_part = make_replayers(parts_fns, not args.no_graph)
-    run_step = make_replayers(step_fns, not args.no_graph)
+    # the step as one graph (forward pipeline, then the backward)
+    run_step = make_replayers([lambda: [f() for f in step_fns]], not args.no_graph)
 
     def parts_pass(e=None):
         if e is not None:
@@ -493,7 +494,8 @@ def run_ours(args, rank, world):
                    "backward": "apr_convolve_backward: data adjoint and tree adjoint on the step's stream, stencil "
                                "gradient concurrently on the library's second stream (fork / join events)",
                    "l2": "flushed before every step (512 MB write, outside the step events)",
-                   "launch": "CUDA graphs (one per part)" if not args.no_graph else "eager",
+                   "launch": "the step as one CUDA graph (the parts and the end-to-end step: one graph per part)"
+                             if not args.no_graph else "eager",
                    "parallelism": f"replicas x{world}"},
         "pixel_equiv_GBps": round(world * pix_bytes / (step_ms * 1e-3) / 1e9, 2),
         "forward_pipeline": {"ms": round(fwd_ms, 5),
