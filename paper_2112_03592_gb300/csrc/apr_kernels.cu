@@ -1278,13 +1278,14 @@ __global__ void __launch_bounds__(NT) radius_hint_kernel(const float *__restrict
 // particle rows (a, b), lanes 4..7: tree rows).
 // ------------------------------------------------------------------------------------------------
 // Warp-level flattened loop over the children: f(segment, index, y, value), values read from vp
-// (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use.
+// (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use. With
+// nparts > 1 the warp takes only part `part` of the children (every nparts-th group of 32 UNROLL).
 template <typename F>
 __device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f,
-                                              int C = 1, int c = 0) {
+                                              int C = 1, int c = 0, int part = 0, int nparts = 1) {
     const int lane = threadIdx.x & 31;
     const ChildSegs cs(lo, n);
-    for (int e0 = 0; e0 < cs.total; e0 += 32 * UNROLL) {
+    for (int e0 = 32 * UNROLL * part; e0 < cs.total; e0 += 32 * UNROLL * nparts) {
         int sg[UNROLL], ix[UNROLL], yv[UNROLL];
         float vv[UNROLL];
 #pragma unroll
@@ -1352,12 +1353,15 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
 
 // Backward through the tree averages, one level l (coarse to fine): each child (particle or tree
 // node of level l+1) of a tree node t receives gt[t] / n_children(t).
+// `split` warps per brick (on coarse levels with few bricks): each computes the nodes' shares and
+// updates its part of the children, so every child is still written once.
 __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           const TreePlan *__restrict__ tplan, int n,
+                                                           const TreePlan *__restrict__ tplan, int n, int split,
                                                            float *__restrict__ gp, float *__restrict__ gt) {
     __shared__ float share[NWARP][BY];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * NWARP + warp;
+    const int gw = blockIdx.x * NWARP + warp;
+    const int bi = gw / split, part = gw % split;
     if (bi >= n) return;
     const Item it = items[bi];
     int lo, cn, tlo, tn;
@@ -1374,10 +1378,13 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
         }
     }
     __syncwarp();
-    warp_children(L, lo, cn, gp, gt, [&](int s, int i, int yv, float v) {
-        float *dst = s >= 4 ? gt : gp;
-        dst[i] = v + share[warp][(yv >> 1) - y0];
-    });
+    warp_children(
+        L, lo, cn, gp, gt,
+        [&](int s, int i, int yv, float v) {
+            float *dst = s >= 4 ? gt : gp;
+            dst[i] = v + share[warp][(yv >> 1) - y0];
+        },
+        1, 0, part, split);
 }
 
 // Shared memory per block sets the blocks per SM (228 KB per SM, 1 KB reserved per block):
@@ -1526,7 +1533,10 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
 
 cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
                                  cudaStream_t s) {
-    if (n > 0) tree_pushdown_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, tp, n, gp, gt);
+    // levels with few bricks: several warps per brick, so that about 4096 warps share the work
+    const int split = n > 0 ? std::max(1, std::min(8, 4096 / n)) : 1;
+    const long long warps = (long long)n * split;
+    if (n > 0) tree_pushdown_kernel<<<int((warps + NWARP - 1) / NWARP), NT, 0, s>>>(L, items, tp, n, split, gp, gt);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -631,12 +632,15 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
 
 // Transpose of the tree restriction for 16 FP32 gradient channels, one level (coarse to fine):
 // every child (particle or tree node of level l+1) gets its parent's gradient / #children added.
+// `split` warps per brick (on coarse levels with few bricks): each computes the nodes' shares and
+// updates its part of the children, so every child is still written once.
 __global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                              const TreePlan *__restrict__ tplan, int n,
+                                                              const TreePlan *__restrict__ tplan, int n, int split,
                                                               float4 *__restrict__ gp, float4 *__restrict__ gt) {
     __shared__ float4 share[NWARP][BY][MC / 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * NWARP + warp;
+    const int gw = blockIdx.x * NWARP + warp;
+    const int bi = gw / split, part = gw % split;
     if (bi >= n) return;
     const Item it = items[bi];
     int lo, cn, tlo, tn;
@@ -672,7 +676,7 @@ __global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L,
     // before any of them is updated
     constexpr int U = 4;
     const ChildSegs cs(lo, cn);
-    for (int k0 = lane; k0 < cs.total * (MC / 4); k0 += 32 * U) {
+    for (int k0 = lane + 32 * U * part; k0 < cs.total * (MC / 4); k0 += 32 * U * split) {
         float4 *d[U];
         float4 v[U];
         int yv[U], c[U];
@@ -1520,9 +1524,11 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
         }
         for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
             const int64_t b = X.tree_level_begin[l], nt = X.tree_level_begin[l + 1] - b;
+            // levels with few bricks: several warps per brick, about 4096 warps in all
+            const int split = nt > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(8, 4096 / nt))) : 1;
             if (nt > 0)
-                mc_tree_pushdown_kernel<<<int((nt + NWARP - 1) / NWARP), NT, 0, stream>>>(
-                    h->L, h->d_tree + b, h->d_tplan + b, int(nt), reinterpret_cast<float4 *>(grad_particles),
+                mc_tree_pushdown_kernel<<<int((nt * split + NWARP - 1) / NWARP), NT, 0, stream>>>(
+                    h->L, h->d_tree + b, h->d_tplan + b, int(nt), split, reinterpret_cast<float4 *>(grad_particles),
                     reinterpret_cast<float4 *>(gt));
             e = cudaGetLastError();
         }
