@@ -14,7 +14,7 @@ cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s,
                             int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr, int tile0 = 0);
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals, float *tree,
-                                 cudaStream_t s, int C = 1, int ch = 0);
+                                 cudaStream_t s, int C, int ch, bool pdl);
 cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                            const float *st, int bc, float *out, cudaStream_t s);
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
@@ -24,7 +24,7 @@ cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int
 cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64_t *level_begin, int l_min,
                                   int n_levels, int K3, float *gw, cudaStream_t s);
 cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool pdl);
 cudaError_t launch_conv_fwd_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
                                   const float *vals, const float *tree, const float *st, int bc, float *out,
                                   cudaStream_t s, int epi_mode, bool flip, const float *aux);
@@ -209,9 +209,11 @@ apr_status_t pushdown_levels(apr_handle_t h, float *grad_tree, float *grad_parti
     if (l0 < X.l_min) l0 = X.l_min;
     if (l1 > X.l_max - 1) l1 = X.l_max - 1;
     cudaError_t e = cudaSuccess;
+    bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = l0; e == cudaSuccess && l <= l1; ++l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, s);
+        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, s, chained);
+        chained = chained || n > 0;
     }
     return cuda_status(e);
 }
@@ -479,10 +481,13 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
     if (channels < 1 || channels > 64) return APR_ERR_INVALID_ARG;
     if ((!particles && h->X.np) || (!tree && h->X.nt)) return APR_ERR_INVALID_ARG;
     const HostIndex &X = h->X;
+    bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = X.l_max - 1; l >= X.l_min; --l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
         for (int c = 0; c < channels; ++c) {  // channels-last values: one strided pass per channel
-            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, h->d_tplan + b, int(n), particles, tree, stream, channels, c);
+            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, h->d_tplan + b, int(n), particles, tree, stream,
+                                                 channels, c, chained);
+            chained = chained || n > 0;
             if (e != cudaSuccess) return cuda_status(e);
         }
     }

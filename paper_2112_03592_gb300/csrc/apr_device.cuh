@@ -121,6 +121,13 @@ struct YVLoader {
 
 // A tree brick's plan, one coalesced 48-byte load per warp: lanes 0..7 get child segment `lane`
 // (lo, n), the other lanes an empty one; every lane gets the brick's tree nodes [tlo, tlo + tn).
+// Programmatic dependent launch (launch_pdl): pdl_trigger lets the next kernel on the stream start
+// (its blocks run their prologue while this kernel finishes); pdl_wait blocks until the kernel before
+// this one on the stream has completed and its writes are visible. In a kernel launched without the
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tree_plan_load(const TreePlan *tp, int lane, int &lo, int &n, int &tlo, int &tn) {
     const uint32_t v = lane < 12 ? __ldg(reinterpret_cast<const uint32_t *>(tp) + lane) : 0u;
     const int k = lane & 7;

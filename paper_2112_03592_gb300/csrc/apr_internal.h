@@ -162,6 +162,25 @@ apr_status_t cuda_status(cudaError_t e);
 // device): later calls make no CUDA call, so launches can be captured into CUDA graphs.
 cudaError_t set_max_dynamic_smem(const void *fn, size_t bytes);
 
+// kernel<<<grid, block, smem, s>>>(args...), with programmatic stream serialization when `pdl`: the
+// kernel may then start while the kernel before it on s finishes, and waits for it with pdl_wait
+// (apr_device.cuh) before it reads what that kernel writes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline int64_t level_cells(int64_t D, int l_max, int l) {
     int64_t s = int64_t(1) << (l_max - l);
     return (D + s - 1) / s;

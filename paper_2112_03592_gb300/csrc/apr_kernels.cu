@@ -1317,15 +1317,22 @@ __global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, co
     __shared__ float slot[NWARP][8][BY];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * NWARP + warp;
-    if (bi >= n) return;
-    const Item it = items[bi];
-    int lo, cn, tlo, tn;
-    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    pdl_trigger();
+    // the work item, its brick plan and the nodes' y (at most BY: two per lane) are static: they are
+    // read before waiting for the finer level's restriction (launched before this one)
+    const bool live = bi < n;   // warp-uniform
+    Item it{};
+    int lo = 0, cn = 0, tlo = 0, tn = 0, ty0 = 0, ty1 = 0;
+    if (live) {
+        it = items[bi];
+        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+        ty0 = lane < tn ? int(L.ty[tlo + lane]) : 0;
+        ty1 = lane + 32 < tn ? int(L.ty[tlo + lane + 32]) : 0;
+    }
+    pdl_wait();
+    if (!live) return;
     const LevelGeo gc = L.geo[it.l + 1];
     const int y0 = it.yb * BY;
-    // the brick's node y values (at most BY: two per lane) are loaded together with the children
-    const int ty0 = lane < tn ? int(L.ty[tlo + lane]) : 0;
-    const int ty1 = lane + 32 < tn ? int(L.ty[tlo + lane + 32]) : 0;
     float(*sl)[BY] = slot[warp];
     warp_children(L, lo, cn, vals, tree, [&](int s, int, int yv, float v) {
         sl[(s & 3) * 2 + (yv & 1)][(yv >> 1) - y0] = v;
@@ -1362,10 +1369,18 @@ __global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * NWARP + warp;
     const int bi = gw / split, part = gw % split;
-    if (bi >= n) return;
-    const Item it = items[bi];
-    int lo, cn, tlo, tn;
-    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    pdl_trigger();
+    // the work item and its brick plan are static: read before waiting for the coarser level's
+    // push-down (launched before this one), whose output this level reads
+    const bool live = bi < n;   // warp-uniform
+    Item it{};
+    int lo = 0, cn = 0, tlo = 0, tn = 0;
+    if (live) {
+        it = items[bi];
+        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    }
+    pdl_wait();
+    if (!live) return;
     const LevelGeo gc = L.geo[it.l + 1];
     const int y0 = it.yb * BY;
 #pragma unroll
@@ -1467,9 +1482,10 @@ cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, 
 }
 
 cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals,
-                                 float *tree, cudaStream_t s, int C, int ch) {
-    if (n > 0) tree_restrict_kernel<<<(n + NWARP - 1) / NWARP, NT, 0, s>>>(L, items, tp, n, vals, tree, C, ch);
-    return cudaGetLastError();
+                                 float *tree, cudaStream_t s, int C, int ch, bool pdl) {
+    if (n <= 0) return cudaSuccess;
+    return launch_pdl(tree_restrict_kernel, dim3((n + NWARP - 1) / NWARP), dim3(NT), 0, s, pdl, L, items, tp, n, vals,
+                      tree, C, ch);
 }
 
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
@@ -1532,12 +1548,13 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
 }
 
 cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool pdl) {
     // levels with few bricks: several warps per brick, so that about 4096 warps share the work
     const int split = n > 0 ? std::max(1, std::min(8, 4096 / n)) : 1;
     const long long warps = (long long)n * split;
-    if (n > 0) tree_pushdown_kernel<<<int((warps + NWARP - 1) / NWARP), NT, 0, s>>>(L, items, tp, n, split, gp, gt);
-    return cudaGetLastError();
+    if (n <= 0) return cudaSuccess;
+    return launch_pdl(tree_pushdown_kernel, dim3(int((warps + NWARP - 1) / NWARP)), dim3(NT), 0, s, pdl, L, items, tp, n,
+                      split, gp, gt);
 }
 
 }  // namespace aprk

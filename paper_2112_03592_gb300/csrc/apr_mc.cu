@@ -559,10 +559,18 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const
     TreeMcSmem &S = *reinterpret_cast<TreeMcSmem *>(smraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * TREE_WARPS + warp;
-    if (bi >= n) return;
-    const Item it = items[bi];
-    int lo, cn, tlo, tn;
-    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    pdl_trigger();
+    // the work item and its brick plan are static: read before waiting for the finer level's
+    // restriction (launched before this one)
+    const bool live = bi < n;   // warp-uniform
+    Item it{};
+    int lo = 0, cn = 0, tlo = 0, tn = 0;
+    if (live) {
+        it = items[bi];
+        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    }
+    pdl_wait();
+    if (!live) return;
     const LevelGeo gc = L.geo[it.l + 1];
     S.pres[warp][lane] = 0;
     S.pres[warp][lane + 32] = 0;
@@ -641,10 +649,18 @@ __global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * NWARP + warp;
     const int bi = gw / split, part = gw % split;
-    if (bi >= n) return;
-    const Item it = items[bi];
-    int lo, cn, tlo, tn;
-    tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    pdl_trigger();
+    // the work item and its brick plan are static: read before waiting for the coarser level's
+    // push-down (launched before this one)
+    const bool live = bi < n;   // warp-uniform
+    Item it{};
+    int lo = 0, cn = 0, tlo = 0, tn = 0;
+    if (live) {
+        it = items[bi];
+        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+    }
+    pdl_wait();
+    if (!live) return;
     const LevelGeo gc = L.geo[it.l + 1];
     // the nodes' shares (at most BY nodes x 4 channel groups: eight items per lane, loads first)
     {
@@ -1434,13 +1450,14 @@ apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, u
     if ((X.np && !particles) || (X.nt && !tree) || !aligned16(particles) || !aligned16(tree)) return APR_ERR_INVALID_ARG;
     const size_t sm = sizeof(TreeMcSmem);
     cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_tree_restrict_kernel), sm);
+    bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = X.l_max - 1; e == cudaSuccess && l >= X.l_min; --l) {
         const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
         if (n > 0)
-            mc_tree_restrict_kernel<<<int((n + TREE_WARPS - 1) / TREE_WARPS), TREE_WARPS * 32, sm, stream>>>(
-                h->L, h->d_tree + b, h->d_tplan + b, int(n), reinterpret_cast<const uint4 *>(particles),
-                reinterpret_cast<uint4 *>(tree));
-        e = cudaGetLastError();
+            e = launch_pdl(mc_tree_restrict_kernel, dim3(int((n + TREE_WARPS - 1) / TREE_WARPS)), dim3(TREE_WARPS * 32),
+                           sm, stream, chained, h->L, h->d_tree + b, h->d_tplan + b, int(n),
+                           reinterpret_cast<const uint4 *>(particles), reinterpret_cast<uint4 *>(tree));
+        chained = chained || n > 0;
     }
     return cuda_status(e);
 }
@@ -1522,15 +1539,16 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
                 h->L, h->d_bwd, wt, bc, reinterpret_cast<const uint4 *>(grad_out), grad_particles, gt);
             e = cudaGetLastError();
         }
+        bool chained = false;   // the launches after the first start early (programmatic dependent launch)
         for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
             const int64_t b = X.tree_level_begin[l], nt = X.tree_level_begin[l + 1] - b;
             // levels with few bricks: several warps per brick, about 4096 warps in all
             const int split = nt > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(8, 4096 / nt))) : 1;
             if (nt > 0)
-                mc_tree_pushdown_kernel<<<int((nt * split + NWARP - 1) / NWARP), NT, 0, stream>>>(
-                    h->L, h->d_tree + b, h->d_tplan + b, int(nt), split, reinterpret_cast<float4 *>(grad_particles),
-                    reinterpret_cast<float4 *>(gt));
-            e = cudaGetLastError();
+                e = launch_pdl(mc_tree_pushdown_kernel, dim3(int((nt * split + NWARP - 1) / NWARP)), dim3(NT), 0, stream,
+                               chained, h->L, h->d_tree + b, h->d_tplan + b, int(nt), split,
+                               reinterpret_cast<float4 *>(grad_particles), reinterpret_cast<float4 *>(gt));
+            chained = chained || nt > 0;
         }
     }
     if (e == cudaSuccess && grad_weights) {
