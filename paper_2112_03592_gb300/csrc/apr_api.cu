@@ -13,7 +13,7 @@ namespace aprk {
 cudaError_t launch_conv_fwd(int k, const DevLayout &L, const Item *items, int n, const float *vals,
                             const float *tree, const float *st, int bc, float *out, cudaStream_t s,
                             int epi_mode = EPI_PLAIN, bool flip = false, const float *aux = nullptr, int tile0 = 0);
-cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals, float *tree,
+cudaError_t launch_tree_restrict(const TreeNodePlan *np, int node0, int n, const float *vals, float *tree,
                                  cudaStream_t s, int C, int ch, bool pdl);
 cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, const float *vals, const float *tree,
                            const float *st, int bc, float *out, cudaStream_t s);
@@ -23,8 +23,8 @@ cudaError_t launch_bwd_stencil(int k, const DevLayout &L, const Item *items, int
                                const float *tree, int bc, const float *gout, float *partial, cudaStream_t s);
 cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64_t *level_begin, int l_min,
                                   int n_levels, int K3, float *gw, cudaStream_t s);
-cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
-                                 cudaStream_t s, bool pdl);
+cudaError_t launch_tree_pushdown(const TreeNodePlan *np, int node0, int n, float *gp, float *gt, cudaStream_t s,
+                                 bool pdl);
 cudaError_t launch_conv_fwd_split(const DevLayout &L, const Item *items, int n_lo, const LevelRanges &lo, int *hint,
                                   const float *vals, const float *tree, const float *st, int bc, float *out,
                                   cudaStream_t s, int epi_mode, bool flip, const float *aux);
@@ -200,6 +200,13 @@ cudaError_t bwd_data_all(apr_handle_t h, int k, const float *st, int bc, const f
         [&](cudaStream_t main) { return launch_bwd_data(k, h->L, h->d_bwd, n - n_lo, st, bc, gout, gp, gt, main, n_lo); });
 }
 
+// The tree nodes of level l (l_min <= l < l_max): [b, b + n) in tree order.
+void tree_level_nodes(const HostIndex &X, int l, int64_t &b, int64_t &n) {
+    const LevelGeo &g = X.geo[l];
+    b = X.trow_ptr[size_t(g.trow0)];
+    n = int64_t(X.trow_ptr[size_t(g.trow0) + size_t(g.dz) * size_t(g.dx)]) - b;
+}
+
 // The tree push-down (apr_tree_restrict_adjoint) of the tree levels [l0, l1] within [l_min, l_max - 1],
 // coarsest first, one launch per level.
 apr_status_t pushdown_levels(apr_handle_t h, float *grad_tree, float *grad_particles, int l0, int l1,
@@ -211,8 +218,9 @@ apr_status_t pushdown_levels(apr_handle_t h, float *grad_tree, float *grad_parti
     cudaError_t e = cudaSuccess;
     bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = l0; e == cudaSuccess && l <= l1; ++l) {
-        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
-        e = launch_tree_pushdown(h->L, h->d_tree + b, h->d_tplan + b, int(n), grad_particles, grad_tree, s, chained);
+        int64_t b = 0, n = 0;
+        tree_level_nodes(X, l, b, n);
+        e = launch_tree_pushdown(h->d_tnplan, int(b), int(n), grad_particles, grad_tree, s, chained);
         chained = chained || n > 0;
     }
     return cuda_status(e);
@@ -320,6 +328,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         if (e == cudaSuccess) e = upload(h, &h->d_bwd, X.bwd_items.data(), X.bwd_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_tree, X.tree_items.data(), X.tree_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_tplan, X.tplan.data(), X.tplan.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_tnplan, X.tnplan.data(), X.tnplan.size());
         if (e == cudaSuccess) e = upload(h, &h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1));
         for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
             const HostFPlan &P = i < 2 ? X.fplan[i] : X.bplan[i - 2];
@@ -380,6 +389,7 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         h->X.mcfplan = HostPlan{};
         h->X.mcbplan = HostPlan{};
         h->X.tplan = std::vector<TreePlan>{};
+        h->X.tnplan = std::vector<TreeNodePlan>{};
         // the second streams of apr_convolve_backward and of the radius split, and their events, are
         // made here, so that no later call creates them inside a stream capture
         e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
@@ -483,10 +493,11 @@ apr_status_t apr_tree_restrict(apr_handle_t h, const float *particles, float *tr
     const HostIndex &X = h->X;
     bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = X.l_max - 1; l >= X.l_min; --l) {
-        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        int64_t b = 0, n = 0;
+        tree_level_nodes(X, l, b, n);
         for (int c = 0; c < channels; ++c) {  // channels-last values: one strided pass per channel
-            cudaError_t e = launch_tree_restrict(h->L, h->d_tree + b, h->d_tplan + b, int(n), particles, tree, stream,
-                                                 channels, c, chained);
+            cudaError_t e = launch_tree_restrict(h->d_tnplan, int(b), int(n), particles, tree, stream, channels, c,
+                                                 chained);
             chained = chained || n > 0;
             if (e != cudaSuccess) return cuda_status(e);
         }

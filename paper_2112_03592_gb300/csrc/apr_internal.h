@@ -55,6 +55,18 @@ struct TreePlan {
     uint32_t tn;
 };
 static_assert(sizeof(TreePlan) == 48, "tree plans are three 16-byte words");
+// Child map of one tree node (built once per APR; one per node, in tree order): for each of the four
+// child rows k = (a, b) = (k >> 1, k & 1) of level l+1 over the node, p[k] = index of its first
+// particle child there and t[k] = index of its first tree child (bits 0..29), and in bits 30, 31 of
+// p[k] (t[k]) whether child cell y = 2 y_node (bit 30) and 2 y_node + 1 (bit 31) is a particle (a
+// tree node). A child cell with neither bit lies outside the grid (or, in a sub-domain's partial
+// index, outside the sub-domain). The second child of a kind in a row follows the first at index + 1.
+struct alignas(16) TreeNodePlan {
+    int32_t p[4];
+    int32_t t[4];
+};
+static_assert(sizeof(TreeNodePlan) == 32, "node plans are two 16-byte words");
+constexpr uint32_t TNP_INDEX = (1u << 30) - 1u;
 struct PlanView {
     const PlanHdr *hdr;
     const PlanEnt *ent;
@@ -113,6 +125,7 @@ struct HostIndex {
     HostFPlan bplan[2];                       // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
     std::vector<TreePlan> tplan;              // tree bricks (tree_plan)
+    std::vector<TreeNodePlan> tnplan;         // child maps of the tree nodes (tree_node_plan)
 };
 
 // Work items of the consecutive levels l0 .. l0 + n - 1: level l0 + i owns items [begin[i], begin[i + 1])
@@ -133,6 +146,9 @@ apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
 bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
 bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P);
+// The child map of every tree node (TreeNodePlan), by one merge of each tree row with its child rows.
+// In a complete index every in-grid child cell of a node is a particle or a node of the next level.
+bool tree_node_plan(const DevLayout &L, const HostIndex &X, std::vector<TreeNodePlan> &P);
 // apr_convolve_adjoint; split: a 5^3 stack's levels below l_max on the handle's split stream
 apr_status_t convolve_adjoint(apr_handle_t h, const float *stencils, int32_t k, int32_t bc, const float *grad_out,
                               float *grad_particles, float *grad_tree, apr_stream_t stream, bool split);
@@ -207,6 +223,7 @@ struct apr_handle_s {
     aprk::PlanHdr *d_plan_hdr[2] = {};
     aprk::PlanEnt *d_plan_ent[2] = {};
     aprk::TreePlan *d_tplan = nullptr;
+    aprk::TreeNodePlan *d_tnplan = nullptr;
     aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
     uint2 *d_fplan_ent[4] = {};
     size_t dev_bytes = 0;

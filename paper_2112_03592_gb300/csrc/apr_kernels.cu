@@ -583,6 +583,7 @@ __global__ void __launch_bounds__(NT, 5) conv_fwd_r1_kernel(const DevLayout L, c
                                                             const float *__restrict__ stencils, int bc, float *out,
                                                             const Epilogue epi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();   // the persistent radius-2 launch after this one is independent of it
     const int tile = int(blockIdx.x);
     const Item it = items[tile];
     if (!outer_taps_zero5(stencils, it.l - L.l_min)) return;
@@ -611,6 +612,7 @@ __global__ void __launch_bounds__(NT, 4) conv_fwd_r2_pool_kernel(const DevLayout
         conv_fwd_tile<2, 2>(L, it, plan_pre(L.fplan[1], h2, h2.count), vals, tree, stencils, bc, out, epi, smem_raw);
         __syncthreads();   // the next tile reuses the shared memory
     }
+    pdl_wait();   // launched beside the radius-1 launch's tail: complete only after it
 }
 
 // Gradient magnitude (Sec. 4.3, Sobel filters with level-rescaled stencils, Eq. adapt_grad):
@@ -1236,6 +1238,7 @@ __global__ void __launch_bounds__(NT, 4) conv_bwd_data_r1_kernel(const DevLayout
                                                                  const float *__restrict__ gout,
                                                                  float *__restrict__ gp, float *__restrict__ gt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();   // the persistent radius-2 launch after this one is independent of it
     const int tile = int(blockIdx.x);
     const Item it = items[tile];
     if (!outer_taps_zero5(stencils, it.l - L.l_min)) return;
@@ -1262,6 +1265,7 @@ __global__ void __launch_bounds__(NT, 3) conv_bwd_data_r2_pool_kernel(const DevL
         conv_bwd_data_tile<2, 2>(L, it, plan_pre(L.bplan[1], h2, bplan_count(h2)), stencils, bc, gout, gp, gt, smem_raw);
         __syncthreads();   // the next tile reuses the shared memory
     }
+    pdl_wait();   // launched beside the radius-1 launch's tail: complete only after it
 }
 
 // Records in *hint whether a level in lr of a 5^3 stack has taps outside the central 3^3 (one block).
@@ -1273,133 +1277,101 @@ __global__ void __launch_bounds__(NT) radius_hint_kernel(const float *__restrict
 }
 
 // ------------------------------------------------------------------------------------------------
-// Tree kernels, one warp per tree brick (l, z, x, yb), eight bricks per block. The children of the
-// brick's nodes live in the 2x2 child rows of level l+1, y-blocks 2yb and 2yb+1 (lanes 0..3:
-// particle rows (a, b), lanes 4..7: tree rows).
+// Tree kernels, one launch per tree level, one thread per tree node. A node's children are the
+// cells (2z + a, 2x + b, 2y + e) of level l+1, each a particle or a tree node of that level; the
+// node's child map (TreeNodePlan, built once per APR) gives their indices, so a thread reads its map
+// and then all eight children at once.
 // ------------------------------------------------------------------------------------------------
-// Warp-level flattened loop over the children: f(segment, index, y, value), values read from vp
-// (particle segments) or vt (tree segments). UNROLL elements per lane are loaded before use. With
-// nparts > 1 the warp takes only part `part` of the children (every nparts-th group of 32 UNROLL).
-template <typename F>
-__device__ __forceinline__ void warp_children(const DevLayout &L, int lo, int n, const float *vp, const float *vt, F f,
-                                              int C = 1, int c = 0, int part = 0, int nparts = 1) {
-    const int lane = threadIdx.x & 31;
-    const ChildSegs cs(lo, n);
-    for (int e0 = 32 * UNROLL * part; e0 < cs.total; e0 += 32 * UNROLL * nparts) {
-        int sg[UNROLL], ix[UNROLL], yv[UNROLL];
-        float vv[UNROLL];
+// The children of one tree node from its child map (TreeNodePlan): child c = 2k + e (k = (a, b) the
+// child row, e the child's y parity; (a, b, e) order) is a particle (kind 1) or a tree node (kind 2)
+// at index ix[c], or not present (kind 0: outside the grid, or missing from a sub-domain's index).
+struct NodeChildren {
+    int ix[8];
+    int kind[8];
+    __device__ __forceinline__ NodeChildren(const int4 &pw, const int4 &tw) {
+        const int pv[4] = {pw.x, pw.y, pw.z, pw.w}, tv[4] = {tw.x, tw.y, tw.z, tw.w};
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const int e = e0 + lane + 32 * u;
-            sg[u] = -1;
-            ix[u] = 0;
-            yv[u] = 0;
-            vv[u] = 0.f;
-            if (e < cs.total) {
-                const int s = cs.seg(e, ix[u]);
-                sg[u] = s;
-                yv[u] = s >= 4 ? int(L.ty[ix[u]]) : int(L.y[ix[u]]);
-                vv[u] = s >= 4 ? vt[size_t(ix[u]) * C + c] : vp[size_t(ix[u]) * C + c];
+        for (int k = 0; k < 4; ++k) {
+            const unsigned pm = unsigned(pv[k]) >> 30, tm = unsigned(tv[k]) >> 30;
+            const int pi = int(unsigned(pv[k]) & TNP_INDEX), ti = int(unsigned(tv[k]) & TNP_INDEX);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                // the second child of a kind follows the first of that kind
+                const int skip = e ? 1 : 0;
+                const bool isp = (pm >> e) & 1u, ist = (tm >> e) & 1u;
+                kind[2 * k + e] = isp ? 1 : (ist ? 2 : 0);
+                ix[2 * k + e] = isp ? pi + (skip & int(pm & 1u)) : ti + (skip & int(tm & 1u));
             }
         }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
-            if (sg[u] >= 0) f(sg[u], ix[u], yv[u], vv[u]);
     }
+};
+
+__device__ __forceinline__ void load_node_plan(const TreeNodePlan *np, int node, int4 &pw, int4 &tw) {
+    const int4 *q = reinterpret_cast<const int4 *>(np + node);
+    pw = __ldg(q);
+    tw = __ldg(q + 1);
 }
 
-// APR tree restriction for one level l (Sec. 3.4): each child value goes to a slot (a, b, y&1) of its
-// parent, then every node averages its in-grid slots in a fixed order.
-__global__ void __launch_bounds__(NT) tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           const TreePlan *__restrict__ tplan, int n,
-                                                           const float *__restrict__ vals,
-                                                           float *__restrict__ tree, int C, int ch) {
-    __shared__ float slot[NWARP][8][BY];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * NWARP + warp;
+// APR tree restriction for one level l (Sec. 3.4), one thread per tree node of the level (nodes
+// [node0, node0 + n)): the node's value is the average of its children (particles and tree nodes of
+// level l+1), summed in (a, b, e) order. Channel ch of C channels-last values.
+__global__ void __launch_bounds__(NT) tree_restrict_kernel(const TreeNodePlan *__restrict__ nplan, int node0, int n,
+                                                           const float *__restrict__ vals, float *tree, int C,
+                                                           int ch) {
     pdl_trigger();
-    // the work item, its brick plan and the nodes' y (at most BY: two per lane) are static: they are
-    // read before waiting for the finer level's restriction (launched before this one)
-    const bool live = bi < n;   // warp-uniform
-    Item it{};
-    int lo = 0, cn = 0, tlo = 0, tn = 0, ty0 = 0, ty1 = 0;
-    if (live) {
-        it = items[bi];
-        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
-        ty0 = lane < tn ? int(L.ty[tlo + lane]) : 0;
-        ty1 = lane + 32 < tn ? int(L.ty[tlo + lane + 32]) : 0;
-    }
+    const int i = int(blockIdx.x) * NT + int(threadIdx.x);
+    const bool live = i < n;
+    // the child map is static: read before waiting for the finer level's restriction (the launch
+    // before this one), whose node values this level reads
+    int4 pw = make_int4(0, 0, 0, 0), tw = pw;
+    if (live) load_node_plan(nplan, node0 + i, pw, tw);
     pdl_wait();
     if (!live) return;
-    const LevelGeo gc = L.geo[it.l + 1];
-    const int y0 = it.yb * BY;
-    float(*sl)[BY] = slot[warp];
-    warp_children(L, lo, cn, vals, tree, [&](int s, int, int yv, float v) {
-        sl[(s & 3) * 2 + (yv & 1)][(yv >> 1) - y0] = v;
-    }, C, ch);
-    __syncwarp();
+    const NodeChildren ch8(pw, tw);
+    float v[8];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
-        if (j >= tn) break;
-        const int yv = h ? ty1 : ty0;
-        const size_t t = size_t(tlo + j);
-        float s = 0.f;
-        int cnt = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int a = c >> 2, b = (c >> 1) & 1, e = c & 1;
-            if (2 * it.a + a < gc.dz && 2 * it.b + b < gc.dx && 2 * yv + e < gc.dy) {
-                s += sl[(a * 2 + b) * 2 + e][yv - y0];
-                ++cnt;
-            }
-        }
-        tree[t * C + ch] = s / float(cnt);
+    for (int c = 0; c < 8; ++c) {
+        const size_t at = size_t(ch8.ix[c]) * C + ch;
+        v[c] = ch8.kind[c] == 1 ? vals[at] : (ch8.kind[c] == 2 ? tree[at] : 0.f);
     }
+    float s = 0.f;
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (ch8.kind[c]) {
+            s += v[c];
+            ++cnt;
+        }
+    tree[size_t(node0 + i) * C + ch] = cnt ? s / float(cnt) : 0.f;
 }
 
-// Backward through the tree averages, one level l (coarse to fine): each child (particle or tree
-// node of level l+1) of a tree node t receives gt[t] / n_children(t).
-// `split` warps per brick (on coarse levels with few bricks): each computes the nodes' shares and
-// updates its part of the children, so every child is still written once.
-__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                           const TreePlan *__restrict__ tplan, int n, int split,
-                                                           float *__restrict__ gp, float *__restrict__ gt) {
-    __shared__ float share[NWARP][BY];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * NWARP + warp;
-    const int bi = gw / split, part = gw % split;
+// Backward through the tree averages, one level l (coarse to fine), one thread per tree node t of the
+// level: each child (particle or tree node of level l+1) receives gt[t] / n_children(t). Every child
+// has one parent, so each is written by one thread.
+__global__ void __launch_bounds__(NT) tree_pushdown_kernel(const TreeNodePlan *__restrict__ nplan, int node0, int n,
+                                                           float *gp, float *gt) {
     pdl_trigger();
-    // the work item and its brick plan are static: read before waiting for the coarser level's
-    // push-down (launched before this one), whose output this level reads
-    const bool live = bi < n;   // warp-uniform
-    Item it{};
-    int lo = 0, cn = 0, tlo = 0, tn = 0;
-    if (live) {
-        it = items[bi];
-        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
-    }
+    const int i = int(blockIdx.x) * NT + int(threadIdx.x);
+    const bool live = i < n;
+    // the child map is static: read before waiting for the coarser level's push-down (the launch
+    // before this one), which writes this level's gt
+    int4 pw = make_int4(0, 0, 0, 0), tw = pw;
+    if (live) load_node_plan(nplan, node0 + i, pw, tw);
     pdl_wait();
     if (!live) return;
-    const LevelGeo gc = L.geo[it.l + 1];
-    const int y0 = it.yb * BY;
+    const NodeChildren ch8(pw, tw);
+    int cnt = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
-        if (j < tn) {
-            const int yv = L.ty[tlo + j];
-            const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv + 1 < gc.dy ? 2 : 1);
-            share[warp][yv - y0] = gt[tlo + j] / float(cnt);
-        }
+    for (int c = 0; c < 8; ++c) cnt += ch8.kind[c] ? 1 : 0;
+    const float share = gt[node0 + i] / float(cnt ? cnt : 1);
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = ch8.kind[c] == 1 ? gp[ch8.ix[c]] : (ch8.kind[c] == 2 ? gt[ch8.ix[c]] : 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (ch8.kind[c] == 1) gp[ch8.ix[c]] = v[c] + share;
+        else if (ch8.kind[c] == 2) gt[ch8.ix[c]] = v[c] + share;
     }
-    __syncwarp();
-    warp_children(
-        L, lo, cn, gp, gt,
-        [&](int s, int i, int yv, float v) {
-            float *dst = s >= 4 ? gt : gp;
-            dst[i] = v + share[warp][(yv >> 1) - y0];
-        },
-        1, 0, part, split);
 }
 
 // Shared memory per block sets the blocks per SM (228 KB per SM, 1 KB reserved per block):
@@ -1481,11 +1453,11 @@ cudaError_t launch_gradmag(int k, const DevLayout &L, const Item *items, int n, 
                   : launch_gradmag_t<2>(L, items, n, vals, tree, st, bc, out, s);
 }
 
-cudaError_t launch_tree_restrict(const DevLayout &L, const Item *items, const TreePlan *tp, int n, const float *vals,
-                                 float *tree, cudaStream_t s, int C, int ch, bool pdl) {
+cudaError_t launch_tree_restrict(const TreeNodePlan *np, int node0, int n, const float *vals, float *tree,
+                                 cudaStream_t s, int C, int ch, bool pdl) {
     if (n <= 0) return cudaSuccess;
-    return launch_pdl(tree_restrict_kernel, dim3((n + NWARP - 1) / NWARP), dim3(NT), 0, s, pdl, L, items, tp, n, vals,
-                      tree, C, ch);
+    return launch_pdl(tree_restrict_kernel, dim3((n + NT - 1) / NT), dim3(NT), 0, s, pdl, np, node0, n, vals, tree, C,
+                      ch);
 }
 
 cudaError_t launch_bwd_data(int k, const DevLayout &L, const Item *items, int n, const float *st, int bc,
@@ -1509,8 +1481,10 @@ cudaError_t launch_conv_fwd_split(const DevLayout &L, const Item *items, int n_l
     if (e == cudaSuccess) e = sm_count(&nsm);
     if (e != cudaSuccess) return e;
     conv_fwd_r1_kernel<<<n_lo, NT, sm1, s>>>(L, items, vals, tree, st, bc, out, epi);
-    conv_fwd_r2_pool_kernel<<<std::min(n_lo, 4 * nsm), NT, sm2, s>>>(L, items, lo, hint, vals, tree, st, bc, out, epi);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pdl(conv_fwd_r2_pool_kernel, dim3(std::min(n_lo, 4 * nsm)), dim3(NT), sm2, s, true, L, items, lo, hint,
+                      vals, tree, st, bc, out, epi);
 }
 
 // The same for the data adjoint (items [0, n_lo) of the adjoint work list).
@@ -1524,8 +1498,10 @@ cudaError_t launch_bwd_data_split(const DevLayout &L, const Item *items, int n_l
     if (e == cudaSuccess) e = sm_count(&nsm);
     if (e != cudaSuccess) return e;
     conv_bwd_data_r1_kernel<<<n_lo, NT, sm1, s>>>(L, items, st, bc, gout, gp, gt);
-    conv_bwd_data_r2_pool_kernel<<<std::min(n_lo, 3 * nsm), NT, sm2, s>>>(L, items, lo, hint, st, bc, gout, gp, gt);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pdl(conv_bwd_data_r2_pool_kernel, dim3(std::min(n_lo, 3 * nsm)), dim3(NT), sm2, s, true, L, items, lo,
+                      hint, st, bc, gout, gp, gt);
 }
 
 // *hint = whether a level of lo (a 5^3 stack) has taps outside the central 3^3: the radius split
@@ -1547,14 +1523,10 @@ cudaError_t launch_stencil_reduce(const float *partial, int n_items, const int64
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_pushdown(const DevLayout &L, const Item *items, const TreePlan *tp, int n, float *gp, float *gt,
-                                 cudaStream_t s, bool pdl) {
-    // levels with few bricks: several warps per brick, so that about 4096 warps share the work
-    const int split = n > 0 ? std::max(1, std::min(8, 4096 / n)) : 1;
-    const long long warps = (long long)n * split;
+cudaError_t launch_tree_pushdown(const TreeNodePlan *np, int node0, int n, float *gp, float *gt, cudaStream_t s,
+                                 bool pdl) {
     if (n <= 0) return cudaSuccess;
-    return launch_pdl(tree_pushdown_kernel, dim3(int((warps + NWARP - 1) / NWARP)), dim3(NT), 0, s, pdl, L, items, tp, n,
-                      split, gp, gt);
+    return launch_pdl(tree_pushdown_kernel, dim3((n + NT - 1) / NT), dim3(NT), 0, s, pdl, np, node0, n, gp, gt);
 }
 
 }  // namespace aprk

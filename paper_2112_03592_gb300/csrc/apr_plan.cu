@@ -148,10 +148,62 @@ bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P)
     return true;
 }
 
+bool tree_node_plan(const DevLayout &L, const HostIndex &X, std::vector<TreeNodePlan> &P) {
+    P.assign(size_t(X.nt), TreeNodePlan{});
+    for (int l = L.l_min; l < L.l_max; ++l) {
+        const LevelGeo g = L.geo[l], gc = L.geo[l + 1];
+        const bool child_tree = l + 1 < L.l_max;
+        for (int z = 0; z < g.dz; ++z)
+            for (int x = 0; x < g.dx; ++x) {
+                const int64_t rr = g.trow0 + int64_t(z) * g.dx + x;
+                const int64_t n0 = L.trow_ptr[rr], n1 = L.trow_ptr[rr + 1];
+                if (n0 == n1) continue;
+                for (int k = 0; k < 4; ++k) {
+                    const int cz = 2 * z + (k >> 1), cx = 2 * x + (k & 1);
+                    const bool in_grid = cz < gc.dz && cx < gc.dx;
+                    // the child row's particles [pa, pe) and tree nodes [ta, te), merged with the
+                    // node row in y order (child cells 2y, 2y + 1 of consecutive nodes increase)
+                    int64_t pa = 0, pe = 0, ta = 0, te = 0;
+                    if (in_grid) {
+                        const int64_t crr = int64_t(cz) * gc.dx + cx;
+                        pa = L.row_ptr[gc.row0 + crr];
+                        pe = L.row_ptr[gc.row0 + crr + 1];
+                        if (child_tree) {
+                            ta = L.trow_ptr[gc.trow0 + crr];
+                            te = L.trow_ptr[gc.trow0 + crr + 1];
+                        }
+                    }
+                    for (int64_t i = n0; i < n1; ++i) {
+                        const int cy0 = 2 * int(L.ty[i]);
+                        while (pa < pe && int(L.y[pa]) < cy0) ++pa;
+                        while (ta < te && int(L.ty[ta]) < cy0) ++ta;
+                        uint32_t pw = uint32_t(pa), tw = uint32_t(ta);
+                        for (int e = 0; e < 2; ++e) {
+                            const int cy = cy0 + e;
+                            if (!in_grid || cy >= gc.dy) continue;
+                            if (pa < pe && int(L.y[pa]) == cy) {
+                                pw |= 1u << (30 + e);
+                                ++pa;
+                            } else if (ta < te && int(L.ty[ta]) == cy) {
+                                tw |= 1u << (30 + e);
+                                ++ta;
+                            }
+                            // else: neither (only in a sub-domain's partial index): the child is left
+                            // out of the node's average and of its push-down
+                        }
+                        P[size_t(i)].p[k] = int32_t(pw);
+                        P[size_t(i)].t[k] = int32_t(tw);
+                    }
+                }
+            }
+    }
+    return true;
+}
+
 apr_status_t build_plans(HostIndex &X) {
     const DevLayout L = host_layout_view(X);
     if (X.np >= FPLAN_MAX_INDEX || X.nt >= FPLAN_MAX_INDEX) return APR_ERR_UNSUPPORTED;
-    apr_status_t st[6] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
+    apr_status_t st[7] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
     auto guarded = [&st](int i, auto f) {
         return [&st, i, f] {
             try {
@@ -161,16 +213,17 @@ apr_status_t build_plans(HostIndex &X) {
             }
         };
     };
-    std::function<void()> jobs[6] = {guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); }),
+    std::function<void()> jobs[7] = {guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); }),
                                      guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); }),
                                      guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); }),
                                      guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }),
                                      guarded(4, [&] { return build_mc_plans(L, X, X.mcfplan, X.mcbplan); }),
-                                     guarded(5, [&] { return tree_plan(L, X, X.tplan); })};
+                                     guarded(5, [&] { return tree_plan(L, X, X.tplan); }),
+                                     guarded(6, [&] { return tree_node_plan(L, X, X.tnplan); })};
     // one thread per plan; a job whose thread cannot be started runs here
     std::vector<std::thread> threads;
     try {
-        threads.reserve(6);
+        threads.reserve(7);
     } catch (...) {  // the jobs then run here
     }
     for (auto &job : jobs) {
