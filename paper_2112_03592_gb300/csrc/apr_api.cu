@@ -200,13 +200,6 @@ cudaError_t bwd_data_all(apr_handle_t h, int k, const float *st, int bc, const f
         [&](cudaStream_t main) { return launch_bwd_data(k, h->L, h->d_bwd, n - n_lo, st, bc, gout, gp, gt, main, n_lo); });
 }
 
-// The tree nodes of level l (l_min <= l < l_max): [b, b + n) in tree order.
-void tree_level_nodes(const HostIndex &X, int l, int64_t &b, int64_t &n) {
-    const LevelGeo &g = X.geo[l];
-    b = X.trow_ptr[size_t(g.trow0)];
-    n = int64_t(X.trow_ptr[size_t(g.trow0) + size_t(g.dz) * size_t(g.dx)]) - b;
-}
-
 // The tree push-down (apr_tree_restrict_adjoint) of the tree levels [l0, l1] within [l_min, l_max - 1],
 // coarsest first, one launch per level.
 apr_status_t pushdown_levels(apr_handle_t h, float *grad_tree, float *grad_particles, int l0, int l1,
@@ -327,7 +320,6 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         if (e == cudaSuccess) e = upload(h, &h->d_fwd, X.fwd_items.data(), X.fwd_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_bwd, X.bwd_items.data(), X.bwd_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_tree, X.tree_items.data(), X.tree_items.size());
-        if (e == cudaSuccess) e = upload(h, &h->d_tplan, X.tplan.data(), X.tplan.size());
         if (e == cudaSuccess) e = upload(h, &h->d_tnplan, X.tnplan.data(), X.tnplan.size());
         if (e == cudaSuccess) e = upload(h, &h->d_fwd_level_begin, X.fwd_level_begin, size_t(MAXL + 1));
         for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
@@ -378,7 +370,6 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
             L.fplan[i] = FPlanView{h->d_fplan_hdr[i], h->d_fplan_ent[i]};
             L.bplan[i] = FPlanView{h->d_fplan_hdr[2 + i], h->d_fplan_ent[2 + i]};
         }
-        L.tplan = h->d_tplan;
         L.mcfplan = PlanView{h->d_plan_hdr[0], h->d_plan_ent[0]};
         L.mcbplan = PlanView{h->d_plan_hdr[1], h->d_plan_ent[1]};
         // the plans live on the device now; the host copies are not needed again
@@ -388,7 +379,6 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         }
         h->X.mcfplan = HostPlan{};
         h->X.mcbplan = HostPlan{};
-        h->X.tplan = std::vector<TreePlan>{};
         h->X.tnplan = std::vector<TreeNodePlan>{};
         // the second streams of apr_convolve_backward and of the radius split, and their events, are
         // made here, so that no later call creates them inside a stream capture

@@ -119,60 +119,12 @@ struct YVLoader {
     }
 };
 
-// A tree brick's plan, one coalesced 48-byte load per warp: lanes 0..7 get child segment `lane`
-// (lo, n), the other lanes an empty one; every lane gets the brick's tree nodes [tlo, tlo + tn).
 // Programmatic dependent launch (launch_pdl): pdl_trigger lets the next kernel on the stream start
 // (its blocks run their prologue while this kernel finishes); pdl_wait blocks until the kernel before
 // this one on the stream has completed and its writes are visible. In a kernel launched without the
 // attribute both are no-ops.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-__device__ __forceinline__ void tree_plan_load(const TreePlan *tp, int lane, int &lo, int &n, int &tlo, int &tn) {
-    const uint32_t v = lane < 12 ? __ldg(reinterpret_cast<const uint32_t *>(tp) + lane) : 0u;
-    const int k = lane & 7;
-    lo = int(__shfl_sync(0xffffffffu, v, k));
-    const uint32_t c = __shfl_sync(0xffffffffu, v, 8 + (k >> 2));
-    n = lane < 8 ? int((c >> (8 * (k & 3))) & 255u) : 0;
-    if (lane >= 8) lo = 0;
-    tlo = int(__shfl_sync(0xffffffffu, v, 10));
-    tn = int(__shfl_sync(0xffffffffu, v, 11));
-}
-
-// The eight child segments of a brick as one flat index range [0, total): element e lies in
-// segment seg(e) at global index first(e). Built from lanes 0..7's (lo, n) by a warp scan.
-struct ChildSegs {
-    int ex[8], sl[8], total;
-    __device__ __forceinline__ ChildSegs(int lo, int n) {
-        const int lane = threadIdx.x & 31;
-        int incl = n;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            ex[k] = __shfl_sync(0xffffffffu, incl - n, k);
-            sl[k] = __shfl_sync(0xffffffffu, lo, k);
-        }
-        total = __shfl_sync(0xffffffffu, incl, 7);
-    }
-    __device__ __forceinline__ int seg(int e, int &i) const {
-        int s = 0;
-#pragma unroll
-        for (int k = 1; k < 8; ++k) s = ex[k] <= e ? k : s;
-        int slo = sl[0], sex = ex[0];
-#pragma unroll
-        for (int k = 1; k < 8; ++k)
-            if (k == s) {
-                slo = sl[k];
-                sex = ex[k];
-            }
-        i = slo + (e - sex);
-        return s;
-    }
-};
 
 // Flattened loop over the elements of nseg segments (segment s: global indices seg_lo[s] ..
 // seg_lo[s] + pre[s+1] - pre[s]), in chunks of SEGID_CAP elements. For every chunk, the threads

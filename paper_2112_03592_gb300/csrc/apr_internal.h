@@ -44,17 +44,6 @@ struct PlanEnt {
     uint16_t meta, pre;
 };
 static_assert(sizeof(PlanEnt) == 8, "plan entries are 8-byte words");
-// Tree brick plan, one per tree work item (built once per APR): the brick's child segments (k = 0..3:
-// the level-(l+1) particle rows (a, b) = (k >> 1, k & 1); k = 4..7: the tree rows), each over the
-// child y-blocks 2 yb, 2 yb + 1, starting at clo[k] with byte k % 4 of cn[k / 4] elements; and the
-// brick's own tree nodes [tlo, tlo + tn).
-struct TreePlan {
-    int32_t clo[8];
-    uint32_t cn[2];
-    int32_t tlo;
-    uint32_t tn;
-};
-static_assert(sizeof(TreePlan) == 48, "tree plans are three 16-byte words");
 // Child map of one tree node (built once per APR; one per node, in tree order): for each of the four
 // child rows k = (a, b) = (k >> 1, k & 1) of level l+1 over the node, p[k] = index of its first
 // particle child there and t[k] = index of its first tree child (bits 0..29), and in bits 30, 31 of
@@ -98,7 +87,6 @@ struct DevLayout {
     LevelGeo geo[MAXL];
     FPlanView fplan[2];  // forward tiles (fwd_items), stencil radius 1 and 2
     FPlanView bplan[2];  // data-adjoint tiles (bwd_items), stencil radius 1 and 2
-    const TreePlan *tplan;  // tree bricks (tree_items)
     PlanView mcfplan;    // multi-channel feature patches of the sub-tiles of fwd_items
     PlanView mcbplan;    // multi-channel data-adjoint sub-tiles of bwd_items
 };
@@ -124,9 +112,15 @@ struct HostIndex {
     HostFPlan fplan[2];                       // forward tile plans (build_plans), radius 1 and 2
     HostFPlan bplan[2];                       // data-adjoint tile plans (build_plans), radius 1 and 2
     HostPlan mcfplan, mcbplan;                // multi-channel sub-tile plans (build_mc_plans)
-    std::vector<TreePlan> tplan;              // tree bricks (tree_plan)
     std::vector<TreeNodePlan> tnplan;         // child maps of the tree nodes (tree_node_plan)
 };
+
+// The tree nodes of level l (l_min <= l < l_max): [b, b + n) in tree order.
+inline void tree_level_nodes(const HostIndex &X, int l, int64_t &b, int64_t &n) {
+    const LevelGeo &g = X.geo[l];
+    b = X.trow_ptr[size_t(g.trow0)];
+    n = int64_t(X.trow_ptr[size_t(g.trow0) + size_t(g.dz) * size_t(g.dx)]) - b;
+}
 
 // Work items of the consecutive levels l0 .. l0 + n - 1: level l0 + i owns items [begin[i], begin[i + 1])
 // (passed to kernels by value).
@@ -145,7 +139,6 @@ apr_status_t build_index(const apr_host_layout &L, uint32_t flags, HostIndex &ou
 apr_status_t build_plans(HostIndex &X);
 // The multi-channel sub-tile plans (apr_mc.cu); true unless a tile overflows the 16-bit counts.
 bool build_mc_plans(const DevLayout &L, const HostIndex &X, HostPlan &feat, HostPlan &adj);
-bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P);
 // The child map of every tree node (TreeNodePlan), by one merge of each tree row with its child rows.
 // In a complete index every in-grid child cell of a node is a particle or a node of the next level.
 bool tree_node_plan(const DevLayout &L, const HostIndex &X, std::vector<TreeNodePlan> &P);
@@ -222,7 +215,6 @@ struct apr_handle_s {
     // tile plans: multi-channel feature, adjoint
     aprk::PlanHdr *d_plan_hdr[2] = {};
     aprk::PlanEnt *d_plan_ent[2] = {};
-    aprk::TreePlan *d_tplan = nullptr;
     aprk::TreeNodePlan *d_tnplan = nullptr;
     aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
     uint2 *d_fplan_ent[4] = {};

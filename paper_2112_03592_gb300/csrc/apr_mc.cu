@@ -544,180 +544,108 @@ __device__ __forceinline__ void store_weights(const uint4 (&w)[4], unsigned char
 }
 
 // ---------------------------------------------------------------- BF16 tree restriction
-constexpr int TREE_WARPS = 4;
-
-struct TreeMcSmem {
-    uint4 child[TREE_WARPS][BY][8][2];  // per parent slot: 8 children (dz, dx, dy order), 16 channels
-    unsigned pres[TREE_WARPS][BY];
-};
-
-__global__ void __launch_bounds__(TREE_WARPS * 32) mc_tree_restrict_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                                           const TreePlan *__restrict__ tplan, int n,
-                                                                           const uint4 *__restrict__ vals,
-                                                                           uint4 *__restrict__ tree) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    TreeMcSmem &S = *reinterpret_cast<TreeMcSmem *>(smraw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * TREE_WARPS + warp;
+// One level of the tree restriction for 16 bf16 channels, one thread per (tree node, 8-channel half):
+// the node's children from its child map (TreeNodePlan, apr_internal.h), summed in FP32 in (a, b, e)
+// order, divided by their count in FP32, rounded to bf16 (round to nearest even).
+__global__ void __launch_bounds__(NT) mc_tree_restrict_kernel(const TreeNodePlan *__restrict__ nplan, int node0, int n,
+                                                              const uint4 *__restrict__ vals, uint4 *tree) {
     pdl_trigger();
-    // the work item and its brick plan are static: read before waiting for the finer level's
-    // restriction (launched before this one)
-    const bool live = bi < n;   // warp-uniform
-    Item it{};
-    int lo = 0, cn = 0, tlo = 0, tn = 0;
+    const int q = int(blockIdx.x) * NT + int(threadIdx.x);
+    const int i = q >> 1, half = q & 1;
+    const bool live = i < n;
+    // the child map is static: read before waiting for the finer level's restriction (the launch
+    // before this one), whose node values this level reads
+    int4 pw = make_int4(0, 0, 0, 0), tw = pw;
     if (live) {
-        it = items[bi];
-        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+        const int4 *m = reinterpret_cast<const int4 *>(nplan + node0 + i);
+        pw = __ldg(m);
+        tw = __ldg(m + 1);
     }
     pdl_wait();
     if (!live) return;
-    const LevelGeo gc = L.geo[it.l + 1];
-    S.pres[warp][lane] = 0;
-    S.pres[warp][lane + 32] = 0;
-    __syncwarp();
-    const int cy0 = 2 * it.yb * BY;
-    // the children of the 2 x 2 child rows (segments 0..3 particles, 4..7 tree nodes), flattened;
-    // four elements per lane in flight
-    constexpr int U = 4;
-    const ChildSegs cs(lo, cn);
-    for (int e0 = lane; e0 < cs.total; e0 += 32 * U) {
-        int sg[U], ix[U], cy[U];
-        uint4 va[U], vb[U];
+    const int pv[4] = {pw.x, pw.y, pw.z, pw.w}, tv[4] = {tw.x, tw.y, tw.z, tw.w};
+    uint4 h[8];
+    bool has[8];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + 32 * u;
-            sg[u] = -1;
-            if (e < cs.total) {
-                sg[u] = cs.seg(e, ix[u]);
-                const bool src = sg[u] >= 4;
-                cy[u] = int(src ? L.ty[ix[u]] : L.y[ix[u]]) - cy0;  // in [0, 2 BY): exact block range
-                const uint4 *v = src ? tree : vals;
-                va[u] = v[2 * size_t(ix[u])];
-                vb[u] = v[2 * size_t(ix[u]) + 1];
-            }
+    for (int k = 0; k < 4; ++k) {
+        const unsigned pm = unsigned(pv[k]) >> 30, tm = unsigned(tv[k]) >> 30;
+        const int pi = int(unsigned(pv[k]) & TNP_INDEX), ti = int(unsigned(tv[k]) & TNP_INDEX);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            // the second child of a kind follows the first of that kind
+            const bool isp = (pm >> e) & 1u, ist = (tm >> e) & 1u;
+            const int ix = isp ? pi + (e ? int(pm & 1u) : 0) : ti + (e ? int(tm & 1u) : 0);
+            has[2 * k + e] = isp || ist;
+            h[2 * k + e] = isp ? vals[2 * size_t(ix) + half] : (ist ? tree[2 * size_t(ix) + half] : make_uint4(0u, 0u, 0u, 0u));
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (sg[u] >= 0) {
-                const int slot = (sg[u] & 3) * 2 + (cy[u] & 1);
-                S.child[warp][cy[u] >> 1][slot][0] = va[u];
-                S.child[warp][cy[u] >> 1][slot][1] = vb[u];
-                atomicOr(&S.pres[warp][cy[u] >> 1], 1u << slot);
-            }
     }
-    __syncwarp();
-    for (int t = tlo + lane; t < tlo + tn; t += 32) {
-        const int sl = int(L.ty[t]) - it.yb * BY;
-        const unsigned m = S.pres[warp][sl];
-        float acc[MC];
+    float acc[8];
 #pragma unroll
-        for (int c = 0; c < MC; ++c) acc[c] = 0.0f;
-        for (int k = 0; k < 8; ++k) {
-            if (!(m & (1u << k))) continue;
-            const uint4 h[2] = {S.child[warp][sl][k][0], S.child[warp][sl][k][1]};
-            const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(h);
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+    int cnt = 0;
 #pragma unroll
-            for (int c = 0; c < MC / 2; ++c) {
-                const float2 f = __bfloat1622float2(p[c]);
-                acc[2 * c] = __fadd_rn(acc[2 * c], f.x);
-                acc[2 * c + 1] = __fadd_rn(acc[2 * c + 1], f.y);
-            }
+    for (int k = 0; k < 8; ++k) {
+        if (!has[k]) continue;
+        ++cnt;
+        const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(&h[k]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float2 f = __bfloat1622float2(p[c]);
+            acc[2 * c] = __fadd_rn(acc[2 * c], f.x);
+            acc[2 * c + 1] = __fadd_rn(acc[2 * c + 1], f.y);
         }
-        const int ny = int(L.ty[t]);
-        const int want = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * ny + 1 < gc.dy ? 2 : 1);
-        const int cnt = __popc(m);
-        if (cnt != want) atomicOr(L.err, ERR_DEVICE_CHECK);
-        const float nf = float(cnt ? cnt : 1);
-        uint4 o[2];
-        __nv_bfloat162 *q = reinterpret_cast<__nv_bfloat162 *>(o);
-#pragma unroll
-        for (int c = 0; c < MC / 2; ++c)
-            q[c] = __floats2bfloat162_rn(__fdiv_rn(acc[2 * c], nf), __fdiv_rn(acc[2 * c + 1], nf));
-        tree[2 * size_t(t)] = o[0];
-        tree[2 * size_t(t) + 1] = o[1];
     }
+    const float nf = float(cnt ? cnt : 1);
+    uint4 o;
+    __nv_bfloat162 *r = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r[c] = __floats2bfloat162_rn(__fdiv_rn(acc[2 * c], nf), __fdiv_rn(acc[2 * c + 1], nf));
+    tree[2 * size_t(node0 + i) + half] = o;
 }
 
-// Transpose of the tree restriction for 16 FP32 gradient channels, one level (coarse to fine):
-// every child (particle or tree node of level l+1) gets its parent's gradient / #children added.
-// `split` warps per brick (on coarse levels with few bricks): each computes the nodes' shares and
-// updates its part of the children, so every child is still written once.
-__global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const DevLayout L, const Item *__restrict__ items,
-                                                              const TreePlan *__restrict__ tplan, int n, int split,
-                                                              float4 *__restrict__ gp, float4 *__restrict__ gt) {
-    __shared__ float4 share[NWARP][BY][MC / 4];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * NWARP + warp;
-    const int bi = gw / split, part = gw % split;
+// Transpose of the tree restriction for 16 FP32 gradient channels, one level (coarse to fine), one
+// thread per (tree node, 4-channel group): every child (particle or tree node of level l+1) gets its
+// parent's gradient / #children added. Every child has one parent, so each is written by one thread.
+__global__ void __launch_bounds__(NT) mc_tree_pushdown_kernel(const TreeNodePlan *__restrict__ nplan, int node0, int n,
+                                                              float4 *gp, float4 *gt) {
     pdl_trigger();
-    // the work item and its brick plan are static: read before waiting for the coarser level's
-    // push-down (launched before this one)
-    const bool live = bi < n;   // warp-uniform
-    Item it{};
-    int lo = 0, cn = 0, tlo = 0, tn = 0;
+    const int q = int(blockIdx.x) * NT + int(threadIdx.x);
+    const int i = q >> 2, cg = q & 3;
+    const bool live = i < n;
+    // the child map is static: read before waiting for the coarser level's push-down (the launch
+    // before this one), which writes this level's gradients
+    int4 pw = make_int4(0, 0, 0, 0), tw = pw;
     if (live) {
-        it = items[bi];
-        tree_plan_load(tplan + bi, lane, lo, cn, tlo, tn);
+        const int4 *m = reinterpret_cast<const int4 *>(nplan + node0 + i);
+        pw = __ldg(m);
+        tw = __ldg(m + 1);
     }
     pdl_wait();
     if (!live) return;
-    const LevelGeo gc = L.geo[it.l + 1];
-    // the nodes' shares (at most BY nodes x 4 channel groups: eight items per lane, loads first)
-    {
-        int yv[8];
-        float4 v[8];
+    const int pv[4] = {pw.x, pw.y, pw.z, pw.w}, tv[4] = {tw.x, tw.y, tw.z, tw.w};
+    float4 *dst[8];
+    float4 v[8];
+    int cnt = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = lane + 32 * u;
-            if (k < tn * (MC / 4)) {
-                const int t = tlo + k / (MC / 4);
-                yv[u] = L.ty[t];
-                v[u] = gt[size_t(t) * (MC / 4) + k % (MC / 4)];
-            }
-        }
+    for (int k = 0; k < 4; ++k) {
+        const unsigned pm = unsigned(pv[k]) >> 30, tm = unsigned(tv[k]) >> 30;
+        const int pi = int(unsigned(pv[k]) & TNP_INDEX), ti = int(unsigned(tv[k]) & TNP_INDEX);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = lane + 32 * u;
-            if (k < tn * (MC / 4)) {
-                const int cnt = (2 * it.a + 1 < gc.dz ? 2 : 1) * (2 * it.b + 1 < gc.dx ? 2 : 1) * (2 * yv[u] + 1 < gc.dy ? 2 : 1);
-                const float f = float(cnt);
-                share[warp][yv[u] - it.yb * BY][k % (MC / 4)] = make_float4(v[u].x / f, v[u].y / f, v[u].z / f, v[u].w / f);
-            }
+        for (int e = 0; e < 2; ++e) {
+            const bool isp = (pm >> e) & 1u, ist = (tm >> e) & 1u;
+            const int ix = isp ? pi + (e ? int(pm & 1u) : 0) : ti + (e ? int(tm & 1u) : 0);
+            dst[2 * k + e] = isp ? gp + size_t(ix) * (MC / 4) + cg : (ist ? gt + size_t(ix) * (MC / 4) + cg : nullptr);
+            cnt += (isp || ist) ? 1 : 0;
         }
     }
-    __syncwarp();
-    // every child (segments 0..3 particles, 4..7 tree nodes) gets its parent's share, 16 channels as
-    // four float4 per element
-    // four (element, channel group) items per lane in flight: their y and gradient loads are issued
-    // before any of them is updated
-    constexpr int U = 4;
-    const ChildSegs cs(lo, cn);
-    for (int k0 = lane + 32 * U * part; k0 < cs.total * (MC / 4); k0 += 32 * U * split) {
-        float4 *d[U];
-        float4 v[U];
-        int yv[U], c[U];
-        bool ok[U];
+    const float4 g = gt[size_t(node0 + i) * (MC / 4) + cg];
+    const float f = float(cnt ? cnt : 1);
+    const float4 s = make_float4(g.x / f, g.y / f, g.z / f, g.w / f);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + 32 * u;
-            ok[u] = k < cs.total * (MC / 4);
-            d[u] = nullptr;
-            if (ok[u]) {
-                c[u] = k % (MC / 4);
-                int i;
-                const bool src = cs.seg(k / (MC / 4), i) >= 4;
-                yv[u] = src ? L.ty[i] : L.y[i];
-                d[u] = (src ? gt : gp) + size_t(i) * (MC / 4) + c[u];
-                v[u] = *d[u];
-            }
-        }
+    for (int k = 0; k < 8; ++k) v[k] = dst[k] ? *dst[k] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (ok[u]) {
-                const float4 s = share[warp][(yv[u] >> 1) - it.yb * BY][c[u]];
-                *d[u] = make_float4(v[u].x + s.x, v[u].y + s.y, v[u].z + s.z, v[u].w + s.w);
-            }
-    }
+    for (int k = 0; k < 8; ++k)
+        if (dst[k]) *dst[k] = make_float4(v[k].x + s.x, v[k].y + s.y, v[k].z + s.z, v[k].w + s.w);
 }
 
 // ---------------------------------------------------------------- forward
@@ -1448,15 +1376,15 @@ apr_status_t apr_tree_restrict_bf16(apr_handle_t h, const uint16_t *particles, u
     if (channels != MC) return APR_ERR_UNSUPPORTED;
     const HostIndex &X = h->X;
     if ((X.np && !particles) || (X.nt && !tree) || !aligned16(particles) || !aligned16(tree)) return APR_ERR_INVALID_ARG;
-    const size_t sm = sizeof(TreeMcSmem);
-    cudaError_t e = set_smem(reinterpret_cast<const void *>(mc_tree_restrict_kernel), sm);
+    cudaError_t e = cudaSuccess;
     bool chained = false;   // the launches after the first start early (programmatic dependent launch)
     for (int l = X.l_max - 1; e == cudaSuccess && l >= X.l_min; --l) {
-        const int64_t b = X.tree_level_begin[l], n = X.tree_level_begin[l + 1] - b;
+        int64_t b = 0, n = 0;
+        tree_level_nodes(X, l, b, n);
         if (n > 0)
-            e = launch_pdl(mc_tree_restrict_kernel, dim3(int((n + TREE_WARPS - 1) / TREE_WARPS)), dim3(TREE_WARPS * 32),
-                           sm, stream, chained, h->L, h->d_tree + b, h->d_tplan + b, int(n),
-                           reinterpret_cast<const uint4 *>(particles), reinterpret_cast<uint4 *>(tree));
+            e = launch_pdl(mc_tree_restrict_kernel, dim3(int((2 * n + NT - 1) / NT)), dim3(NT), 0, stream, chained,
+                           h->d_tnplan, int(b), int(n), reinterpret_cast<const uint4 *>(particles),
+                           reinterpret_cast<uint4 *>(tree));
         chained = chained || n > 0;
     }
     return cuda_status(e);
@@ -1541,13 +1469,12 @@ apr_status_t apr_convolve_mc_backward(apr_handle_t h, const uint16_t *particles,
         }
         bool chained = false;   // the launches after the first start early (programmatic dependent launch)
         for (int l = X.l_min; e == cudaSuccess && l < X.l_max; ++l) {
-            const int64_t b = X.tree_level_begin[l], nt = X.tree_level_begin[l + 1] - b;
-            // levels with few bricks: several warps per brick, about 4096 warps in all
-            const int split = nt > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(8, 4096 / nt))) : 1;
+            int64_t b = 0, nt = 0;
+            tree_level_nodes(X, l, b, nt);
             if (nt > 0)
-                e = launch_pdl(mc_tree_pushdown_kernel, dim3(int((nt * split + NWARP - 1) / NWARP)), dim3(NT), 0, stream,
-                               chained, h->L, h->d_tree + b, h->d_tplan + b, int(nt), split,
-                               reinterpret_cast<float4 *>(grad_particles), reinterpret_cast<float4 *>(gt));
+                e = launch_pdl(mc_tree_pushdown_kernel, dim3(int((4 * nt + NT - 1) / NT)), dim3(NT), 0, stream, chained,
+                               h->d_tnplan, int(b), int(nt), reinterpret_cast<float4 *>(grad_particles),
+                               reinterpret_cast<float4 *>(gt));
             chained = chained || nt > 0;
         }
     }

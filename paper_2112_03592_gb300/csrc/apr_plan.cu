@@ -119,35 +119,6 @@ bool bwd_plan(const DevLayout &L, const std::vector<Item> &items, HostFPlan &P) 
 
 }  // namespace
 
-bool tree_plan(const DevLayout &L, const HostIndex &X, std::vector<TreePlan> &P) {
-    P.assign(X.tree_items.size(), TreePlan{});
-    for (size_t i = 0; i < X.tree_items.size(); ++i) {
-        const Item &it = X.tree_items[i];
-        const LevelGeo g = L.geo[it.l], gc = L.geo[it.l + 1];
-        TreePlan &p = P[i];
-        for (int k = 0; k < 8; ++k) {
-            const int kind = k >> 2, cz = 2 * it.a + ((k >> 1) & 1), cx = 2 * it.b + (k & 1);
-            uint32_t lo = 0, n = 0;
-            if (cz < gc.dz && cx < gc.dx && (kind == 0 || it.l + 1 < L.l_max)) {
-                const int crr = cz * gc.dx + cx, j0 = 2 * it.yb, j1 = imin(2 * it.yb + 2, gc.nb);
-                const uint32_t *rp = kind ? L.trow_ptr : L.row_ptr;
-                const uint16_t *off = kind ? L.toff : L.off;
-                const int row0 = kind ? gc.trow0 : gc.row0, off0 = kind ? gc.toff0 : gc.off0;
-                lo = blk_start(rp, off, row0, off0, gc.nb, crr, j0);
-                n = blk_start(rp, off, row0, off0, gc.nb, crr, j1) - lo;
-            }
-            if (n > 255) return false;  // two y-blocks hold at most 2 BY cells
-            p.clo[k] = int32_t(lo);
-            p.cn[k >> 2] |= n << (8 * (k & 3));
-        }
-        const int rr = it.a * g.dx + it.b;
-        const uint32_t t0 = blk_start(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, it.yb);
-        p.tlo = int32_t(t0);
-        p.tn = blk_start(L.trow_ptr, L.toff, g.trow0, g.toff0, g.nb, rr, it.yb + 1) - t0;
-    }
-    return true;
-}
-
 bool tree_node_plan(const DevLayout &L, const HostIndex &X, std::vector<TreeNodePlan> &P) {
     P.assign(size_t(X.nt), TreeNodePlan{});
     for (int l = L.l_min; l < L.l_max; ++l) {
@@ -203,7 +174,7 @@ bool tree_node_plan(const DevLayout &L, const HostIndex &X, std::vector<TreeNode
 apr_status_t build_plans(HostIndex &X) {
     const DevLayout L = host_layout_view(X);
     if (X.np >= FPLAN_MAX_INDEX || X.nt >= FPLAN_MAX_INDEX) return APR_ERR_UNSUPPORTED;
-    apr_status_t st[7] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
+    apr_status_t st[6] = {APR_OK, APR_OK, APR_OK, APR_OK, APR_OK, APR_OK};
     auto guarded = [&st](int i, auto f) {
         return [&st, i, f] {
             try {
@@ -213,17 +184,16 @@ apr_status_t build_plans(HostIndex &X) {
             }
         };
     };
-    std::function<void()> jobs[7] = {guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); }),
+    std::function<void()> jobs[6] = {guarded(0, [&] { return fwd_plan<1>(L, X.fwd_items, X.fplan[0]); }),
                                      guarded(1, [&] { return fwd_plan<2>(L, X.fwd_items, X.fplan[1]); }),
                                      guarded(2, [&] { return bwd_plan<1>(L, X.bwd_items, X.bplan[0]); }),
                                      guarded(3, [&] { return bwd_plan<2>(L, X.bwd_items, X.bplan[1]); }),
                                      guarded(4, [&] { return build_mc_plans(L, X, X.mcfplan, X.mcbplan); }),
-                                     guarded(5, [&] { return tree_plan(L, X, X.tplan); }),
-                                     guarded(6, [&] { return tree_node_plan(L, X, X.tnplan); })};
+                                     guarded(5, [&] { return tree_node_plan(L, X, X.tnplan); })};
     // one thread per plan; a job whose thread cannot be started runs here
     std::vector<std::thread> threads;
     try {
-        threads.reserve(7);
+        threads.reserve(6);
     } catch (...) {  // the jobs then run here
     }
     for (auto &job : jobs) {
