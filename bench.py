@@ -106,23 +106,30 @@ TRAFFIC_SOURCES = ["paper_2112_03592_gb300/csrc/apr_kernels.cu", "paper_2112_035
                    "paper_2112_03592_gb300/csrc/apr_tile.cuh", "paper_2112_03592_gb300/csrc/apr_plan.cu"]
 
 
-def kernel_source_hash():
-    """sha1 prefix of the sources the single-channel kernels are built from."""
+MC_TRAFFIC_SOURCES = ["paper_2112_03592_gb300/csrc/apr_mc.cu", "paper_2112_03592_gb300/csrc/apr_device.cuh",
+                      "paper_2112_03592_gb300/csrc/apr_plan.cu"]
+
+
+def kernel_source_hash(sources=None):
+    """sha1 prefix of the sources the single-channel (or the given) kernels are built from."""
     import hashlib
     h = hashlib.sha1()
-    for rel in TRAFFIC_SOURCES:
+    for rel in sources or TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(call):
+def recorded_traffic(call, section=None):
     """DRAM bytes of one call of `call` (the sum over its launches) from the committed ncu summary,
-    if the kernel sources are unchanged since that capture (sha1 prefix match); else None."""
+    if the kernel sources are unchanged since that capture (sha1 prefix match); else None.
+    section "mc": the multi-channel record (its own sources and hash)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        sha = kernel_source_hash()
+        if section:
+            rec = rec[section]
+        sha = kernel_source_hash(MC_TRAFFIC_SOURCES if section == "mc" else None)
     except (OSError, KeyError, ValueError):
         return None
     if sha != rec.get("sha1_prefix"):
@@ -697,6 +704,7 @@ def run_mc(args, rank, world, full=True):
     hbm, tc = float(peaks["hbm_gbs"]), float(peaks.get("bf16_tflops", 1900.0))
     names = ["tree_restrict_bf16", "convolve_mc", "data_adjoint", "weight_grad"]
     dom = max(range(1, 4), key=lambda j: parts[j])
+    mc_traffic = recorded_traffic(names[dom], "mc")
     n_tree_levels = len(set(lay.export(G._abi.APR_STRUCT_TREE_ITEMS)[:, 0].tolist()))
     # per step: BF16 tree (one launch per level), weight layout + forward, weight layout + data
     # adjoint, push-down (one per level), weight gradient + its reduction
@@ -718,7 +726,9 @@ def run_mc(args, rank, world, full=True):
         "roofline": {"kernel": {1: "mc_fwd_kernel (apr_convolve_mc)", 2: "mc_bwd_data_kernel (+ push-down)",
                                 3: "mc_wgrad_kernel (+ reduce)"}[dom],
                      "bound": "hbm", "achieved": round(byts / (parts[dom] * 1e-3) / 1e9, 2), "peak": hbm, "unit": "GB/s",
-                     "frac": round(byts / (parts[dom] * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                     "frac": round(byts / (parts[dom] * 1e-3) / 1e9 / hbm, 4), "traffic": mc_traffic,
+                     "traffic_source": "profiles/traffic.json (mc: ncu dram bytes of the call's launches, same "
+                     "source)" if mc_traffic else None,
                      "peak_source": src + " (hbm_gbs)", "algorithmic_bytes_per_launch": byts,
                      "tensor_tflops": round(flops / (parts[dom] * 1e-3) / 1e12, 2),
                      "tensor_frac": round(flops / (parts[dom] * 1e-3) / 1e12 / tc, 4),
@@ -1275,13 +1285,35 @@ def run_reference_rl(args, rank, world):
 
 
 def ncu_launches(part, reps=3):
-    """Runs one part of the default step `reps` times on the 1024x1024x512 APR, for an ncu capture
-    of that kernel (no timing); prints a one-line JSON note."""
+    """Runs one part of the default step `reps` times on the 1024x1024x512 APR (parts mc_*: of the
+    multi-channel step on the 256^3 APR), for an ncu capture of that kernel (no timing); prints a
+    one-line JSON note."""
     import numpy as np
     import torch
 
     import aprsynth as S
     import paper_2112_03592_gb300 as G
+    if part.startswith("mc_"):
+        apr = S.make_config(MC_WORKLOAD)
+        lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
+        xh, wh, gh = mc_inputs(apr)
+        bf = lambda a: torch.as_tensor(a.astype(np.float32), device="cuda").to(torch.bfloat16).contiguous()
+        x, w, g = bf(xh), bf(wh), bf(gh)
+        tree = G.apr_tree_restrict_bf16(lay, x)
+        out = torch.empty((apr.n_particles, MC_C), device="cuda")
+        gp = torch.empty((apr.n_particles, MC_C), device="cuda")
+        gw = torch.empty((apr.n_levels, MC_C, MC_C, 27), device="cuda")
+        run = {"mc_convolve": lambda: G.apr_convolve_mc(lay, x, tree, w, G.APR_BC_REFLECT, out),
+               "mc_adjoint": lambda: G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT,
+                                                                need_weights=False, grad_particles=gp),
+               "mc_wgrad": lambda: G.apr_convolve_mc_backward(lay, x, tree, w, g, G.APR_BC_REFLECT,
+                                                              need_particles=False, grad_weights=gw)}[part]
+        for _ in range(reps):
+            run()
+        torch.cuda.synchronize()
+        lay.sync_status()
+        print(json.dumps({"ncu_launches": part, "reps": reps, "workload": MC_WORKLOAD}))
+        return
     apr = S.make_config(WORKLOAD)
     lay = G.AprLayout.from_apr(apr, G.APR_VALIDATE | G.APR_REQUIRE_BALANCE)
     w = S.gaussian_stencil(K, SIGMA).astype(np.float32)
@@ -1324,7 +1356,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain 5^3 (unrestricted) arm of the default line")
     ap.add_argument("--no-rl", action="store_true", help="skip the Richardson-Lucy summary of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
-    ap.add_argument("--ncu-launches", choices=["restrict", "convolve", "adjoint", "stencil_grad"],
+    ap.add_argument("--ncu-launches", choices=["restrict", "convolve", "adjoint", "stencil_grad", "mc_convolve", "mc_adjoint",
+                                                    "mc_wgrad"],
                     help="run one part of the step 3 times for an ncu capture, no timing")
     args = ap.parse_args()
     if args.ncu_launches:
