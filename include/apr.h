@@ -94,8 +94,9 @@ typedef struct {
  * values are computed later by apr_tree_restrict. y indices are stored as uint16. For every tile
  * the host also lists the non-empty source segments of its staged patch with the prefix of their
  * 8-element packets (tile plans, for stencil radius 1 and 2 and for the multi-channel sub-tiles),
- * so the convolution kernels never evaluate row offsets per call; on a 1024x1024x512 image with
- * 8 M particles the handle holds about 212 MB, plans included (the image itself would be 2.1 GB).
+ * so the convolution kernels never evaluate row offsets per call, and for every tree node the indices
+ * of its children (32 bytes per node); on a 1024x1024x512 image with 8 M particles the handle holds
+ * about 243 MB, plans included (the image itself would be 2.1 GB).
  * The index is allocated stream-ordered (cudaMallocAsync on `stream`) and uploaded on `stream`;
  * it is ready for work enqueued on `stream` (other streams synchronise with it first). The handle
  * also creates two streams and four events for the concurrent parts of later calls, and 8 bytes of
@@ -107,7 +108,8 @@ apr_status_t apr_build_device(const apr_host_layout *layout, uint32_t flags, apr
                               apr_handle_t *out);
 
 /* A caller allocator for the handle's device memory (e.g. a framework's caching allocator).
- * alloc(bytes, stream, ctx) returns device memory usable in stream order on `stream` (NULL on
+ * alloc(bytes, stream, ctx) returns device memory, 16-byte aligned at least (the kernels read the
+ * index with 16-byte loads), usable in stream order on `stream` (NULL on
  * failure: the build returns APR_ERR_OOM); free(ptr, bytes, stream, ctx) releases it, called by
  * apr_destroy after the device has been synchronised. `stream` is the build stream; it must stay
  * valid until apr_destroy. */

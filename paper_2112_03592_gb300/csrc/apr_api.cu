@@ -46,6 +46,11 @@ cudaError_t dev_alloc(apr_handle_s *h, void **p, size_t bytes) {
     if (h->has_alloc) {
         *p = h->alloc.alloc(bytes, h->stream, h->alloc.ctx);
         if (!*p) return cudaErrorMemoryAllocation;
+        if (reinterpret_cast<uintptr_t>(*p) % 16 != 0) {  // the kernels read the index with 16-byte loads
+            h->alloc.free(*p, bytes, h->stream, h->alloc.ctx);
+            *p = nullptr;
+            return cudaErrorMisalignedAddress;
+        }
     } else {
         const cudaError_t e = cudaMallocAsync(p, bytes, reinterpret_cast<cudaStream_t>(h->stream));
         if (e != cudaSuccess) return e;
