@@ -87,6 +87,12 @@ typedef struct {
 #define APR_STRUCT_FWD_ITEMS 4     /* int32 [n][4]    convolution work items (l, tz, tx, yb) */
 #define APR_STRUCT_TREE_ITEMS 5    /* int32 [n][4]    tree work items (l, z, x, yb) */
 #define APR_STRUCT_BWD_ITEMS 6     /* int32 [n][4]    data-adjoint work items (l, tz, tx, yb) */
+/* int32 [N_t][8] child map of every tree node (what the tree kernels read): words k = 0..3 for the
+ * child rows (2z + (k >> 1), 2x + (k & 1)) of level l+1, first the particle word, then (words 4..7)
+ * the tree word: bits 0..29 the index of the row's first particle (tree node) child, bit 30 (31) set
+ * when child cell y = 2 y_node (2 y_node + 1) is a particle (a tree node). Neither bit: the cell lies
+ * outside the grid. A row's second child of a kind sits at the first one's index + 1. */
+#define APR_STRUCT_TREE_NODE_MAP 7
 
 /* Build the device-resident index of an APR (Sec. 3.1 LinearAccess for the particles, Sec. 3.4
  * APR tree structure, and the list of non-empty tiles the kernels are launched on, Sec. 5.2 last

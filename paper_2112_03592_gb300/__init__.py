@@ -154,7 +154,8 @@ class AprLayout:
             pass
 
     # ---- structure export (bit-exact checks)
-    _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32, 6: np.int32}
+    _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32, 6: np.int32,
+                      7: np.int32}
 
     def export(self, which: int) -> np.ndarray:
         nbytes = int(self._lib.apr_structure_bytes(self._h, which))
@@ -163,6 +164,8 @@ class AprLayout:
         _abi.check("apr_export_structure",
                    self._lib.apr_export_structure(self._h, which, out.ctypes.data_as(ctypes.c_void_p), nbytes))
         out = out[:nbytes // np.dtype(dt).itemsize]
+        if which == 7:
+            return out.reshape(-1, 8)
         return out.reshape(-1, 4) if which in (4, 5, 6) else out
 
     def workspace(self, k):

@@ -16,6 +16,7 @@ APR_VALIDATE, APR_REQUIRE_BALANCE, APR_HOST_ONLY, APR_SUBDOMAIN = 1, 2, 4, 8
 APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
 APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS, APR_STRUCT_BWD_ITEMS = 4, 5, 6
+APR_STRUCT_TREE_NODE_MAP = 7
 APR_TILE_ZX, APR_BLOCK_Y = 8, 64  # work-item geometry, as in include/apr.h
 
 # every function include/apr.h declares, with (restype, argtypes)

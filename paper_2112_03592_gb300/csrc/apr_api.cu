@@ -306,6 +306,16 @@ apr_status_t apr_build_device_ex(const apr_host_layout *layout, uint32_t flags, 
         return st;
     }
     h->host_only = (flags & APR_HOST_ONLY) != 0;
+    if (h->host_only) {
+        // the tree-node child maps, for apr_export_structure (a device handle builds them with its plans)
+        try {
+            tree_node_plan(host_layout_view(h->X), h->X, h->X.tnplan);
+        } catch (const std::bad_alloc &) {
+            snprintf(g_last_msg, sizeof(g_last_msg), "%s", "host allocation failed (tree-node child maps)");
+            delete h;
+            return APR_ERR_OOM;
+        }
+    }
     if (!h->host_only) {
         const apr_status_t pst = build_plans(h->X);
         if (pst != APR_OK) {
@@ -448,6 +458,7 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
         case APR_STRUCT_FWD_ITEMS: return X.fwd_items.size() * sizeof(Item);
         case APR_STRUCT_TREE_ITEMS: return X.tree_items.size() * sizeof(Item);
         case APR_STRUCT_BWD_ITEMS: return X.bwd_items.size() * sizeof(Item);
+        case APR_STRUCT_TREE_NODE_MAP: return size_t(X.nt) * sizeof(TreeNodePlan);
     }
     return 0;
 }
@@ -455,7 +466,7 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
 apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes) {
     if (!h || (!dst && bytes)) return APR_ERR_INVALID_ARG;
     const size_t need = apr_structure_bytes(h, which);
-    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_BWD_ITEMS) return APR_ERR_INVALID_ARG;
+    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_TREE_NODE_MAP) return APR_ERR_INVALID_ARG;
     if (bytes < need) return APR_ERR_INVALID_ARG;
     if (need == 0) return APR_OK;
     const HostIndex &X = h->X;
@@ -468,6 +479,7 @@ apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size
         case APR_STRUCT_TREE_Y_IDX: host_src = X.ty.data(); dev_src = h->d_ty; break;
         case APR_STRUCT_FWD_ITEMS: host_src = X.fwd_items.data(); dev_src = h->d_fwd; break;
         case APR_STRUCT_TREE_ITEMS: host_src = X.tree_items.data(); dev_src = h->d_tree; break;
+        case APR_STRUCT_TREE_NODE_MAP: host_src = X.tnplan.data(); dev_src = h->d_tnplan; break;
         case APR_STRUCT_BWD_ITEMS: host_src = X.bwd_items.data(); dev_src = h->d_bwd; break;
     }
     if (h->host_only) {
