@@ -198,6 +198,46 @@ def test_structure_on_device_is_bit_exact():
     assert np.array_equal(lay.export(_abi.APR_STRUCT_Y_IDX), apr.y_idx.astype(np.uint16))
     assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_ROW_PTR), rp.astype(np.uint32))
     assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_Y_IDX), ty.astype(np.uint16))
+    # the tree kernels' child maps on the device equal the host-built ones (pinned on the CPU)
+    host = G.AprLayout.from_apr(apr, FLAGS | G.APR_HOST_ONLY)
+    assert np.array_equal(lay.export(_abi.APR_STRUCT_TREE_NODE_MAP), host.export(_abi.APR_STRUCT_TREE_NODE_MAP))
+
+
+def test_misaligned_caller_allocation_is_refused():
+    """A caller allocator whose blocks are off the 16-byte grid the kernels' vector loads need: the
+    build fails with APR_ERR_CUDA, hands every block back, and the library keeps working."""
+    import ctypes
+    apr = S.make_config("blob64", use_cache=False)
+    lib = _abi.load()
+    held = {}
+
+    def alloc(nbytes, stream, ctx):
+        p = int(torch.cuda.caching_allocator_alloc(int(nbytes) + 16, torch.cuda.current_device(),
+                                                   stream if stream else 0))
+        held[p + 4] = p
+        return p + 4
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(held.pop(int(ptr)))
+
+    fa, ff = _abi.ALLOC_FN(alloc), _abi.FREE_FN(free)
+    al = _abi.AprAllocator(fa, ff, None)
+    rp = np.ascontiguousarray(apr.row_ptr.astype(np.int64))
+    yi = np.ascontiguousarray(apr.y_idx.astype(np.int32))
+    L = _abi.AprHostLayout()
+    L.l_min, L.l_max = apr.l_min, apr.l_max
+    for a in range(3):
+        L.dims[a] = int(apr.dims[a])
+    L.row_ptr = rp.ctypes.data_as(ctypes.c_void_p)
+    L.y_idx = yi.ctypes.data_as(ctypes.c_void_p)
+    L.n_particles = int(yi.size)
+    h = ctypes.c_void_p()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.apr_build_device_ex(ctypes.byref(L), FLAGS, stream, ctypes.byref(al), ctypes.byref(h))
+    torch.cuda.synchronize()
+    assert rc == _abi.APR_ERR_CUDA and not h.value and not held
+    lay = G.AprLayout.from_apr(apr, FLAGS, allocator="torch")
+    assert lay.layout_bytes() > 0
 
 
 def test_backward_parts_compose_to_backward():
