@@ -66,3 +66,22 @@ def test_oracle_sampled_step_estimate():
     est, t_fixed, t_s = bench.oracle_sampled_step(100000, 0.5, run, 2000, np.random.default_rng(0))
     assert calls == [16, 2000]
     assert 0.5 + 0.01 <= est and abs(est - (0.5 + 0.01 + 1.0)) < 0.5
+
+
+def test_recorded_traffic_follows_the_kernel_sources():
+    """roofline.traffic comes from the committed ncu record only while the kernel sources hash to the
+    recorded value: the committed record matches the tree, and a changed source hash gives None."""
+    import json
+    rec = json.loads((pathlib.Path(bench.ROOT) / "profiles" / "traffic.json").read_text())
+    assert rec["sha1_prefix"] == bench.kernel_source_hash()
+    assert rec["mc"]["sha1_prefix"] == bench.kernel_source_hash(bench.MC_TRAFFIC_SOURCES)
+    adj = bench.recorded_traffic("apr_convolve_adjoint")
+    assert adj == rec["dram_bytes_per_call"]["apr_convolve_adjoint"] and adj > 0
+    assert bench.recorded_traffic("data_adjoint", "mc") == rec["mc"]["dram_bytes_per_call"]["data_adjoint"]
+    saved = bench.kernel_source_hash
+    try:
+        bench.kernel_source_hash = lambda sources=None: "000000000000"
+        assert bench.recorded_traffic("apr_convolve_adjoint") is None
+        assert bench.recorded_traffic("data_adjoint", "mc") is None
+    finally:
+        bench.kernel_source_hash = saved
