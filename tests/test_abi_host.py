@@ -55,6 +55,21 @@ def _check_structure(apr):
     tc = o.tree_coords()
     tref = sorted(set(zip(tc[:, 0].tolist(), tc[:, 1].tolist(), tc[:, 2].tolist(), (tc[:, 3] // B).tolist())))
     assert [tuple(r) for r in lay.export(_abi.APR_STRUCT_TREE_ITEMS).tolist()] == tref
+    # data-adjoint work list: the tiles with a cell within Chebyshev distance 2 of a particle of their
+    # level (the cells a 5^3 window around a target reaches), by dense dilation of each level's grid
+    from scipy import ndimage
+    bref = []
+    for l in range(apr.l_min, apr.l_max + 1):
+        sel = lev == l
+        if not sel.any():
+            continue
+        dz, dx, dy = apr.level_dims(l)
+        grid = np.zeros((dz, dx, dy), bool)
+        grid[z[sel], x[sel], y[sel]] = True
+        near = ndimage.binary_dilation(grid, structure=np.ones((5, 5, 5), bool))
+        nz, nx, ny = np.nonzero(near)
+        bref += sorted(set(zip([l] * nz.size, (nz // T).tolist(), (nx // T).tolist(), (ny // B).tolist())))
+    assert [tuple(r) for r in lay.export(_abi.APR_STRUCT_BWD_ITEMS).tolist()] == bref
 
 
 @pytest.mark.parametrize("maker", [
