@@ -93,6 +93,17 @@ typedef struct {
  * when child cell y = 2 y_node (2 y_node + 1) is a particle (a tree node). Neither bit: the cell lies
  * outside the grid. A row's second child of a kind sits at the first one's index + 1. */
 #define APR_STRUCT_TREE_NODE_MAP 7
+/* Tile plans, host-only handles only (built on the first request; 0 bytes for a device handle):
+ * uint32 [n_items][2] headers {first entry, count} for the items of APR_STRUCT_FWD_ITEMS (forward, stencil
+ * radius 1 or 2) or APR_STRUCT_BWD_ITEMS (data adjoint: count = gradient rows | routing segments << 16),
+ * then uint32 [n_entries][2] entries, one per non-empty source segment of an item's patch and one
+ * after them holding the item's packet total: word 0 = first element (bits 0..27) | element count
+ * bits 0..3 << 28, word 1 = prefix of 8-element packets (bits 0..15) | segment word (11 bits) << 16
+ * | element count bits 4..7 << 27. */
+#define APR_STRUCT_FWD_PLAN_R1 8
+#define APR_STRUCT_FWD_PLAN_R2 9
+#define APR_STRUCT_BWD_PLAN_R1 10
+#define APR_STRUCT_BWD_PLAN_R2 11
 
 /* Build the device-resident index of an APR (Sec. 3.1 LinearAccess for the particles, Sec. 3.4
  * APR tree structure, and the list of non-empty tiles the kernels are launched on, Sec. 5.2 last

@@ -155,7 +155,7 @@ class AprLayout:
 
     # ---- structure export (bit-exact checks)
     _EXPORT_DTYPES = {0: np.uint32, 1: np.uint16, 2: np.uint32, 3: np.uint16, 4: np.int32, 5: np.int32, 6: np.int32,
-                      7: np.int32}
+                      7: np.int32, 8: np.uint32, 9: np.uint32, 10: np.uint32, 11: np.uint32}
 
     def export(self, which: int) -> np.ndarray:
         nbytes = int(self._lib.apr_structure_bytes(self._h, which))
@@ -166,6 +166,8 @@ class AprLayout:
         out = out[:nbytes // np.dtype(dt).itemsize]
         if which == 7:
             return out.reshape(-1, 8)
+        if which >= 8:
+            return out.reshape(-1, 2)
         return out.reshape(-1, 4) if which in (4, 5, 6) else out
 
     def workspace(self, k):

@@ -17,6 +17,7 @@ APR_BC_REFLECT, APR_BC_ZERO = 0, 1
 APR_STRUCT_ROW_PTR, APR_STRUCT_Y_IDX, APR_STRUCT_TREE_ROW_PTR, APR_STRUCT_TREE_Y_IDX = 0, 1, 2, 3
 APR_STRUCT_FWD_ITEMS, APR_STRUCT_TREE_ITEMS, APR_STRUCT_BWD_ITEMS = 4, 5, 6
 APR_STRUCT_TREE_NODE_MAP = 7
+APR_STRUCT_FWD_PLAN_R1, APR_STRUCT_FWD_PLAN_R2, APR_STRUCT_BWD_PLAN_R1, APR_STRUCT_BWD_PLAN_R2 = 8, 9, 10, 11
 APR_TILE_ZX, APR_BLOCK_Y = 8, 64  # work-item geometry, as in include/apr.h
 
 # every function include/apr.h declares, with (restype, argtypes)

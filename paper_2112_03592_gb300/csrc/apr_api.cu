@@ -447,9 +447,28 @@ apr_status_t apr_level_range(apr_handle_t h, int32_t *l_min, int32_t *l_max) {
 
 size_t apr_layout_bytes(apr_handle_t h) { return h ? h->dev_bytes : 0; }
 
+namespace {
+// The tile plans of a host-only handle (built once, on request); nullptr for a device handle, whose
+// plans live only on the device.
+const HostFPlan *host_plan(apr_handle_t h, int32_t which) {
+    if (!h->host_only || which < APR_STRUCT_FWD_PLAN_R1 || which > APR_STRUCT_BWD_PLAN_R2) return nullptr;
+    std::lock_guard<std::mutex> lk(h->plan_mu);
+    if (!h->host_plans) {
+        if (build_plans(h->X) != APR_OK) return nullptr;
+        h->host_plans = true;
+    }
+    const int i = which - APR_STRUCT_FWD_PLAN_R1;
+    return i < 2 ? &h->X.fplan[i] : &h->X.bplan[i - 2];
+}
+}  // namespace
+
 size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
     if (!h) return 0;
     const HostIndex &X = h->X;
+    if (which >= APR_STRUCT_FWD_PLAN_R1 && which <= APR_STRUCT_BWD_PLAN_R2) {
+        const HostFPlan *P = host_plan(h, which);
+        return P ? (P->hdr.size() + P->ent.size()) * sizeof(uint2) : 0;
+    }
     switch (which) {
         case APR_STRUCT_ROW_PTR: return X.row_ptr.size() * sizeof(uint32_t);
         case APR_STRUCT_Y_IDX: return X.y.size() * sizeof(uint16_t);
@@ -466,9 +485,15 @@ size_t apr_structure_bytes(apr_handle_t h, int32_t which) {
 apr_status_t apr_export_structure(apr_handle_t h, int32_t which, void *dst, size_t bytes) {
     if (!h || (!dst && bytes)) return APR_ERR_INVALID_ARG;
     const size_t need = apr_structure_bytes(h, which);
-    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_TREE_NODE_MAP) return APR_ERR_INVALID_ARG;
+    if (which < APR_STRUCT_ROW_PTR || which > APR_STRUCT_BWD_PLAN_R2) return APR_ERR_INVALID_ARG;
     if (bytes < need) return APR_ERR_INVALID_ARG;
     if (need == 0) return APR_OK;
+    if (which >= APR_STRUCT_FWD_PLAN_R1) {  // host-only handle (need > 0)
+        const HostFPlan *P = host_plan(h, which);
+        memcpy(dst, P->hdr.data(), P->hdr.size() * sizeof(PlanHdr));
+        memcpy(static_cast<char *>(dst) + P->hdr.size() * sizeof(PlanHdr), P->ent.data(), P->ent.size() * sizeof(uint2));
+        return APR_OK;
+    }
     const HostIndex &X = h->X;
     const void *host_src = nullptr;
     const void *dev_src = nullptr;

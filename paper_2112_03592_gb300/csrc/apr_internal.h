@@ -216,6 +216,9 @@ struct apr_handle_s {
     aprk::PlanHdr *d_plan_hdr[2] = {};
     aprk::PlanEnt *d_plan_ent[2] = {};
     aprk::TreeNodePlan *d_tnplan = nullptr;
+    // host-only handles: tile plans built on the first apr_export_structure request for them
+    std::mutex plan_mu;
+    bool host_plans = false;
     aprk::PlanHdr *d_fplan_hdr[4] = {};   // forward radius 1, 2; adjoint radius 1, 2
     uint2 *d_fplan_ent[4] = {};
     size_t dev_bytes = 0;
